@@ -1,0 +1,211 @@
+"""Pins for the oracle's assignment step, projections and Algorithm 1 (CPU).
+
+Assignment: brute force over all permutations.  Projections: closed forms
+(one half-space, one dominating point), a 1-D scan over segments in 2-D, and
+the KKT conditions in higher dimension.  Algorithm 1: Thm 3 / Cor. on
+instances whose achievable set C is enumerable (all permutations x all
+simple schedulers), and Lemma 6 on every direction it produces.
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+from scipy.optimize import nnls
+
+import instances as I
+from oracle import core as C
+from oracle import pareto as P
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(oracle_lib):
+    return oracle_lib
+
+
+# ---------------------------------------------------------------- assignment
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 6])
+def test_assignment_matches_permutation_brute_force(n):
+    rng = np.random.default_rng(n)
+    for _ in range(5):
+        Cm = rng.normal(size=(n, n))
+        if n > 2:
+            Cm[0, :] = Cm[1, :]  # some ties
+        f = C.assignment(Cm)
+        got = sum(Cm[f[j], j] for j in range(n))
+        best = max(sum(Cm[p[j], j] for j in range(n)) for p in itertools.permutations(range(n)))
+        assert got == pytest.approx(best, abs=1e-12)
+        assert sorted(f.tolist()) == list(range(n))
+
+
+def test_pad_square_dummy_agents():
+    Cm = np.array([[1.0, 2.0, 3.0], [4.0, 0.5, 0.1]])
+    S = C.pad_square(Cm)
+    assert S.shape == (3, 3) and np.all(S[2] == 0)
+    f = C.assignment(S)
+    # best: agent 0 -> task 2 (3), agent 1 -> task 0 (4), dummy -> task 1
+    assert f[2] == 0 and f[0] == 1 and f[1] == 2
+
+
+# ---------------------------------------------------------------- projections
+
+
+def test_halfspace_projection_closed_form():
+    rng = np.random.default_rng(0)
+    for _ in range(10):
+        n = 4
+        A = rng.normal(size=(n, n))
+        M = A @ A.T + n * np.eye(n)
+        w = rng.dirichlet(np.ones(n))
+        t = rng.normal(size=n)
+        b = w @ t - 0.7
+        z = P.project_halfspaces(t, w[None, :], np.array([b]), M)
+        Minv_w = np.linalg.solve(M, w)
+        want = t - (w @ t - b) / (w @ Minv_w) * Minv_w
+        assert np.max(np.abs(z - want)) < 1e-7
+
+
+def test_halfspace_projection_kkt():
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        n, m = 5, 6
+        Wt = rng.dirichlet(np.ones(n), size=m)
+        R = rng.normal(size=(m, n))
+        b = np.einsum("ij,ij->i", Wt, R)
+        t = R.max(axis=0) + rng.uniform(0.1, 1.0, size=n)
+        M = np.eye(n)
+        z = P.project_halfspaces(t, Wt, b, M)
+        assert np.all(Wt @ z <= b + 1e-8)
+        act = np.abs(Wt @ z - b) < 1e-6
+        mu, res = nnls(Wt[act].T, M @ (t - z))
+        assert res < 1e-6
+
+
+def test_down_hull_single_point_is_componentwise_min():
+    t = np.array([-1.0, 0.9, 0.3])
+    r = np.array([-2.0, 0.5, 0.8])
+    x = P.project_down_hull(t, r[None, :], np.eye(3))
+    assert np.max(np.abs(x - np.minimum(t, r))) < 1e-8
+
+
+def _proj_down_2d_scan(t, pts):
+    """2-D brute force: min over segments [a, b] of ||(t - y)_+||, y on the
+    segment (convex in the segment parameter; golden-section search)."""
+    best, best_x = np.inf, None
+    for a, b in itertools.combinations_with_replacement(range(len(pts)), 2):
+        pa, pb = pts[a], pts[b]
+
+        def f(lam):
+            y = lam * pa + (1 - lam) * pb
+            return np.linalg.norm(np.maximum(t - y, 0)), np.minimum(t, y)
+
+        lo, hi = 0.0, 1.0
+        g = (np.sqrt(5) - 1) / 2
+        for _ in range(200):
+            m1, m2 = hi - g * (hi - lo), lo + g * (hi - lo)
+            if f(m1)[0] <= f(m2)[0]:
+                hi = m2
+            else:
+                lo = m1
+        d, x = f(0.5 * (lo + hi))
+        if d < best:
+            best, best_x = d, x
+    return best, best_x
+
+
+def test_down_hull_2d_scan():
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        pts = np.column_stack([-rng.uniform(1, 5, size=4), rng.uniform(0, 1, size=4)])
+        t = np.array([-rng.uniform(0.5, 3), rng.uniform(0.3, 1.2)])
+        d, x_scan = _proj_down_2d_scan(t, pts)
+        x = P.project_down_hull(t, pts, np.eye(2))
+        assert np.linalg.norm(t - x) == pytest.approx(d, abs=1e-6)
+        assert np.max(np.abs(x - x_scan)) < 1e-4
+
+
+# ---------------------------------------------------------------- Algorithm 1
+
+
+def _achievable_points(prods):
+    """All points reachable by a deterministic assignment and simple
+    schedulers: C = down(conv of these) (Sec. 3.2)."""
+    nI, nJ = len(prods), len(prods[0])
+    pair_pts = {}
+    for i in range(nI):
+        for j in range(nJ):
+            _, out = C.brute_force(prods[i][j], 0.5, 0.5)
+            pair_pts[i, j] = sorted({(a, b) for _, _, (a, b) in out if np.isfinite(a)})
+    n = max(nI, nJ)
+    pts = []
+    for perm in itertools.permutations(range(n)):
+        pairs = [(perm[j], j) for j in range(nJ) if perm[j] < nI]
+        for choice in itertools.product(*[pair_pts[p] for p in pairs]):
+            r = np.zeros(nI + nJ)
+            for (i, j), (c, pr) in zip(pairs, choice):
+                r[i] = c
+                r[nI + j] = pr
+            pts.append(r)
+    return np.unique(np.array(pts), axis=0)
+
+
+def test_alg1_fig2_projects_onto_C():
+    """Fig. 2 with t_u = (-1.8, 0.9): infeasible; t_down converges to the
+    projection of t_u onto C (Thm 3 (iii), Cor. (iii))."""
+    prods = [[C.Product(I.fig2_agent(), I.fig2_task())]]
+    pts = _achievable_points(prods)
+    t = np.array([-1.8, 0.9])
+    supp = lambda w: C.supporting_point(prods, w, eps1=1e-12)[0]
+    res = P.alg1(supp, t, eps=1e-7)
+    d, x = _proj_down_2d_scan(t, pts)
+    assert not res["feasible"]
+    assert np.linalg.norm(res["t_dn"] - x) < 1e-5
+    assert np.linalg.norm(res["t_up"] - x) < 1e-5
+    # the first two directions: e_1, then straight up (M = I)
+    assert np.allclose(res["history"][0]["w"], [1, 0])
+    assert np.allclose(res["history"][1]["w"], [0, 1], atol=1e-7)
+
+
+def test_alg1_fig2_feasible_point():
+    prods = [[C.Product(I.fig2_agent(), I.fig2_task())]]
+    t = np.array([-3.0, 0.5])
+    supp = lambda w: C.supporting_point(prods, w, eps1=1e-12)[0]
+    res = P.alg1(supp, t, eps=1e-7)
+    assert res["feasible"]
+    assert np.allclose(res["t_dn"], t)
+
+
+def _tiny_instance(seed):
+    agents = [I.random_tiny_agent(seed, k, n_states=3, n_actions=(1, 1), n_succ=(1, 2)) for k in range(2)]
+    tasks = [I.random_tiny_task(seed, 10 + k, n_locs=2, n_ap=2) for k in range(2)]
+    return C.products(agents, tasks)
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_alg1_theorem3_on_enumerable_instances(seed):
+    prods = _tiny_instance(seed)
+    pts = _achievable_points(prods)
+    rng = np.random.default_rng(seed)
+    n = 4
+    M = np.eye(n)
+    for _ in range(3):
+        hi = pts.max(axis=0)
+        t = hi + rng.uniform(-0.6, 0.3, size=n)
+        supp = lambda w: C.supporting_point(prods, w, eps1=1e-12)[0]
+        res = P.alg1(supp, t, M=M, eps=1e-7)
+        x_true = P.project_down_hull(t, pts, M)
+        dist = np.linalg.norm(t - x_true)
+        for h in res["history"]:
+            w = h["w"]
+            assert np.all(w >= -1e-12) and abs(w.sum() - 1) < 1e-9  # Lemma 6
+            # Lemma 7 over the whole achievable set
+            assert np.all(pts @ w <= w @ h["r"] + 1e-8)
+            # Thm 3 (i) and (iii)
+            assert np.linalg.norm(h["t_up"] - P.project_down_hull(h["t_up"], pts, M)) < 1e-6
+            assert np.linalg.norm(t - h["t_dn"]) <= dist + 1e-6
+            assert dist <= np.linalg.norm(t - h["t_up"]) + 1e-6
+        assert np.linalg.norm(res["t_dn"] - x_true) < 1e-5
+        feasible_true = dist < 1e-9
+        assert res["feasible"] == feasible_true
