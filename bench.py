@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark: batched supporting-point computation (Algorithm 2) on the
+10-agent x 20-task 32x32-grid workload, K = 16 weight vectors per batch.
+
+One step = one pass of the whole hot path over one batch:
+  product construction on the device (from HBM-resident agent/task arrays),
+  Algorithm 3 for all 200 products x 16 weights (FP32 round-down sweeps,
+  FP64 sweeps to eps = 1e-8, scheduler finalisation), the assignment step
+  per weight, Algorithm 4 on the assigned products (FP64, eps = 1e-11), and
+  one Pareto update of a threshold point (both projections of Algorithm 1).
+
+Printed (rank 0, one JSON line): the metric, value = transition-updates/s of
+the whole job, the device-resident timing, the end-to-end timing through the
+C-ABI with host buffers, the roofline of the dominant kernel (the FP32 sweep)
+measured live with CUDA events, the plain one-model-at-a-time FP64 GPU value
+iteration on a sample of the same pairs, the oracle on the host cores on a
+bounded sample, and the SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Bellman transition-updates/s & point queries/s: batched FP32 vs plain FP64 GPU VI"
+UNIT = "transition-updates/s"
+WORKLOAD = "grid32-10x20-K16"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region (read-only queries)."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        import statistics
+
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _reduce_sum(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- oracle arm
+
+
+def _oracle_sample(inst, budget_s, seed=0):
+    """Time the oracle (as it stands) on a bounded sample of the workload:
+    (product, weight) pairs in a seeded order over all products x weights,
+    Algorithm 3 plus both Algorithm 4 evaluations per pair, until budget_s
+    seconds of solver time (product construction is not timed, as in the
+    paper's measurements).  Updates are counted as for the engine."""
+    import numpy as np
+
+    from oracle import core as O
+
+    nI, nJ = len(inst.agents), len(inst.tasks)
+    W = inst.weights
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(nI * nJ * len(W))
+    cache = {}
+    updates, pairs, solve_s = 0, 0, 0.0
+    for idx in order:
+        p, k = divmod(int(idx), len(W))
+        i, j = divmod(p, nJ)
+        prod = cache.get(p)
+        if prod is None:
+            prod = cache[p] = O.Product(inst.agents[i], inst.tasks[j])
+        t0 = time.perf_counter()
+        r = O.solve_pair(prod, W[k][i], W[k][nI + j])
+        solve_s += time.perf_counter() - t0
+        a = prod.state_ptr[: prod.n - 1] + r["mu"][: prod.n - 1]
+        t_mu = int(np.sum(prod.sa_ptr[a + 1] - prod.sa_ptr[a]))
+        updates += r["sweeps"] * prod.n_trans + (r["eval_sweeps"][0] + r["eval_sweeps"][1]) * t_mu
+        pairs += 1
+        if solve_s > budget_s:
+            break
+    return updates / solve_s, pairs, solve_s
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import instances as I
+
+    inst = I.config_grid32()
+    per_step = []
+    samples = []
+    for step in range(args.warmup + args.steps):
+        v, pairs, dt = _oracle_sample(inst, args.ref_budget, seed=step)
+        if step >= args.warmup:
+            per_step.append((v, pairs, dt))
+            samples.append(pairs)
+    import statistics
+
+    value = statistics.mean(v for v, _, _ in per_step)
+    ms = statistics.mean(dt for _, _, dt in per_step) * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "eps_vi": 1e-8, "eps_eval": 1e-11},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step: {samples[0]}.. (product, weight) pairs of the workload, "
+                                   f"~{args.ref_budget:.0f} s of single-thread FP64 C oracle work"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- engine arm
+
+
+def run_engine(args):
+    import numpy as np
+    import torch
+
+    import instances as I
+    from paper_2305_04397_gb300 import build as engine_build
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2305_04397_gb300", "libmorap.so")):
+        engine_build.build()
+    _barrier(ws)
+    from paper_2305_04397_gb300 import morap as M
+
+    # weak scaling: every rank solves its own instance of the workload
+    inst = I.config_grid32(seed=1 + rank)
+    nI, nJ = len(inst.agents), len(inst.tasks)
+    W = np.ascontiguousarray(inst.weights)
+    t_point = inst.thresholds[0]
+    stream = torch.cuda.current_stream().cuda_stream
+    cfg = M.morap_config_default()
+    cfg.device = local
+    cfg.launch_mode = args.launch_mode
+    ctx = M.Context(cfg)
+    ctx.add(inst.agents, inst.tasks)
+    fp = ctx.build(stream)
+
+    def step(e2e=False):
+        if e2e:
+            f = ctx.build(stream)  # host arrays -> device, then construction
+        else:
+            ctx.rebuild(stream)  # construction from the resident arrays
+        out = ctx.supporting_points(W, stream)
+        st = ctx.stats()
+        r = out["r"]
+        b = np.einsum("kn,kn->k", W, r)
+        M.morap_project_halfspaces(t_point, W, b)
+        M.morap_project_down_hull(t_point, r)
+        h2d = (f["h2d_bytes"] if e2e else 0) + st["h2d_bytes"]
+        return st, h2d, st["d2h_bytes"]
+
+    def timed(n, e2e):
+        tot = {"updates": 0, "bytes_fp32": 0, "ms_fp32": 0.0, "sweeps32": 0, "launches": 0, "h2d": 0, "d2h": 0,
+               "ms_fp64": 0.0, "ms_eval": 0.0, "bytes_fp64": 0, "bytes_eval": 0}
+        _barrier(ws)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        ev0.record()
+        for _ in range(n):
+            st, h2d, d2h = step(e2e)
+            tot["updates"] += st["updates_fp32"] + st["updates_fp64"] + st["updates_eval"]
+            tot["bytes_fp32"] += st["bytes_fp32"]
+            tot["ms_fp32"] += st["ms_fp32"]
+            tot["bytes_fp64"] += st["bytes_fp64"]
+            tot["ms_fp64"] += st["ms_fp64"]
+            tot["bytes_eval"] += st["bytes_eval"]
+            tot["ms_eval"] += st["ms_eval"]
+            tot["sweeps32"] += st["fp32_sweeps"]
+            tot["launches"] += st["kernel_launches"] + 2  # + the two construction kernels
+            tot["h2d"] += h2d
+            tot["d2h"] += d2h
+        ev1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        _barrier(ws)
+        ms = ev0.elapsed_time(ev1)
+        tot["ms"] = max(ms, wall * 1e3)
+        return tot
+
+    for _ in range(args.warmup):
+        step(False)
+    with ClockSampler(local) as clk:
+        dev = timed(args.steps, e2e=False)
+    clocks = clk.summary()
+    for _ in range(max(1, args.warmup // 2)):
+        step(True)
+    e2e = timed(args.steps, e2e=True)
+
+    secs = _reduce_max(dev["ms"], ws) / 1e3
+    value = _reduce_sum(dev["updates"], ws) / secs
+    e2e_secs = _reduce_max(e2e["ms"], ws) / 1e3
+    e2e_value = _reduce_sum(e2e["updates"], ws) / e2e_secs
+
+    peak, peak_kind = _peaks()
+    achieved = dev["bytes_fp32"] / (dev["ms_fp32"] / 1e3) / 1e9 if dev["ms_fp32"] > 0 else None
+    roofline = {"bound": "hbm", "kernel": "k_sweep<float,16> (FP32 Bellman sweep, graph-launched loop)",
+                "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "bytes_per_sweep": dev["bytes_fp32"] / max(dev["sweeps32"], 1),
+                "ms_per_sweep": dev["ms_fp32"] / max(dev["sweeps32"], 1),
+                "other_phases_GBps": {"fp64_sweeps": dev["bytes_fp64"] / max(dev["ms_fp64"], 1e-9) / 1e6,
+                                      "evaluation": dev["bytes_eval"] / max(dev["ms_eval"], 1e-9) / 1e6}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "products": nI * nJ, "K": len(W), "states": fp["n_states"],
+                   "transitions": fp["n_trans"], "eps_vi": cfg.eps_vi, "eps_eval": cfg.eps_eval,
+                   "l2": "per-step working set (CSR + FP32/FP64 value buffers) exceeds the 129 MB L2; no flush",
+                   "parallelism": f"{ws} independent instance(s), one per GPU"},
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"] // args.steps,
+                "d2h_bytes_per_step": e2e["d2h"] // args.steps, "ms_per_step": e2e_secs * 1e3 / args.steps},
+        "gpu_launches": dev["launches"],
+        "launch_mode": args.launch_mode,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_plain:
+        # plain per-model FP64 GPU VI on a sample of the same pairs
+        rng = np.random.default_rng(0)
+        ps = rng.choice(nI * nJ, size=args.plain_pairs, replace=False)
+        ks = 1 + np.arange(args.plain_pairs) % (len(W) - 1)
+        pw = [(W[k][p // nJ], W[k][nI + p % nJ]) for p, k in zip(ps, ks)]
+        vi = M.morap_solve_plain(ctx.h, ps, pw, stream, evaluate=False)
+        full = M.morap_solve_plain(ctx.h, ps, pw, stream, evaluate=True)
+        t_vi = vi["ms"] / len(ps)
+        t_eval = max(full["ms"] - vi["ms"], 0.0) / len(ps)
+        alg2_ms = nI * nJ * len(W) * t_vi + nJ * len(W) * t_eval
+        line["plain_fp64_gpu"] = {
+            "value": full["updates"] / (full["ms"] / 1e3), "unit": UNIT,
+            "sample": f"{len(ps)} (product, weight) pairs: Algorithm 3 then both Algorithm 4 evaluations",
+            "ms_per_pair_vi": t_vi, "ms_per_pair_eval": t_eval,
+            "est_ms_per_step": alg2_ms,
+            "speedup_time_to_solution": alg2_ms / (secs * 1e3 / args.steps),
+        }
+    if rank == 0 and not args.no_cpu:
+        v, pairs, dt = _oracle_sample(inst, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{pairs} (product, weight) pairs, {dt:.1f} s single-thread FP64 C oracle"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--launch-mode", type=int, default=0,
+                    help="0: sweep loops as CUDA graphs with a device-side while node; 1: host-driven bodies "
+                         "(same kernels; lets ncu list the kernels inside the loops)")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--plain-pairs", type=int, default=6)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_engine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

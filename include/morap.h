@@ -1,0 +1,301 @@
+/*
+ * morap.h -- C-ABI of the GB300 engine for multi-objective random task
+ * assignment and planning (MORAP, arxiv 2305.04397).
+ *
+ * The engine solves, for every agent x task product MDP M_i (x) A_j
+ * (Sec. 2 "Product MDP", Sec. 3.1), the weighted-sum value iteration of
+ * Algorithm 3, evaluates the cost and probability objectives of the
+ * returned scheduler with Algorithm 4 (Appendix A.4), chooses the task
+ * assignment of Algorithm 2 (Sec. 3.3), and answers threshold-point queries
+ * with the point-oriented Pareto loop of Algorithm 1 (Sec. 3.3, Thm 3).
+ *
+ * Conventions
+ *  - Every call returns an int status (MORAP_OK = 0).  On failure the
+ *    message of the calling thread's last error is available from
+ *    morap_last_error(); no call aborts the process.
+ *  - Inputs are caller-owned and are copied (or fully consumed) during the
+ *    call.  Outputs go to caller-allocated HOST arrays whose sizes are given
+ *    per call.  Handles are opaque and destroyed explicitly (the paper's
+ *    models are owned by exactly one owner, Sec. 4 "Programming").
+ *  - Objectives are maximised.  Costs enter as negative rewards (Sec. 3.1):
+ *    "expected cost <= 8" is the threshold c_i = -8.  The objective vector
+ *    has |I| + |J| entries: k = i for agent i's cost, k = |I| + j for task j's
+ *    probability (Def. 1, Algorithm 1 input t = (c, p)).
+ *  - "stream" arguments are cudaStream_t values passed as void*; NULL means
+ *    the legacy default stream.
+ *  - A context is not thread-safe: one host thread drives it at a time.
+ *  - No call of this library waits on the device without a bound: every
+ *    device loop has a sweep cap (MORAP_ENOTCONV when it is reached).
+ */
+#ifndef MORAP_H
+#define MORAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+    MORAP_OK = 0,
+    MORAP_EINVAL = 1,   /* malformed argument or model (message says which)   */
+    MORAP_ENOMEM = 2,   /* HBM budget or device allocation refused            */
+    MORAP_ENOTCONV = 3, /* a sweep cap was reached; outputs hold the last iterate */
+    MORAP_ECUDA = 4,    /* a CUDA runtime call failed (message has the error) */
+    MORAP_EBUSY = 5,    /* serving: the query is still in flight              */
+    MORAP_ESTATE = 6    /* call order violated (e.g. solve before build)      */
+};
+
+/* Precision modes for the optimisation sweeps (Algorithm 3). */
+enum {
+    /* FP32 sweeps with every operation rounded toward -inf (a certified lower
+     * bound of the FP64 iterate), then FP64 sweeps from that bound until the
+     * FP64 residual is <= eps_vi.  Used for products whose agent has a
+     * zero-cost action in every state; other products run MORAP_PREC_FP64. */
+    MORAP_PREC_MIXED = 0,
+    /* FP64 sweeps from 0, as printed. */
+    MORAP_PREC_FP64 = 1
+};
+
+/* Optional device allocator.  alloc returns a device pointer (or NULL on
+ * failure) valid on the context's device; free releases it.  When both are
+ * NULL the library uses cudaMalloc / cudaFree. */
+typedef void *(*morap_alloc_fn)(size_t bytes, void *user);
+typedef void (*morap_free_fn)(void *ptr, size_t bytes, void *user);
+
+typedef struct morap_config {
+    double eps_vi;      /* epsilon_1 of Algorithm 3 (stop when max|y - x| <= eps_vi); default 1e-8     */
+    double eps_eval;    /* epsilon_2 of Algorithm 4; default 1e-11 (its stop error grows with the
+                           expected number of steps, so it is kept below the 1e-6 value tolerance)   */
+    double tau_policy;  /* tie tolerance of the returned scheduler, see morap_solve; default 1e-9     */
+    int32_t max_sweeps; /* cap on sweeps per phase (FP32, FP64, evaluation); default 100000         */
+    int32_t precision;  /* MORAP_PREC_MIXED (default) or MORAP_PREC_FP64                            */
+    int32_t device;     /* CUDA device ordinal; default 0                                            */
+    int32_t launch_mode;/* 0 (default): each sweep loop is one CUDA graph whose while node runs
+                           bodies of six sweeps until the device work list is empty; 1: the host
+                           launches the same kernels body by body and reads the work list between
+                           bodies (same results; for profilers that cannot enter conditional graphs) */
+    size_t hbm_budget;  /* admission limit in bytes for all device memory of the context; 0 = none  */
+    morap_alloc_fn alloc;
+    morap_free_fn free;
+    void *alloc_user;
+} morap_config;
+
+typedef struct morap_ctx morap_ctx;
+
+/* Fill *cfg with the defaults listed above. */
+void morap_config_default(morap_config *cfg);
+
+/* Create a context on cfg->device (cfg may be NULL for the defaults).
+ * Errors: EINVAL (bad config), ECUDA. */
+int morap_ctx_create(const morap_config *cfg, morap_ctx **out);
+
+/* Release every device and host resource of the context.  NULL is a no-op. */
+int morap_ctx_destroy(morap_ctx *ctx);
+
+/* Message of the calling thread's most recent failed call ("" if none).
+ * The pointer stays valid until the thread's next failing call. */
+const char *morap_last_error(void);
+
+/* ---------------------------------------------------------------- models */
+
+/* Add agent i (a labelled MDP with a cost per action, Sec. 2 "Markov
+ * Decision Process"; its reward structure rho_i(s, a) = -cost(s, a)).
+ *   n_states        |S|, >= 1;  s0 the initial state
+ *   state_ptr[n+1]  actions of state s are rows state_ptr[s] .. state_ptr[s+1]-1
+ *                   (every state needs >= 1 enabled action); the local index of
+ *                   an action is its position in that range
+ *   sa_ptr[SA+1]    successors of row a are sa_ptr[a] .. sa_ptr[a+1]-1
+ *   succ[T], prob[T] successor states and probabilities; each row must sum to
+ *                   1 within 1e-9 (enabled actions, Sec. 2); duplicates are
+ *                   merged and zero entries dropped
+ *   cost[SA]        finite, >= 0
+ *   label_ptr[n+1], label_ap[]  L(s): the atomic propositions (any int32 ids)
+ *                   holding in state s
+ * *agent_id receives the agent's index (0, 1, ... in call order).
+ * Errors: EINVAL (message names the offending row), ESTATE after build. */
+int morap_add_agent(morap_ctx *ctx, int32_t n_states, int32_t s0, const int32_t *state_ptr,
+                    const int32_t *sa_ptr, const int32_t *succ, const double *prob, const double *cost,
+                    const int32_t *label_ptr, const int32_t *label_ap, int32_t *agent_id);
+
+/* Add task j, a DFA (Q, q0, Q_F, 2^AP, delta) whose accepting locations are
+ * sinks (Sec. 2 "Deterministic Finite Automata").
+ *   n_ap in 0..8    letters are 0 .. 2^n_ap - 1, bit b set iff ap_ids[b] in L(s)
+ *   delta[n_locs * 2^n_ap]  delta[q * 2^n_ap + letter]
+ *   accepting[n_locs]       1 for accepting locations
+ * The library computes the traps Q_R (no run reaches Q_F), done_j = Q_F u Q_R,
+ * and the pre-sinks carrying rho_{j+|I|} (Sec. 3.1).  Every transition into
+ * Q_F that does not leave from a pre-sink is redirected through one added
+ * pre-sink location, so the one-off reward counts every accomplishment.
+ * Errors: EINVAL (accepting location not a sink, target out of range),
+ * ESTATE after build. */
+int morap_add_task(morap_ctx *ctx, int32_t n_locs, int32_t q0, int32_t n_ap, const int32_t *ap_ids,
+                   const int32_t *delta, const uint8_t *accepting, int32_t *task_id);
+
+typedef struct morap_footprint {
+    int64_t n_products;   /* |I| * |J|                                        */
+    int64_t n_states;     /* product states over all products (done slots included) */
+    int64_t n_sa;         /* state-action rows                                 */
+    int64_t n_trans;      /* transitions                                       */
+    int64_t csr_bytes;    /* device bytes of the product CSRs                  */
+    int64_t device_bytes; /* all device bytes the context holds now            */
+    int64_t h2d_bytes;    /* host->device bytes this build copied              */
+} morap_footprint;
+
+/* Upload the agents and tasks and build all |I| x |J| product MDPs on the
+ * device (Sec. 2 "Product MDP": P'((s,q),a,(s',q')) = P(s,a,s') iff
+ * q' = delta(q, L(s')); product states whose location is in done_j are one
+ * absorbing slot of value 0).  Device-resident until the context is
+ * destroyed; calling it again rebuilds in place.  fp may be NULL.
+ * Errors: ESTATE (no agent or task), ENOMEM (hbm_budget), ECUDA. */
+int morap_build(morap_ctx *ctx, void *stream, morap_footprint *fp);
+
+/* Re-run the product construction on the device from the agent and task
+ * arrays already resident since the last morap_build (no host transfer).
+ * Enqueued on `stream`; returns once the launches are queued.
+ * Errors: ESTATE (no build yet), ECUDA. */
+int morap_rebuild(morap_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------------ the solver */
+
+/* Algorithm 2, loop 1 for K weight vectors at once, plus Algorithm 4 for the
+ * cost and probability of EVERY product under its returned scheduler.
+ *   W[K][|I|+|J|]           weight vectors (entries >= 0)
+ *   c_out[K][|I|][|J|]      c_ij = optimal scalarised value at (s_i0, q_j0)
+ *   rcost_out, rprob_out    same layout: E[rho_i] and E[rho_{|I|+j}] under
+ *                           the returned scheduler (may be NULL to skip
+ *                           Algorithm 4)
+ *   status_out[K][|I|][|J|] may be NULL; MORAP_OK or MORAP_ENOTCONV per pair
+ * The returned scheduler mu keeps, in each state, the action Algorithm 3 last
+ * recorded when its Q-value on the final values is within tau_policy of the
+ * maximum, and otherwise the lowest-index maximiser.
+ * Returns ENOTCONV if any pair hit the sweep cap (outputs still written). */
+int morap_solve(morap_ctx *ctx, int32_t K, const double *W, void *stream, double *c_out, double *rcost_out,
+                double *rprob_out, int32_t *status_out);
+
+/* Algorithm 2 in full for K weight vectors in one batch: loop 1 over all
+ * products, the assignment f maximising sum_j c_{f(j), j} (Hungarian;
+ * |I| != |J| is padded with zero-valued dummy agents or tasks), and loop 2
+ * (Algorithm 4) on the assigned products only.
+ *   r_out[K][|I|+|J|]   the supporting point r for each w (agents without a
+ *                       real task and tasks without a real agent get 0)
+ *   assign_out[K][|J|]  f(j) (an agent index, or -1 for a dummy agent); may be NULL
+ *   c_out[K][|I|][|J|]  may be NULL
+ * Errors as morap_solve. */
+int morap_supporting_points(morap_ctx *ctx, int32_t K, const double *W, void *stream, double *r_out,
+                            int32_t *assign_out, double *c_out);
+
+/* Statistics of the last morap_solve / morap_supporting_points call. */
+typedef struct morap_solve_stats {
+    int32_t K;                /* weights in the batch                              */
+    int32_t fp32_sweeps;      /* sweep launches of the FP32 phase (0 if unused)    */
+    int32_t fp64_sweeps;      /* sweep launches of the FP64 phase                   */
+    int32_t eval_sweeps;      /* sweep launches of the evaluation phase             */
+    int64_t updates_fp32;     /* transition-updates: one (s,a,s') term for one weight in one sweep */
+    int64_t updates_fp64;
+    int64_t updates_eval;     /* one (s, mu(s), s') term for one objective pair      */
+    int64_t bytes_fp32;       /* algorithmic bytes the sweeps had to move           */
+    int64_t bytes_fp64;
+    int64_t bytes_eval;
+    double ms_fp32;           /* device time of each phase's sweep loop (CUDA events on the
+                                 launching stream around the loop's graph launch)       */
+    double ms_fp64;
+    double ms_finalise;
+    double ms_eval;
+    double ms_host;           /* host assignment and bookkeeping inside the call    */
+    double ms_total;          /* whole call, host wall clock                        */
+    int32_t pairs_not_converged;
+    int32_t eval_pairs;
+    int64_t h2d_bytes;        /* host->device bytes the call copied                  */
+    int64_t d2h_bytes;        /* device->host bytes the call copied                  */
+    int32_t kernel_launches;  /* kernels of this library the call launched          */
+    int32_t reserved;
+} morap_solve_stats;
+
+int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out);
+
+/* The plain one-model-at-a-time FP64 GPU value iteration (the baseline the
+ * paper's GPU path uses: per model and weight, a CSR SpMV kernel, a segmented
+ * max/argmax kernel with the residual, and a host convergence check after
+ * every sweep; then Algorithm 4 the same way).
+ *   n_pairs, pair_product[n]  product index p = i*|J| + j
+ *   pair_w[n][2]              (w_i, w_{|I|+j}) for each pair
+ *   c_out, rcost_out, rprob_out [n]
+ * stats_out may be NULL: {sweeps_vi, sweeps_eval, updates, milliseconds}. */
+int morap_solve_plain(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_product, const double *pair_w,
+                      void *stream, double *c_out, double *rcost_out, double *rprob_out, double *stats_out);
+
+/* ------------------------------------------------------ point queries */
+
+typedef struct morap_point_result {
+    int32_t feasible;     /* 1 iff t_down == t when the loop stopped (Cor. (ii))      */
+    int32_t iterations;   /* supporting points computed                               */
+    int32_t converged;    /* 1 iff ||t_down - t_up|| <= eps when it stopped           */
+    int32_t status;       /* MORAP_OK or the first failing status                     */
+    double distance;      /* ||t_down - t_up||                                         */
+    double *t_up;         /* caller-provided [|I|+|J|] or NULL                          */
+    double *t_down;       /* caller-provided [|I|+|J|] or NULL                          */
+    double *w_hist;       /* caller-provided [max_iter][|I|+|J|] or NULL                */
+    double *r_hist;       /* caller-provided [max_iter][|I|+|J|] or NULL                */
+} morap_point_result;
+
+/* Algorithm 1 for threshold t = (c, p) with norm ||v|| = sqrt(v^T M v)
+ * (M symmetric positive definite, [n][n] row-major, NULL = identity) and
+ * tolerance eps.  The first direction is e_1; after each supporting point
+ * the outer bound t_down (projection of t onto {z : w'.z <= w'.r'}) is
+ * updated when w.r < w.t_down, the inner bound t_up (projection onto
+ * down(conv Phi)) is refreshed, and the loop stops when
+ * ||t_down - t_up|| <= eps or after max_iter points.
+ * Errors: EINVAL, ENOTCONV (max_iter reached or a sweep cap), ECUDA. */
+int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, int32_t max_iter, void *stream,
+                morap_point_result *res);
+
+/* ------------------------------------------------ host-side building blocks
+ * These run on the CPU only (no device needed) and are what morap_query and
+ * morap_supporting_points use. */
+
+/* Hungarian assignment: f_out[j] = the row assigned to column j maximising
+ * sum_j C[f(j)][j] for a square C [n][n] (row-major, rows = agents). */
+int morap_assign_max(int32_t n, const double *C, int32_t *f_out);
+
+/* argmin_z ||t - z||_M subject to A z <= b; A is [m][n] row-major. */
+int morap_project_halfspaces(int32_t n, int32_t m, const double *t, const double *A, const double *b,
+                             const double *M, double *z_out);
+
+/* argmin_x ||t - x||_M over x in down(conv{Phi_0..Phi_{m-1}}); Phi is [m][n]. */
+int morap_project_down_hull(int32_t n, int32_t m, const double *t, const double *Phi, const double *M,
+                            double *x_out);
+
+/* Task preprocessing as morap_add_task does it, exposed for checking:
+ * n_locs_out = locations after the optional pre-sink insertion (<= n_locs+1),
+ * flags_out[n_locs+1]: bit0 accepting, bit1 trap, bit2 pre-sink, bit3 done. */
+int morap_task_preprocess(int32_t n_locs, int32_t q0, int32_t n_ap, const int32_t *delta,
+                          const uint8_t *accepting, int32_t *n_locs_out, uint8_t *flags_out);
+
+/* ------------------------------------------------------ introspection */
+
+/* info_out[10] for product p = i*|J| + j: {S_agent, n_nondone_locations,
+ * n_states (incl. the done slot), n_sa, n_trans, init_local (local index of
+ * (s_i0, q_j0); the done slot when q_j0 is done), state_offset, pre_begin
+ * (first local state whose location is a pre-sink), agent i, task j}. */
+int morap_product_info(const morap_ctx *ctx, int32_t p, int64_t *info_out);
+
+/* Copy product p's CSR to host arrays sized from morap_product_info:
+ * state_sa[n_states+1], sa_tr[n_sa+1] (both rebased to 0), col[n_trans]
+ * (local state index; n_states-1 is the done slot), prob[n_trans],
+ * cost[n_sa], loc_out[n_nondone_locations] (the DFA location, after
+ * preprocessing, of each product location index).  Any pointer may be NULL. */
+int morap_product_download(morap_ctx *ctx, int32_t p, int64_t *state_sa, int64_t *sa_tr, int32_t *col,
+                           double *prob, double *cost, int32_t *loc_out);
+
+/* After morap_solve: the returned scheduler (local action index) and the final
+ * FP64 values of weight k on product p, over its local states. */
+int morap_last_policy(morap_ctx *ctx, int32_t k, int32_t p, uint8_t *mu_out, double *values_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MORAP_H */

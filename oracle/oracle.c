@@ -127,8 +127,17 @@ int orc_alg3(int n, const int *state_ptr, const int *sa_ptr, const int *col, con
 }
 
 /* The scheduler returned for Algorithm 3.  On the final values x, keep the
- * recorded action when its Q-value is within tau of the maximum; otherwise
- * take the lowest-index maximiser. */
+ * recorded action when its Q-value is within tau of the maximum.  Otherwise
+ * take the lowest-index action within tau of the maximum that is not a
+ * self-loop (an action whose only successor is u itself); only when every
+ * such action is a self-loop take the lowest-index one.  (At a fixed point a
+ * zero-reward self-loop always ties with the maximum, so preferring it would
+ * return "stay forever" in states where the value came from moving.) */
+static int is_self_loop(int u, int a, const int *sa_ptr, const int *col)
+{
+    return sa_ptr[a + 1] - sa_ptr[a] == 1 && col[sa_ptr[a]] == u;
+}
+
 void orc_finalise_policy(int n, const int *state_ptr, const int *sa_ptr, const int *col, const double *prob,
                          const double *rew, const double *x, const int *a_rec, double tau, int *mu)
 {
@@ -139,16 +148,28 @@ void orc_finalise_policy(int n, const int *state_ptr, const int *sa_ptr, const i
             continue;
         }
         double best = q_value(a0, sa_ptr, col, prob, rew, x);
-        int best_a = 0;
         for (int a = a0 + 1; a < a1; ++a) {
             const double qa = q_value(a, sa_ptr, col, prob, rew, x);
-            if (qa > best) {
+            if (qa > best)
                 best = qa;
-                best_a = a - a0;
-            }
         }
         const double q_rec = q_value(a0 + a_rec[u], sa_ptr, col, prob, rew, x);
-        mu[u] = (q_rec >= best - tau) ? a_rec[u] : best_a;
+        if (q_rec >= best - tau) {
+            mu[u] = a_rec[u];
+            continue;
+        }
+        int pick = -1, pick_loop = -1;
+        for (int a = a0; a < a1; ++a) {
+            if (q_value(a, sa_ptr, col, prob, rew, x) < best - tau)
+                continue;
+            if (is_self_loop(u, a, sa_ptr, col)) {
+                if (pick_loop < 0)
+                    pick_loop = a - a0;
+            } else if (pick < 0) {
+                pick = a - a0;
+            }
+        }
+        mu[u] = pick >= 0 ? pick : pick_loop;
     }
 }
 

@@ -1,0 +1,198 @@
+// Internal declarations shared by the engine's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <vector_types.h>
+
+#include "../../include/morap.h"
+
+namespace morap {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+// ------------------------------------------------------------- host models
+struct HostAgent {
+    int32_t n_states = 0, s0 = 0;
+    std::vector<int32_t> state_ptr, sa_ptr, succ;
+    std::vector<double> prob, cost;
+    std::vector<int32_t> label_ptr, label_ap;
+    bool free_action_everywhere = false;  // every state has a zero-cost action
+};
+
+// A task after preprocessing.  Product locations are the non-done
+// locations, numbered with the pre-sinks last so that "pre-sink" is a
+// single threshold on the product-local state index.
+struct HostTask {
+    int32_t n_locs = 0;  // after pre-sink insertion
+    int32_t q0 = 0;
+    int32_t n_ap = 0, n_letters = 1;
+    std::vector<int32_t> ap_ids;
+    std::vector<int32_t> delta;   // [n_locs][n_letters]
+    std::vector<uint8_t> flags;   // bit0 accepting, bit1 trap, bit2 pre-sink, bit3 done
+    std::vector<int32_t> ploc;    // product location index of each location, -1 if done
+    std::vector<int32_t> loc_of;  // location of each product location index
+    int32_t n_nd = 0, n_pre = 0;
+    // nd_delta[pl * n_letters + letter] = product location index of the
+    // successor location, or -1 when it is done.
+    std::vector<int16_t> nd_delta;
+};
+
+int preprocess_task(int32_t n_locs, int32_t q0, int32_t n_ap, const int32_t *ap_ids, const int32_t *delta,
+                    const uint8_t *accepting, HostTask &out);
+
+// --------------------------------------------------------- host algorithms
+// Square assignment maximising sum_j C[f(j)][j]; C row-major [n][n].
+void hungarian_max(int n, const double *C, int *f);
+
+// Dense convex QP: min 1/2 x'Gx + c'x  s.t.  A x <= b (m rows), E x = d (p rows).
+// Mehrotra predictor-corrector primal-dual interior point.  Returns 0 on
+// convergence.
+int qp_solve(int n, const double *G, const double *c, int m, const double *A, const double *b, int p,
+             const double *E, const double *d, double *x, double tol = 1e-13, int max_iter = 200);
+
+int project_halfspaces(int n, int m, const double *t, const double *A, const double *b, const double *M,
+                       double *z);
+int project_down_hull(int n, int m, const double *t, const double *Phi, const double *M, double *x);
+
+// ------------------------------------------------------ device layout
+struct ProdDesc {
+    uint32_t state_off;  // global index of the product's first state
+    uint32_t n_nd;       // non-done states (Qn * S); the done slot is state_off + n_nd
+    uint32_t pre_begin;  // local states >= pre_begin sit at a pre-sink location
+    int32_t init_local;  // local index of (s0, q0), == n_nd when q0 is done
+    uint32_t sa_off, tr_off;
+    int32_t agent, task;
+    uint32_t S, SA, T;   // agent sizes
+    int32_t Qn;
+    uint32_t letter_off; // offset of this product's letter table (per agent state)
+};
+
+struct AgentDesc {
+    uint32_t sp_off;    // into the concatenated state_ptr arrays (S+1 each)
+    uint32_t sap_off;   // into the concatenated sa_ptr arrays (SA+1 each)
+    uint32_t cost_off;  // into the concatenated cost arrays (SA each)
+    uint32_t tr_off;    // into the concatenated succ/prob arrays (T each)
+    uint32_t lp_off;    // into the concatenated label_ptr arrays (S+1 each)
+    uint32_t la_off;    // into the concatenated label_ap arrays
+    uint32_t S, SA, T;
+    int32_t s0;
+};
+
+struct TaskDesc {
+    uint32_t delta_off;  // into nd_delta
+    uint32_t ap_off;     // into ap_ids
+    int32_t n_ap, n_letters, Qn, n_pre;
+    int32_t q0_ploc;     // product location index of q0, -1 if done
+};
+
+// Loop control block for one device-side sweep loop (see sweep.cu).
+struct LoopCtl {
+    unsigned int cnt[3];   // length of work list L[n % 3]
+    unsigned int next[3];  // dynamic scheduling cursor of sweep n into L[n % 3]
+    unsigned int sweep_base;
+    unsigned int hit_cap;
+    unsigned int cap;
+    unsigned int pad;
+    unsigned long long updates;
+    unsigned long long bytes;
+};
+
+constexpr int kChunk = 512;      // states per work item of the optimisation sweeps
+constexpr int kEvalChunk = 256;  // states per work item of the evaluation sweeps
+constexpr int kThreads = 256;
+constexpr int kGatherBatch = 4;  // independent successor gathers a thread issues back to back
+
+struct SweepArgs {
+    const uint32_t *state_sa;
+    const uint32_t *sa_tr;
+    const int32_t *col;
+    const int2 *cp32;     // per transition {col, p rounded down as float bits}
+    const double *p64;
+    const float *cost32;
+    const double *cost64;
+    const int4 *chunks;   // {product, begin, end, first}
+    const ProdDesc *prods;
+    const float2 *w32;    // per pair (p*Kp + k): (w_i rounded up, w_p rounded down)
+    const double2 *w64;   // per pair: (w_i, w_p)
+    const double *thr;    // per pair freeze threshold of this phase
+    unsigned long long *res[3];  // per pair residual of sweep n % 3 (double bits)
+    int32_t *sweeps_pair;
+    uint8_t *frozen;      // per pair: 1 once its residual fell to the threshold
+    unsigned int *list[3];
+    LoopCtl *ctl;
+    void *V[2];
+    uint8_t *a_rec;
+    double eps1;
+    int P;
+};
+
+struct EvalArgs {
+    const uint32_t *state_sa;
+    const uint32_t *sa_tr;
+    const int32_t *col;
+    const double *p64;
+    const double *cost64;
+    const ProdDesc *prods;
+    const uint8_t *policy;  // [state][Kp]
+    int Kp;
+    const int4 *chunks;     // {eval pair, begin, end, first}
+    const int4 *pairs;      // {product, k, value offset, 0}
+    double thr;
+    unsigned long long *res[3];
+    int32_t *sweeps_pair;
+    uint8_t *frozen;
+    unsigned int *list[3];
+    LoopCtl *ctl;
+    double2 *E[2];
+};
+
+// ---------------------------------------------------------- kernel launchers
+// (defined in the .cu files; every launcher enqueues on `s` and returns the
+// cudaError_t of the launch as an int)
+int launch_letters(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
+                   const int32_t *label_ptr, const int32_t *label_ap, const int32_t *ap_ids, uint8_t *letters,
+                   uint32_t max_S, void *s);
+int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
+                 const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ, const double *a_prob,
+                 const double *a_cost, const uint8_t *letters, const int16_t *nd_delta, uint32_t *state_sa,
+                 uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float *cost32, double *cost64,
+                 uint32_t total_states, uint32_t total_sa, uint32_t total_tr, uint32_t max_work, void *s);
+
+int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W,
+                         float2 *w32, double2 *w64, double *thr32, double *thr64, double eps1, void *s);
+int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
+                     size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s);
+int launch_sweep(bool fp64, int Kp, const SweepArgs &a, int pos, int grid, void *s);
+int sweep_blocks_per_sm(bool fp64, int Kp);
+int eval_blocks_per_sm();
+int launch_loop_control(LoopCtl *ctl, unsigned long long handle, int next_idx, void *s);
+int launch_loop_control_host(LoopCtl *ctl, int next_idx, void *s);
+int launch_convert(const float *v32, double *v64a, double *v64b, size_t n, void *s);
+int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, void *s);
+int launch_gather_c(int Kp, const ProdDesc *prods, int P, const double *V64, const uint8_t *frozen, double *c_out,
+                    int32_t *status_out, void *s);
+int launch_eval_sweep(const EvalArgs &a, int pos, int grid, void *s);
+int launch_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const double2 *E, double *rc,
+                       double *rp, void *s);
+// plain baseline
+int launch_plain_spmv(const uint32_t *sa_tr, const int32_t *col, const double *p64, const double *cost64,
+                      uint32_t sa_begin, uint32_t n_sa, double wi, double wp, uint32_t pre_sa_begin,
+                      uint32_t state_off, const double *x, double *q, void *s);
+int launch_plain_reduce(const uint32_t *state_sa, uint32_t state_off, uint32_t n_states, uint32_t sa_begin,
+                        const double *q, const double *x, double *y, int32_t *a_rec, double eps,
+                        unsigned long long *res, void *s);
+int launch_plain_finalize(const uint32_t *state_sa, const uint32_t *sa_tr, const int32_t *col, uint32_t state_off,
+                          uint32_t n_states, uint32_t sa_begin, const double *q, const int32_t *a_rec, double tau,
+                          int32_t *mu, void *s);
+int launch_plain_eval(const uint32_t *state_sa, const uint32_t *sa_tr, const int32_t *col, const double *p64,
+                      const double *cost64, uint32_t state_off, uint32_t n_states, uint32_t pre_begin,
+                      const int32_t *mu, int objective, const double *x, double *y, unsigned long long *res,
+                      void *s);
+
+}  // namespace morap

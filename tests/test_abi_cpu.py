@@ -1,0 +1,121 @@
+"""The C-ABI library on the CPU: it loads, exports every symbol include/morap.h
+declares, and its host-side building blocks (task preprocessing, the
+assignment of Algorithm 2, the two projections of Algorithm 1) agree with
+the oracle.  No device call is made here."""
+
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import instances as I
+from oracle import dfa as D
+from oracle import core as C
+from oracle import pareto as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2305_04397_gb300 import build
+
+    build.build()
+    from paper_2305_04397_gb300 import morap
+
+    morap.lib()
+    return morap
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "morap.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(morap_[a-z_0-9]+)\s*\(", src)) - {"morap_alloc_fn", "morap_free_fn"})
+
+
+def test_exports_every_declared_symbol(M):
+    import ctypes
+
+    lib = ctypes.CDLL(M.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(M.declared_symbols())
+
+
+def test_config_default(M):
+    cfg = M.morap_config_default()
+    assert cfg.eps_vi == 1e-8 and cfg.eps_eval == 1e-11 and cfg.tau_policy == 1e-9
+    assert cfg.precision == M.PREC_MIXED and cfg.max_sweeps == 100000
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 6, 7])
+def test_assignment_vs_brute_force(M, n):
+    rng = np.random.default_rng(10 + n)
+    for _ in range(4):
+        Cm = rng.normal(size=(n, n))
+        f = M.morap_assign_max(Cm)
+        got = sum(Cm[f[j], j] for j in range(n))
+        best = max(sum(Cm[p[j], j] for j in range(n)) for p in itertools.permutations(range(n)))
+        assert got == pytest.approx(best, abs=1e-12)
+        assert sorted(f) == list(range(n))
+
+
+def test_assignment_large_vs_oracle(M):
+    rng = np.random.default_rng(1)
+    Cm = rng.normal(size=(60, 60))
+    f = M.morap_assign_max(Cm)
+    fo = C.assignment(Cm)
+    assert sum(Cm[f[j], j] for j in range(60)) == pytest.approx(sum(Cm[fo[j], j] for j in range(60)), abs=1e-9)
+
+
+def test_halfspace_projection_vs_oracle(M):
+    rng = np.random.default_rng(2)
+    for n, m in [(2, 1), (3, 3), (5, 6), (8, 10)]:
+        Wt = rng.dirichlet(np.ones(n), size=m)
+        R = rng.normal(size=(m, n))
+        b = np.einsum("ij,ij->i", Wt, R)
+        t = R.max(axis=0) + rng.uniform(0.1, 1.0, size=n)
+        A = rng.normal(size=(n, n))
+        Mm = A @ A.T + n * np.eye(n)
+        for MM in (None, Mm):
+            z = M.morap_project_halfspaces(t, Wt, b, MM)
+            zo = P.project_halfspaces(t, Wt, b, np.eye(n) if MM is None else MM)
+            assert np.all(Wt @ z <= b + 1e-9)
+            assert np.max(np.abs(z - zo)) < 1e-6
+
+
+def test_down_hull_projection_vs_oracle_and_scan(M):
+    rng = np.random.default_rng(3)
+    for n, m in [(2, 1), (2, 3), (3, 4), (5, 6), (6, 9)]:
+        Phi = np.column_stack([-rng.uniform(1, 5, size=(m, max(n // 2, 1))),
+                               rng.uniform(0, 1, size=(m, n - max(n // 2, 1)))])
+        t = Phi.max(axis=0) + rng.uniform(-0.5, 0.5, size=n)
+        x = M.morap_project_down_hull(t, Phi)
+        xo = P.project_down_hull(t, Phi, np.eye(n))
+        assert np.linalg.norm(t - x) == pytest.approx(np.linalg.norm(t - xo), abs=1e-7)
+        assert np.max(np.abs(x - xo)) < 1e-5
+
+
+def test_task_preprocess_vs_oracle(M):
+    tasks = [I.fig2_task(), I.sequence_task([1, 2, 3]), I.sequence_task([4, 5], avoid_ap=9)]
+    tasks += [I.random_tiny_task(7, k, n_locs=4, n_ap=2) for k in range(6)]
+    for t in tasks:
+        n, flags = M.morap_task_preprocess(t.n_locs, t.q0, t.n_ap, t.delta, t.accepting)
+        d = D.preprocess(t)
+        assert n == d["n_locs"]
+        assert [bool(f & 1) for f in flags] == list(d["accepting"])
+        assert [bool(f & 2) for f in flags] == list(d["trap"])
+        assert [bool(f & 4) for f in flags] == list(d["pre"])
+        assert [bool(f & 8) for f in flags] == list(d["done"])
+
+
+def test_task_preprocess_rejects_non_sink_accepting(M):
+    delta = np.array([[1, 1], [0, 1]], np.int32).reshape(-1)
+    with pytest.raises(M.MorapError) as e:
+        M.morap_task_preprocess(2, 0, 1, delta, np.array([0, 1], np.uint8))
+    assert e.value.code == M.EINVAL
+    assert "not a sink" in str(e.value)

@@ -1,0 +1,419 @@
+"""Parity of the CUDA engine with the FP64 oracle, through the C-ABI.
+
+Tolerances (the benchmark spec): per-objective values within 1e-6 absolute at
+eps_vi = 1e-8; schedulers identical wherever the oracle's action gap
+exceeds 1e-9; product CSRs identical (structure exact, probabilities
+bit-exact).  Full-size checks run the 10 x 20 grid instance in the launch
+configuration the benchmark times (one supporting-point batch of K = 16)
+and compare sampled products one by one.
+"""
+
+import numpy as np
+import pytest
+
+import instances as I
+from oracle import core as O
+from oracle import pareto as OP
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2305_04397_gb300 import build
+
+    build.build()
+    from paper_2305_04397_gb300 import morap
+
+    return morap
+
+
+def make_ctx(M, inst_or_pair, **cfg_kw):
+    cfg = M.morap_config_default()
+    for k, v in cfg_kw.items():
+        setattr(cfg, k, v)
+    ctx = M.Context(cfg)
+    agents, tasks = (inst_or_pair.agents, inst_or_pair.tasks) if hasattr(inst_or_pair, "agents") else inst_or_pair
+    ctx.add(agents, tasks)
+    ctx.build()
+    return ctx
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return I.config_tiny()
+
+
+@pytest.fixture(scope="module")
+def tiny_prods(tiny):
+    return O.products(tiny.agents, tiny.tasks)
+
+
+def tiny_weights(tiny):
+    extra = np.array([[0.01, 0.02, 0.5, 0.3, 0.17], [0.2, 0.2, 0.2, 0.2, 0.2], [0.0, 0.0, 1.0, 0.0, 0.0]])
+    return np.vstack([tiny.weights, extra])
+
+
+def canon_device(D):
+    info = D["info"]
+    S, n = info["S"], info["n_states"]
+    done = n - 1
+    out = {}
+    for u in range(n - 1):
+        key_s = (u % S, int(D["loc"][u // S]))
+        for a in range(D["state_sa"][u + 1] - D["state_sa"][u]):
+            sa = D["state_sa"][u] + a
+            row = {}
+            for t in range(D["sa_tr"][sa], D["sa_tr"][sa + 1]):
+                c = int(D["col"][t])
+                k = ("DONE",) if c == done else (c % S, int(D["loc"][c // S]))
+                row[k] = row.get(k, 0.0) + float(D["prob"][t])
+            out[key_s + (a,)] = (row, float(D["cost"][sa]))
+    return out
+
+
+def canon_oracle(p):
+    out = {}
+    for u in range(p.n - 1):
+        ks = p.key(u)
+        for a in range(p.state_ptr[u + 1] - p.state_ptr[u]):
+            sa = p.state_ptr[u] + a
+            row = {p.key(int(p.col[t])): float(p.prob[t]) for t in range(p.sa_ptr[sa], p.sa_ptr[sa + 1])}
+            out[ks + (a,)] = (row, float(p.sa_cost[sa]))
+    return out
+
+
+# ------------------------------------------------------------- products
+
+
+def test_product_csr_matches_oracle(M, tiny):
+    for agents, tasks in [(tiny.agents, tiny.tasks), ([I.fig2_agent()], [I.fig2_task()])]:
+        ctx = make_ctx(M, (agents, tasks))
+        for i, a in enumerate(agents):
+            for j, t in enumerate(tasks):
+                D = M.morap_product_download(ctx.h, i * len(tasks) + j)
+                p = O.Product(a, t)
+                assert D["info"]["n_states"] == p.n
+                assert D["info"]["n_trans"] >= p.n_trans
+                assert canon_device(D) == canon_oracle(p)
+                assert p.key(p.init) == (("DONE",) if D["info"]["init_local"] == p.n - 1 else
+                                         (D["info"]["init_local"] % D["info"]["S"],
+                                          int(D["loc"][D["info"]["init_local"] // D["info"]["S"]])))
+        ctx.close()
+
+
+# ------------------------------------------------------------- Algorithm 3 / 4
+
+
+def _oracle_pairs(prods, W, nI, nJ):
+    K = len(W)
+    c = np.zeros((K, nI, nJ))
+    rc = np.zeros_like(c)
+    rp = np.zeros_like(c)
+    res = {}
+    for k, w in enumerate(W):
+        for i in range(nI):
+            for j in range(nJ):
+                r = O.solve_pair(prods[i][j], w[i], w[nI + j])
+                c[k, i, j], rc[k, i, j], rp[k, i, j] = r["c"], r["r_cost"], r["r_prob"]
+                res[k, i, j] = r
+    return c, rc, rp, res
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_matches_oracle(M, tiny, tiny_prods, precision):
+    W = tiny_weights(tiny)
+    nI, nJ = len(tiny.agents), len(tiny.tasks)
+    ctx = make_ctx(M, tiny, precision=precision)
+    out = ctx.solve(W)
+    c, rc, rp, res = _oracle_pairs(tiny_prods, W, nI, nJ)
+    assert np.all(out["status"] == 0)
+    assert np.max(np.abs(out["c"] - c)) < TOL
+    # A zero weight on one of the pair's two objectives leaves that objective
+    # free among the optimal schedulers (ties), so only the weighted one and
+    # the scalarised value are unique there; otherwise both must match.
+    wc = W[:, :nI][:, :, None] * np.ones((1, 1, nJ))
+    wp = W[:, nI:][:, None, :] * np.ones((1, nI, 1))
+    both = (wc > 0) & (wp > 0)
+    assert np.max(np.abs(out["r_cost"] - rc)[both | ((wc > 0) & (wp == 0))]) < TOL
+    assert np.max(np.abs(out["r_prob"] - rp)[both | ((wp > 0) & (wc == 0))]) < TOL
+    assert np.max(np.abs(wc * out["r_cost"] + wp * out["r_prob"] - c)) < TOL
+    # schedulers: identical wherever the oracle's action gap exceeds 1e-9
+    checked = 0
+    for k in range(len(W)):
+        for i in range(nI):
+            for j in range(nJ):
+                p = tiny_prods[i][j]
+                r = res[k, i, j]
+                mu, _ = M.morap_last_policy(ctx.h, k, i * nJ + j)
+                q = O.q_values(p, r["rew"], r["x"])
+                for u in range(p.n - 1):
+                    a0, a1 = p.state_ptr[u], p.state_ptr[u + 1]
+                    qa = q[a0:a1]
+                    m = r["mu"][u]
+                    others = np.delete(qa, m)
+                    gap = qa[m] - (others.max() if len(others) else -np.inf)
+                    if gap > 1e-9:
+                        assert mu[u] == m, (k, i, j, u)
+                        checked += 1
+    assert checked > 20
+    st = ctx.stats()
+    if precision == 0:
+        assert st["fp32_sweeps"] > 0
+    else:
+        assert st["fp32_sweeps"] == 0
+    ctx.close()
+
+
+def test_fp64_only_path_without_free_action(M):
+    """The Fig. 2 agent has no zero-cost action, so the engine runs FP64 from
+    0 (the FP32 lower-bound argument needs one); values match the oracle."""
+    a, t = I.fig2_agent(), I.fig2_task()
+    ctx = make_ctx(M, ([a], [t]))
+    W = np.array([[1.0, 0.0], [0.4, 0.6], [0.0, 1.0], [0.2, 0.8]])
+    out = ctx.solve(W)
+    p = O.Product(a, t)
+    for k, w in enumerate(W):
+        r = O.solve_pair(p, w[0], w[1])
+        assert out["c"][k, 0, 0] == pytest.approx(r["c"], abs=TOL)
+        assert out["r_cost"][k, 0, 0] == pytest.approx(r["r_cost"], abs=TOL)
+        assert out["r_prob"][k, 0, 0] == pytest.approx(r["r_prob"], abs=TOL)
+    assert ctx.stats()["fp32_sweeps"] == 0
+    # the paper's printed r1 for w = (1, 0)
+    assert out["r_cost"][0, 0, 0] == pytest.approx(-1.1, abs=1e-9)
+    assert out["r_prob"][0, 0, 0] == pytest.approx(0.1, abs=1e-9)
+    ctx.close()
+
+
+# ------------------------------------------------------------- Algorithm 2
+
+
+def _check_supporting(out, prods, W, nI, nJ):
+    for k, w in enumerate(W):
+        r, f, C, RC, RP = O.supporting_point(prods, w)
+        Cp = O.pad_square(C)
+        fg = out["assign"][k]
+        real = [i for i in fg if i >= 0]
+        assert len(set(real)) == len(real)  # a (partial) permutation
+        # the engine's assignment is optimal for the oracle's c matrix
+        tot = sum(C[fg[j], j] for j in range(nJ) if fg[j] >= 0)
+        best = sum(Cp[f[j], j] for j in range(nJ))
+        assert tot == pytest.approx(best, abs=TOL)
+        assert w @ out["r"][k] == pytest.approx(w @ r, abs=TOL)
+        # r is the point of that assignment (both objectives are unique only
+        # when both weights of the pair are positive)
+        for j in range(nJ):
+            i = fg[j]
+            if i >= 0 and w[i] > 0 and w[nI + j] > 0:
+                assert out["r"][k][nI + j] == pytest.approx(RP[i, j], abs=TOL)
+                assert out["r"][k][i] == pytest.approx(RC[i, j], abs=TOL)
+
+
+def test_supporting_points_match_oracle(M, tiny, tiny_prods):
+    W = tiny_weights(tiny)
+    ctx = make_ctx(M, tiny)
+    out = ctx.supporting_points(W)
+    _check_supporting(out, tiny_prods, W, len(tiny.agents), len(tiny.tasks))
+    ctx.close()
+
+
+# ------------------------------------------------------------- Algorithm 1
+
+
+def test_query_matches_oracle_alg1(M, tiny, tiny_prods):
+    ctx = make_ctx(M, tiny)
+    for t in [tiny.thresholds[0], np.array([-12.0, -12.0, 0.6, 0.6, 0.6]), np.array([-1.0, -1.0, 0.2, 0.2, 0.2])]:
+        got = ctx.query(t, eps=1e-6, max_iter=40)
+        supp = lambda w: O.supporting_point(tiny_prods, w)[0]
+        want = OP.alg1(supp, t, eps=1e-6, max_iter=40)
+        assert got["feasible"] == want["feasible"]
+        assert np.max(np.abs(got["t_down"] - want["t_dn"])) < 1e-4
+        assert np.max(np.abs(got["t_up"] - want["t_up"])) < 1e-4
+        # Lemma 6 on every direction the engine produced
+        for w in got["w_hist"]:
+            assert np.all(w >= 0) and abs(w.sum() - 1) < 1e-9
+    ctx.close()
+
+
+def test_query_fig2(M):
+    ctx = make_ctx(M, ([I.fig2_agent()], [I.fig2_task()]))
+    prods = [[O.Product(I.fig2_agent(), I.fig2_task())]]
+    supp = lambda w: O.supporting_point(prods, w)[0]
+    for t in ([-1.8, 0.9], [-3.0, 0.5], [-2.5, 0.7]):
+        got = ctx.query(np.array(t), eps=1e-7)
+        want = OP.alg1(supp, np.array(t), eps=1e-7)
+        assert got["feasible"] == want["feasible"]
+        assert np.max(np.abs(got["t_down"] - want["t_dn"])) < 1e-5
+    ctx.close()
+
+
+# ------------------------------------------------------------- full size
+
+
+@pytest.fixture(scope="module")
+def grid32():
+    return I.config_grid32()
+
+
+def test_grid32_full_size_sampled(M, grid32):
+    """10 agents x 20 tasks (200 products of ~3.5k states) with K = 16 in one
+    supporting-point batch (the benchmark's launch); sampled products are
+    recomputed by the oracle one by one."""
+    inst = grid32
+    nI, nJ = len(inst.agents), len(inst.tasks)
+    ctx = make_ctx(M, inst)
+    W = inst.weights
+    out = ctx.supporting_points(W, want_c=True)
+    st = ctx.stats()
+    assert st["pairs_not_converged"] == 0
+    rng = np.random.default_rng(0)
+    sample = [(int(i), int(j)) for i, j in zip(rng.integers(0, nI, 5), rng.integers(0, nJ, 5))]
+    sample += [(int(out["assign"][k][j]), j) for k, j in [(3, 0), (7, 5), (11, 19)] if out["assign"][k][j] >= 0]
+    for i, j in sample:
+        p = O.Product(inst.agents[i], inst.tasks[j])
+        for k in range(len(W)):
+            r = O.solve_pair(p, W[k][i], W[k][nI + j])
+            assert out["c"][k, i, j] == pytest.approx(r["c"], abs=TOL), (i, j, k)
+            if out["assign"][k][j] == i:
+                assert out["r"][k][i] == pytest.approx(r["r_cost"], abs=TOL), (i, j, k)
+                assert out["r"][k][nI + j] == pytest.approx(r["r_prob"], abs=TOL), (i, j, k)
+    # properties that hold at any size: probabilities in [0, 1], costs <= 0,
+    # c consistent with w.r on the assigned products
+    assert np.all(out["r"][:, nI:] >= -1e-12) and np.all(out["r"][:, nI:] <= 1 + 1e-12)
+    assert np.all(out["r"][:, :nI] <= 1e-12)
+    for k, w in enumerate(W):
+        tot = sum(out["c"][k, out["assign"][k][j], j] for j in range(nJ) if out["assign"][k][j] >= 0)
+        assert w @ out["r"][k] == pytest.approx(tot, abs=1e-5)
+    ctx.close()
+
+
+def test_host_driven_loop_matches_graph_loop(M, tiny):
+    """launch_mode 1 (host-driven bodies, for profilers) runs the same
+    kernels in the same order as the CUDA-graph while loop."""
+    a = make_ctx(M, tiny)
+    b = make_ctx(M, tiny, launch_mode=1)
+    ra = a.supporting_points(tiny.weights, want_c=True)
+    rb = b.supporting_points(tiny.weights, want_c=True)
+    assert np.array_equal(ra["c"], rb["c"]) and np.array_equal(ra["r"], rb["r"])
+    assert a.stats()["fp32_sweeps"] == b.stats()["fp32_sweeps"]
+    a.close()
+    b.close()
+
+
+def test_batch_invariance(M, grid32):
+    """Each pair runs exactly its own sweeps: a weight alone and inside the
+    K = 16 batch gives bitwise-identical c and points."""
+    inst = grid32
+    ctx = make_ctx(M, inst)
+    W = inst.weights
+    full = ctx.solve(W, evaluate=True)
+    for k in (0, 5, 13):
+        one = ctx.solve(W[k:k + 1], evaluate=True)
+        assert np.array_equal(one["c"][0], full["c"][k])
+        assert np.array_equal(one["r_cost"][0], full["r_cost"][k])
+        assert np.array_equal(one["r_prob"][0], full["r_prob"][k])
+    ctx.close()
+
+
+# ------------------------------------------------------------- edge cases
+
+
+def test_edge_cases(M, tiny, tiny_prods):
+    nI, nJ = len(tiny.agents), len(tiny.tasks)
+    ctx = make_ctx(M, tiny)
+    # K not a power of two, and K > 64 (two batches)
+    rng = np.random.default_rng(4)
+    W = rng.dirichlet(np.ones(nI + nJ), size=70)
+    W[3] = 0.0
+    out = ctx.solve(W)
+    c, rc, rp, _ = _oracle_pairs(tiny_prods, W[[0, 3, 65, 69]], nI, nJ)
+    got = out["c"][[0, 3, 65, 69]]
+    assert np.max(np.abs(got - c)) < TOL
+    assert np.all(out["c"][3] == 0.0)
+    ctx.close()
+    # task accepting at q0, and a task that can never be accomplished
+    acc0 = I.Task(1, 0, 1, np.array([I.GRID_AP(0, 0)], np.int32), np.zeros(2, np.int32), np.array([1], np.uint8))
+    never = I.sequence_task([I.GRID_AP(9, 9)])  # not on the 4x4 grid
+    ctx = make_ctx(M, (tiny.agents, [acc0, never]))
+    out = ctx.solve(np.array([[0.2, 0.2, 0.3, 0.3]]))
+    assert np.all(out["c"] == 0.0) and np.all(out["r_prob"] == 0.0) and np.all(out["r_cost"] == 0.0)
+    ctx.close()
+
+
+def test_sweep_cap_reports_not_converged(M, grid32):
+    ctx = make_ctx(M, grid32, max_sweeps=6)
+    out = ctx.solve(grid32.weights[:4], check=False)
+    assert out["code"] == M.ENOTCONV
+    assert np.any(out["status"] == M.ENOTCONV)
+    ctx.close()
+
+
+def test_invalid_inputs(M, tiny):
+    ctx = M.Context()
+    a = tiny.agents[0]
+    bad = a.prob.copy()
+    bad[0] += 0.01
+    with pytest.raises(M.MorapError) as e:
+        M.morap_add_agent(ctx.h, a.n_states, a.s0, a.state_ptr, a.sa_ptr, a.succ, bad, a.cost, a.label_ptr,
+                          a.label_ap)
+    assert e.value.code == M.EINVAL
+    with pytest.raises(M.MorapError) as e:
+        ctx.solve(np.ones((1, 2)))
+    assert e.value.code == M.ESTATE
+    ctx.add(tiny.agents, tiny.tasks)
+    ctx.build()
+    W = tiny.weights.copy()
+    W[0, 0] = -0.5
+    with pytest.raises(M.MorapError) as e:
+        ctx.solve(W)
+    assert e.value.code == M.EINVAL
+    ctx.close()
+
+
+def test_hbm_budget_refuses_before_allocating(M, grid32):
+    cfg = M.morap_config_default()
+    cfg.hbm_budget = 1 << 20
+    ctx = M.Context(cfg)
+    ctx.add(grid32.agents, grid32.tasks)
+    with pytest.raises(M.MorapError) as e:
+        ctx.build()
+    assert e.value.code == M.ENOMEM
+    ctx.close()
+
+
+# ------------------------------------------------------------- plain baseline
+
+
+def test_plain_baseline_matches_oracle(M, tiny, tiny_prods):
+    nI, nJ = len(tiny.agents), len(tiny.tasks)
+    ctx = make_ctx(M, tiny)
+    pairs = [(0, 0, 0.1, 0.9), (1, 2, 0.3, 0.7), (0, 1, 1.0, 0.0), (1, 0, 0.02, 0.98)]
+    out = M.morap_solve_plain(ctx.h, [i * nJ + j for i, j, _, _ in pairs], [(a, b) for _, _, a, b in pairs])
+    for e, (i, j, wc, wp) in enumerate(pairs):
+        r = O.solve_pair(tiny_prods[i][j], wc, wp)
+        assert out["c"][e] == pytest.approx(r["c"], abs=TOL)
+        assert out["r_cost"][e] == pytest.approx(r["r_cost"], abs=TOL)
+        assert out["r_prob"][e] == pytest.approx(r["r_prob"], abs=TOL)
+        assert out["sweeps_vi"] > 0
+    ctx.close()
+
+
+def test_torch_allocator_and_stream(M, tiny):
+    import torch
+
+    cfg = M.morap_config_default()
+    ctx = M.Context(cfg, use_torch_allocator=True)
+    ctx.add(tiny.agents, tiny.tasks)
+    s = torch.cuda.Stream()
+    ctx.build(s.cuda_stream)
+    a = ctx.solve(tiny.weights, stream=s.cuda_stream)
+    ctx.close()
+    ctx2 = make_ctx(M, tiny)
+    b = ctx2.solve(tiny.weights)
+    ctx2.close()
+    assert np.array_equal(a["c"], b["c"])

@@ -234,6 +234,24 @@ def test_record_rule_avoids_stay_ties():
     assert int(np.argmax(greedy[a0:a1] >= greedy[a0:a1].max() - 1e-9)) == 0
 
 
+def test_finalise_fallback_prefers_moving_over_self_loop():
+    """When the recorded action is stale (more than tau below the maximum) the
+    scheduler falls back to a near-maximiser that is not a self-loop: at a
+    fixed point the free stay ties with the maximum, and choosing it would
+    return "stay forever" where the value came from moving."""
+    a = I.corridor_agent(6, 0.0, 0)
+    t = I.sequence_task([I.GRID_AP(4, 0)])
+    p = C.Product(a, t)
+    rew = p.reward_scalarised(0.01, 0.99)
+    x, a_rec, _, _ = C.alg3(p, rew, 1e-14)
+    stale = np.full_like(a_rec, 4)  # W: away from the target
+    mu = C.finalise(p, rew, x, stale)
+    for s in range(4):  # states left of the target: the move towards it (E = 3)
+        assert mu[s] == 3, (s, mu[s])
+    v = C.exact_policy_values(p, p.reward_prob(), mu)
+    assert v[p.init] == pytest.approx(1.0, abs=1e-12)
+
+
 # ---------------------------------------------------------------- DFA and product
 
 
