@@ -297,18 +297,18 @@ def run_engine(args):
 
     peak, peak_kind = _peaks()
     achieved = dev["bytes_fp32"] / (dev["ms_fp32"] / 1e3) / 1e9 if dev["ms_fp32"] > 0 else None
-    roofline = {"bound": "hbm", "kernel": "k_sweep<float,16> (FP32 Bellman sweep, graph-launched loop)",
+    roofline = {"bound": "hbm", "kernel": "k_sweep<ArithF32,16> (FP32 round-down Bellman sweep, graph-launched loop)",
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
                 "bytes_per_sweep": dev["bytes_fp32"] / max(dev["sweeps32"], 1),
                 "ms_per_sweep": dev["ms_fp32"] / max(dev["sweeps32"], 1),
-                "other_phases_GBps": {"fp64_sweeps": dev["bytes_fp64"] / max(dev["ms_fp64"], 1e-9) / 1e6,
+                "other_phases_GBps": {"df64_sweeps": dev["bytes_fp64"] / max(dev["ms_fp64"], 1e-9) / 1e6,
                                       "evaluation": dev["bytes_eval"] / max(dev["ms_eval"], 1e-9) / 1e6}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
+        "dtype": "f32+df64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "products": nI * nJ, "K": len(W), "states": fp["n_states"],
                    "transitions": fp["n_trans"], "eps_vi": cfg.eps_vi, "eps_eval": cfg.eps_eval,
                    "l2": "per-step working set (CSR + FP32/FP64 value buffers) exceeds the 129 MB L2; no flush",

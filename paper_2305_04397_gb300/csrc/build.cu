@@ -17,6 +17,12 @@ namespace morap {
 
 namespace {
 
+// a double as an unevaluated sum hi + lo of two floats
+__device__ __forceinline__ float2 to_df(double d) {
+    const float h = __double2float_rn(d);
+    return make_float2(h, __double2float_rn(d - (double)h));
+}
+
 // letter of task j on every agent state s: bit b set iff ap_ids[b] in L(s)
 __global__ void k_letters(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                           const int32_t *label_ptr, const int32_t *label_ap, const int32_t *ap_ids,
@@ -41,8 +47,9 @@ __global__ void k_letters(const ProdDesc *prods, int P, const AgentDesc *agents,
 __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                         const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ,
                         const double *a_prob, const double *a_cost, const uint8_t *letters, const int16_t *nd_delta,
-                        uint32_t *state_sa, uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float *cost32,
-                        double *cost64, uint32_t total_states, uint32_t total_sa, uint32_t total_tr) {
+                        uint32_t *state_sa, uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf,
+                        float *cost32, double *cost64, float2 *costdf, uint32_t total_states, uint32_t total_sa,
+                        uint32_t total_tr) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     if (blockIdx.y == 0 && tid == 0) {
         state_sa[total_states] = total_sa;
@@ -72,6 +79,7 @@ __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, c
             const double c = a_cost[ad.cost_off + a];
             cost64[pd.sa_off + v] = c;
             cost32[pd.sa_off + v] = __double2float_ru(c);
+            costdf[pd.sa_off + v] = to_df(c);
         }
         // transitions
         const uint32_t n_tr = (uint32_t)td.Qn * T;
@@ -85,6 +93,7 @@ __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, c
             const double pr = a_prob[ad.tr_off + e];
             col[pd.tr_off + t] = cg;
             p64[pd.tr_off + t] = pr;
+            pdf[pd.tr_off + t] = to_df(pr);
             cp32[pd.tr_off + t] = make_int2(cg, __float_as_int(__double2float_rd(pr)));
         }
     }
@@ -104,13 +113,14 @@ int launch_letters(const ProdDesc *prods, int P, const AgentDesc *agents, const 
 int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                  const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ, const double *a_prob,
                  const double *a_cost, const uint8_t *letters, const int16_t *nd_delta, uint32_t *state_sa,
-                 uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float *cost32, double *cost64,
-                 uint32_t total_states, uint32_t total_sa, uint32_t total_tr, uint32_t max_work, void *s) {
+                 uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf, float *cost32, double *cost64,
+                 float2 *costdf, uint32_t total_states, uint32_t total_sa, uint32_t total_tr, uint32_t max_work,
+                 void *s) {
     dim3 grid((max_work + 255) / 256 < 64 ? (max_work + 255) / 256 : 64, P < 65535 ? P : 65535);
     if (grid.x == 0) grid.x = 1;
     k_build<<<grid, 256, 0, (cudaStream_t)s>>>(prods, P, agents, tasks, a_state_ptr, a_sa_ptr, a_succ, a_prob, a_cost,
-                                                letters, nd_delta, state_sa, sa_tr, col, cp32, p64, cost32, cost64,
-                                                total_states, total_sa, total_tr);
+                                                letters, nd_delta, state_sa, sa_tr, col, cp32, p64, pdf, cost32,
+                                                cost64, costdf, total_states, total_sa, total_tr);
     return (int)cudaGetLastError();
 }
 

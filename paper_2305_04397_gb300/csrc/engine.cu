@@ -92,6 +92,7 @@ struct morap_ctx {
     uint32_t *state_sa = nullptr, *sa_tr = nullptr;
     int32_t *col = nullptr;
     int2 *cp32 = nullptr;
+    float2 *pdf = nullptr, *costdf = nullptr;
     float *cost32 = nullptr;
     double *p64 = nullptr, *cost64 = nullptr;
     std::vector<void *> build_allocs;
@@ -114,6 +115,7 @@ struct morap_ctx {
     uint8_t *a_rec = nullptr, *policy = nullptr, *frozen = nullptr;
     float2 *w32 = nullptr;
     double2 *w64 = nullptr;
+    float4 *wdf = nullptr;
     double *thr32 = nullptr, *thr64 = nullptr, *d_W = nullptr, *d_c = nullptr;
     int32_t *d_status = nullptr, *sweeps_pair = nullptr;
     unsigned long long *res[3] = {};
@@ -302,6 +304,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
     CKR(dev_alloc(c, L, &c->frozen, np));
     CKR(dev_alloc(c, L, &c->w32, np * sizeof(float2)));
     CKR(dev_alloc(c, L, &c->w64, np * sizeof(double2)));
+    CKR(dev_alloc(c, L, &c->wdf, np * sizeof(float4)));
     CKR(dev_alloc(c, L, &c->thr32, np * sizeof(double)));
     CKR(dev_alloc(c, L, &c->thr64, np * sizeof(double)));
     CKR(dev_alloc(c, L, &c->d_W, (size_t)Kp * (c->nI + c->nJ) * sizeof(double)));
@@ -320,6 +323,9 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a.sa_tr = c->sa_tr;
     a.col = c->col;
     a.cp32 = c->cp32;
+    a.pdf = c->pdf;
+    a.costdf = c->costdf;
+    a.wdf = c->wdf;
     a.p64 = c->p64;
     a.cost32 = c->cost32;
     a.cost64 = c->cost64;
@@ -452,8 +458,8 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     CKR(stage(c, std::max(nW * sizeof(double), np * (sizeof(double) + sizeof(int32_t)) + 3 * sizeof(LoopCtl))));
     std::memcpy(c->h_stage, W, nW * sizeof(double));
     CK(cudaMemcpyAsync(c->d_W, c->h_stage, nW * sizeof(double), cudaMemcpyHostToDevice, s));
-    CKL(launch_setup_weights(c->d_prods, c->P, c->nI, c->nJ, K, Kp, c->d_W, c->w32, c->w64, c->thr32, c->thr64,
-                             c->cfg.eps_vi, s));
+    CKL(launch_setup_weights(c->d_prods, c->P, c->nI, c->nJ, K, Kp, c->d_W, c->w32, c->w64, c->wdf, c->thr32,
+                             c->thr64, c->cfg.eps_vi, s));
     const size_t nv = (size_t)c->TS * Kp;
     const unsigned int cap = (unsigned int)std::max(1, c->cfg.max_sweeps);
     const unsigned int n_items = (unsigned int)c->h_chunks.size();
@@ -473,7 +479,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
             }));
         }
         CK(cudaEventRecord(c->ev[1], s));
-        CKL(launch_convert((const float *)c->V32[0], (double *)c->V64[0], (double *)c->V64[1], nv, s));
+        CKL(launch_convert((const float *)c->V32[0], (float2 *)c->V64[0], (float2 *)c->V64[1], nv, s));
         launches += 2;
     } else {
         CK(cudaMemsetAsync(c->V64[0], 0, nv * sizeof(double), s));
@@ -490,7 +496,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     }
     CK(cudaEventRecord(c->ev[2], s));
     CKL(launch_finalize(Kp, c->args64, (int)n_items, c->cfg.tau_policy, c->policy, s));
-    CKL(launch_gather_c(Kp, c->d_prods, c->P, (const double *)c->V64[0], c->frozen, c->d_c, c->d_status, s));
+    CKL(launch_gather_c(Kp, c->d_prods, c->P, (const float2 *)c->V64[0], c->frozen, c->d_c, c->d_status, s));
     CK(cudaEventRecord(c->ev[3], s));
     launches += 3;
     double *hc = c->h_stage;
@@ -720,8 +726,8 @@ int validate_agent(int32_t n, int32_t s0, const int32_t *state_ptr, const int32_
 int run_construction(morap_ctx *c, cudaStream_t s) {
     CKL(launch_letters(c->d_prods, c->P, c->d_ad, c->d_td, c->d_lp, c->d_la, c->d_ap, c->d_letters, c->max_S, s));
     CKL(launch_build(c->d_prods, c->P, c->d_ad, c->d_td, c->d_sp, c->d_sap, c->d_succ, c->d_prob, c->d_cost,
-                     c->d_letters, c->d_nd, c->state_sa, c->sa_tr, c->col, c->cp32, c->p64, c->cost32, c->cost64,
-                     c->TS, c->TSA, c->TT, c->max_work, s));
+                     c->d_letters, c->d_nd, c->state_sa, c->sa_tr, c->col, c->cp32, c->p64, c->pdf, c->cost32,
+                     c->cost64, c->costdf, c->TS, c->TSA, c->TT, c->max_work, s));
     return MORAP_OK;
 }
 
@@ -830,12 +836,15 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         c->max_S = max_S;
         c->max_work = (uint32_t)std::min<uint64_t>(max_work, 0xffffffffull);
         c->all_free_action = all_free;
-        c->csr_bytes = (int64_t)(4 * (TS + 1) + 4 * (TSA + 1) + 4 * TT + 8 * TT + 8 * TT + 4 * TSA + 8 * TSA);
+        c->csr_bytes =
+            (int64_t)(4 * (TS + 1) + 4 * (TSA + 1) + 4 * TT + 8 * TT + 8 * TT + 8 * TT + 4 * TSA + 8 * TSA + 8 * TSA);
         auto &L = c->build_allocs;
         CKR(dev_alloc(c, L, &c->state_sa, (TS + 1) * 4));
         CKR(dev_alloc(c, L, &c->sa_tr, (TSA + 1) * 4));
         CKR(dev_alloc(c, L, &c->col, std::max<uint64_t>(TT, 1) * 4));
         CKR(dev_alloc(c, L, &c->cp32, std::max<uint64_t>(TT, 1) * 8));
+        CKR(dev_alloc(c, L, &c->pdf, std::max<uint64_t>(TT, 1) * 8));
+        CKR(dev_alloc(c, L, &c->costdf, std::max<uint64_t>(TSA, 1) * 8));
         CKR(dev_alloc(c, L, &c->p64, std::max<uint64_t>(TT, 1) * 8));
         CKR(dev_alloc(c, L, &c->cost32, std::max<uint64_t>(TSA, 1) * 4));
         CKR(dev_alloc(c, L, &c->cost64, std::max<uint64_t>(TSA, 1) * 8));
@@ -1398,10 +1407,10 @@ int morap_last_policy(morap_ctx *ctx, int32_t k, int32_t p, uint8_t *mu_out, dou
         for (size_t u = 0; u < n; ++u) mu_out[u] = buf[u * Kp + k];
     }
     if (values_out) {
-        std::vector<double> buf(n * Kp);
-        CK(cudaMemcpy(buf.data(), (double *)ctx->V64[0] + (size_t)pd.state_off * Kp, n * Kp * 8,
+        std::vector<float2> buf(n * Kp);
+        CK(cudaMemcpy(buf.data(), (float2 *)ctx->V64[0] + (size_t)pd.state_off * Kp, n * Kp * 8,
                       cudaMemcpyDeviceToHost));
-        for (size_t u = 0; u < n; ++u) values_out[u] = buf[u * Kp + k];
+        for (size_t u = 0; u < n; ++u) values_out[u] = (double)buf[u * Kp + k].x + (double)buf[u * Kp + k].y;
     }
     return MORAP_OK;
     API_END

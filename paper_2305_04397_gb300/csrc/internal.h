@@ -103,7 +103,7 @@ struct LoopCtl {
     unsigned long long bytes;
 };
 
-constexpr int kChunk = 512;      // states per work item of the optimisation sweeps
+constexpr int kChunk = 128;      // states per (warp) work item of the optimisation sweeps
 constexpr int kEvalChunk = 256;  // states per work item of the evaluation sweeps
 constexpr int kThreads = 256;
 constexpr int kGatherBatch = 4;  // independent successor gathers a thread issues back to back
@@ -118,8 +118,11 @@ struct SweepArgs {
     const double *cost64;
     const int4 *chunks;   // {product, begin, end, first}
     const ProdDesc *prods;
+    const float2 *pdf;    // per transition: p as a double-float (hi, lo)
+    const float2 *costdf; // per state-action: cost as a double-float
     const float2 *w32;    // per pair (p*Kp + k): (w_i rounded up, w_p rounded down)
     const double2 *w64;   // per pair: (w_i, w_p)
+    const float4 *wdf;    // per pair: (w_i.hi, w_i.lo, w_p.hi, w_p.lo)
     const double *thr;    // per pair freeze threshold of this phase
     unsigned long long *res[3];  // per pair residual of sweep n % 3 (double bits)
     int32_t *sweeps_pair;
@@ -161,11 +164,12 @@ int launch_letters(const ProdDesc *prods, int P, const AgentDesc *agents, const 
 int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                  const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ, const double *a_prob,
                  const double *a_cost, const uint8_t *letters, const int16_t *nd_delta, uint32_t *state_sa,
-                 uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float *cost32, double *cost64,
-                 uint32_t total_states, uint32_t total_sa, uint32_t total_tr, uint32_t max_work, void *s);
+                 uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf, float *cost32, double *cost64,
+                 float2 *costdf, uint32_t total_states, uint32_t total_sa, uint32_t total_tr, uint32_t max_work,
+                 void *s);
 
 int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W,
-                         float2 *w32, double2 *w64, double *thr32, double *thr64, double eps1, void *s);
+                         float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1, void *s);
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
                      size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s);
 int launch_sweep(bool fp64, int Kp, const SweepArgs &a, int pos, int grid, void *s);
@@ -173,9 +177,9 @@ int sweep_blocks_per_sm(bool fp64, int Kp);
 int eval_blocks_per_sm();
 int launch_loop_control(LoopCtl *ctl, unsigned long long handle, int next_idx, void *s);
 int launch_loop_control_host(LoopCtl *ctl, int next_idx, void *s);
-int launch_convert(const float *v32, double *v64a, double *v64b, size_t n, void *s);
+int launch_convert(const float *v32, float2 *vda, float2 *vdb, size_t n, void *s);
 int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, void *s);
-int launch_gather_c(int Kp, const ProdDesc *prods, int P, const double *V64, const uint8_t *frozen, double *c_out,
+int launch_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V64, const uint8_t *frozen, double *c_out,
                     int32_t *status_out, void *s);
 int launch_eval_sweep(const EvalArgs &a, int pos, int grid, void *s);
 int launch_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const double2 *E, double *rc,

@@ -36,52 +36,178 @@ namespace morap {
 
 namespace {
 
-template <typename T>
-struct Arith;
+// ------------------------------------------------------------ arithmetic
+//
+// Two value formats run the same sweep code:
+//  * FP32 with every rounding toward -inf (phase 1).  With V >= 0, the
+//    probabilities rounded down and the rewards rounded down, each computed
+//    Q is <= the exact Q of the same iterate, so every iterate is a lower
+//    bound of the exact one and of the fixed point reached from 0.
+//  * double-float (phase 2): a value is an unevaluated sum hi + lo of two
+//    FP32 numbers (about 48 significant bits).  Sums use Knuth's two-sum,
+//    products Dekker's two-product through an FMA; GB300's FP64 units run at
+//    a small fraction of the FP32 rate, so this is the fast way to carry the
+//    precision the stopping rule eps1 = 1e-8 needs.
 
-// FP32 with every rounding toward -inf: with V >= 0, p rounded down and the
-// reward rounded down, each computed Q is <= the exact Q of the same iterate,
-// so every FP32 iterate is a lower bound of the exact one (and of the fixed
-// point reached from 0).
-template <>
-struct Arith<float> {
-    using W = float2;
-    static __device__ __forceinline__ float reward(float2 w, float cost, bool pre) {
-        return __fsub_rd(pre ? w.y : 0.0f, __fmul_ru(w.x, cost));
-    }
-    static __device__ __forceinline__ float mac(float p, float v, float acc) { return __fmaf_rd(p, v, acc); }
-    // Algorithm 3 records the maximiser when the value moves by more than
-    // eps1.  In FP32 a move of a few ulps is rounding, not propagation, so the
-    // FP32 phase records only moves above 64 ulps of the new value (the FP64
-    // phase that follows records with eps1 itself).
-    static __device__ __forceinline__ double record_threshold(float y, double eps1) {
-        const double rel = (double)y * 7.62939453125e-06; /* 2^-17 */
-        return rel > eps1 ? rel : eps1;
-    }
-    static __device__ __forceinline__ float cost(const SweepArgs &a, uint32_t sa) { return __ldg(a.cost32 + sa); }
-    static __device__ __forceinline__ void edge(const SweepArgs &a, uint32_t t, int32_t &c, float &p) {
+struct DF {
+    float h, l;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    const float e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fadd_rn(b, -__fadd_rn(s, -a))};
+}
+
+__device__ __forceinline__ DF df_norm(DF x) { return fast_two_sum(x.h, x.l); }
+
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    DF s = two_sum(x.h, y.h);
+    s.l = __fadd_rn(s.l, __fadd_rn(x.l, y.l));
+    return fast_two_sum(s.h, s.l);
+}
+
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ bool df_gt(DF a, DF b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+
+struct ArithF32 {
+    using Val = float;
+    using W = float2;    // (w_i rounded up, w_p rounded down)
+    using Cost = float;  // rounded up
+    using Prob = float;  // rounded down
+    static constexpr int WORDS = 1;
+    static __device__ __forceinline__ W weight(const SweepArgs &a, size_t pair) { return a.w32[pair]; }
+    static __device__ __forceinline__ Cost cost(const SweepArgs &a, uint32_t sa) { return __ldg(a.cost32 + sa); }
+    static __device__ __forceinline__ void edge(const SweepArgs &a, uint32_t t, int32_t &c, Prob &p) {
         const int2 e = __ldg(a.cp32 + t);
         c = e.x;
         p = __int_as_float(e.y);
     }
-    static __device__ __forceinline__ float2 weight(const SweepArgs &a, size_t pair) { return a.w32[pair]; }
+    static __device__ __forceinline__ Val reward(W w, Cost c, bool pre) {
+        return __fsub_rd(pre ? w.y : 0.0f, __fmul_ru(w.x, c));
+    }
+    static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) { acc = __fmaf_rd(p, v, acc); }
+    static __device__ __forceinline__ void close(Val &) {}
+    static __device__ __forceinline__ bool gt(Val a, Val b) { return a > b; }
+    static __device__ __forceinline__ Val neg_inf() { return -CUDART_INF_F; }
+    static __device__ __forceinline__ Val zero() { return 0.0f; }
+    static __device__ __forceinline__ float diff(Val y, Val x) { return fabsf(y - x); }
+    static __device__ __forceinline__ Val from_words(const float *w) { return w[0]; }
+    static __device__ __forceinline__ void to_words(Val v, float *w) { w[0] = v; }
+    // Algorithm 3 records the maximiser when the value moves by more than
+    // eps1.  In FP32 a move of a few ulps is rounding, not propagation, so
+    // this phase records only moves above 64 ulps of the new value (the
+    // double-float phase that follows records with eps1 itself).
+    static __device__ __forceinline__ float record_threshold(Val y, double eps1) {
+        const float rel = y * 7.62939453125e-06f; /* 2^-17 */
+        return rel > (float)eps1 ? rel : (float)eps1;
+    }
 };
 
-template <>
-struct Arith<double> {
-    using W = double2;
-    static __device__ __forceinline__ double reward(double2 w, double cost, bool pre) {
-        return (pre ? w.y : 0.0) - w.x * cost;
+struct ArithDF {
+    using Val = DF;
+    using W = float4;    // (w_i.h, w_i.l, w_p.h, w_p.l)
+    using Cost = DF;
+    using Prob = DF;
+    static constexpr int WORDS = 2;
+    static __device__ __forceinline__ W weight(const SweepArgs &a, size_t pair) { return a.wdf[pair]; }
+    static __device__ __forceinline__ Cost cost(const SweepArgs &a, uint32_t sa) {
+        const float2 c = __ldg(a.costdf + sa);
+        return {c.x, c.y};
     }
-    static __device__ __forceinline__ double mac(double p, double v, double acc) { return fma(p, v, acc); }
-    static __device__ __forceinline__ double record_threshold(double, double eps1) { return eps1; }
-    static __device__ __forceinline__ double cost(const SweepArgs &a, uint32_t sa) { return __ldg(a.cost64 + sa); }
-    static __device__ __forceinline__ void edge(const SweepArgs &a, uint32_t t, int32_t &c, double &p) {
+    static __device__ __forceinline__ void edge(const SweepArgs &a, uint32_t t, int32_t &c, Prob &p) {
         c = __ldg(a.col + t);
-        p = __ldg(a.p64 + t);
+        const float2 q = __ldg(a.pdf + t);
+        p = {q.x, q.y};
     }
-    static __device__ __forceinline__ double2 weight(const SweepArgs &a, size_t pair) { return a.w64[pair]; }
+    static __device__ __forceinline__ Val reward(W w, Cost c, bool pre) {
+        const DF m = df_mul({w.x, w.y}, c);
+        const DF base = pre ? DF{w.z, w.w} : DF{0.0f, 0.0f};
+        return df_add(base, {-m.h, -m.l});
+    }
+    // acc += p * v with the sum left unnormalised until the action closes
+    static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) {
+        const float ph = __fmul_rn(p.h, v.h);
+        float pe = __fmaf_rn(p.h, v.h, -ph);
+        pe = __fmaf_rn(p.h, v.l, pe);
+        pe = __fmaf_rn(p.l, v.h, pe);
+        const DF s = two_sum(acc.h, ph);
+        acc.h = s.h;
+        acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, pe));
+    }
+    static __device__ __forceinline__ void close(Val &v) { v = df_norm(v); }
+    static __device__ __forceinline__ bool gt(Val a, Val b) { return df_gt(a, b); }
+    static __device__ __forceinline__ Val neg_inf() { return {-CUDART_INF_F, 0.0f}; }
+    static __device__ __forceinline__ Val zero() { return {0.0f, 0.0f}; }
+    static __device__ __forceinline__ float diff(Val y, Val x) {
+        return fabsf(__fadd_rn(__fadd_rn(y.h, -x.h), __fadd_rn(y.l, -x.l)));
+    }
+    static __device__ __forceinline__ Val from_words(const float *w) { return {w[0], w[1]}; }
+    static __device__ __forceinline__ void to_words(Val v, float *w) {
+        w[0] = v.h;
+        w[1] = v.l;
+    }
+    static __device__ __forceinline__ float record_threshold(Val, double eps1) { return (float)eps1; }
 };
+
+// Load / store NW consecutive 32-bit words with the widest aligned accesses.
+template <int NW>
+__device__ __forceinline__ void load_words(const float *p, float (&w)[NW]) {
+    if constexpr (NW >= 4) {
+#pragma unroll
+        for (int i = 0; i < NW / 4; ++i) {
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(p) + i);
+            w[4 * i] = q.x, w[4 * i + 1] = q.y, w[4 * i + 2] = q.z, w[4 * i + 3] = q.w;
+        }
+    } else if constexpr (NW == 2) {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+        w[0] = q.x, w[1] = q.y;
+    } else {
+        w[0] = __ldg(p);
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void store_words(float *p, const float (&w)[NW]) {
+    if constexpr (NW >= 4) {
+#pragma unroll
+        for (int i = 0; i < NW / 4; ++i)
+            reinterpret_cast<float4 *>(p)[i] = make_float4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    } else if constexpr (NW == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(w[0], w[1]);
+    } else {
+        p[0] = w[0];
+    }
+}
+
+// Lanes per state and weights per lane for each (format, Kp).
+template <class Ar, int KP>
+struct Shape {
+    static constexpr int VMAX = Ar::WORDS == 1 ? 8 : 4;  // weights per lane
+    static constexpr int VEC = KP < VMAX ? KP : VMAX;
+    static constexpr int LPS = KP / VEC;                  // lanes per state (<= 32)
+    static constexpr int SPW = 32 / LPS;                  // states per warp round
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double as_double(unsigned long long b) { return __longlong_as_double((long long)b); }
 
 template <typename T, int VEC>
 struct Vec {
@@ -92,274 +218,205 @@ template <typename T, int VEC>
 __device__ __forceinline__ Vec<T, VEC> vload(const T *p) {
     Vec<T, VEC> r;
     if constexpr (sizeof(T) * VEC == 16) {
-        if constexpr (sizeof(T) == 4) {
-            const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
-            r.v[0] = q.x, r.v[1] = q.y, r.v[2] = q.z, r.v[3] = q.w;
-        } else {
-            const double2 q = __ldg(reinterpret_cast<const double2 *>(p));
-            r.v[0] = q.x, r.v[1] = q.y;
-        }
-    } else if constexpr (sizeof(T) * VEC == 8) {
-        if constexpr (sizeof(T) == 4) {
-            const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
-            r.v[0] = q.x, r.v[1] = q.y;
-        } else {
-            r.v[0] = __ldg(p);
-        }
+        const double2 q = __ldg(reinterpret_cast<const double2 *>(p));
+        r.v[0] = q.x, r.v[1] = q.y;
     } else {
         r.v[0] = __ldg(p);
     }
     return r;
 }
 
-template <typename T, int VEC>
-__device__ __forceinline__ void vstore(T *p, const Vec<T, VEC> &x) {
-    if constexpr (sizeof(T) * VEC == 16) {
-        if constexpr (sizeof(T) == 4)
-            *reinterpret_cast<float4 *>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
-        else
-            *reinterpret_cast<double2 *>(p) = make_double2(x.v[0], x.v[1]);
-    } else if constexpr (sizeof(T) * VEC == 8) {
-        if constexpr (sizeof(T) == 4)
-            *reinterpret_cast<float2 *>(p) = make_float2(x.v[0], x.v[1]);
-        else
-            p[0] = x.v[0];
-    } else {
-        p[0] = x.v[0];
-    }
-}
-
-template <typename T, int KP>
-struct Layout {
-    static constexpr int VEC = (16 / sizeof(T)) < KP ? (16 / (int)sizeof(T)) : KP;
-    static constexpr int LPS = KP / VEC;               // lanes per state
-    static constexpr int SPR = kThreads / LPS;         // states per block round
-    static constexpr int WARPS = kThreads / 32;
-};
-
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
-    // non-negative doubles order like their bit patterns
-    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
-}
-
-__device__ __forceinline__ double as_double(unsigned long long b) { return __longlong_as_double((long long)b); }
-
 // ------------------------------------------------------------- the sweep
-template <typename T, int KP>
+//
+// Work items are 128-state ranges of one product taken by whole warps
+// (dynamic scheduling, no block barriers).  Inside a warp, LPS lanes share a
+// state and each lane owns VEC of the Kp weights, so a successor's value row
+// is read once, coalesced, for all weights.  Each lane consumes its state's
+// transitions as one stream across the actions, issuing kGatherBatch
+// independent gathers before it consumes them.
+template <class Ar, int KP>
 __global__ void __launch_bounds__(kThreads, 3) k_sweep(SweepArgs a, int pos) {
-    using L = Layout<T, KP>;
-    using Ar = Arith<T>;
-    constexpr int VEC = L::VEC, LPS = L::LPS, SPR = L::SPR;
-    constexpr int D = kGatherBatch;
+    using Val = typename Ar::Val;
+    using SH = Shape<Ar, KP>;
+    constexpr int VEC = SH::VEC, LPS = SH::LPS, SPW = SH::SPW;
+    constexpr int NW = VEC * Ar::WORDS;      // 32-bit words a lane moves per state row
+    constexpr int D = NW >= 8 ? kGatherBatch / 2 : kGatherBatch;  // keep the batch within registers
+    constexpr int ROW = KP * Ar::WORDS;      // words per state row
     const int cur = pos % 3, nxt = (pos + 1) % 3, far = (pos + 2) % 3;
-    const T *__restrict__ Vold = static_cast<const T *>(a.V[pos & 1]);
-    T *__restrict__ Vnew = static_cast<T *>(a.V[(pos + 1) & 1]);
+    const float *__restrict__ Vold = static_cast<const float *>(a.V[pos & 1]);
+    float *__restrict__ Vnew = static_cast<float *>(a.V[(pos + 1) & 1]);
     const unsigned long long *res_prev = a.res[far];
     unsigned long long *res_cur = a.res[cur];
     unsigned long long *res_next = a.res[nxt];
     LoopCtl *ctl = a.ctl;
-
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->cnt[far] = 0;
         ctl->next[far] = 0;
     }
     const unsigned int n_items = ctl->cnt[cur];
     const unsigned int sweep = ctl->sweep_base + pos;
-
-    __shared__ unsigned int s_item;
-    __shared__ int s_active[KP];
-    __shared__ int s_any_active, s_any_nonzero;
-    __shared__ double s_red[L::WARPS][KP];
-
-    const int lane_in_state = threadIdx.x % LPS;
-    const int slot = threadIdx.x / LPS;
-    const int k0 = lane_in_state * VEC;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / LPS, li = lane % LPS, k0 = li * VEC;
 
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_item = atomicAdd(&ctl->next[cur], 1u);
-            s_any_active = 0;
-            s_any_nonzero = 0;
-        }
-        __syncthreads();
-        const unsigned int it = s_item;
+        unsigned int it = 0;
+        if (lane == 0) it = atomicAdd(&ctl->next[cur], 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
         const unsigned int item = a.list[cur][it];
         const int4 ch = a.chunks[item];
         const int p = ch.x;
         const size_t pair0 = (size_t)p * KP;
-        if (threadIdx.x < KP) {
-            const double prev = as_double(res_prev[pair0 + threadIdx.x]);
-            const int act = prev > a.thr[pair0 + threadIdx.x];
-            s_active[threadIdx.x] = act;
-            if (act) atomicOr(&s_any_active, 1);
-            if (prev > 0.0) atomicOr(&s_any_nonzero, 1);
+        // activity of the product's weights from the previous sweep's residuals
+        unsigned int act_w[2] = {0u, 0u}, nz_w[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < (KP + 31) / 32; ++h) {
+            const int k = lane + 32 * h;
+            bool act = false, nz = false;
+            if (k < KP) {
+                const double prev = as_double(res_prev[pair0 + k]);
+                act = prev > a.thr[pair0 + k];
+                nz = prev > 0.0;
+            }
+            act_w[h] = __ballot_sync(0xffffffffu, act);
+            nz_w[h] = __ballot_sync(0xffffffffu, nz);
         }
-        __syncthreads();
-        const bool any_active = s_any_active != 0;
-        if (s_any_nonzero == 0) {  // converged earlier and already copied: drop
-            if (ch.w && threadIdx.x < KP) a.frozen[pair0 + threadIdx.x] = 1;
-            __syncthreads();
+        const bool any_active = (act_w[0] | act_w[1]) != 0u;
+        if ((nz_w[0] | nz_w[1]) == 0u) {  // converged earlier and already copied: drop
+            if (ch.w)
+                for (int k = lane; k < KP; k += 32) a.frozen[pair0 + k] = 1;
             continue;
         }
         const ProdDesc pd = a.prods[p];
-        if (threadIdx.x == 0 && any_active) {
+        if (lane == 0 && any_active) {
             const unsigned int at = atomicAdd(&ctl->cnt[nxt], 1u);
             a.list[nxt][at] = item;
         }
-        if (ch.w && threadIdx.x < KP) {
-            res_next[pair0 + threadIdx.x] = 0ull;
-            if (s_active[threadIdx.x])
-                a.sweeps_pair[pair0 + threadIdx.x] = (int32_t)(sweep + 1);
-            else
-                a.frozen[pair0 + threadIdx.x] = 1;
-        }
+        if (ch.w)
+            for (int k = lane; k < KP; k += 32) {
+                res_next[pair0 + k] = 0ull;
+                if ((act_w[k >> 5] >> (k & 31)) & 1u)
+                    a.sweeps_pair[pair0 + k] = (int32_t)(sweep + 1);
+                else
+                    a.frozen[pair0 + k] = 1;
+            }
         bool act[VEC];
         typename Ar::W w[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-            act[v] = s_active[k0 + v] != 0;
-            w[v] = Ar::weight(a, pair0 + k0 + v);
+            const int k = k0 + v;
+            act[v] = ((act_w[k >> 5] >> (k & 31)) & 1u) != 0u;
+            w[v] = Ar::weight(a, pair0 + k);
         }
-        T rmax[VEC];
+        float rmax[VEC];
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) rmax[v] = T(0);
+        for (int v = 0; v < VEC; ++v) rmax[v] = 0.0f;
 
-        for (int s = ch.y + slot; s < ch.z; s += SPR) {
+        for (int s = ch.y + grp; s < ch.z; s += SPW) {
             const uint32_t u = pd.state_off + (uint32_t)s;
-            const size_t row = (size_t)u * KP + k0;
-            const Vec<T, VEC> x = vload<T, VEC>(Vold + row);
-            Vec<T, VEC> y = x;
-            if (any_active) {
-                const bool pre = (uint32_t)s >= pd.pre_begin;
-                const uint32_t a0 = __ldg(a.state_sa + u), a1 = __ldg(a.state_sa + u + 1);
-                const uint32_t te = __ldg(a.sa_tr + a1);
-                T best[VEC], acc[VEC];
-                uint32_t best_a[VEC];
-                uint32_t sa = a0, bound = __ldg(a.sa_tr + a0 + 1);
-                {
-                    const T c0 = Ar::cost(a, a0);
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        best[v] = -CUDART_INF;
-                        best_a[v] = 0;
-                        acc[v] = Ar::reward(w[v], c0, pre);
-                    }
-                }
-                // The state's transitions form one stream over its actions;
-                // D gathers are issued back to back before they are consumed.
-                for (uint32_t base = __ldg(a.sa_tr + a0); base < te; base += D) {
-                    int32_t cl[D];
-                    T pr[D];
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        const uint32_t t = base + i;
-                        if (t < te) {
-                            Ar::edge(a, t, cl[i], pr[i]);
-                        } else {
-                            cl[i] = -1;
-                            pr[i] = T(0);
-                        }
-                    }
-                    Vec<T, VEC> xv[D];
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        if (cl[i] >= 0) {
-                            xv[i] = vload<T, VEC>(Vold + (size_t)cl[i] * KP + k0);
-                        } else {
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) xv[i].v[v] = T(0);
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        if (cl[i] < 0) continue;
-                        while (base + i >= bound) {  // close action sa, open the next one
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v)
-                                if (acc[v] > best[v]) {
-                                    best[v] = acc[v];
-                                    best_a[v] = sa - a0;
-                                }
-                            ++sa;
-                            bound = __ldg(a.sa_tr + sa + 1);
-                            const T cs = Ar::cost(a, sa);
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(w[v], cs, pre);
-                        }
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[v] = Ar::mac(pr[i], xv[i].v[v], acc[v]);
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < VEC; ++v)
-                    if (acc[v] > best[v]) {
-                        best[v] = acc[v];
-                        best_a[v] = sa - a0;
-                    }
-                uint32_t rec_mask = 0;
+            const size_t row = (size_t)u * ROW + (size_t)k0 * Ar::WORDS;
+            float yw[NW];
+            if (!any_active) {  // every weight of the product froze: copy the row
+                load_words<NW>(Vold + row, yw);
+                store_words<NW>(Vnew + row, yw);
+                continue;
+            }
+            const bool pre = (uint32_t)s >= pd.pre_begin;
+            const uint32_t a0 = __ldg(a.state_sa + u), a1 = __ldg(a.state_sa + u + 1);
+            const uint32_t te = __ldg(a.sa_tr + a1);
+            Val best[VEC], acc[VEC];
+            uint32_t best_a[(VEC + 3) / 4];  // recorded-action candidates, 8 bits per weight
+            uint32_t sa = a0, bound = __ldg(a.sa_tr + a0 + 1);
+            {
+                const typename Ar::Cost c0 = Ar::cost(a, a0);
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
-                    if (!act[v]) continue;
-                    y.v[v] = best[v];
-                    const T d = fabs(best[v] - x.v[v]);
-                    rmax[v] = d > rmax[v] ? d : rmax[v];
-                    if ((double)d > Ar::record_threshold(best[v], a.eps1)) rec_mask |= 1u << v;
+                    best[v] = Ar::neg_inf();
+                    acc[v] = Ar::reward(w[v], c0, pre);
                 }
-                if (rec_mask) {
-                    if constexpr (VEC == 4) {
-                        if (rec_mask == 0xFu) {
-                            *reinterpret_cast<uint32_t *>(a.a_rec + row) =
-                                best_a[0] | (best_a[1] << 8) | (best_a[2] << 16) | (best_a[3] << 24);
-                        } else {
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v)
-                                if (rec_mask & (1u << v)) a.a_rec[row + v] = (uint8_t)best_a[v];
-                        }
+                for (int i = 0; i < (VEC + 3) / 4; ++i) best_a[i] = 0u;
+            }
+            for (uint32_t base = __ldg(a.sa_tr + a0); base < te; base += D) {
+                int32_t cl[D];
+                typename Ar::Prob pr[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    if (base + i < te) {
+                        Ar::edge(a, base + i, cl[i], pr[i]);
                     } else {
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v)
-                            if (rec_mask & (1u << v)) a.a_rec[row + v] = (uint8_t)best_a[v];
+                        cl[i] = -1;
                     }
                 }
+                float gw[D][NW];
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    if (cl[i] >= 0) load_words<NW>(Vold + (size_t)cl[i] * ROW + (size_t)k0 * Ar::WORDS, gw[i]);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    if (cl[i] < 0) continue;
+                    while (base + i >= bound) {  // close action sa, open the next one
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            Ar::close(acc[v]);
+                            if (Ar::gt(acc[v], best[v])) {
+                                best[v] = acc[v];
+                                best_a[v / 4] = (best_a[v / 4] & ~(0xFFu << (8 * (v % 4)))) | ((sa - a0) << (8 * (v % 4)));
+                            }
+                        }
+                        ++sa;
+                        bound = __ldg(a.sa_tr + sa + 1);
+                        const typename Ar::Cost cs = Ar::cost(a, sa);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(w[v], cs, pre);
+                    }
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], pr[i], Ar::from_words(&gw[i][v * Ar::WORDS]));
+                }
             }
-            vstore<T, VEC>(Vnew + row, y);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                Ar::close(acc[v]);
+                if (Ar::gt(acc[v], best[v])) {
+                    best[v] = acc[v];
+                    best_a[v / 4] = (best_a[v / 4] & ~(0xFFu << (8 * (v % 4)))) | ((sa - a0) << (8 * (v % 4)));
+                }
+            }
+            load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                if (!act[v]) continue;
+                const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
+                rmax[v] = d > rmax[v] ? d : rmax[v];
+                if (d > Ar::record_threshold(best[v], a.eps1))
+                    a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)(best_a[v / 4] >> (8 * (v % 4)));
+                Ar::to_words(best[v], &yw[v * Ar::WORDS]);
+            }
+            store_words<NW>(Vnew + row, yw);
         }
-        // residual reduction: lanes with the same lane_in_state share weights
+        // residual: lanes with the same li share weights
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-            T r = rmax[v];
+            float r = rmax[v];
 #pragma unroll
-            for (int off = LPS; off < 32; off <<= 1) {
-                const T o = __shfl_xor_sync(0xffffffffu, r, off);
-                r = o > r ? o : r;
-            }
-            if (lane < LPS) s_red[warp][lane * VEC + v] = (double)r;
+            for (int off = LPS; off < 32; off <<= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
+            if (grp == 0 && any_active && r > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)r);
         }
-        __syncthreads();
-        if (any_active && threadIdx.x < KP) {
-            double r = 0.0;
-#pragma unroll
-            for (int wi = 0; wi < L::WARPS; ++wi) r = s_red[wi][threadIdx.x] > r ? s_red[wi][threadIdx.x] : r;
-            if (r > 0.0) atomic_max_nonneg(res_cur + pair0 + threadIdx.x, r);
-        }
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             const uint32_t n_s = (uint32_t)(ch.z - ch.y);
             const uint32_t u0 = pd.state_off + ch.y, u1 = pd.state_off + ch.z;
-            unsigned long long bytes = 2ull * n_s * KP * sizeof(T);
+            unsigned long long bytes = 2ull * n_s * ROW * 4;
             if (any_active) {
                 const uint32_t sa0 = a.state_sa[u0], sa1 = a.state_sa[u1];
                 const uint32_t tr0 = a.sa_tr[sa0], tr1 = a.sa_tr[sa1];
-                int n_act = 0;
-                for (int k = 0; k < KP; ++k) n_act += s_active[k];
+                const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
                 atomicAdd(&ctl->updates, (unsigned long long)(tr1 - tr0) * (unsigned long long)n_act);
-                bytes += 4ull * (n_s + 1) + 4ull * (sa1 - sa0 + 1) + (unsigned long long)(sa1 - sa0) * sizeof(T) +
-                         (unsigned long long)(tr1 - tr0) * (4 + sizeof(T));  // col + p per transition
+                // state_sa, sa_tr, cost and (col, p) per transition, 4 bytes per word
+                bytes += 4ull * (n_s + 1) + 4ull * (sa1 - sa0 + 1) + 4ull * Ar::WORDS * (sa1 - sa0) +
+                         4ull * (1 + Ar::WORDS) * (tr1 - tr0);
             }
             atomicAdd(&ctl->bytes, bytes);
         }
-        __syncthreads();
     }
 }
 
@@ -371,10 +428,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(SweepArgs a, int pos) {
 // such action is a self-loop the lowest-index one.
 template <int KP>
 __global__ void __launch_bounds__(kThreads) k_finalize(SweepArgs a, int n_chunks, double tau, uint8_t *policy) {
-    using L = Layout<double, KP>;
-    constexpr int VEC = L::VEC, LPS = L::LPS, SPR = L::SPR;
+    constexpr int VEC = KP < 2 ? KP : 2, LPS = KP / VEC, SPR = kThreads / LPS;
     constexpr int MAXA = 32;  // actions scanned twice per state: first for the max, then for the choice
-    const double *__restrict__ V = static_cast<const double *>(a.V[0]);
+    const float2 *__restrict__ V = static_cast<const float2 *>(a.V[0]);  // double-float values
     const int k0 = (threadIdx.x % LPS) * VEC, slot = threadIdx.x / LPS;
     for (int item = blockIdx.x; item < n_chunks; item += gridDim.x) {
         const int4 ch = a.chunks[item];
@@ -409,9 +465,11 @@ __global__ void __launch_bounds__(kThreads) k_finalize(SweepArgs a, int n_chunks
                     for (uint32_t t = t0; t < t1; ++t) {
                         const int32_t cl = a.col[t];
                         const double pr = a.p64[t];
-                        const Vec<double, VEC> xv = vload<double, VEC>(V + (size_t)cl * KP + k0);
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[v] = fma(pr, xv.v[v], acc[v]);
+                        for (int v = 0; v < VEC; ++v) {
+                            const float2 xv = V[(size_t)cl * KP + k0 + v];
+                            acc[v] = fma(pr, (double)xv.x + (double)xv.y, acc[v]);
+                        }
                     }
                     const uint8_t la = (uint8_t)(sa - a0);
 #pragma unroll
@@ -547,8 +605,13 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
 
 // ------------------------------------------------------------- small kernels
 
+__device__ __forceinline__ float2 to_df(double d) {
+    const float h = __double2float_rn(d);
+    return make_float2(h, __double2float_rn(d - (double)h));
+}
+
 __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W,
-                                float2 *w32, double2 *w64, double *thr32, double *thr64, double eps1) {
+                                float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1) {
     const size_t n = (size_t)P * Kp;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
         const int p = (int)(idx / Kp), k = (int)(idx % Kp);
@@ -560,6 +623,8 @@ __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, in
         }
         w64[idx] = make_double2(wi, wp);
         w32[idx] = make_float2(__double2float_ru(wi), __double2float_rd(wp));
+        const float2 a = to_df(wi), b = to_df(wp);
+        wdf[idx] = make_float4(a.x, a.y, b.x, b.y);
         // FP32 phase: stop once the residual is within a few ulps of the
         // largest possible value (values lie in [0, w_p]); FP64 phase: eps1.
         thr32[idx] = fmax(eps1, wp * 9.5367431640625e-07 /* 2^-20 */);
@@ -610,9 +675,9 @@ __global__ void k_loop_control_host(LoopCtl *ctl, int next_idx) {
     if (ctl->cnt[next_idx] > 0 && ctl->sweep_base >= ctl->cap) ctl->hit_cap = 1;
 }
 
-__global__ void k_convert(const float *v32, double *a, double *b, size_t n) {
+__global__ void k_convert(const float *v32, float2 *a, float2 *b, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double v = (double)v32[i];
+        const float2 v = make_float2(v32[i], 0.0f);
         a[i] = v;
         b[i] = v;
     }
@@ -620,13 +685,17 @@ __global__ void k_convert(const float *v32, double *a, double *b, size_t n) {
 
 // c_ij = V(s0, q0) for every (product, weight); a pair that never froze
 // stopped at the sweep cap.
-__global__ void k_gather_c(int Kp, const ProdDesc *prods, int P, const double *V, const uint8_t *frozen,
+__global__ void k_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V, const uint8_t *frozen,
                            double *c_out, int32_t *status_out) {
     const size_t n = (size_t)P * Kp;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
         const int p = (int)(idx / Kp), k = (int)(idx % Kp);
         const ProdDesc pd = prods[p];
-        const double v = (uint32_t)pd.init_local >= pd.n_nd ? 0.0 : V[(size_t)(pd.state_off + pd.init_local) * Kp + k];
+        double v = 0.0;
+        if ((uint32_t)pd.init_local < pd.n_nd) {
+            const float2 x = V[(size_t)(pd.state_off + pd.init_local) * Kp + k];
+            v = (double)x.x + (double)x.y;
+        }
         c_out[idx] = v;
         status_out[idx] = frozen[idx] ? MORAP_OK : MORAP_ENOTCONV;
     }
@@ -648,16 +717,16 @@ __global__ void k_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *pr
     }
 }
 
-template <typename T>
+template <class Ar>
 int launch_sweep_t(int Kp, const SweepArgs &a, int pos, int grid, cudaStream_t s) {
     switch (Kp) {
-    case 1: k_sweep<T, 1><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 2: k_sweep<T, 2><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 4: k_sweep<T, 4><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 8: k_sweep<T, 8><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 16: k_sweep<T, 16><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 32: k_sweep<T, 32><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 64: k_sweep<T, 64><<<grid, kThreads, 0, s>>>(a, pos); break;
+    case 1: k_sweep<Ar, 1><<<grid, kThreads, 0, s>>>(a, pos); break;
+    case 2: k_sweep<Ar, 2><<<grid, kThreads, 0, s>>>(a, pos); break;
+    case 4: k_sweep<Ar, 4><<<grid, kThreads, 0, s>>>(a, pos); break;
+    case 8: k_sweep<Ar, 8><<<grid, kThreads, 0, s>>>(a, pos); break;
+    case 16: k_sweep<Ar, 16><<<grid, kThreads, 0, s>>>(a, pos); break;
+    case 32: k_sweep<Ar, 32><<<grid, kThreads, 0, s>>>(a, pos); break;
+    case 64: k_sweep<Ar, 64><<<grid, kThreads, 0, s>>>(a, pos); break;
     default: return (int)cudaErrorInvalidValue;
     }
     return (int)cudaGetLastError();
@@ -665,18 +734,18 @@ int launch_sweep_t(int Kp, const SweepArgs &a, int pos, int grid, cudaStream_t s
 
 }  // namespace
 
-template <typename T>
+template <class Ar>
 int blocks_per_sm_t(int Kp) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (Kp) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, 1>, kThreads, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, 2>, kThreads, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, 4>, kThreads, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, 8>, kThreads, 0); break;
-    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, 16>, kThreads, 0); break;
-    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, 32>, kThreads, 0); break;
-    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, 64>, kThreads, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 1>, kThreads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 2>, kThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 4>, kThreads, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 8>, kThreads, 0); break;
+    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 16>, kThreads, 0); break;
+    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 32>, kThreads, 0); break;
+    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 64>, kThreads, 0); break;
     default: break;
     }
     if (e != cudaSuccess) {
@@ -686,7 +755,7 @@ int blocks_per_sm_t(int Kp) {
     return n > 0 ? n : 1;
 }
 
-int sweep_blocks_per_sm(bool fp64, int Kp) { return fp64 ? blocks_per_sm_t<double>(Kp) : blocks_per_sm_t<float>(Kp); }
+int sweep_blocks_per_sm(bool fp64, int Kp) { return fp64 ? blocks_per_sm_t<ArithDF>(Kp) : blocks_per_sm_t<ArithF32>(Kp); }
 
 int eval_blocks_per_sm() {
     int n = 0;
@@ -698,8 +767,8 @@ int eval_blocks_per_sm() {
 }
 
 int launch_sweep(bool fp64, int Kp, const SweepArgs &a, int pos, int grid, void *s) {
-    return fp64 ? launch_sweep_t<double>(Kp, a, pos, grid, (cudaStream_t)s)
-                : launch_sweep_t<float>(Kp, a, pos, grid, (cudaStream_t)s);
+    return fp64 ? launch_sweep_t<ArithDF>(Kp, a, pos, grid, (cudaStream_t)s)
+                : launch_sweep_t<ArithF32>(Kp, a, pos, grid, (cudaStream_t)s);
 }
 
 int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, void *sv) {
@@ -725,11 +794,11 @@ int launch_eval_sweep(const EvalArgs &a, int pos, int grid, void *s) {
 }
 
 int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W, float2 *w32,
-                         double2 *w64, double *thr32, double *thr64, double eps1, void *s) {
+                         double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1, void *s) {
     const size_t n = (size_t)P * Kp;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_setup_weights<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(prods, P, nI, nJ, K, Kp, W, w32, w64, thr32,
-                                                                     thr64, eps1);
+    k_setup_weights<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(prods, P, nI, nJ, K, Kp, W, w32, w64, wdf,
+                                                                     thr32, thr64, eps1);
     return (int)cudaGetLastError();
 }
 
@@ -752,13 +821,13 @@ int launch_loop_control_host(LoopCtl *ctl, int next_idx, void *s) {
     return (int)cudaGetLastError();
 }
 
-int launch_convert(const float *v32, double *v64a, double *v64b, size_t n, void *s) {
+int launch_convert(const float *v32, float2 *vda, float2 *vdb, size_t n, void *s) {
     const int grid = (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
-    k_convert<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(v32, v64a, v64b, n);
+    k_convert<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(v32, vda, vdb, n);
     return (int)cudaGetLastError();
 }
 
-int launch_gather_c(int Kp, const ProdDesc *prods, int P, const double *V64, const uint8_t *frozen, double *c_out,
+int launch_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V64, const uint8_t *frozen, double *c_out,
                     int32_t *status_out, void *s) {
     const size_t n = (size_t)P * Kp;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
