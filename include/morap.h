@@ -227,6 +227,43 @@ int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out);
 int morap_solve_plain(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_product, const double *pair_w,
                       void *stream, double *c_out, double *rcost_out, double *rprob_out, double *stats_out);
 
+/* Allocation-free plain value iteration for one product and one weight
+ * vector (the paper has no counterpart: this is an interface for callers).
+ * Some callers may not allocate device memory: code that records a CUDA
+ * graph (a cudaMalloc inside a stream capture breaks the capture), hosts
+ * that hand every byte of the GPU to their own memory pool and treat any
+ * outside cudaMalloc as a leak or a deadlock risk, and real-time loops that
+ * forbid allocation after start-up.  This call allocates nothing (no
+ * cudaMalloc, cudaFree, pinned host memory or allocating library routine):
+ * the caller passes the inputs and outputs, and the scratch it needs (second
+ * value buffer, state-action values, recorded actions, residual word) lives
+ * in one static device array of about 6.3 MB that every GPU which loads this
+ * library holds until the process exits.
+ *   Limits: n_states <= 131071 (plus the done slot) and n_sa <= 655360;
+ *   larger products are rejected with MORAP_EINVAL.
+ *   Inputs (device memory, the product's CSR with local indices, e.g. as
+ *   morap_product_download returns it): state_sa[n_states + 1] and
+ *   sa_tr[n_sa + 1] (uint32), col[] (int32; n_states is the absorbing done
+ *   slot), prob[] and cost[] (double); pre_begin = first state at a pre-sink
+ *   location; init_state = the state whose value is returned in *c_out.
+ *   Outputs: values[n_states + 1] (device, double; the final iterate with
+ *   values[n_states] = 0), policy[n_states] (device, int32: the returned
+ *   scheduler), *c_out and *sweeps_out (host, either may be NULL).
+ *   The computation is morap_solve_plain's: Algorithm 3 in FP64 from 0 with
+ *   a host convergence check after every sweep, then the scheduler reading.
+ * The call is synchronous on `stream`.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call on a
+ * device shares the one array and clears what must start at zero; calls
+ * that overlap on the GPU (other threads or streams) race on it.
+ * Errors: EINVAL (sizes over the limits, bad arguments), ENOTCONV (sweep cap
+ * reached; outputs hold the last iterate), ECUDA. */
+int morap_plain_vi_noalloc(int32_t n_states, int32_t n_sa, const uint32_t *state_sa, const uint32_t *sa_tr,
+                           const int32_t *col, const double *prob, const double *cost, int32_t pre_begin,
+                           int32_t init_state, double w_cost, double w_prob, double eps, double tau,
+                           int32_t max_sweeps, void *stream, double *values, int32_t *policy, double *c_out,
+                           int32_t *sweeps_out);
+
 /* ------------------------------------------------------ point queries */
 
 typedef struct morap_point_result {

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmorap.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["engine.cu", "sweep.cu", "build.cu", "plain.cu", "host_alg.cpp"]
+SOURCES = ["engine.cu", "sweep.cu", "build.cu", "plain.cu", "noalloc.cu", "host_alg.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-v"]
 

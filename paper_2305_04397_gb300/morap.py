@@ -111,6 +111,9 @@ _SIGS = {
     "morap_product_info": (ctypes.c_int, [_P, ctypes.c_int32, _I64P]),
     "morap_product_download": (ctypes.c_int, [_P, ctypes.c_int32, _I64P, _I64P, _I32P, _DP, _DP, _I32P]),
     "morap_last_policy": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _U8P, _DP]),
+    "morap_plain_vi_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_int32, _P, _P, _P, _DP, _I32P]),
 }
 
 
@@ -345,6 +348,21 @@ def morap_last_policy(ctx, k, p):
     v = np.zeros(info["n_states"])
     _check(lib().morap_last_policy(ctx, int(k), int(p), _ptr(mu, ctypes.c_uint8), _ptr(v, ctypes.c_double)))
     return mu, v
+
+
+def morap_plain_vi_noalloc(n_states, n_sa, state_sa, sa_tr, col, prob, cost, pre_begin, init_state, w_cost, w_prob,
+                           eps, tau, max_sweeps, values, policy, stream=None):
+    """All array arguments are device addresses (ints); returns (code, c, sweeps)."""
+    c = ctypes.c_double()
+    sw = ctypes.c_int32()
+    vp = lambda x: ctypes.c_void_p(int(x))
+    code = lib().morap_plain_vi_noalloc(int(n_states), int(n_sa), vp(state_sa), vp(sa_tr), vp(col), vp(prob),
+                                        vp(cost), int(pre_begin), int(init_state), float(w_cost), float(w_prob),
+                                        float(eps), float(tau), int(max_sweeps), _stream(stream), vp(values),
+                                        vp(policy), ctypes.byref(c), ctypes.byref(sw))
+    if code not in (OK, ENOTCONV):
+        _check(code)
+    return code, c.value, sw.value
 
 
 # ---------------------------------------------------------------- convenience
