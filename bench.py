@@ -204,6 +204,99 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ serving
+
+
+def serving_instances(n_inst, seed=7):
+    """Resident instances for the point-query workload: the 2x3 4x4-grid
+    instance and 2x3 / 3x4 / 4x6 agent-task subsets of 32x32-grid
+    instances, cycled (each instance a different seed or subset)."""
+    import instances as I
+
+    grids = [I.config_grid32(seed=seed + g) for g in range(2)]
+    out = []
+    for s in range(n_inst):
+        kind = s % 4
+        if kind == 0:
+            tiny = I.config_tiny(seed=s)
+            out.append((tiny.agents, tiny.tasks))
+        else:
+            nI, nJ = [(2, 3), (3, 4), (4, 6)][kind - 1]
+            g = grids[s % 2]
+            a0 = (s * 3) % (len(g.agents) - nI + 1)
+            t0 = (s * 5) % (len(g.tasks) - nJ + 1)
+            out.append((g.agents[a0:a0 + nI], g.tasks[t0:t0 + nJ]))
+    return out
+
+
+def run_serving(M, args):
+    """Point queries/s of the continuous-batching server (Algorithm 1 per
+    query) over resident instances: saturation throughput with every query
+    submitted at once, then Poisson arrivals at 80% of it for the latency
+    percentiles."""
+    import numpy as np
+
+    insts = serving_instances(args.serve_instances)
+    ctxs = []
+    for a, t in insts:
+        c = M.Context()
+        c.add(a, t)
+        c.build()
+        ctxs.append(c)
+    rng = np.random.default_rng(11)
+
+    def queries(n):
+        out = []
+        for _ in range(n):
+            i = int(rng.integers(0, len(ctxs)))
+            nI, nJ = ctxs[i].n_agents, ctxs[i].n_tasks
+            out.append((i, np.concatenate([-rng.uniform(5.0, 50.0, size=nI), rng.uniform(0.5, 0.99, size=nJ)])))
+        return out
+
+    kw = dict(max_batch=64, n_workers=4, eps=1e-6, max_iter=args.serve_max_iter)
+    srv = M.Server(ctxs, **kw)
+    for i, t in queries(len(ctxs)):  # warm every instance once
+        srv.submit(i, t)
+    srv.wait(600.0)
+    srv.close()
+    srv = M.Server(ctxs, **kw)
+    qs = queries(args.serve_queries)
+    t0 = time.perf_counter()
+    for i, t in qs:
+        srv.submit(i, t)
+    srv.wait(600.0)
+    sat_wall = time.perf_counter() - t0
+    st_sat = srv.stats()
+    srv.close()
+    sat = len(qs) / sat_wall
+    rate = 0.8 * sat
+    srv = M.Server(ctxs, **kw)
+    qs = queries(args.serve_queries)
+    gaps = rng.exponential(1.0 / rate, size=len(qs))
+    t0 = time.perf_counter()
+    due = t0
+    for (i, t), g in zip(qs, gaps):
+        due += g
+        now = time.perf_counter()
+        if due > now:
+            time.sleep(due - now)
+        srv.submit(i, t)
+    srv.wait(600.0)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    for c in ctxs:
+        c.close()
+    return {
+        "metric": "point queries/s", "value": len(qs) / wall, "unit": "queries/s",
+        "saturation_qps": sat, "offered_qps": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+        "mean_batch": st["mean_batch"], "saturation_mean_batch": st_sat["mean_batch"],
+        "queries": len(qs), "instances": len(ctxs), "max_iter": args.serve_max_iter, "eps": 1e-6,
+        "workload": "resident 4x4-grid 2x3 and 32x32-grid 2x3/3x4/4x6 instances; per query an instance "
+                    "uniformly, c_i = -U[5,50], p_j = U[0.5,0.99]; Poisson arrivals at 80% of saturation",
+    }
+
+
 # ---------------------------------------------------------------- engine arm
 
 
@@ -342,9 +435,11 @@ def run_engine(args):
         v, pairs, dt = _oracle_sample(inst, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{pairs} (product, weight) pairs, {dt:.1f} s single-thread FP64 C oracle"}
+    ctx.close()
+    if rank == 0 and not args.no_serving:
+        line["serving"] = run_serving(M, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         import torch.distributed as dist
 
@@ -366,6 +461,10 @@ def main():
     ap.add_argument("--plain-pairs", type=int, default=6)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-instances", type=int, default=64)
+    ap.add_argument("--serve-queries", type=int, default=256)
+    ap.add_argument("--serve-max-iter", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

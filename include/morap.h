@@ -175,6 +175,18 @@ int morap_rebuild(morap_ctx *ctx, void *stream);
 int morap_solve(morap_ctx *ctx, int32_t K, const double *W, void *stream, double *c_out, double *rcost_out,
                 double *rprob_out, int32_t *status_out);
 
+/* Algorithm 4 (both objectives) for chosen (product, weight) pairs under
+ * the schedulers of the last morap_solve / morap_supporting_points batch on
+ * this context (its last block of at most 64 weights): pair e is product
+ * pair_product[e] (= i * |J| + j) under weight pair_weight[e] (index within
+ * that block).  rcost_out[e] = E[rho_i], rprob_out[e] = E[rho_{|I|+j}].
+ * This is loop 2 of Algorithm 2 run separately, for drivers that choose the
+ * assignment themselves (e.g. from c values gathered across devices).
+ * Errors: EINVAL (index out of range), ESTATE (no solve since the build),
+ * ENOTCONV (a pair reached the sweep cap; outputs still written), ECUDA. */
+int morap_evaluate(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_product, const int32_t *pair_weight,
+                   void *stream, double *rcost_out, double *rprob_out);
+
 /* Algorithm 2 in full for K weight vectors in one batch: loop 1 over all
  * products, the assignment f maximising sum_j c_{f(j), j} (Hungarian;
  * |I| != |J| is padded with zero-valued dummy agents or tasks), and loop 2
@@ -289,6 +301,78 @@ typedef struct morap_point_result {
 int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, int32_t max_iter, void *stream,
                 morap_point_result *res);
 
+/* Algorithm 1 with the supporting points supplied by the caller, one at a
+ * time: for drivers that compute them elsewhere (products sharded over
+ * several devices or processes, another solver).  morap_query is this loop
+ * fed by morap_supporting_points on one context.  Host-only; the handle is
+ * owned by the caller and not thread-safe.
+ *   morap_pareto_create: n objectives, t[n], M as for morap_query (copied),
+ *     eps >= 0, max_iter >= 1.  Errors: EINVAL.
+ *   morap_pareto_next: *done = 1 once the loop stopped; otherwise w_out[n]
+ *     receives the direction whose supporting point the next step needs
+ *     (e_1 first).
+ *   morap_pareto_step: r[n] = the supporting point for that direction (the
+ *     r of Algorithm 2); solve_status = the status of the call that computed
+ *     it (MORAP_OK or MORAP_ENOTCONV, which is carried into the result).
+ *     Errors: EINVAL (null, non-finite r), ESTATE (the loop already stopped).
+ *   morap_pareto_result: fills *res as morap_query does; returns its status.
+ */
+typedef struct morap_pareto morap_pareto;
+int morap_pareto_create(int32_t n, const double *t, const double *M, double eps, int32_t max_iter,
+                        morap_pareto **out);
+int morap_pareto_next(const morap_pareto *ps, double *w_out, int32_t *done);
+int morap_pareto_step(morap_pareto *ps, const double *r, int32_t solve_status);
+int morap_pareto_result(const morap_pareto *ps, morap_point_result *res);
+void morap_pareto_destroy(morap_pareto *ps);
+
+/* ------------------------------------------------------------- serving
+ * Continuous batching of threshold-point queries (Algorithm 1) over several
+ * resident instances (built contexts).  Each query runs Algorithm 1 with
+ * M = I and the server's eps / max_iter.  A query waiting for its next
+ * supporting point joins the next batch of its instance: an idle instance
+ * takes every waiting query (up to max_batch) as one morap_supporting_points
+ * batch.  Instances run on their own CUDA streams from n_workers host
+ * threads, so batches of different instances overlap on the device.
+ * Admission: queries are admitted in arrival order while the device bytes of
+ * their weight slots (26 bytes per product state of the instance) fit
+ * hbm_budget (0 = no limit); at least one query is always admitted.
+ * A query's result does not depend on the batch it rides in.
+ * The instances must outlive the server and must not be used by the caller
+ * while the server runs. */
+typedef struct morap_server morap_server;
+
+typedef struct morap_server_config {
+    size_t hbm_budget;  /* admission budget in bytes, 0 = none                   */
+    int32_t max_batch;  /* queries per instance batch, 1..64 (default 64)        */
+    int32_t n_workers;  /* host threads driving instances (default 4)            */
+    double eps;         /* Algorithm 1 tolerance of every query (default 1e-6)   */
+    int32_t max_iter;   /* supporting points per query (default 64)              */
+    int32_t reserved;
+} morap_server_config;
+
+typedef struct morap_serving_stats {
+    int64_t submitted, completed, batches;
+    double mean_batch;     /* queries per batch                                    */
+    double p50_ms, p99_ms; /* submit-to-completion latency percentiles             */
+    double queries_per_s;  /* completed / (last completion - first submit)         */
+    double wall_s;
+    int64_t bytes_in_use;  /* admitted weight-slot bytes                            */
+} morap_serving_stats;
+
+void morap_server_config_default(morap_server_config *cfg);
+int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const morap_server_config *cfg,
+                        morap_server **out);
+/* Stops the threads (queries still in flight are abandoned) and frees the server. */
+int morap_server_destroy(morap_server *server);
+/* Non-blocking.  t has |I| + |J| entries of that instance.  Errors: EINVAL. */
+int morap_submit(morap_server *server, int32_t instance, const double *t, int64_t *ticket_out);
+/* MORAP_EBUSY while the query runs; then fills *res as morap_query does
+ * (w_hist / r_hist, when given, need iterations x (|I|+|J|) entries). */
+int morap_poll(morap_server *server, int64_t ticket, morap_point_result *res);
+/* Block until every submitted query completed or timeout_s passed (EBUSY). */
+int morap_server_wait(morap_server *server, double timeout_s);
+int morap_server_stats(morap_server *server, morap_serving_stats *stats);
+
 /* ------------------------------------------------ host-side building blocks
  * These run on the CPU only (no device needed) and are what morap_query and
  * morap_supporting_points use. */
@@ -296,6 +380,14 @@ int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, in
 /* Hungarian assignment: f_out[j] = the row assigned to column j maximising
  * sum_j C[f(j)][j] for a square C [n][n] (row-major, rows = agents). */
 int morap_assign_max(int32_t n, const double *C, int32_t *f_out);
+
+/* Algorithm 2's assignment for each of K value matrices c[K][|I|][|J|]
+ * (c_ij = optimal scalarised value of agent i on task j): with |I| != |J|
+ * the matrix is padded with zero rows or columns to a square one (a padded
+ * agent does nothing, a padded task is not done); assign_out[K][|J|] = the
+ * agent given task j, or -1 when no agent is.  The same routine the
+ * supporting-point calls use. */
+int morap_assign_tasks(int32_t n_agents, int32_t n_tasks, int32_t K, const double *c, int32_t *assign_out);
 
 /* argmin_z ||t - z||_M subject to A z <= b; A is [m][n] row-major. */
 int morap_project_halfspaces(int32_t n, int32_t m, const double *t, const double *A, const double *b,

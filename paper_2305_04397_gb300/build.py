@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmorap.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["engine.cu", "sweep.cu", "build.cu", "plain.cu", "noalloc.cu", "host_alg.cpp"]
+SOURCES = ["engine.cu", "sweep.cu", "build.cu", "plain.cu", "noalloc.cu", "server.cu", "host_alg.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-v"]
 
@@ -30,7 +30,10 @@ def nvcc() -> str:
 
 def _compile(src: str) -> tuple[str, str]:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-I", os.path.join(HERE, "..", "include"), "-c", os.path.join(CSRC, src), "-o", obj]
+    # MORAP_NVCC_DEFINES: extra -D options (kernel-shape tuning builds only)
+    extra = os.environ.get("MORAP_NVCC_DEFINES", "").split()
+    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-I", os.path.join(HERE, "..", "include"), "-c", os.path.join(CSRC, src),
+           "-o", obj]
     if src.endswith(".cpp"):
         cmd[1:1] = ["-x", "cu"]
     r = subprocess.run(cmd, capture_output=True, text=True)

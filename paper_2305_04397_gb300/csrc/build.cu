@@ -47,12 +47,13 @@ __global__ void k_letters(const ProdDesc *prods, int P, const AgentDesc *agents,
 __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                         const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ,
                         const double *a_prob, const double *a_cost, const uint8_t *letters, const int16_t *nd_delta,
-                        uint32_t *state_sa, uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf,
-                        float *cost32, double *cost64, float2 *costdf, uint32_t total_states, uint32_t total_sa,
-                        uint32_t total_tr) {
+                        uint32_t *state_sa, uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32,
+                        double *p64, float2 *pdf, float *cost32, double *cost64, float2 *costdf,
+                        uint32_t total_states, uint32_t total_sa, uint32_t total_tr) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     if (blockIdx.y == 0 && tid == 0) {
         state_sa[total_states] = total_sa;
+        state_tr[total_states] = total_tr;
         sa_tr[total_sa] = total_tr;
     }
     for (int p = blockIdx.y; p < P; p += gridDim.y) {
@@ -70,6 +71,14 @@ __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, c
                 v = (uint32_t)td.Qn * SA;
             }
             state_sa[pd.state_off + u] = pd.sa_off + v;
+            uint32_t t0;
+            if (u < pd.n_nd) {
+                const uint32_t pl = u / S, s = u - pl * S;
+                t0 = pl * T + (uint32_t)a_sa_ptr[ad.sap_off + a_state_ptr[ad.sp_off + s]];
+            } else {
+                t0 = (uint32_t)td.Qn * T;
+            }
+            state_tr[pd.state_off + u] = pd.tr_off + t0;
         }
         // state-action rows
         const uint32_t n_sa = (uint32_t)td.Qn * SA;
@@ -113,14 +122,14 @@ int launch_letters(const ProdDesc *prods, int P, const AgentDesc *agents, const 
 int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                  const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ, const double *a_prob,
                  const double *a_cost, const uint8_t *letters, const int16_t *nd_delta, uint32_t *state_sa,
-                 uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf, float *cost32, double *cost64,
-                 float2 *costdf, uint32_t total_states, uint32_t total_sa, uint32_t total_tr, uint32_t max_work,
-                 void *s) {
+                 uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf,
+                 float *cost32, double *cost64, float2 *costdf, uint32_t total_states, uint32_t total_sa,
+                 uint32_t total_tr, uint32_t max_work, void *s) {
     dim3 grid((max_work + 255) / 256 < 64 ? (max_work + 255) / 256 : 64, P < 65535 ? P : 65535);
     if (grid.x == 0) grid.x = 1;
     k_build<<<grid, 256, 0, (cudaStream_t)s>>>(prods, P, agents, tasks, a_state_ptr, a_sa_ptr, a_succ, a_prob, a_cost,
-                                                letters, nd_delta, state_sa, sa_tr, col, cp32, p64, pdf, cost32,
-                                                cost64, costdf, total_states, total_sa, total_tr);
+                                                letters, nd_delta, state_sa, state_tr, sa_tr, col, cp32, p64, pdf,
+                                                cost32, cost64, costdf, total_states, total_sa, total_tr);
     return (int)cudaGetLastError();
 }
 

@@ -89,7 +89,7 @@ struct morap_ctx {
     AgentDesc *d_agents = nullptr;
     TaskDesc *d_tasks = nullptr;
     int4 *d_chunks = nullptr;
-    uint32_t *state_sa = nullptr, *sa_tr = nullptr;
+    uint32_t *state_sa = nullptr, *state_tr = nullptr, *sa_tr = nullptr;
     int32_t *col = nullptr;
     int2 *cp32 = nullptr;
     float2 *pdf = nullptr, *costdf = nullptr;
@@ -105,6 +105,7 @@ struct morap_ctx {
     int16_t *d_nd = nullptr;
     uint8_t *d_letters = nullptr;
     uint32_t max_S = 1, max_work = 1;
+    int max_row = 1;  // longest action row (successors) of any agent
     std::vector<size_t> layout_sig;
     int64_t last_h2d_bytes = 0;
 
@@ -134,6 +135,8 @@ struct morap_ctx {
     int32_t *esweeps = nullptr;
     uint8_t *efrozen = nullptr;
     double *d_rc = nullptr, *d_rp = nullptr;
+    int32_t *ecol = nullptr;
+    double *ep = nullptr, *ecost = nullptr;
     LoopGraph geval;
     bool eval_ready = false;
     EvalArgs eargs{};
@@ -145,6 +148,7 @@ struct morap_ctx {
 
     morap_solve_stats stats{};
     std::vector<int> last_assign;  // [K][nJ] of the last supporting-point call
+    int last_K = 0;                // weights whose schedulers the last optimisation left on the device
 };
 
 namespace {
@@ -320,6 +324,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
 
     SweepArgs a{};
     a.state_sa = c->state_sa;
+    a.state_tr = c->state_tr;
     a.sa_tr = c->sa_tr;
     a.col = c->col;
     a.cp32 = c->cp32;
@@ -353,6 +358,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a64.V[1] = c->V64[1];
     c->args32 = a32;
     c->args64 = a64;
+    CKL(sweep_setup_attributes());
     c->g32.grid = sweep_grid(c, sweep_blocks_per_sm(false, Kp));
     c->g64.grid = sweep_grid(c, sweep_blocks_per_sm(true, Kp));
     if (c->cfg.launch_mode == 0) {
@@ -391,6 +397,9 @@ int ensure_eval(morap_ctx *c, size_t n_pairs, size_t n_chunks, size_t n_states) 
     CKR(dev_alloc(c, L, &c->efrozen, n_pairs));
     CKR(dev_alloc(c, L, &c->d_rc, n_pairs * sizeof(double)));
     CKR(dev_alloc(c, L, &c->d_rp, n_pairs * sizeof(double)));
+    CKR(dev_alloc(c, L, &c->ecol, n_states * (size_t)c->max_row * sizeof(int32_t)));
+    CKR(dev_alloc(c, L, &c->ep, n_states * (size_t)c->max_row * sizeof(double)));
+    CKR(dev_alloc(c, L, &c->ecost, n_states * sizeof(double)));
     c->eval_cap_pairs = n_pairs;
     c->eval_cap_chunks = n_chunks;
     c->eval_cap_states = n_states;
@@ -415,6 +424,10 @@ int ensure_eval(morap_ctx *c, size_t n_pairs, size_t n_chunks, size_t n_states) 
     e.ctl = c->ctl + 2;
     e.E[0] = c->E[0];
     e.E[1] = c->E[1];
+    e.ecol = c->ecol;
+    e.ep = c->ep;
+    e.ecost = c->ecost;
+    e.stride = c->max_row;
     c->eargs = e;
     const int grid = sweep_grid(c, eval_blocks_per_sm());
     c->geval.grid = grid;
@@ -452,6 +465,7 @@ int check_weights(morap_ctx *c, int K, const double *W) {
 int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::vector<double> &h_c,
                      std::vector<int32_t> &h_status) {
     const int Kp = next_pow2(K);
+    c->last_K = 0;
     CKR(ensure_solve(c, Kp));
     const size_t np = (size_t)c->P * Kp;
     const size_t nW = (size_t)K * (c->nI + c->nJ);
@@ -531,6 +545,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     for (int p = 0; p < c->P; ++p)
         for (int k = 0; k < K; ++k) bad += h_status[(size_t)p * Kp + k] != MORAP_OK;
     st.pairs_not_converged = bad;
+    c->last_K = K;
     return MORAP_OK;
 }
 
@@ -562,6 +577,7 @@ int run_evaluation(morap_ctx *c, const std::vector<int4> &pairs_in, cudaStream_t
     }
     CK(cudaMemsetAsync(c->E[0], 0, off * sizeof(double2), s));
     CK(cudaMemsetAsync(c->E[1], 0, off * sizeof(double2), s));
+    CKL(launch_eval_compact(c->eargs, (int)chunks.size(), s));
     const unsigned int cap = (unsigned int)std::max(1, c->cfg.max_sweeps);
     CKL(launch_loop_init(c->ctl + 2, c->elist[0], (unsigned int)chunks.size(), c->eres, npair, c->esweeps,
                          c->efrozen, cap, s));
@@ -598,7 +614,7 @@ int run_evaluation(morap_ctx *c, const std::vector<int4> &pairs_in, cudaStream_t
     c->stats.eval_pairs = (int32_t)npair;
     c->stats.h2d_bytes += (int64_t)((npair + chunks.size()) * sizeof(int4));
     c->stats.d2h_bytes += (int64_t)(npair * (2 * sizeof(double) + 1) + sizeof(LoopCtl));
-    c->stats.kernel_launches += 2 + c->stats.eval_sweeps + c->stats.eval_sweeps / 6;
+    c->stats.kernel_launches += 3 + c->stats.eval_sweeps + c->stats.eval_sweeps / 6;
     return MORAP_OK;
 }
 
@@ -610,19 +626,15 @@ int supporting_batch(morap_ctx *c, int K, const double *W, cudaStream_t s, doubl
     std::vector<int32_t> hs;
     CKR(run_optimisation(c, K, W, s, hc, hs));
     const auto t1 = clk::now();
-    const int Kp = c->Kp, nI = c->nI, nJ = c->nJ, n = std::max(nI, nJ);
-    std::vector<double> Cm((size_t)n * n);
-    std::vector<int> f(n);
+    const int Kp = c->Kp, nI = c->nI, nJ = c->nJ;
+    std::vector<double> Cm((size_t)nI * nJ);
     std::vector<int4> pairs;
     std::vector<int> assign((size_t)K * nJ, -1);
     for (int k = 0; k < K; ++k) {
-        std::fill(Cm.begin(), Cm.end(), 0.0);
-        for (int i = 0; i < nI; ++i)
-            for (int j = 0; j < nJ; ++j) Cm[(size_t)i * n + j] = hc[(size_t)(i * nJ + j) * Kp + k];
-        hungarian_max(n, Cm.data(), f.data());
+        for (int p = 0; p < nI * nJ; ++p) Cm[p] = hc[(size_t)p * Kp + k];
+        assign_tasks(nI, nJ, Cm.data(), assign.data() + (size_t)k * nJ);
         for (int j = 0; j < nJ; ++j) {
-            const int i = f[j] < nI ? f[j] : -1;
-            assign[(size_t)k * nJ + j] = i;
+            const int i = assign[(size_t)k * nJ + j];
             if (i >= 0) pairs.push_back(make_int4(i * nJ + j, k, 0, 0));
         }
     }
@@ -726,8 +738,8 @@ int validate_agent(int32_t n, int32_t s0, const int32_t *state_ptr, const int32_
 int run_construction(morap_ctx *c, cudaStream_t s) {
     CKL(launch_letters(c->d_prods, c->P, c->d_ad, c->d_td, c->d_lp, c->d_la, c->d_ap, c->d_letters, c->max_S, s));
     CKL(launch_build(c->d_prods, c->P, c->d_ad, c->d_td, c->d_sp, c->d_sap, c->d_succ, c->d_prob, c->d_cost,
-                     c->d_letters, c->d_nd, c->state_sa, c->sa_tr, c->col, c->cp32, c->p64, c->pdf, c->cost32,
-                     c->cost64, c->costdf, c->TS, c->TSA, c->TT, c->max_work, s));
+                     c->d_letters, c->d_nd, c->state_sa, c->state_tr, c->sa_tr, c->col, c->cp32, c->p64, c->pdf,
+                     c->cost32, c->cost64, c->costdf, c->TS, c->TSA, c->TT, c->max_work, s));
     return MORAP_OK;
 }
 
@@ -739,6 +751,7 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
     std::vector<int32_t> a_sp, a_sap, a_succ, a_lp, a_la;
     std::vector<double> a_prob, a_cost;
     uint32_t max_S = 1;
+    int max_row_new = 1;
     bool all_free = true;
     for (int i = 0; i < nI; ++i) {
         const HostAgent &A = c->agents[i];
@@ -762,6 +775,7 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         a_la.insert(a_la.end(), A.label_ap.begin(), A.label_ap.end());
         max_S = std::max(max_S, d.S);
         all_free = all_free && A.free_action_everywhere;
+        for (size_t r = 0; r + 1 < A.sa_ptr.size(); ++r) max_row_new = std::max(max_row_new, A.sa_ptr[r + 1] - A.sa_ptr[r]);
     }
     std::vector<TaskDesc> td(nJ);
     std::vector<int16_t> nd_delta;
@@ -817,7 +831,8 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
     // buffers and their graphs.
     std::vector<size_t> sig = {(size_t)nI, (size_t)nJ, (size_t)TS, (size_t)TSA, (size_t)TT, a_sp.size(),
                                a_sap.size(), a_succ.size(), a_lp.size(), a_la.size(), ap_ids.size(),
-                               nd_delta.size(), (size_t)letters, chunks.size(), (size_t)all_free};
+                               nd_delta.size(), (size_t)letters, chunks.size(), (size_t)all_free,
+                               (size_t)max_row_new};
     const bool reuse = c->built && sig == c->layout_sig &&
                        std::memcmp(prods.data(), c->h_prods.data(), P * sizeof(ProdDesc)) == 0;
     if (!reuse) {
@@ -836,10 +851,12 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         c->max_S = max_S;
         c->max_work = (uint32_t)std::min<uint64_t>(max_work, 0xffffffffull);
         c->all_free_action = all_free;
-        c->csr_bytes =
-            (int64_t)(4 * (TS + 1) + 4 * (TSA + 1) + 4 * TT + 8 * TT + 8 * TT + 8 * TT + 4 * TSA + 8 * TSA + 8 * TSA);
+        c->max_row = max_row_new;
+        c->csr_bytes = (int64_t)(8 * (TS + 1) + 4 * (TSA + 1) + 4 * TT + 8 * TT + 8 * TT + 8 * TT + 4 * TSA +
+                                 8 * TSA + 8 * TSA);
         auto &L = c->build_allocs;
         CKR(dev_alloc(c, L, &c->state_sa, (TS + 1) * 4));
+        CKR(dev_alloc(c, L, &c->state_tr, (TS + 1) * 4));
         CKR(dev_alloc(c, L, &c->sa_tr, (TSA + 1) * 4));
         CKR(dev_alloc(c, L, &c->col, std::max<uint64_t>(TT, 1) * 4));
         CKR(dev_alloc(c, L, &c->cp32, std::max<uint64_t>(TT, 1) * 8));
@@ -902,15 +919,6 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
     return MORAP_OK;
 }
 
-double mnorm(int n, const double *v, const double *M) {
-    double acc = 0.0;
-    for (int i = 0; i < n; ++i) {
-        double mv = 0.0;
-        for (int j = 0; j < n; ++j) mv += (M ? M[(size_t)i * n + j] : (i == j ? 1.0 : 0.0)) * v[j];
-        acc += v[i] * mv;
-    }
-    return std::sqrt(std::max(acc, 0.0));
-}
 
 }  // namespace
 
@@ -1081,6 +1089,31 @@ int morap_solve(morap_ctx *ctx, int32_t K, const double *W, void *stream, double
     API_END
 }
 
+int morap_evaluate(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_product, const int32_t *pair_weight,
+                   void *stream, double *rcost_out, double *rprob_out) {
+    API_BEGIN
+    if (!ctx || n_pairs < 0 || (n_pairs > 0 && (!pair_product || !pair_weight || !rcost_out || !rprob_out)))
+        return fail(MORAP_EINVAL, "null argument");
+    if (!ctx->built || ctx->last_K == 0) return fail(MORAP_ESTATE, "evaluate before a solve");
+    std::vector<int4> pairs((size_t)n_pairs);
+    for (int e = 0; e < n_pairs; ++e) {
+        if (pair_product[e] < 0 || pair_product[e] >= ctx->P) return fail(MORAP_EINVAL, "product index out of range");
+        if (pair_weight[e] < 0 || pair_weight[e] >= ctx->last_K)
+            return fail(MORAP_EINVAL, "weight index out of range of the last solve");
+        pairs[e] = make_int4(pair_product[e], pair_weight[e], 0, 0);
+    }
+    if (n_pairs == 0) return MORAP_OK;
+    CK(cudaSetDevice(ctx->cfg.device));
+    std::vector<double> rc, rp;
+    int nc = 0;
+    CKR(run_evaluation(ctx, pairs, (cudaStream_t)stream, rc, rp, nc));
+    std::copy(rc.begin(), rc.end(), rcost_out);
+    std::copy(rp.begin(), rp.end(), rprob_out);
+    if (nc) return fail(MORAP_ENOTCONV, "an evaluation reached the sweep cap");
+    return MORAP_OK;
+    API_END
+}
+
 int morap_supporting_points(morap_ctx *ctx, int32_t K, const double *W, void *stream, double *r_out,
                             int32_t *assign_out, double *c_out) {
     API_BEGIN
@@ -1120,59 +1153,73 @@ int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, in
     const int n = ctx->nI + ctx->nJ;
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(t[i])) return fail(MORAP_EINVAL, "threshold entries must be finite");
-    std::vector<double> w(n, 0.0), r(n), t_dn(t, t + n), t_up(n, -HUGE_VAL), d(n);
-    std::vector<double> Phi, A, b;
-    w[0] = 1.0;
-    bool moved = false;
-    int it = 0, status = MORAP_OK;
-    double dist = HUGE_VAL;
-    for (;;) {
-        const int rc = morap_supporting_points(ctx, 1, w.data(), stream, r.data(), nullptr, nullptr);
+    Alg1 q;
+    q.init(n, t, M, eps, max_iter);
+    std::vector<double> r(n);
+    while (!q.done) {
+        const int rc = morap_supporting_points(ctx, 1, q.w.data(), stream, r.data(), nullptr, nullptr);
         if (rc == MORAP_ENOTCONV)
-            status = rc;
+            q.status = rc;
         else if (rc != MORAP_OK)
             return rc;
-        if (res->w_hist) std::copy(w.begin(), w.end(), res->w_hist + (size_t)it * n);
-        if (res->r_hist) std::copy(r.begin(), r.end(), res->r_hist + (size_t)it * n);
-        ++it;
-        Phi.insert(Phi.end(), r.begin(), r.end());
-        A.insert(A.end(), w.begin(), w.end());
-        double wr = 0.0, wt = 0.0;
-        for (int i = 0; i < n; ++i) {
-            wr += w[i] * r[i];
-            wt += w[i] * t_dn[i];
-        }
-        b.push_back(wr);
-        if (wr < wt) {
-            project_halfspaces(n, (int)b.size(), t, A.data(), b.data(), M, t_dn.data());
-            moved = true;
-        }
-        project_down_hull(n, it, t, Phi.data(), M, t_up.data());
-        for (int i = 0; i < n; ++i) d[i] = t_dn[i] - t_up[i];
-        dist = mnorm(n, d.data(), M);
-        if (dist <= eps || it >= max_iter) break;
-        for (int i = 0; i < n; ++i) {
-            double acc = 0.0;
-            for (int j = 0; j < n; ++j) acc += (M ? M[(size_t)i * n + j] : (i == j ? 1.0 : 0.0)) * (t[j] - t_up[j]);
-            d[i] = acc;
-        }
-        double l1 = 0.0;
-        for (int i = 0; i < n; ++i) l1 += std::fabs(d[i]);
-        if (!(l1 > 0.0)) break;
-        for (int i = 0; i < n; ++i) w[i] = std::max(d[i], 0.0) / l1;
+        q.step(r.data());
     }
-    res->feasible = moved ? 0 : 1;
-    res->iterations = it;
-    res->converged = dist <= eps ? 1 : 0;
-    res->distance = dist;
-    if (res->t_up) std::copy(t_up.begin(), t_up.end(), res->t_up);
-    if (res->t_down) std::copy(t_dn.begin(), t_dn.end(), res->t_down);
-    if (!res->converged && status == MORAP_OK) status = MORAP_ENOTCONV;
-    res->status = status;
+    const int status = alg1_result(q, res);
     if (status != MORAP_OK) return fail(status, "query stopped before ||t_down - t_up|| <= eps");
     return MORAP_OK;
     API_END
 }
+
+struct morap_pareto {
+    Alg1 q;
+};
+
+int morap_pareto_create(int32_t n, const double *t, const double *M, double eps, int32_t max_iter,
+                        morap_pareto **out) {
+    API_BEGIN
+    if (!t || !out || n < 1) return fail(MORAP_EINVAL, "pareto_create: n >= 1, t and out required");
+    if (!(eps >= 0) || max_iter < 1) return fail(MORAP_EINVAL, "eps >= 0 and max_iter >= 1 required");
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(t[i])) return fail(MORAP_EINVAL, "threshold entries must be finite");
+    auto *ps = new morap_pareto();
+    ps->q.init(n, t, M, eps, max_iter);
+    *out = ps;
+    return MORAP_OK;
+    API_END
+}
+
+int morap_pareto_next(const morap_pareto *ps, double *w_out, int32_t *done) {
+    if (!ps || !done) return fail(MORAP_EINVAL, "pareto_next: null argument");
+    *done = ps->q.done ? 1 : 0;
+    if (!ps->q.done) {
+        if (!w_out) return fail(MORAP_EINVAL, "pareto_next: w_out required");
+        std::copy(ps->q.w.begin(), ps->q.w.end(), w_out);
+    }
+    return MORAP_OK;
+}
+
+int morap_pareto_step(morap_pareto *ps, const double *r, int32_t solve_status) {
+    API_BEGIN
+    if (!ps || !r) return fail(MORAP_EINVAL, "pareto_step: null argument");
+    if (ps->q.done) return fail(MORAP_ESTATE, "pareto_step: the loop already stopped");
+    if (solve_status != MORAP_OK && solve_status != MORAP_ENOTCONV)
+        return fail(MORAP_EINVAL, "pareto_step: solve_status must be MORAP_OK or MORAP_ENOTCONV");
+    for (int i = 0; i < ps->q.n; ++i)
+        if (!std::isfinite(r[i])) return fail(MORAP_EINVAL, "supporting point entries must be finite");
+    if (solve_status == MORAP_ENOTCONV && ps->q.status == MORAP_OK) ps->q.status = MORAP_ENOTCONV;
+    ps->q.step(r);
+    return MORAP_OK;
+    API_END
+}
+
+int morap_pareto_result(const morap_pareto *ps, morap_point_result *res) {
+    if (!ps || !res) return fail(MORAP_EINVAL, "pareto_result: null argument");
+    const int st = alg1_result(ps->q, res);
+    if (st != MORAP_OK) return fail(st, "loop stopped before ||t_down - t_up|| <= eps");
+    return MORAP_OK;
+}
+
+void morap_pareto_destroy(morap_pareto *ps) { delete ps; }
 
 int morap_solve_plain(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_product, const double *pair_w,
                       void *stream, double *c_out, double *rcost_out, double *rprob_out, double *stats_out) {
@@ -1303,6 +1350,16 @@ int morap_assign_max(int32_t n, const double *C, int32_t *f_out) {
     std::vector<int> f(n);
     if (n) hungarian_max(n, C, f.data());
     for (int j = 0; j < n; ++j) f_out[j] = f[j];
+    return MORAP_OK;
+    API_END
+}
+
+int morap_assign_tasks(int32_t n_agents, int32_t n_tasks, int32_t K, const double *c, int32_t *assign_out) {
+    API_BEGIN
+    if (n_agents < 0 || n_tasks < 0 || K < 0) return fail(MORAP_EINVAL, "negative size");
+    if ((size_t)n_agents * n_tasks * K > 0 && (!c || !assign_out)) return fail(MORAP_EINVAL, "null argument");
+    for (int k = 0; k < K; ++k)
+        assign_tasks(n_agents, n_tasks, c + (size_t)k * n_agents * n_tasks, assign_out + (size_t)k * n_tasks);
     return MORAP_OK;
     API_END
 }

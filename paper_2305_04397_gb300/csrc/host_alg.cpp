@@ -158,6 +158,20 @@ void hungarian_max(int n, const double *C, int *f) {
 
 // ------------------------------------------------------------ dense QP (IPM)
 
+// Algorithm 2's assignment for |I| agents and |J| tasks: the |I| x |J| value
+// matrix is padded with zero rows (dummy agents that do nothing) or zero
+// columns (dummy tasks) to a square matrix; task j goes to agent f(j), or
+// to no agent (-1) when a dummy agent takes it.
+void assign_tasks(int nI, int nJ, const double *C, int32_t *assign) {
+    const int n = std::max(nI, nJ);
+    std::vector<double> Cm((size_t)n * n, 0.0);
+    for (int i = 0; i < nI; ++i)
+        for (int j = 0; j < nJ; ++j) Cm[(size_t)i * n + j] = C[(size_t)i * nJ + j];
+    std::vector<int> f(n);
+    if (n) hungarian_max(n, Cm.data(), f.data());
+    for (int j = 0; j < nJ; ++j) assign[j] = f[j] < nI ? f[j] : -1;
+}
+
 namespace {
 
 // In-place LU with partial pivoting of a dense [n][n] matrix; returns false
@@ -377,6 +391,103 @@ int project_down_hull(int n, int m, const double *t, const double *Phi, const do
     const int rc = qp_solve(N, G.data(), c.data(), mi, A.data(), b.data(), 1, E.data(), d.data(), v.data());
     for (int i = 0; i < n; ++i) x[i] = std::min(v[i], t[i]);
     return rc;
+}
+
+// ------------------------------------------------------------- Algorithm 1
+
+double mnorm(int n, const double *v, const double *M) {
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double mv = 0.0;
+        for (int j = 0; j < n; ++j) mv += (M ? M[(size_t)i * n + j] : (i == j ? 1.0 : 0.0)) * v[j];
+        acc += v[i] * mv;
+    }
+    return std::sqrt(std::max(acc, 0.0));
+}
+
+void Alg1::init(int n_obj, const double *t_in, const double *M_in, double eps_in, int max_iter_in) {
+    n = n_obj;
+    t.assign(t_in, t_in + n);
+    if (M_in)
+        M.assign(M_in, M_in + (size_t)n * n);
+    else
+        M.clear();
+    w.assign(n, 0.0);
+    w[0] = 1.0;  // the first direction is e_1
+    t_dn = t;
+    t_up.assign(n, -HUGE_VAL);
+    Phi.clear();
+    A.clear();
+    b.clear();
+    w_hist.clear();
+    r_hist.clear();
+    moved = false;
+    done = false;
+    it = 0;
+    status = 0;
+    dist = HUGE_VAL;
+    eps = eps_in;
+    max_iter = max_iter_in;
+}
+
+// One pass of the loop body with the supporting point r for direction w:
+// the point joins Phi and the halfspace {z : w.z <= w.r} joins Lambda; the
+// outer bound moves when w.r < w.t_down; the inner bound is re-projected;
+// then the loop test on ||t_down - t_up||_M, and the next direction
+// w = M (t - t_up) / ||M (t - t_up)||_1.
+void Alg1::step(const double *r) {
+    const double *Mp = M.empty() ? nullptr : M.data();
+    w_hist.insert(w_hist.end(), w.begin(), w.end());
+    r_hist.insert(r_hist.end(), r, r + n);
+    ++it;
+    Phi.insert(Phi.end(), r, r + n);
+    A.insert(A.end(), w.begin(), w.end());
+    double wr = 0.0, wt = 0.0;
+    for (int i = 0; i < n; ++i) {
+        wr += w[i] * r[i];
+        wt += w[i] * t_dn[i];
+    }
+    b.push_back(wr);
+    if (wr < wt) {
+        project_halfspaces(n, (int)b.size(), t.data(), A.data(), b.data(), Mp, t_dn.data());
+        moved = true;
+    }
+    project_down_hull(n, it, t.data(), Phi.data(), Mp, t_up.data());
+    std::vector<double> d(n);
+    for (int i = 0; i < n; ++i) d[i] = t_dn[i] - t_up[i];
+    dist = mnorm(n, d.data(), Mp);
+    if (dist <= eps || it >= max_iter) {
+        done = true;
+        return;
+    }
+    double l1 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += (Mp ? Mp[(size_t)i * n + j] : (i == j ? 1.0 : 0.0)) * (t[j] - t_up[j]);
+        d[i] = acc;
+        l1 += std::fabs(acc);
+    }
+    if (!(l1 > 0.0)) {  // t_up == t: t is achievable, nothing left to separate
+        done = true;
+        return;
+    }
+    for (int i = 0; i < n; ++i) w[i] = std::max(d[i], 0.0) / l1;
+}
+
+int alg1_result(const Alg1 &q, morap_point_result *res) {
+    int status = q.status;
+    const bool converged = q.dist <= q.eps;
+    if (!converged && status == MORAP_OK) status = MORAP_ENOTCONV;
+    res->feasible = q.moved ? 0 : 1;
+    res->iterations = q.it;
+    res->converged = converged ? 1 : 0;
+    res->status = status;
+    res->distance = q.dist;
+    if (res->t_up) std::copy(q.t_up.begin(), q.t_up.end(), res->t_up);
+    if (res->t_down) std::copy(q.t_dn.begin(), q.t_dn.end(), res->t_down);
+    if (res->w_hist) std::copy(q.w_hist.begin(), q.w_hist.end(), res->w_hist);
+    if (res->r_hist) std::copy(q.r_hist.begin(), q.r_hist.end(), res->r_hist);
+    return status;
 }
 
 }  // namespace morap

@@ -1,6 +1,7 @@
 // Internal declarations shared by the engine's translation units.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -49,6 +50,9 @@ int preprocess_task(int32_t n_locs, int32_t q0, int32_t n_ap, const int32_t *ap_
 // --------------------------------------------------------- host algorithms
 // Square assignment maximising sum_j C[f(j)][j]; C row-major [n][n].
 void hungarian_max(int n, const double *C, int *f);
+// Rectangular assignment of Algorithm 2 (C row-major [nI][nJ]): assign[j] =
+// agent of task j, -1 for none.
+void assign_tasks(int nI, int nJ, const double *C, int32_t *assign);
 
 // Dense convex QP: min 1/2 x'Gx + c'x  s.t.  A x <= b (m rows), E x = d (p rows).
 // Mehrotra predictor-corrector primal-dual interior point.  Returns 0 on
@@ -59,6 +63,23 @@ int qp_solve(int n, const double *G, const double *c, int m, const double *A, co
 int project_halfspaces(int n, int m, const double *t, const double *A, const double *b, const double *M,
                        double *z);
 int project_down_hull(int n, int m, const double *t, const double *Phi, const double *M, double *x);
+
+// ||v||_M = sqrt(v' M v); M row-major [n][n], NULL = identity.
+double mnorm(int n, const double *v, const double *M);
+
+// Algorithm 1 advanced one supporting point at a time: `w` is the direction
+// whose supporting point step() expects next, until `done`.
+struct Alg1 {
+    int n = 0, it = 0, max_iter = 64, status = 0;
+    double eps = 1e-6, dist = HUGE_VAL;
+    bool moved = false, done = false;
+    std::vector<double> t, M, w, t_dn, t_up, Phi, A, b, w_hist, r_hist;
+    void init(int n_obj, const double *t_in, const double *M_in, double eps_in, int max_iter_in);
+    void step(const double *r);
+};
+// Fill *res from a finished run; returns its status (ENOTCONV when it
+// stopped with ||t_down - t_up|| > eps).
+int alg1_result(const Alg1 &q, morap_point_result *res);
 
 // ------------------------------------------------------ device layout
 struct ProdDesc {
@@ -107,9 +128,12 @@ constexpr int kChunk = 128;      // states per (warp) work item of the optimisat
 constexpr int kEvalChunk = 256;  // states per work item of the evaluation sweeps
 constexpr int kThreads = 256;
 constexpr int kGatherBatch = 4;  // independent successor gathers a thread issues back to back
+int sweep_smem_bytes(bool fp64);
+int sweep_setup_attributes();
 
 struct SweepArgs {
     const uint32_t *state_sa;
+    const uint32_t *state_tr;  // first transition of each state (= sa_tr[state_sa[u]])
     const uint32_t *sa_tr;
     const int32_t *col;
     const int2 *cp32;     // per transition {col, p rounded down as float bits}
@@ -120,7 +144,7 @@ struct SweepArgs {
     const ProdDesc *prods;
     const float2 *pdf;    // per transition: p as a double-float (hi, lo)
     const float2 *costdf; // per state-action: cost as a double-float
-    const float2 *w32;    // per pair (p*Kp + k): (w_i rounded up, w_p rounded down)
+    const float2 *w32;    // per pair (p*Kp + k): (-(w_i rounded up), w_p rounded down)
     const double2 *w64;   // per pair: (w_i, w_p)
     const float4 *wdf;    // per pair: (w_i.hi, w_i.lo, w_p.hi, w_p.lo)
     const double *thr;    // per pair freeze threshold of this phase
@@ -153,6 +177,13 @@ struct EvalArgs {
     unsigned int *list[3];
     LoopCtl *ctl;
     double2 *E[2];
+    // compact scheduler rows of the evaluated pairs (built once per call):
+    // for pair e with value offset off and n + 1 states (done slot n), slot j
+    // of state s is at off * stride + j * (n + 1) + s
+    int32_t *ecol;   // local successor (n = done slot for padding)
+    double *ep;      // probability (0 for padding)
+    double *ecost;   // cost of the scheduler's action, at off + s
+    int stride;      // slots per state: the longest action row of any agent
 };
 
 // ---------------------------------------------------------- kernel launchers
@@ -164,9 +195,9 @@ int launch_letters(const ProdDesc *prods, int P, const AgentDesc *agents, const 
 int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                  const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ, const double *a_prob,
                  const double *a_cost, const uint8_t *letters, const int16_t *nd_delta, uint32_t *state_sa,
-                 uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf, float *cost32, double *cost64,
-                 float2 *costdf, uint32_t total_states, uint32_t total_sa, uint32_t total_tr, uint32_t max_work,
-                 void *s);
+                 uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf,
+                 float *cost32, double *cost64, float2 *costdf, uint32_t total_states, uint32_t total_sa,
+                 uint32_t total_tr, uint32_t max_work, void *s);
 
 int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W,
                          float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1, void *s);
@@ -182,6 +213,7 @@ int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_
 int launch_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V64, const uint8_t *frozen, double *c_out,
                     int32_t *status_out, void *s);
 int launch_eval_sweep(const EvalArgs &a, int pos, int grid, void *s);
+int launch_eval_compact(const EvalArgs &a, int n_chunks, void *s);
 int launch_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const double2 *E, double *rc,
                        double *rp, void *s);
 // plain baseline

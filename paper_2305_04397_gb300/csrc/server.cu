@@ -1,0 +1,298 @@
+// Serving: threshold-point queries (Algorithm 1, Sec. 3.3) over several
+// resident instances with continuous batching.
+//
+// Every query is an Algorithm 1 state machine on the host.  A query that
+// needs its next supporting point waits on its instance; an idle instance
+// takes every waiting query (up to max_batch) as one batch of weight
+// vectors for morap_supporting_points, so queries that arrive while a batch
+// runs join the next one.  Instances run on their own streams from a pool
+// of worker threads, so the batches of different instances overlap on the
+// device.  Queries are admitted in arrival order while the device bytes
+// their weights occupy (values, recorded actions, schedulers) fit the
+// budget; results do not depend on the batch a query rides in, because each
+// (product, weight) pair runs exactly its own sweeps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+namespace morap {
+
+}  // namespace morap
+
+using namespace morap;
+
+struct ServerQuery {
+    int64_t ticket;
+    int inst;
+    Alg1 ps;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    bool admitted = false;
+    int64_t cost = 0;
+};
+
+struct morap_server {
+    std::vector<morap_ctx *> inst;
+    std::vector<int> n_obj;
+    std::vector<int64_t> bytes_per_weight;
+    std::vector<cudaStream_t> streams;
+    std::vector<char> busy;
+    morap_server_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv, cv_done;
+    std::deque<int64_t> pending;                 // submitted, not admitted (arrival order)
+    std::vector<std::deque<int64_t>> ready;      // admitted, waiting for a supporting point
+    std::unordered_map<int64_t, ServerQuery> queries;
+    int64_t next_ticket = 1, in_use = 0;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    std::thread scheduler;
+    std::deque<int> jobs;  // instances with a batch to run
+    // stats
+    std::vector<double> latencies_ms;
+    int64_t submitted = 0, completed = 0, batches = 0, batch_queries = 0;
+    std::chrono::steady_clock::time_point t_first{}, t_last{};
+    bool have_first = false;
+};
+
+namespace {
+
+void scheduler_loop(morap_server *S) {
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        // admission in arrival order, by the device bytes of one weight slot
+        while (!S->pending.empty()) {
+            ServerQuery &q = S->queries[S->pending.front()];
+            if (S->cfg.hbm_budget && S->in_use + q.cost > (int64_t)S->cfg.hbm_budget && S->in_use > 0) break;
+            q.admitted = true;
+            S->in_use += q.cost;
+            S->ready[q.inst].push_back(q.ticket);
+            S->pending.pop_front();
+        }
+        bool dispatched = false;
+        for (size_t i = 0; i < S->inst.size(); ++i)
+            if (!S->busy[i] && !S->ready[i].empty()) {
+                S->busy[i] = 1;
+                S->jobs.push_back((int)i);
+                dispatched = true;
+            }
+        if (dispatched) S->cv.notify_all();
+        S->cv.wait(lk);
+    }
+}
+
+void worker_loop(morap_server *S) {
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        while (!S->stop && S->jobs.empty()) S->cv.wait(lk);
+        if (S->stop) return;
+        const int i = S->jobs.front();
+        S->jobs.pop_front();
+        // take every ready query of the instance (continuous batching)
+        std::vector<int64_t> batch;
+        while (!S->ready[i].empty() && (int)batch.size() < S->cfg.max_batch) {
+            batch.push_back(S->ready[i].front());
+            S->ready[i].pop_front();
+        }
+        const int n = S->n_obj[i];
+        std::vector<double> W(batch.size() * n), R(batch.size() * n);
+        for (size_t b = 0; b < batch.size(); ++b) {
+            const ServerQuery &q = S->queries[batch[b]];
+            std::copy(q.ps.w.begin(), q.ps.w.end(), W.begin() + b * n);
+        }
+        lk.unlock();
+        const int rc = morap_supporting_points(S->inst[i], (int32_t)batch.size(), W.data(), (void *)S->streams[i],
+                                               R.data(), nullptr, nullptr);
+        lk.lock();
+        S->batches += 1;
+        S->batch_queries += (int64_t)batch.size();
+        const auto now = std::chrono::steady_clock::now();
+        for (size_t b = 0; b < batch.size(); ++b) {
+            ServerQuery &q = S->queries[batch[b]];
+            if (rc != MORAP_OK && rc != MORAP_ENOTCONV) {
+                q.ps.status = rc;
+                q.ps.done = true;
+            } else {
+                // host QPs of this query, outside the lock, on a private copy
+                Alg1 ps = q.ps;
+                if (rc == MORAP_ENOTCONV && ps.status == MORAP_OK) ps.status = rc;
+                lk.unlock();
+                ps.step(R.data() + b * n);
+                lk.lock();
+                q.ps = std::move(ps);
+            }
+            if (q.ps.done) {
+                q.t_done = now;
+                S->in_use -= q.cost;
+                S->completed += 1;
+                S->latencies_ms.push_back(std::chrono::duration<double, std::milli>(q.t_done - q.t_submit).count());
+                S->t_last = now;
+            } else {
+                S->ready[i].push_back(q.ticket);
+            }
+        }
+        S->busy[i] = 0;
+        S->cv.notify_all();
+        S->cv_done.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void morap_server_config_default(morap_server_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->max_batch = 64;
+    cfg->n_workers = 4;
+    cfg->eps = 1e-6;
+    cfg->max_iter = 64;
+}
+
+int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const morap_server_config *cfg_in,
+                        morap_server **out) {
+    if (!instances || n_instances < 1 || !out) return fail(MORAP_EINVAL, "server: bad arguments");
+    morap_server_config cfg;
+    if (cfg_in)
+        cfg = *cfg_in;
+    else
+        morap_server_config_default(&cfg);
+    if (cfg.max_batch < 1 || cfg.max_batch > 64 || cfg.n_workers < 1 || !(cfg.eps >= 0) || cfg.max_iter < 1)
+        return fail(MORAP_EINVAL, "server: max_batch in 1..64, n_workers >= 1, eps >= 0, max_iter >= 1");
+    auto *S = new morap_server();
+    S->cfg = cfg;
+    for (int i = 0; i < n_instances; ++i) {
+        morap_ctx *c = instances[i];
+        int64_t info[10];
+        if (!c || morap_product_info(c, 0, info) != MORAP_OK) {
+            delete S;
+            return fail(MORAP_ESTATE, "server: every instance must be a built context");
+        }
+        // objectives and device bytes of one weight slot: values (FP32 x2 and
+        // double-float x2), recorded action and scheduler per product state
+        int64_t states = 0;
+        int32_t p = 0;
+        int nI = 0, nJ = 0;
+        while (morap_product_info(c, p, info) == MORAP_OK) {
+            states += info[2];
+            nI = std::max<int>(nI, (int)info[8] + 1);
+            nJ = std::max<int>(nJ, (int)info[9] + 1);
+            ++p;
+        }
+        set_error("");
+        S->inst.push_back(c);
+        S->n_obj.push_back(nI + nJ);
+        S->bytes_per_weight.push_back(states * (2 * 4 + 2 * 8 + 1 + 1));
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (auto s : S->streams) cudaStreamDestroy(s);
+            delete S;
+            return fail(MORAP_ECUDA, "server: cudaStreamCreate");
+        }
+        S->streams.push_back(st);
+    }
+    S->busy.assign(n_instances, 0);
+    S->ready.resize(n_instances);
+    S->scheduler = std::thread(scheduler_loop, S);
+    for (int k = 0; k < cfg.n_workers; ++k) S->workers.emplace_back(worker_loop, S);
+    *out = S;
+    return MORAP_OK;
+}
+
+int morap_server_destroy(morap_server *S) {
+    if (!S) return MORAP_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->scheduler.joinable()) S->scheduler.join();
+    for (auto &t : S->workers)
+        if (t.joinable()) t.join();
+    for (auto s : S->streams) cudaStreamDestroy(s);
+    delete S;
+    return MORAP_OK;
+}
+
+int morap_submit(morap_server *S, int32_t instance, const double *t, int64_t *ticket_out) {
+    if (!S || !t || !ticket_out) return fail(MORAP_EINVAL, "submit: null argument");
+    if (instance < 0 || instance >= (int32_t)S->inst.size()) return fail(MORAP_EINVAL, "submit: no such instance");
+    const int n = S->n_obj[instance];
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(t[i])) return fail(MORAP_EINVAL, "submit: threshold entries must be finite");
+    std::lock_guard<std::mutex> lk(S->mu);
+    const int64_t tk = S->next_ticket++;
+    ServerQuery &q = S->queries[tk];
+    q.ticket = tk;
+    q.inst = instance;
+    q.ps.init(n, t, nullptr, S->cfg.eps, S->cfg.max_iter);
+    q.t_submit = std::chrono::steady_clock::now();
+    q.cost = S->bytes_per_weight[instance];
+    if (!S->have_first) {
+        S->t_first = q.t_submit;
+        S->have_first = true;
+    }
+    S->pending.push_back(tk);
+    S->submitted += 1;
+    *ticket_out = tk;
+    S->cv.notify_all();
+    return MORAP_OK;
+}
+
+int morap_poll(morap_server *S, int64_t ticket, morap_point_result *res) {
+    if (!S || !res) return fail(MORAP_EINVAL, "poll: null argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto itq = S->queries.find(ticket);
+    if (itq == S->queries.end()) return fail(MORAP_EINVAL, "poll: unknown ticket");
+    const ServerQuery &q = itq->second;
+    if (!q.ps.done) return MORAP_EBUSY;
+    alg1_result(q.ps, res);
+    return MORAP_OK;
+}
+
+int morap_server_wait(morap_server *S, double timeout_s) {
+    if (!S) return fail(MORAP_EINVAL, "wait: null server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    while (S->completed < S->submitted) {
+        if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout && S->completed < S->submitted)
+            return MORAP_EBUSY;
+    }
+    return MORAP_OK;
+}
+
+int morap_server_stats(morap_server *S, morap_serving_stats *st) {
+    if (!S || !st) return fail(MORAP_EINVAL, "stats: null argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::memset(st, 0, sizeof(*st));
+    st->submitted = S->submitted;
+    st->completed = S->completed;
+    st->batches = S->batches;
+    st->mean_batch = S->batches ? (double)S->batch_queries / (double)S->batches : 0.0;
+    std::vector<double> l = S->latencies_ms;
+    if (!l.empty()) {
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double q) { return l[std::min(l.size() - 1, (size_t)std::floor(q * (l.size() - 1) + 0.5))]; };
+        st->p50_ms = pct(0.50);
+        st->p99_ms = pct(0.99);
+        const double wall = std::chrono::duration<double>(S->t_last - S->t_first).count();
+        st->wall_s = wall;
+        st->queries_per_s = wall > 0 ? (double)S->completed / wall : 0.0;
+    }
+    st->bytes_in_use = S->in_use;
+    return MORAP_OK;
+}
+
+}  // extern "C"

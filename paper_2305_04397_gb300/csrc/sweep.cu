@@ -83,22 +83,60 @@ __device__ __forceinline__ DF df_mul(DF x, DF y) {
 
 __device__ __forceinline__ bool df_gt(DF a, DF b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
 
+__device__ __forceinline__ void cp_async4(void *smem, const void *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(g));
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(g));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Per-warp staging capacity: up to kStageStates states whose rows and
+// transitions fit AMAX / EMAX entries are copied to shared memory per batch.
+constexpr int kStageStates = 32;  // states per batch (at most; fewer when the rows do not fit)
+
 struct ArithF32 {
     using Val = float;
-    using W = float2;    // (w_i rounded up, w_p rounded down)
+    static constexpr int AMAX = 192, EMAX = 448;
+    // ssa[kStageStates + 1] | str[AMAX + 1] | cost[AMAX] | edge[EMAX] (int2)
+    static constexpr int OFF_STR = 136, OFF_COST = OFF_STR + 4 * (AMAX + 2), OFF_EDGE = OFF_COST + 4 * AMAX;
+    static constexpr int STAGE_BYTES = OFF_EDGE + 8 * EMAX;
+    struct View {
+        const uint32_t *str;
+        const float *cost;
+        const int2 *edge;
+    };
+    static __device__ __forceinline__ View smem_view(unsigned char *b) {
+        return {reinterpret_cast<const uint32_t *>(b + OFF_STR), reinterpret_cast<const float *>(b + OFF_COST),
+                reinterpret_cast<const int2 *>(b + OFF_EDGE)};
+    }
+    static __device__ __forceinline__ View global_view(const SweepArgs &a, uint32_t A0, uint32_t T0) {
+        return {a.sa_tr + A0, a.cost32 + A0, a.cp32 + T0};
+    }
+    static __device__ __forceinline__ void stage(const SweepArgs &a, unsigned char *b, uint32_t A0, uint32_t nA,
+                                                 uint32_t T0, uint32_t nT, int lane) {
+        uint32_t *str = reinterpret_cast<uint32_t *>(b + OFF_STR);
+        float *cost = reinterpret_cast<float *>(b + OFF_COST);
+        int2 *edge = reinterpret_cast<int2 *>(b + OFF_EDGE);
+        for (uint32_t i = lane; i <= nA; i += 32) cp_async4(str + i, a.sa_tr + A0 + i);
+        for (uint32_t i = lane; i < nA; i += 32) cp_async4(cost + i, a.cost32 + A0 + i);
+        for (uint32_t i = lane; i < nT; i += 32) cp_async8(edge + i, a.cp32 + T0 + i);
+    }
+    using W = float2;    // (-w_i rounded away from zero, w_p rounded down)
     using Cost = float;  // rounded up
     using Prob = float;  // rounded down
     static constexpr int WORDS = 1;
     static __device__ __forceinline__ W weight(const SweepArgs &a, size_t pair) { return a.w32[pair]; }
-    static __device__ __forceinline__ Cost cost(const SweepArgs &a, uint32_t sa) { return __ldg(a.cost32 + sa); }
-    static __device__ __forceinline__ void edge(const SweepArgs &a, uint32_t t, int32_t &c, Prob &p) {
-        const int2 e = __ldg(a.cp32 + t);
+    static __device__ __forceinline__ Cost cost(const View &v, uint32_t la) { return v.cost[la]; }
+    static __device__ __forceinline__ void edge(const View &v, uint32_t lt, int32_t &c, Prob &p) {
+        const int2 e = v.edge[lt];
         c = e.x;
         p = __int_as_float(e.y);
     }
-    static __device__ __forceinline__ Val reward(W w, Cost c, bool pre) {
-        return __fsub_rd(pre ? w.y : 0.0f, __fmul_ru(w.x, c));
-    }
+    // rd(base - w_i' c) with w_i' >= w_i: one FMA, a lower bound of the reward
+    static __device__ __forceinline__ Val reward(W w, Cost c, bool pre) { return __fmaf_rd(w.x, c, pre ? w.y : 0.0f); }
     static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) { acc = __fmaf_rd(p, v, acc); }
     static __device__ __forceinline__ void close(Val &) {}
     static __device__ __forceinline__ bool gt(Val a, Val b) { return a > b; }
@@ -119,18 +157,49 @@ struct ArithF32 {
 
 struct ArithDF {
     using Val = DF;
+    static constexpr int AMAX = 192, EMAX = 448;
+    // ssa | str[AMAX + 1] | cost[AMAX] (float2) | col[EMAX] | p[EMAX] (float2)
+    static constexpr int OFF_STR = 136, OFF_COST = OFF_STR + 4 * (AMAX + 2), OFF_COL = OFF_COST + 8 * AMAX,
+                         OFF_P = OFF_COL + 4 * EMAX;
+    static constexpr int STAGE_BYTES = OFF_P + 8 * EMAX;
+    struct View {
+        const uint32_t *str;
+        const float2 *cost;
+        const int32_t *col;
+        const float2 *p;
+    };
+    static __device__ __forceinline__ View smem_view(unsigned char *b) {
+        return {reinterpret_cast<const uint32_t *>(b + OFF_STR), reinterpret_cast<const float2 *>(b + OFF_COST),
+                reinterpret_cast<const int32_t *>(b + OFF_COL), reinterpret_cast<const float2 *>(b + OFF_P)};
+    }
+    static __device__ __forceinline__ View global_view(const SweepArgs &a, uint32_t A0, uint32_t T0) {
+        return {a.sa_tr + A0, a.costdf + A0, a.col + T0, a.pdf + T0};
+    }
+    static __device__ __forceinline__ void stage(const SweepArgs &a, unsigned char *b, uint32_t A0, uint32_t nA,
+                                                 uint32_t T0, uint32_t nT, int lane) {
+        uint32_t *str = reinterpret_cast<uint32_t *>(b + OFF_STR);
+        float2 *cost = reinterpret_cast<float2 *>(b + OFF_COST);
+        int32_t *col = reinterpret_cast<int32_t *>(b + OFF_COL);
+        float2 *p = reinterpret_cast<float2 *>(b + OFF_P);
+        for (uint32_t i = lane; i <= nA; i += 32) cp_async4(str + i, a.sa_tr + A0 + i);
+        for (uint32_t i = lane; i < nA; i += 32) cp_async8(cost + i, a.costdf + A0 + i);
+        for (uint32_t i = lane; i < nT; i += 32) {
+            cp_async4(col + i, a.col + T0 + i);
+            cp_async8(p + i, a.pdf + T0 + i);
+        }
+    }
     using W = float4;    // (w_i.h, w_i.l, w_p.h, w_p.l)
     using Cost = DF;
     using Prob = DF;
     static constexpr int WORDS = 2;
     static __device__ __forceinline__ W weight(const SweepArgs &a, size_t pair) { return a.wdf[pair]; }
-    static __device__ __forceinline__ Cost cost(const SweepArgs &a, uint32_t sa) {
-        const float2 c = __ldg(a.costdf + sa);
+    static __device__ __forceinline__ Cost cost(const View &v, uint32_t la) {
+        const float2 c = v.cost[la];
         return {c.x, c.y};
     }
-    static __device__ __forceinline__ void edge(const SweepArgs &a, uint32_t t, int32_t &c, Prob &p) {
-        c = __ldg(a.col + t);
-        const float2 q = __ldg(a.pdf + t);
+    static __device__ __forceinline__ void edge(const View &v, uint32_t lt, int32_t &c, Prob &p) {
+        c = v.col[lt];
+        const float2 q = v.p[lt];
         p = {q.x, q.y};
     }
     static __device__ __forceinline__ Val reward(W w, Cost c, bool pre) {
@@ -193,10 +262,28 @@ __device__ __forceinline__ void store_words(float *p, const float (&w)[NW]) {
     }
 }
 
+// Weights per lane (FP32 / double-float phase) and the minimum resident
+// blocks the register allocation is sized for.
+#ifndef MORAP_VMAX_F32
+#define MORAP_VMAX_F32 8
+#endif
+#ifndef MORAP_VMAX_DF
+#define MORAP_VMAX_DF 4
+#endif
+#ifndef MORAP_SWEEP_MIN_BLOCKS
+#define MORAP_SWEEP_MIN_BLOCKS 2
+#endif
+#ifndef MORAP_GATHER_D
+#define MORAP_GATHER_D 4
+#endif
+#ifndef MORAP_GATHER_D_WIDE
+#define MORAP_GATHER_D_WIDE 3
+#endif
+
 // Lanes per state and weights per lane for each (format, Kp).
 template <class Ar, int KP>
 struct Shape {
-    static constexpr int VMAX = Ar::WORDS == 1 ? 8 : 4;  // weights per lane
+    static constexpr int VMAX = Ar::WORDS == 1 ? MORAP_VMAX_F32 : MORAP_VMAX_DF;  // weights per lane
     static constexpr int VEC = KP < VMAX ? KP : VMAX;
     static constexpr int LPS = KP / VEC;                  // lanes per state (<= 32)
     static constexpr int SPW = 32 / LPS;                  // states per warp round
@@ -229,19 +316,105 @@ __device__ __forceinline__ Vec<T, VEC> vload(const T *p) {
 // ------------------------------------------------------------- the sweep
 //
 // Work items are 128-state ranges of one product taken by whole warps
-// (dynamic scheduling, no block barriers).  Inside a warp, LPS lanes share a
-// state and each lane owns VEC of the Kp weights, so a successor's value row
-// is read once, coalesced, for all weights.  Each lane consumes its state's
+// (dynamic scheduling, no block barriers).  A warp walks its item in
+// batches: it copies the batch's state starts, action-row starts, costs and
+// (successor, probability) stream into its own shared-memory buffer with
+// cp.async (one coalesced round trip per batch instead of one per
+// transition), then computes.  Inside the batch, LPS lanes share a state and
+// each lane owns VEC of the Kp weights, so a successor's value row is read
+// once, coalesced, for all weights; each lane consumes its state's
 // transitions as one stream across the actions, issuing kGatherBatch
-// independent gathers before it consumes them.
+// independent value gathers before it consumes them.
 template <class Ar, int KP>
-__global__ void __launch_bounds__(kThreads, 3) k_sweep(SweepArgs a, int pos) {
+__device__ __forceinline__ void process_state(const SweepArgs &a, const typename Ar::View &vw, const uint32_t *ssa,
+                                              uint32_t A0, uint32_t T0, int i, uint32_t u, bool pre,
+                                              const typename Ar::W *__restrict__ sw, const unsigned int act_bits,
+                                              const float *__restrict__ Vold, float *__restrict__ Vnew, int k0,
+                                              float (&rmax)[Shape<Ar, KP>::VEC]) {
     using Val = typename Ar::Val;
     using SH = Shape<Ar, KP>;
+    constexpr int VEC = SH::VEC;
+    constexpr int NW = VEC * Ar::WORDS;
+    constexpr int ROW = KP * Ar::WORDS;
+    constexpr int D = NW >= 8 ? MORAP_GATHER_D_WIDE : MORAP_GATHER_D;  // gathers in flight within one action
+    const size_t row = (size_t)u * ROW + (size_t)k0 * Ar::WORDS;
+    const uint32_t la0 = ssa[i] - A0, la1 = ssa[i + 1] - A0;
+    Val best[VEC];
+    uint32_t best_a[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+        best[v] = Ar::neg_inf();
+        best_a[v] = 0u;
+    }
+    uint32_t t0 = vw.str[la0] - T0;
+    // Actions are the outer loop: every lane closes an action at the same
+    // point of the instruction stream, whatever its transition counts.
+    for (uint32_t la = la0; la < la1; ++la) {
+        const uint32_t t1 = vw.str[la + 1] - T0;
+        Val acc[VEC];
+        {
+            const typename Ar::Cost c = Ar::cost(vw, la);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c, pre);
+        }
+        for (uint32_t base = t0; base < t1; base += D) {
+            int32_t cl[D];
+            typename Ar::Prob pr[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                if (base + j < t1) {
+                    Ar::edge(vw, base + j, cl[j], pr[j]);
+                } else {
+                    cl[j] = -1;
+                }
+            }
+            float gw[D][NW];
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                if (cl[j] >= 0) load_words<NW>(Vold + (size_t)cl[j] * ROW + (size_t)k0 * Ar::WORDS, gw[j]);
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                if (cl[j] < 0) continue;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], pr[j], Ar::from_words(&gw[j][v * Ar::WORDS]));
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            Ar::close(acc[v]);
+            const bool better = Ar::gt(acc[v], best[v]);
+            best[v] = better ? acc[v] : best[v];
+            best_a[v] = better ? la - la0 : best_a[v];
+        }
+        t0 = t1;
+    }
+    float yw[NW];
+    load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+        if (!((act_bits >> v) & 1u)) continue;
+        const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
+        rmax[v] = d > rmax[v] ? d : rmax[v];
+        if (d > Ar::record_threshold(best[v], a.eps1)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
+        Ar::to_words(best[v], &yw[v * Ar::WORDS]);
+    }
+    store_words<NW>(Vnew + row, yw);
+}
+
+// Work items are 128-state ranges of one product taken by whole warps
+// (dynamic scheduling, no block barriers), walked in batches of up to 32
+// states: the warp copies the batch's state starts, action-row starts, costs
+// and (successor, probability) stream into its own shared-memory buffer with
+// cp.async, then computes.  Inside a batch, LPS lanes share a state and each
+// lane owns VEC of the Kp weights, so a successor's value row is read once,
+// coalesced, for all weights.
+template <class Ar, int KP>
+__global__ void __launch_bounds__(kThreads, MORAP_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs a, int pos) {
+    using SH = Shape<Ar, KP>;
     constexpr int VEC = SH::VEC, LPS = SH::LPS, SPW = SH::SPW;
-    constexpr int NW = VEC * Ar::WORDS;      // 32-bit words a lane moves per state row
-    constexpr int D = NW >= 8 ? kGatherBatch / 2 : kGatherBatch;  // keep the batch within registers
-    constexpr int ROW = KP * Ar::WORDS;      // words per state row
+    constexpr int NW = VEC * Ar::WORDS;
+    constexpr int ROW = KP * Ar::WORDS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int cur = pos % 3, nxt = (pos + 1) % 3, far = (pos + 2) % 3;
     const float *__restrict__ Vold = static_cast<const float *>(a.V[pos & 1]);
     float *__restrict__ Vnew = static_cast<float *>(a.V[(pos + 1) & 1]);
@@ -257,6 +430,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(SweepArgs a, int pos) {
     const unsigned int sweep = ctl->sweep_base + pos;
     const int lane = threadIdx.x & 31;
     const int grp = lane / LPS, li = lane % LPS, k0 = li * VEC;
+    unsigned char *warp_buf = smem_raw + (threadIdx.x >> 5) * (Ar::STAGE_BYTES + KP * (int)sizeof(typename Ar::W));
+    unsigned char *stage_buf = warp_buf;
+    uint32_t *ssa = reinterpret_cast<uint32_t *>(stage_buf);
+    typename Ar::W *wsm = reinterpret_cast<typename Ar::W *>(warp_buf + Ar::STAGE_BYTES);  // the item's weights
 
     for (;;) {
         unsigned int it = 0;
@@ -300,99 +477,58 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(SweepArgs a, int pos) {
                 else
                     a.frozen[pair0 + k] = 1;
             }
-        bool act[VEC];
-        typename Ar::W w[VEC];
+        unsigned int act_bits = 0u;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
             const int k = k0 + v;
-            act[v] = ((act_w[k >> 5] >> (k & 31)) & 1u) != 0u;
-            w[v] = Ar::weight(a, pair0 + k);
+            act_bits |= ((act_w[k >> 5] >> (k & 31)) & 1u) << v;
         }
+        for (int k = lane; k < KP; k += 32) wsm[k] = Ar::weight(a, pair0 + k);
+        __syncwarp();
         float rmax[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) rmax[v] = 0.0f;
 
-        for (int s = ch.y + grp; s < ch.z; s += SPW) {
-            const uint32_t u = pd.state_off + (uint32_t)s;
-            const size_t row = (size_t)u * ROW + (size_t)k0 * Ar::WORDS;
-            float yw[NW];
-            if (!any_active) {  // every weight of the product froze: copy the row
+        if (!any_active) {  // every weight of the product froze: copy its rows once
+            for (int s = ch.y + grp; s < ch.z; s += SPW) {
+                const size_t row = (size_t)(pd.state_off + (uint32_t)s) * ROW + (size_t)k0 * Ar::WORDS;
+                float yw[NW];
                 load_words<NW>(Vold + row, yw);
                 store_words<NW>(Vnew + row, yw);
-                continue;
             }
-            const bool pre = (uint32_t)s >= pd.pre_begin;
-            const uint32_t a0 = __ldg(a.state_sa + u), a1 = __ldg(a.state_sa + u + 1);
-            const uint32_t te = __ldg(a.sa_tr + a1);
-            Val best[VEC], acc[VEC];
-            uint32_t best_a[(VEC + 3) / 4];  // recorded-action candidates, 8 bits per weight
-            uint32_t sa = a0, bound = __ldg(a.sa_tr + a0 + 1);
-            {
-                const typename Ar::Cost c0 = Ar::cost(a, a0);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    best[v] = Ar::neg_inf();
-                    acc[v] = Ar::reward(w[v], c0, pre);
+        } else {
+            for (int s0 = ch.y; s0 < ch.z;) {
+                const int m_max = min(kStageStates, ch.z - s0);
+                const uint32_t u0 = pd.state_off + (uint32_t)s0;
+                uint32_t my_sa = 0, my_tr = 0;
+                if (lane <= m_max) {
+                    my_sa = __ldg(a.state_sa + u0 + lane);
+                    my_tr = __ldg(a.state_tr + u0 + lane);
                 }
-#pragma unroll
-                for (int i = 0; i < (VEC + 3) / 4; ++i) best_a[i] = 0u;
-            }
-            for (uint32_t base = __ldg(a.sa_tr + a0); base < te; base += D) {
-                int32_t cl[D];
-                typename Ar::Prob pr[D];
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    if (base + i < te) {
-                        Ar::edge(a, base + i, cl[i], pr[i]);
-                    } else {
-                        cl[i] = -1;
-                    }
+                const uint32_t A0 = __shfl_sync(0xffffffffu, my_sa, 0);
+                const uint32_t T0 = __shfl_sync(0xffffffffu, my_tr, 0);
+                const bool fits = lane <= m_max && my_sa - A0 <= (uint32_t)Ar::AMAX && my_tr - T0 <= (uint32_t)Ar::EMAX;
+                int m = __popc(__ballot_sync(0xffffffffu, fits)) - 1;  // boundaries 0..m fit
+                const bool staged = m >= 1;
+                if (!staged) m = 1;  // one state too large for the buffer: read it from global memory
+                const uint32_t A1 = __shfl_sync(0xffffffffu, my_sa, m);
+                const uint32_t T1 = __shfl_sync(0xffffffffu, my_tr, m);
+                if (lane <= m) ssa[lane] = my_sa;
+                typename Ar::View vw;
+                if (staged) {
+                    Ar::stage(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
+                    cp_async_wait_all();
+                    vw = Ar::smem_view(stage_buf);
+                } else {
+                    vw = Ar::global_view(a, A0, T0);
                 }
-                float gw[D][NW];
-#pragma unroll
-                for (int i = 0; i < D; ++i)
-                    if (cl[i] >= 0) load_words<NW>(Vold + (size_t)cl[i] * ROW + (size_t)k0 * Ar::WORDS, gw[i]);
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    if (cl[i] < 0) continue;
-                    while (base + i >= bound) {  // close action sa, open the next one
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            Ar::close(acc[v]);
-                            if (Ar::gt(acc[v], best[v])) {
-                                best[v] = acc[v];
-                                best_a[v / 4] = (best_a[v / 4] & ~(0xFFu << (8 * (v % 4)))) | ((sa - a0) << (8 * (v % 4)));
-                            }
-                        }
-                        ++sa;
-                        bound = __ldg(a.sa_tr + sa + 1);
-                        const typename Ar::Cost cs = Ar::cost(a, sa);
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(w[v], cs, pre);
-                    }
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], pr[i], Ar::from_words(&gw[i][v * Ar::WORDS]));
-                }
+                __syncwarp();
+                for (int i = grp; i < m; i += SPW)
+                    process_state<Ar, KP>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i, (uint32_t)(s0 + i) >= pd.pre_begin,
+                                          wsm + k0, act_bits, Vold, Vnew, k0, rmax);
+                __syncwarp();  // the next batch reuses the buffer
+                s0 += m;
             }
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                Ar::close(acc[v]);
-                if (Ar::gt(acc[v], best[v])) {
-                    best[v] = acc[v];
-                    best_a[v / 4] = (best_a[v / 4] & ~(0xFFu << (8 * (v % 4)))) | ((sa - a0) << (8 * (v % 4)));
-                }
-            }
-            load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                if (!act[v]) continue;
-                const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
-                rmax[v] = d > rmax[v] ? d : rmax[v];
-                if (d > Ar::record_threshold(best[v], a.eps1))
-                    a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)(best_a[v / 4] >> (8 * (v % 4)));
-                Ar::to_words(best[v], &yw[v * Ar::WORDS]);
-            }
-            store_words<NW>(Vnew + row, yw);
         }
         // residual: lanes with the same li share weights
 #pragma unroll
@@ -408,11 +544,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(SweepArgs a, int pos) {
             unsigned long long bytes = 2ull * n_s * ROW * 4;
             if (any_active) {
                 const uint32_t sa0 = a.state_sa[u0], sa1 = a.state_sa[u1];
-                const uint32_t tr0 = a.sa_tr[sa0], tr1 = a.sa_tr[sa1];
+                const uint32_t tr0 = a.state_tr[u0], tr1 = a.state_tr[u1];
                 const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
                 atomicAdd(&ctl->updates, (unsigned long long)(tr1 - tr0) * (unsigned long long)n_act);
-                // state_sa, sa_tr, cost and (col, p) per transition, 4 bytes per word
-                bytes += 4ull * (n_s + 1) + 4ull * (sa1 - sa0 + 1) + 4ull * Ar::WORDS * (sa1 - sa0) +
+                // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
+                bytes += 8ull * (n_s + 1) + 4ull * (sa1 - sa0 + 1) + 4ull * Ar::WORDS * (sa1 - sa0) +
                          4ull * (1 + Ar::WORDS) * (tr1 - tr0);
             }
             atomicAdd(&ctl->bytes, bytes);
@@ -501,7 +637,36 @@ __global__ void __launch_bounds__(kThreads) k_finalize(SweepArgs a, int n_chunks
 
 // ------------------------------------------------------------- evaluation
 // Algorithm 4 for both objectives of a pair at once: E[u] = (cost, prob)
-// with y = (-cost(u, mu(u)), pre(u)) + sum p E[u'].
+// with y = (-cost(u, mu(u)), pre(u)) + sum p E[u'].  The scheduler's rows
+// are first gathered into a compact structure-of-arrays layout with a fixed
+// number of slots per state, so a sweep reads independent coalesced words
+// instead of chasing scheduler -> state -> row -> transition pointers.
+__global__ void __launch_bounds__(kThreads) k_eval_compact(EvalArgs a, int n_chunks) {
+    for (int item = blockIdx.x; item < n_chunks; item += gridDim.x) {
+        const int4 ch = a.chunks[item];
+        const int4 pr = a.pairs[ch.x];
+        const ProdDesc pd = a.prods[pr.x];
+        const uint32_t n1 = pd.n_nd + 1;
+        const size_t off = (size_t)pr.z;
+        const int s = ch.y + threadIdx.x;
+        if (s >= ch.z) continue;
+        const uint32_t u = pd.state_off + (uint32_t)s;
+        const uint32_t sa = a.state_sa[u] + a.policy[(size_t)u * a.Kp + pr.y];
+        const uint32_t t0 = a.sa_tr[sa], t1 = a.sa_tr[sa + 1];
+        a.ecost[off + s] = a.cost64[sa];
+        for (int j = 0; j < a.stride; ++j) {
+            const size_t at = off * a.stride + (size_t)j * n1 + s;
+            if (t0 + j < t1) {
+                a.ecol[at] = a.col[t0 + j] - (int32_t)pd.state_off;
+                a.ep[at] = a.p64[t0 + j];
+            } else {
+                a.ecol[at] = (int32_t)pd.n_nd;
+                a.ep[at] = 0.0;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
     const int cur = pos % 3, nxt = (pos + 1) % 3, far = (pos + 2) % 3;
     const double2 *__restrict__ Eold = a.E[pos & 1];
@@ -515,7 +680,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
     const unsigned int sweep = ctl->sweep_base + pos;
     __shared__ unsigned int s_item;
     __shared__ double s_red[kThreads / 32];
-    __shared__ unsigned int s_nt[kThreads / 32];
+    const int stride = a.stride;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&ctl->next[cur], 1u);
         __syncthreads();
@@ -545,25 +710,40 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
                 a.frozen[e] = 1;
         }
         double r = 0.0;
-        unsigned int n_t = 0;
         const int s = ch.y + threadIdx.x;
+        const size_t off = (size_t)pr.z;
+        const uint32_t n1 = pd.n_nd + 1;
         if (s < ch.z) {
-            const size_t off = (size_t)pr.z;
             const double2 x = Eold[off + s];
             double2 y = x;
             if (active) {
-                const uint32_t u = pd.state_off + (uint32_t)s;
-                const uint32_t sa = a.state_sa[u] + a.policy[(size_t)u * a.Kp + pr.y];
-                double yc = -a.cost64[sa];
+                double yc = -a.ecost[off + s];
                 double yp = ((uint32_t)s >= pd.pre_begin) ? 1.0 : 0.0;
-                const uint32_t t0 = a.sa_tr[sa], t1 = a.sa_tr[sa + 1];
-                n_t = t1 - t0;
-                for (uint32_t t = t0; t < t1; ++t) {
-                    const uint32_t loc = (uint32_t)a.col[t] - pd.state_off;
-                    const double p = a.p64[t];
-                    const double2 xv = Eold[off + loc];
-                    yc = fma(p, xv.x, yc);
-                    yp = fma(p, xv.y, yp);
+                const size_t base = off * stride + s;
+                int j = 0;
+                for (; j + 4 <= stride; j += 4) {
+                    int32_t c[4];
+                    double p[4];
+                    double2 v[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        c[q] = a.ecol[base + (size_t)(j + q) * n1];
+                        p[q] = a.ep[base + (size_t)(j + q) * n1];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v[q] = Eold[off + c[q]];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        yc = fma(p[q], v[q].x, yc);
+                        yp = fma(p[q], v[q].y, yp);
+                    }
+                }
+                for (; j < stride; ++j) {
+                    const int32_t c = a.ecol[base + (size_t)j * n1];
+                    const double p = a.ep[base + (size_t)j * n1];
+                    const double2 v = Eold[off + c];
+                    yc = fma(p, v.x, yc);
+                    yp = fma(p, v.y, yp);
                 }
                 y = make_double2(yc, yp);
                 r = fmax(fabs(yc - x.x), fabs(yp - x.y));
@@ -571,31 +751,20 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
             Enew[off + s] = y;
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            r = fmax(r, __shfl_xor_sync(0xffffffffu, r, off));
-            n_t += __shfl_xor_sync(0xffffffffu, n_t, off);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            s_red[threadIdx.x / 32] = r;
-            s_nt[threadIdx.x / 32] = n_t;
-        }
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x / 32] = r;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double m = 0.0;
-            unsigned long long nt = 0;
-            for (int wi = 0; wi < kThreads / 32; ++wi) {
-                m = fmax(m, s_red[wi]);
-                nt += s_nt[wi];
-            }
-            if (active && m > 0.0) atomic_max_nonneg(a.res[cur] + e, m);
+            double mx = 0.0;
+            for (int wi = 0; wi < kThreads / 32; ++wi) mx = fmax(mx, s_red[wi]);
+            if (active && mx > 0.0) atomic_max_nonneg(a.res[cur] + e, mx);
             const unsigned long long n_s = (unsigned long long)(ch.z - ch.y);
-            // values: read + write 16 B per state; when computing also the
-            // policy byte, state_sa and sa_tr (4 + 8), the cost (8) and the
-            // policy row's transitions (col 4 + p 8 each)
+            // values read + written (16 B each); when computing also the cost
+            // (8) and every slot's successor and probability (4 + 8)
             unsigned long long bytes = n_s * 32ull;
             if (active) {
-                bytes += n_s * (1 + 4 + 8 + 8) + nt * 12ull;
-                atomicAdd(&ctl->updates, nt * 2ull);
+                bytes += n_s * (8ull + 12ull * (unsigned long long)stride);
+                atomicAdd(&ctl->updates, n_s * (unsigned long long)stride * 2ull);
             }
             atomicAdd(&ctl->bytes, bytes);
         }
@@ -622,7 +791,7 @@ __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, in
             wp = W[(size_t)k * (nI + nJ) + nI + pd.task];
         }
         w64[idx] = make_double2(wi, wp);
-        w32[idx] = make_float2(__double2float_ru(wi), __double2float_rd(wp));
+        w32[idx] = make_float2(-__double2float_ru(wi), __double2float_rd(wp));
         const float2 a = to_df(wi), b = to_df(wp);
         wdf[idx] = make_float4(a.x, a.y, b.x, b.y);
         // FP32 phase: stop once the residual is within a few ulps of the
@@ -718,18 +887,38 @@ __global__ void k_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *pr
 }
 
 template <class Ar>
+constexpr int smem_of() {
+    return (kThreads / 32) * (Ar::STAGE_BYTES + 64 * (int)sizeof(typename Ar::W));  // sized for the largest Kp
+}
+
+template <class Ar>
 int launch_sweep_t(int Kp, const SweepArgs &a, int pos, int grid, cudaStream_t s) {
+    constexpr int sm = smem_of<Ar>();
     switch (Kp) {
-    case 1: k_sweep<Ar, 1><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 2: k_sweep<Ar, 2><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 4: k_sweep<Ar, 4><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 8: k_sweep<Ar, 8><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 16: k_sweep<Ar, 16><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 32: k_sweep<Ar, 32><<<grid, kThreads, 0, s>>>(a, pos); break;
-    case 64: k_sweep<Ar, 64><<<grid, kThreads, 0, s>>>(a, pos); break;
+    case 1: k_sweep<Ar, 1><<<grid, kThreads, sm, s>>>(a, pos); break;
+    case 2: k_sweep<Ar, 2><<<grid, kThreads, sm, s>>>(a, pos); break;
+    case 4: k_sweep<Ar, 4><<<grid, kThreads, sm, s>>>(a, pos); break;
+    case 8: k_sweep<Ar, 8><<<grid, kThreads, sm, s>>>(a, pos); break;
+    case 16: k_sweep<Ar, 16><<<grid, kThreads, sm, s>>>(a, pos); break;
+    case 32: k_sweep<Ar, 32><<<grid, kThreads, sm, s>>>(a, pos); break;
+    case 64: k_sweep<Ar, 64><<<grid, kThreads, sm, s>>>(a, pos); break;
     default: return (int)cudaErrorInvalidValue;
     }
     return (int)cudaGetLastError();
+}
+
+template <class Ar>
+cudaError_t set_attr_t() {
+    constexpr int sm = smem_of<Ar>();
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
 }
 
 }  // namespace
@@ -738,14 +927,15 @@ template <class Ar>
 int blocks_per_sm_t(int Kp) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
+    constexpr int sm = smem_of<Ar>();
     switch (Kp) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 1>, kThreads, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 2>, kThreads, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 4>, kThreads, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 8>, kThreads, 0); break;
-    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 16>, kThreads, 0); break;
-    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 32>, kThreads, 0); break;
-    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 64>, kThreads, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 1>, kThreads, sm); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 2>, kThreads, sm); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 4>, kThreads, sm); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 8>, kThreads, sm); break;
+    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 16>, kThreads, sm); break;
+    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 32>, kThreads, sm); break;
+    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 64>, kThreads, sm); break;
     default: break;
     }
     if (e != cudaSuccess) {
@@ -754,6 +944,14 @@ int blocks_per_sm_t(int Kp) {
     }
     return n > 0 ? n : 1;
 }
+
+int sweep_setup_attributes() {
+    cudaError_t e = set_attr_t<ArithF32>();
+    if (e == cudaSuccess) e = set_attr_t<ArithDF>();
+    return (int)e;
+}
+
+int sweep_smem_bytes(bool fp64) { return fp64 ? smem_of<ArithDF>() : smem_of<ArithF32>(); }
 
 int sweep_blocks_per_sm(bool fp64, int Kp) { return fp64 ? blocks_per_sm_t<ArithDF>(Kp) : blocks_per_sm_t<ArithF32>(Kp); }
 
@@ -785,6 +983,12 @@ int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_
     case 64: k_finalize<64><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy); break;
     default: return (int)cudaErrorInvalidValue;
     }
+    return (int)cudaGetLastError();
+}
+
+int launch_eval_compact(const EvalArgs &a, int n_chunks, void *s) {
+    if (n_chunks <= 0) return 0;
+    k_eval_compact<<<n_chunks < 65535 ? n_chunks : 65535, kThreads, 0, (cudaStream_t)s>>>(a, n_chunks);
     return (int)cudaGetLastError();
 }
 

@@ -71,6 +71,20 @@ class SolveStats(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("n_workers", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("queries_per_s", ctypes.c_double), ("wall_s", ctypes.c_double), ("bytes_in_use", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class PointResult(ctypes.Structure):
     _fields_ = [
         ("feasible", ctypes.c_int32), ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
@@ -104,6 +118,14 @@ _SIGS = {
     "morap_solve_plain": (ctypes.c_int, [_P, ctypes.c_int32, _I32P, _DP, _P, _DP, _DP, _DP, _DP]),
     "morap_query": (ctypes.c_int, [_P, _DP, _DP, ctypes.c_double, ctypes.c_int32, _P, ctypes.POINTER(PointResult)]),
     "morap_assign_max": (ctypes.c_int, [ctypes.c_int32, _DP, _I32P]),
+    "morap_assign_tasks": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _DP, _I32P]),
+    "morap_evaluate": (ctypes.c_int, [_P, ctypes.c_int32, _I32P, _I32P, _P, _DP, _DP]),
+    "morap_pareto_create": (ctypes.c_int, [ctypes.c_int32, _DP, _DP, ctypes.c_double, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "morap_pareto_next": (ctypes.c_int, [_P, _DP, _I32P]),
+    "morap_pareto_step": (ctypes.c_int, [_P, _DP, ctypes.c_int32]),
+    "morap_pareto_result": (ctypes.c_int, [_P, ctypes.POINTER(PointResult)]),
+    "morap_pareto_destroy": (None, [_P]),
     "morap_project_halfspaces": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _DP, _DP, _DP, _DP, _DP]),
     "morap_project_down_hull": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _DP, _DP, _DP, _DP]),
     "morap_task_preprocess": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _I32P, _U8P, _I32P,
@@ -111,6 +133,14 @@ _SIGS = {
     "morap_product_info": (ctypes.c_int, [_P, ctypes.c_int32, _I64P]),
     "morap_product_download": (ctypes.c_int, [_P, ctypes.c_int32, _I64P, _I64P, _I32P, _DP, _DP, _I32P]),
     "morap_last_policy": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _U8P, _DP]),
+    "morap_server_config_default": (None, [ctypes.POINTER(ServerConfig)]),
+    "morap_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                           ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    "morap_server_destroy": (ctypes.c_int, [_P]),
+    "morap_submit": (ctypes.c_int, [_P, ctypes.c_int32, _DP, ctypes.POINTER(ctypes.c_int64)]),
+    "morap_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(PointResult)]),
+    "morap_server_wait": (ctypes.c_int, [_P, ctypes.c_double]),
+    "morap_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     "morap_plain_vi_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int32, _P, _P, _P, _DP, _I32P]),
@@ -279,6 +309,81 @@ def morap_query(ctx, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True):
             "code": code}
 
 
+class Pareto:
+    """Algorithm 1 fed one supporting point at a time (morap_pareto_*)."""
+
+    def __init__(self, t, M=None, eps=1e-6, max_iter=64):
+        self.t = _arr(t, np.float64)
+        self.n = len(self.t)
+        self.max_iter = int(max_iter)
+        Mm = _arr(M, np.float64) if M is not None else None
+        h = ctypes.c_void_p()
+        _check(lib().morap_pareto_create(self.n, _ptr(self.t, ctypes.c_double), _ptr(Mm, ctypes.c_double),
+                                         float(eps), self.max_iter, ctypes.byref(h)))
+        self.h = h
+
+    def next(self):
+        """The direction w whose supporting point step() needs, or None once the loop stopped."""
+        w = np.zeros(self.n)
+        done = ctypes.c_int32()
+        _check(lib().morap_pareto_next(self.h, _ptr(w, ctypes.c_double), ctypes.byref(done)))
+        return None if done.value else w
+
+    def step(self, r, solve_status=OK):
+        r = _arr(r, np.float64)
+        _check(lib().morap_pareto_step(self.h, _ptr(r, ctypes.c_double), int(solve_status)))
+
+    def result(self):
+        n, it = self.n, self.max_iter
+        t_up, t_dn = np.zeros(n), np.zeros(n)
+        wh, rh = np.zeros((it, n)), np.zeros((it, n))
+        res = PointResult()
+        res.t_up = _ptr(t_up, ctypes.c_double)
+        res.t_down = _ptr(t_dn, ctypes.c_double)
+        res.w_hist = _ptr(wh, ctypes.c_double)
+        res.r_hist = _ptr(rh, ctypes.c_double)
+        code = lib().morap_pareto_result(self.h, ctypes.byref(res))
+        if code not in (OK, ENOTCONV):
+            _check(code)
+        k = res.iterations
+        return {"feasible": bool(res.feasible), "iterations": k, "converged": bool(res.converged),
+                "distance": res.distance, "t_up": t_up, "t_down": t_dn, "w_hist": wh[:k], "r_hist": rh[:k],
+                "code": code}
+
+    def close(self):
+        if self.h:
+            lib().morap_pareto_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def morap_assign_tasks(c):
+    """Algorithm 2's assignment for c[K][|I|][|J|]: [K][|J|] agent per task (-1 = none)."""
+    c = _arr(np.asarray(c, np.float64).reshape((-1,) + np.shape(c)[-2:]), np.float64)
+    K, nI, nJ = c.shape
+    f = np.zeros((K, nJ), np.int32)
+    _check(lib().morap_assign_tasks(nI, nJ, K, _ptr(c, ctypes.c_double), _ptr(f, ctypes.c_int32)))
+    return f
+
+
+def morap_evaluate(ctx, pair_product, pair_weight, stream=None, check=True):
+    """Algorithm 4 for chosen (product, weight-index) pairs of the last solve on ctx."""
+    pp = _arr(pair_product, np.int32)
+    pw = _arr(pair_weight, np.int32)
+    rc = np.zeros(len(pp))
+    rp = np.zeros(len(pp))
+    code = lib().morap_evaluate(ctx, len(pp), _ptr(pp, ctypes.c_int32), _ptr(pw, ctypes.c_int32), _stream(stream),
+                                _ptr(rc, ctypes.c_double), _ptr(rp, ctypes.c_double))
+    if check and code != ENOTCONV:
+        _check(code)
+    return {"r_cost": rc, "r_prob": rp, "code": code}
+
+
 def morap_assign_max(C):
     C = _arr(C, np.float64)
     n = C.shape[0]
@@ -363,6 +468,60 @@ def morap_plain_vi_noalloc(n_states, n_sa, state_sa, sa_tr, col, prob, cost, pre
     if code not in (OK, ENOTCONV):
         _check(code)
     return code, c.value, sw.value
+
+
+class Server:
+    """Continuous-batching query server over built Contexts (morap_server_*)."""
+
+    def __init__(self, contexts, max_batch=64, n_workers=4, eps=1e-6, max_iter=64, hbm_budget=0):
+        cfg = ServerConfig()
+        lib().morap_server_config_default(ctypes.byref(cfg))
+        cfg.max_batch, cfg.n_workers, cfg.eps, cfg.max_iter, cfg.hbm_budget = max_batch, n_workers, eps, max_iter, \
+            hbm_budget
+        self.contexts = list(contexts)
+        self.n_obj = [c.n_agents + c.n_tasks for c in self.contexts]
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        self.h = ctypes.c_void_p()
+        _check(lib().morap_server_create(arr, len(self.contexts), ctypes.byref(cfg), ctypes.byref(self.h)))
+        self.max_iter = max_iter
+
+    def submit(self, instance, t):
+        t = _arr(t, np.float64)
+        tk = ctypes.c_int64()
+        _check(lib().morap_submit(self.h, int(instance), _ptr(t, ctypes.c_double), ctypes.byref(tk)))
+        return tk.value
+
+    def poll(self, ticket, instance):
+        n = self.n_obj[instance]
+        t_up, t_dn = np.zeros(n), np.zeros(n)
+        res = PointResult()
+        res.t_up = _ptr(t_up, ctypes.c_double)
+        res.t_down = _ptr(t_dn, ctypes.c_double)
+        code = lib().morap_poll(self.h, int(ticket), ctypes.byref(res))
+        if code == EBUSY:
+            return None
+        _check(code)
+        return {"feasible": bool(res.feasible), "iterations": res.iterations, "converged": bool(res.converged),
+                "distance": res.distance, "t_up": t_up, "t_down": t_dn, "status": res.status}
+
+    def wait(self, timeout_s=600.0):
+        return lib().morap_server_wait(self.h, float(timeout_s))
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().morap_server_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self.h:
+            lib().morap_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- convenience

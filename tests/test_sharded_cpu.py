@@ -1,0 +1,149 @@
+"""The multi-process path (products of one instance sharded by agent over
+ranks, Algorithm 2's c values all-gathered, the assignment replicated, the
+r vectors summed) on CPU: world_size-2 gloo ranks whose per-rank solver is
+the oracle.  The sharded supporting points and the Algorithm 1 loop built on
+them must equal the oracle's unsharded ones on every rank."""
+
+import os
+import socket
+import tempfile
+
+import numpy as np
+import pytest
+
+import instances as I
+from paper_2305_04397_gb300 import sharded as S
+
+
+class OracleShard:
+    """Per-rank work of the sharded driver done by the oracle (one FP64 CPU
+    solve per product and weight)."""
+
+    def __init__(self, agents, tasks, agent_ids):
+        from oracle import core as O
+
+        self.O = O
+        self.agents, self.tasks = agents, tasks
+        self.agent_ids = list(agent_ids)
+        self.n_agents, self.n_tasks = len(agents), len(tasks)
+        self.prods = {(i, j): O.Product(agents[i], tasks[j]) for i in self.agent_ids for j in range(self.n_tasks)}
+        self.last = {}
+
+    def optimise(self, W):
+        W = np.atleast_2d(W)
+        K, nI = W.shape[0], self.n_agents
+        c = np.zeros((K, len(self.agent_ids), self.n_tasks))
+        self.last = {}
+        for k in range(K):
+            for row, i in enumerate(self.agent_ids):
+                for j in range(self.n_tasks):
+                    res = self.O.solve_pair(self.prods[(i, j)], W[k][i], W[k][nI + j])
+                    c[k, row, j] = res["c"]
+                    self.last[(k, i, j)] = (res["r_cost"], res["r_prob"])
+        return c, False
+
+    def evaluate(self, assign):
+        K = assign.shape[0]
+        r = np.zeros((K, self.n_agents + self.n_tasks))
+        for _, k, i, j in S.owned_pairs(assign, self.agent_ids, self.n_tasks):
+            r[k, i], r[k, self.n_agents + j] = self.last[(k, i, j)]
+        return r, False
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inst = I.config_tiny()
+        nI, nJ = len(inst.agents), len(inst.tasks)
+        parts = S.partition_agents(S.agent_loads(inst.agents, inst.tasks), world)
+        shard = OracleShard(inst.agents, inst.tasks, parts[rank])
+        sp = S.ShardedSupportingPoints(shard, parts, nI, nJ, S.TorchComm())
+        out = sp(inst.weights[:3])
+        q = sp.query(inst.thresholds[0], eps=1e-6, max_iter=12)
+        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), r=out["r"], assign=out["assign"], c=out["c"],
+                 t_up=q["t_up"], t_down=q["t_down"], it=q["iterations"], feasible=q["feasible"],
+                 w_hist=q["w_hist"])
+    finally:
+        dist.destroy_process_group()
+
+
+def test_partition_covers_every_agent_once_and_balances():
+    loads = [5.0, 1.0, 7.0, 3.0, 3.0, 2.0, 9.0]
+    for world in (1, 2, 3, 7, 9):
+        parts = S.partition_agents(loads, world)
+        assert len(parts) == world
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(loads)))
+        tot = [sum(loads[i] for i in p) for p in parts]
+        # greedy LPT: no rank exceeds the lightest by more than the largest load
+        assert max(tot) - min(tot) <= max(loads)
+        assert parts == S.partition_agents(loads, world)
+
+
+def test_assemble_and_owned_pairs():
+    ids = [[0, 2], [1]]
+    parts = [np.arange(2 * 2 * 3, dtype=float).reshape(2, 2, 3), 100 + np.arange(2 * 2 * 3).reshape(2, 2, 3)]
+    C = S.assemble_c(parts, ids, 3)
+    assert np.array_equal(C[:, 0], parts[0][:, 0]) and np.array_equal(C[:, 2], parts[0][:, 1])
+    assert np.array_equal(C[:, 1], parts[1][:, 0])  # padded row 1 of rank 1 is ignored
+    assign = np.array([[2, -1, 1], [0, 1, 2]])
+    assert S.owned_pairs(assign, [0, 2], 3) == [(1 * 3 + 0, 0, 2, 0), (0 * 3 + 0, 1, 0, 0), (1 * 3 + 2, 1, 2, 2)]
+    assert S.owned_pairs(assign, [1], 3) == [(0 * 3 + 2, 0, 1, 2), (0 * 3 + 1, 1, 1, 1)]
+
+
+def test_sharded_world2_gloo_matches_unsharded_oracle(oracle_lib):
+    import torch.multiprocessing as mp
+
+    from oracle import core as O
+    from oracle import pareto as OP
+
+    inst = I.config_tiny()
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_rank_main, args=(2, _free_port(), d), nprocs=2, join=True, start_method="spawn")
+        res = [dict(np.load(os.path.join(d, f"rank{r}.npz"))) for r in range(2)]
+    # every rank holds the same numbers
+    for key in res[0]:
+        assert np.array_equal(res[0][key], res[1][key]), key
+    prods = O.products(inst.agents, inst.tasks)
+    for k in range(3):
+        r, f, C, _, _ = O.supporting_point(prods, inst.weights[k])
+        assert np.max(np.abs(res[0]["c"][k] - C)) < 1e-12
+        assert np.array_equal(res[0]["assign"][k], np.where(f < len(inst.agents), f, -1))
+        assert np.max(np.abs(res[0]["r"][k] - r)) < 1e-12
+    ref = OP.alg1(lambda w: O.supporting_point(prods, w)[0], inst.thresholds[0], eps=1e-6, max_iter=12)
+    assert int(res[0]["it"]) == ref["iterations"]
+    assert bool(res[0]["feasible"]) == ref["feasible"]
+    assert np.max(np.abs(res[0]["t_up"] - ref["t_up"])) < 1e-6
+    assert np.max(np.abs(res[0]["t_down"] - ref["t_dn"])) < 1e-6
+
+
+def test_sharded_world1_equals_local_driver(oracle_lib):
+    """One shard with every agent and loop-back collectives gives the oracle's
+    supporting point (the gather / reduce bookkeeping is the identity)."""
+
+    class Loop:
+        def all_gather(self, a):
+            return [a]
+
+        def all_reduce_sum(self, a):
+            return a
+
+    from oracle import core as O
+
+    inst = I.config_tiny()
+    nI, nJ = len(inst.agents), len(inst.tasks)
+    sp = S.ShardedSupportingPoints(OracleShard(inst.agents, inst.tasks, range(nI)), [list(range(nI))], nI, nJ,
+                                   Loop())
+    out = sp(inst.weights[1:2])
+    r, _, _, _, _ = O.supporting_point(O.products(inst.agents, inst.tasks), inst.weights[1])
+    assert np.max(np.abs(out["r"][0] - r)) < 1e-12 and out["code"] == 0
