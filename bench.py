@@ -34,7 +34,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Bellman transition-updates/s & point queries/s: batched FP32 vs plain FP64 GPU VI"
 UNIT = "transition-updates/s"
+WORKLOADS = {
+    # name: (generator, eps_vi)
+    "grid32-10x20-K16": ("config_grid32", 1e-8),
+    "uneven-50x100-K64": ("config_uneven", 1e-6),
+    "large128-20x50-K32": ("config_large", 1e-8),
+}
 WORKLOAD = "grid32-10x20-K16"
+
+
+def make_workload(name, rank=0):
+    import instances as I
+
+    gen, eps = WORKLOADS[name]
+    return getattr(I, gen)(seed={"config_grid32": 1, "config_uneven": 2, "config_large": 3}[gen] + rank), eps
 
 
 def _peaks():
@@ -138,7 +151,7 @@ def _barrier(ws):
 # ---------------------------------------------------------------- oracle arm
 
 
-def _oracle_sample(inst, budget_s, seed=0):
+def _oracle_sample(inst, budget_s, seed=0, eps1=1e-8):
     """Time the oracle (as it stands) on a bounded sample of the workload:
     (product, weight) pairs in a seeded order over all products x weights,
     Algorithm 3 plus both Algorithm 4 evaluations per pair, until budget_s
@@ -161,7 +174,7 @@ def _oracle_sample(inst, budget_s, seed=0):
         if prod is None:
             prod = cache[p] = O.Product(inst.agents[i], inst.tasks[j])
         t0 = time.perf_counter()
-        r = O.solve_pair(prod, W[k][i], W[k][nI + j])
+        r = O.solve_pair(prod, W[k][i], W[k][nI + j], eps1=eps1)
         solve_s += time.perf_counter() - t0
         a = prod.state_ptr[: prod.n - 1] + r["mu"][: prod.n - 1]
         t_mu = int(np.sum(prod.sa_ptr[a + 1] - prod.sa_ptr[a]))
@@ -178,11 +191,11 @@ def run_reference(args):
         return 0
     import instances as I
 
-    inst = I.config_grid32()
+    inst, eps_vi = make_workload(args.workload)
     per_step = []
     samples = []
     for step in range(args.warmup + args.steps):
-        v, pairs, dt = _oracle_sample(inst, args.ref_budget, seed=step)
+        v, pairs, dt = _oracle_sample(inst, args.ref_budget, seed=step, eps1=eps_vi)
         if step >= args.warmup:
             per_step.append((v, pairs, dt))
             samples.append(pairs)
@@ -194,7 +207,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "eps_vi": 1e-8, "eps_eval": 1e-11},
+        "config": {"workload": args.workload, "eps_vi": eps_vi, "eps_eval": 1e-11},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"per step: {samples[0]}.. (product, weight) pairs of the workload, "
                                    f"~{args.ref_budget:.0f} s of single-thread FP64 C oracle work"},
@@ -253,7 +266,7 @@ def run_serving(M, args):
             out.append((i, np.concatenate([-rng.uniform(5.0, 50.0, size=nI), rng.uniform(0.5, 0.99, size=nJ)])))
         return out
 
-    kw = dict(max_batch=64, n_workers=4, eps=1e-6, max_iter=args.serve_max_iter)
+    kw = dict(max_batch=64, n_workers=8, eps=1e-6, max_iter=args.serve_max_iter)
     srv = M.Server(ctxs, **kw)
     for i, t in queries(len(ctxs)):  # warm every instance once
         srv.submit(i, t)
@@ -319,7 +332,7 @@ def run_engine(args):
     from paper_2305_04397_gb300 import morap as M
 
     # weak scaling: every rank solves its own instance of the workload
-    inst = I.config_grid32(seed=1 + rank)
+    inst, eps_vi = make_workload(args.workload, rank)
     nI, nJ = len(inst.agents), len(inst.tasks)
     W = np.ascontiguousarray(inst.weights)
     t_point = inst.thresholds[0]
@@ -327,6 +340,7 @@ def run_engine(args):
     cfg = M.morap_config_default()
     cfg.device = local
     cfg.launch_mode = args.launch_mode
+    cfg.eps_vi = eps_vi
     ctx = M.Context(cfg)
     ctx.add(inst.agents, inst.tasks)
     fp = ctx.build(stream)
@@ -402,7 +416,7 @@ def run_engine(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+df64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "products": nI * nJ, "K": len(W), "states": fp["n_states"],
+        "config": {"workload": args.workload, "products": nI * nJ, "K": len(W), "states": fp["n_states"],
                    "transitions": fp["n_trans"], "eps_vi": cfg.eps_vi, "eps_eval": cfg.eps_eval,
                    "l2": "per-step working set (CSR + FP32/FP64 value buffers) exceeds the 129 MB L2; no flush",
                    "parallelism": f"{ws} independent instance(s), one per GPU"},
@@ -432,7 +446,7 @@ def run_engine(args):
             "speedup_time_to_solution": alg2_ms / (secs * 1e3 / args.steps),
         }
     if rank == 0 and not args.no_cpu:
-        v, pairs, dt = _oracle_sample(inst, args.cpu_budget)
+        v, pairs, dt = _oracle_sample(inst, args.cpu_budget, eps1=eps_vi)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{pairs} (product, weight) pairs, {dt:.1f} s single-thread FP64 C oracle"}
     ctx.close()
@@ -453,6 +467,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD,
+                    help="the 32x32-grid batch (default, the headline), the 5000-product uneven batch or the "
+                         "1000-product 128x128 batch (the latter two take minutes: use --steps 1 --warmup 1)")
     ap.add_argument("--launch-mode", type=int, default=0,
                     help="0: sweep loops as CUDA graphs with a device-side while node; 1: host-driven bodies "
                          "(same kernels; lets ncu list the kernels inside the loops)")

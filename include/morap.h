@@ -81,6 +81,12 @@ typedef struct morap_config {
     morap_alloc_fn alloc;
     morap_free_fn free;
     void *alloc_user;
+    int32_t sweep_variant_fp32; /* kernel shape of the FP32 / double-float sweeps: -1 (default) =   */
+    int32_t sweep_variant_fp64; /* tuned: the first solve with a given padded batch size times the
+                                   first sweeps of every shape and keeps the fastest (instances with
+                                   fewer than 2^24 transition-weights per sweep use shape 0);
+                                   >= 0 forces one (0 .. 3).  Every shape gives bit-identical
+                                   results.                                                         */
 } morap_config;
 
 typedef struct morap_ctx morap_ctx;
@@ -223,7 +229,10 @@ typedef struct morap_solve_stats {
     int64_t h2d_bytes;        /* host->device bytes the call copied                  */
     int64_t d2h_bytes;        /* device->host bytes the call copied                  */
     int32_t kernel_launches;  /* kernels of this library the call launched          */
+    int32_t variant_fp32;     /* kernel shapes the sweeps used (-1: phase not run)  */
+    int32_t variant_fp64;
     int32_t reserved;
+    double ms_tune;           /* host time the context has spent tuning shapes      */
 } morap_solve_stats;
 
 int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out);
@@ -344,7 +353,7 @@ typedef struct morap_server morap_server;
 typedef struct morap_server_config {
     size_t hbm_budget;  /* admission budget in bytes, 0 = none                   */
     int32_t max_batch;  /* queries per instance batch, 1..64 (default 64)        */
-    int32_t n_workers;  /* host threads driving instances (default 4)            */
+    int32_t n_workers;  /* host threads driving instances (default 8)            */
     double eps;         /* Algorithm 1 tolerance of every query (default 1e-6)   */
     int32_t max_iter;   /* supporting points per query (default 64)              */
     int32_t reserved;

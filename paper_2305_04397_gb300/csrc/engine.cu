@@ -66,6 +66,7 @@ struct DevAlloc {
 struct LoopGraph {
     cudaGraphExec_t exec = nullptr;
     int grid = 0;
+    int variant = -1;  // kernel shape of the sweeps (chosen before the graph is built)
 };
 
 struct morap_ctx {
@@ -122,13 +123,15 @@ struct morap_ctx {
     unsigned long long *res[3] = {};
     unsigned int *list[3] = {};
     LoopCtl *ctl = nullptr;  // [3]: FP32, FP64, evaluation
-    LoopGraph g32, g64;
+    LoopGraph g32[7], g64[7];  // per Kp = 1, 2, 4, ..., 64 (log2 index)
+    int Kcap = 0;              // weights per product the solve buffers hold
+    double ms_tune = 0.0;      // host time spent choosing kernel shapes (cumulative)
     SweepArgs args32{}, args64{};
 
     // evaluation buffers (capacity-based)
     std::vector<void *> eval_allocs;
     size_t eval_cap_pairs = 0, eval_cap_chunks = 0, eval_cap_states = 0;
-    double2 *E[2] = {};
+    float4 *E[2] = {};
     int4 *d_epairs = nullptr, *d_echunks = nullptr;
     unsigned long long *eres[3] = {};
     unsigned int *elist[3] = {};
@@ -136,8 +139,9 @@ struct morap_ctx {
     uint8_t *efrozen = nullptr;
     double *d_rc = nullptr, *d_rp = nullptr;
     int32_t *ecol = nullptr;
-    double *ep = nullptr, *ecost = nullptr;
-    LoopGraph geval;
+    float2 *ep = nullptr, *ecost = nullptr;
+    LoopGraph geval[24];  // per grid bucket: min(full grid, 2^b) blocks
+    int eval_full_grid = 0;
     bool eval_ready = false;
     EvalArgs eargs{};
 
@@ -217,14 +221,28 @@ void destroy_graph(LoopGraph &g) {
 }
 
 void free_solve(morap_ctx *c) {
-    destroy_graph(c->g32);
-    destroy_graph(c->g64);
+    for (int i = 0; i < 7; ++i) {
+        destroy_graph(c->g32[i]);
+        destroy_graph(c->g64[i]);
+        c->g32[i].grid = c->g64[i].grid = 0;
+        c->g32[i].variant = c->g64[i].variant = -1;
+    }
     dev_free_list(c, c->solve_allocs);
     c->Kp = 0;
+    c->Kcap = 0;
+}
+
+int log2_of(int Kp) {
+    int l = 0;
+    while ((1 << l) < Kp) ++l;
+    return l;
 }
 
 void free_eval(morap_ctx *c) {
-    destroy_graph(c->geval);
+    for (auto &g : c->geval) {
+        destroy_graph(g);
+        g.grid = 0;
+    }
     c->eval_ready = false;
     dev_free_list(c, c->eval_allocs);
     c->eval_cap_pairs = c->eval_cap_chunks = c->eval_cap_states = 0;
@@ -291,8 +309,87 @@ int run_loop(morap_ctx *c, LoopGraph &g, LoopCtl *ctl, cudaStream_t s, F &&launc
     return MORAP_OK;
 }
 
+// Blocks of a sweep launch with kernel shape v: every co-resident block, but
+// no more than one warp per work item needs.
+int sweep_launch_grid(morap_ctx *c, bool fp64, int Kp, int v) {
+    const size_t useful = (c->h_chunks.size() + kThreads / 32 - 1) / (kThreads / 32);
+    return std::max(1, (int)std::min<size_t>((size_t)sweep_grid(c, sweep_blocks_per_sm(fp64, Kp, v)), useful));
+}
+
+// The tuner: time the first sweeps from V = 0 on the batch's weights with each
+// kernel shape and keep the fastest.  Shapes give bit-identical values, so the
+// choice changes only the speed.  Leaves the phase's buffers dirty; the solve
+// initialises them afterwards.
+int tune_sweep_variant(morap_ctx *c, bool fp64, int Kp, cudaStream_t s, int &best_v) {
+    const SweepArgs a = fp64 ? c->args64 : c->args32;
+    const size_t nv = (size_t)c->TS * Kp, np = (size_t)c->P * Kp;
+    const unsigned int n_items = (unsigned int)c->h_chunks.size();
+    constexpr int kReps = 3;
+    float best = HUGE_VALF;
+    best_v = 0;
+    for (int v = 0; v < sweep_variant_count(fp64); ++v) {
+        const int grid = sweep_launch_grid(c, fp64, Kp, v);
+        CK(cudaMemsetAsync(a.V[0], 0, nv * (fp64 ? sizeof(float2) : sizeof(float)), s));
+        CK(cudaMemsetAsync(a.V[1], 0, nv * (fp64 ? sizeof(float2) : sizeof(float)), s));
+        CKL(launch_loop_init(a.ctl, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, 1u << 30, s));
+        CKL(launch_sweep(fp64, Kp, v, a, 0, grid, s));  // warm-up
+        CK(cudaEventRecord(c->ev[7], s));
+        for (int pos = 1; pos <= kReps; ++pos) CKL(launch_sweep(fp64, Kp, v, a, pos, grid, s));
+        CK(cudaEventRecord(c->ev[0], s));
+        CK(cudaEventSynchronize(c->ev[0]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[7], c->ev[0]));
+        if (ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    return MORAP_OK;
+}
+
+// Choose the kernel shapes for Kp (forced by the config, else tuned on the
+// current weights) and build the loop graphs with them.
+int prepare_loops(morap_ctx *c, int Kp, cudaStream_t s) {
+    LoopGraph *G[2] = {&c->g32[log2_of(Kp)], &c->g64[log2_of(Kp)]};
+    const bool need[2] = {c->V32[0] != nullptr, true};
+    if (G[1]->grid) return MORAP_OK;
+    CKL(sweep_setup_attributes());
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int f = 0; f < 2; ++f) {
+        if (!need[f]) continue;
+        const bool fp64 = f == 1;
+        const int forced = fp64 ? c->cfg.sweep_variant_fp64 : c->cfg.sweep_variant_fp32;
+        int v = forced;
+        // tuning pays off only when a sweep is long enough for the shape to matter
+        const bool worth = (double)c->TT * (double)Kp >= (double)(1u << 24);
+        if (v < 0) {
+            if (worth)
+                CKR(tune_sweep_variant(c, fp64, Kp, s, v));
+            else
+                v = 0;
+        }
+        G[f]->variant = v;
+        G[f]->grid = sweep_launch_grid(c, fp64, Kp, v);
+        if (c->cfg.launch_mode == 0) {
+            const SweepArgs a = fp64 ? c->args64 : c->args32;
+            const int grid = G[f]->grid;
+            CKR(build_loop_graph(c, *G[f], a.ctl, [&](int pos, cudaStream_t st) {
+                return launch_sweep(fp64, Kp, v, a, pos, grid, st);
+            }));
+        }
+    }
+    c->ms_tune += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return MORAP_OK;
+}
+
+// Solve buffers are sized for the largest Kp seen so far (a [state][Kp]
+// layout for a smaller Kp fits inside), so batches of varying size do not
+// reallocate; the loop graphs are kept per Kp.
 int ensure_solve(morap_ctx *c, int Kp) {
-    if (c->Kp == Kp) return MORAP_OK;
+    if (Kp <= c->Kcap) {
+        c->Kp = Kp;
+        return MORAP_OK;
+    }
     free_solve(c);
     const size_t TS = c->TS, P = c->P;
     const size_t np = P * Kp;
@@ -321,6 +418,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
     }
     CKR(dev_alloc(c, L, &c->ctl, 3 * sizeof(LoopCtl)));
     c->Kp = Kp;
+    c->Kcap = Kp;
 
     SweepArgs a{};
     a.state_sa = c->state_sa;
@@ -358,35 +456,20 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a64.V[1] = c->V64[1];
     c->args32 = a32;
     c->args64 = a64;
-    CKL(sweep_setup_attributes());
-    c->g32.grid = sweep_grid(c, sweep_blocks_per_sm(false, Kp));
-    c->g64.grid = sweep_grid(c, sweep_blocks_per_sm(true, Kp));
-    if (c->cfg.launch_mode == 0) {
-        if (c->V32[0]) {
-            const int grid = c->g32.grid;
-            CKR(build_loop_graph(c, c->g32, a32.ctl, [&](int pos, cudaStream_t s) {
-                return launch_sweep(false, Kp, a32, pos, grid, s);
-            }));
-        }
-        const int grid = c->g64.grid;
-        CKR(build_loop_graph(c, c->g64, a64.ctl, [&](int pos, cudaStream_t s) {
-            return launch_sweep(true, Kp, a64, pos, grid, s);
-        }));
-    }
     return MORAP_OK;
 }
 
 int ensure_eval(morap_ctx *c, size_t n_pairs, size_t n_chunks, size_t n_states) {
     if (n_pairs <= c->eval_cap_pairs && n_chunks <= c->eval_cap_chunks && n_states <= c->eval_cap_states &&
-        c->eval_ready && c->eargs.Kp == c->Kp && c->eargs.policy == c->policy)
+        c->eval_ready && c->eargs.policy == c->policy)
         return MORAP_OK;
     free_eval(c);
     n_pairs = std::max<size_t>(n_pairs, 1);
     n_chunks = std::max<size_t>(n_chunks, 1);
     n_states = std::max<size_t>(n_states, 1);
     auto &L = c->eval_allocs;
-    CKR(dev_alloc(c, L, &c->E[0], n_states * sizeof(double2)));
-    CKR(dev_alloc(c, L, &c->E[1], n_states * sizeof(double2)));
+    CKR(dev_alloc(c, L, &c->E[0], n_states * sizeof(float4)));
+    CKR(dev_alloc(c, L, &c->E[1], n_states * sizeof(float4)));
     CKR(dev_alloc(c, L, &c->d_epairs, n_pairs * sizeof(int4)));
     CKR(dev_alloc(c, L, &c->d_echunks, n_chunks * sizeof(int4)));
     for (int i = 0; i < 3; ++i) {
@@ -398,8 +481,8 @@ int ensure_eval(morap_ctx *c, size_t n_pairs, size_t n_chunks, size_t n_states) 
     CKR(dev_alloc(c, L, &c->d_rc, n_pairs * sizeof(double)));
     CKR(dev_alloc(c, L, &c->d_rp, n_pairs * sizeof(double)));
     CKR(dev_alloc(c, L, &c->ecol, n_states * (size_t)c->max_row * sizeof(int32_t)));
-    CKR(dev_alloc(c, L, &c->ep, n_states * (size_t)c->max_row * sizeof(double)));
-    CKR(dev_alloc(c, L, &c->ecost, n_states * sizeof(double)));
+    CKR(dev_alloc(c, L, &c->ep, n_states * (size_t)c->max_row * sizeof(float2)));
+    CKR(dev_alloc(c, L, &c->ecost, n_states * sizeof(float2)));
     c->eval_cap_pairs = n_pairs;
     c->eval_cap_chunks = n_chunks;
     c->eval_cap_states = n_states;
@@ -407,8 +490,8 @@ int ensure_eval(morap_ctx *c, size_t n_pairs, size_t n_chunks, size_t n_states) 
     e.state_sa = c->state_sa;
     e.sa_tr = c->sa_tr;
     e.col = c->col;
-    e.p64 = c->p64;
-    e.cost64 = c->cost64;
+    e.pdf = c->pdf;
+    e.costdf = c->costdf;
     e.prods = c->d_prods;
     e.policy = c->policy;
     e.Kp = c->Kp;
@@ -429,14 +512,26 @@ int ensure_eval(morap_ctx *c, size_t n_pairs, size_t n_chunks, size_t n_states) 
     e.ecost = c->ecost;
     e.stride = c->max_row;
     c->eargs = e;
-    const int grid = sweep_grid(c, eval_blocks_per_sm());
-    c->geval.grid = grid;
+    c->eval_full_grid = sweep_grid(c, eval_blocks_per_sm());
     c->eval_ready = true;
-    if (c->cfg.launch_mode == 0)
-        CKR(build_loop_graph(c, c->geval, e.ctl, [&](int pos, cudaStream_t s) {
-            return launch_eval_sweep(e, pos, grid, s);
-        }));
     return MORAP_OK;
+}
+
+// The evaluation loop for n_chunks work items (one block each): a graph per
+// power-of-two grid bucket, so small evaluations do not occupy every SM.
+LoopGraph *eval_graph(morap_ctx *c, size_t n_chunks, int &rc) {
+    int b = 0;
+    while (((size_t)1 << b) < n_chunks && b < 23) ++b;
+    LoopGraph &g = c->geval[b];
+    rc = MORAP_OK;
+    if (g.grid) return &g;
+    g.grid = std::max(1, (int)std::min<size_t>((size_t)c->eval_full_grid, (size_t)1 << b));
+    if (c->cfg.launch_mode == 0) {
+        const EvalArgs e = c->eargs;
+        const int grid = g.grid;
+        rc = build_loop_graph(c, g, e.ctl, [&](int pos, cudaStream_t s) { return launch_eval_sweep(e, pos, grid, s); });
+    }
+    return &g;
 }
 
 double ms_between(cudaEvent_t a, cudaEvent_t b) {
@@ -474,6 +569,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     CK(cudaMemcpyAsync(c->d_W, c->h_stage, nW * sizeof(double), cudaMemcpyHostToDevice, s));
     CKL(launch_setup_weights(c->d_prods, c->P, c->nI, c->nJ, K, Kp, c->d_W, c->w32, c->w64, c->wdf, c->thr32,
                              c->thr64, c->cfg.eps_vi, s));
+    CKR(prepare_loops(c, Kp, s));
     const size_t nv = (size_t)c->TS * Kp;
     const unsigned int cap = (unsigned int)std::max(1, c->cfg.max_sweeps);
     const unsigned int n_items = (unsigned int)c->h_chunks.size();
@@ -487,9 +583,10 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         CK(cudaEventRecord(c->ev[0], s));
         {
             const SweepArgs a32 = c->args32;
-            const int grid = c->g32.grid;
-            CKR(run_loop(c, c->g32, c->ctl + 0, s, [&](int pos, cudaStream_t st) {
-                return launch_sweep(false, Kp, a32, pos, grid, st);
+            const LoopGraph &G = c->g32[log2_of(Kp)];
+            const int grid = G.grid, v = G.variant;
+            CKR(run_loop(c, c->g32[log2_of(Kp)], c->ctl + 0, s, [&](int pos, cudaStream_t st) {
+                return launch_sweep(false, Kp, v, a32, pos, grid, st);
             }));
         }
         CK(cudaEventRecord(c->ev[1], s));
@@ -503,9 +600,10 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     CK(cudaEventRecord(c->ev[6], s));
     {
         const SweepArgs a64 = c->args64;
-        const int grid = c->g64.grid;
-        CKR(run_loop(c, c->g64, c->ctl + 1, s, [&](int pos, cudaStream_t st) {
-            return launch_sweep(true, Kp, a64, pos, grid, st);
+        const LoopGraph &G = c->g64[log2_of(Kp)];
+        const int grid = G.grid, v = G.variant;
+        CKR(run_loop(c, c->g64[log2_of(Kp)], c->ctl + 1, s, [&](int pos, cudaStream_t st) {
+            return launch_sweep(true, Kp, v, a64, pos, grid, st);
         }));
     }
     CK(cudaEventRecord(c->ev[2], s));
@@ -541,6 +639,9 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     // sweep launches plus one control launch per body of six
     launches += st.fp32_sweeps + st.fp32_sweeps / 6 + st.fp64_sweeps + st.fp64_sweeps / 6;
     st.kernel_launches = launches;
+    st.variant_fp32 = mixed ? c->g32[log2_of(Kp)].variant : -1;
+    st.variant_fp64 = c->g64[log2_of(Kp)].variant;
+    st.ms_tune = c->ms_tune;
     int bad = 0;
     for (int p = 0; p < c->P; ++p)
         for (int k = 0; k < K; ++k) bad += h_status[(size_t)p * Kp + k] != MORAP_OK;
@@ -551,8 +652,8 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
 
 // Algorithm 4 for a list of (product, weight) pairs under the scheduler in
 // c->policy; returns r_cost and r_prob per pair.
-int run_evaluation(morap_ctx *c, const std::vector<int4> &pairs_in, cudaStream_t s, std::vector<double> &rc,
-                   std::vector<double> &rp, int &not_conv) {
+int run_evaluation_group(morap_ctx *c, const std::vector<int4> &pairs_in, cudaStream_t s, std::vector<double> &rc,
+                         std::vector<double> &rp, int &not_conv) {
     std::vector<int4> pairs = pairs_in;
     std::vector<int4> chunks;
     size_t off = 0;
@@ -575,17 +676,24 @@ int run_evaluation(morap_ctx *c, const std::vector<int4> &pairs_in, cudaStream_t
         CK(cudaMemcpyAsync(c->d_echunks, (char *)c->h_stage + npair * sizeof(int4), chunks.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, s));
     }
-    CK(cudaMemsetAsync(c->E[0], 0, off * sizeof(double2), s));
-    CK(cudaMemsetAsync(c->E[1], 0, off * sizeof(double2), s));
-    CKL(launch_eval_compact(c->eargs, (int)chunks.size(), s));
+    CK(cudaMemsetAsync(c->E[0], 0, off * sizeof(float4), s));
+    CK(cudaMemsetAsync(c->E[1], 0, off * sizeof(float4), s));
+    {
+        EvalArgs ea = c->eargs;  // the scheduler layout of the last solve
+        ea.Kp = c->Kp;
+        CKL(launch_eval_compact(ea, (int)chunks.size(), s));
+    }
     const unsigned int cap = (unsigned int)std::max(1, c->cfg.max_sweeps);
     CKL(launch_loop_init(c->ctl + 2, c->elist[0], (unsigned int)chunks.size(), c->eres, npair, c->esweeps,
                          c->efrozen, cap, s));
     CK(cudaEventRecord(c->ev[4], s));
     {
         const EvalArgs ea = c->eargs;
-        const int grid = c->geval.grid;
-        CKR(run_loop(c, c->geval, c->ctl + 2, s, [&](int pos, cudaStream_t st) {
+        int rc = MORAP_OK;
+        LoopGraph *ge = eval_graph(c, chunks.size(), rc);
+        CKR(rc);
+        const int grid = ge->grid;
+        CKR(run_loop(c, *ge, c->ctl + 2, s, [&](int pos, cudaStream_t st) {
             return launch_eval_sweep(ea, pos, grid, st);
         }));
     }
@@ -615,6 +723,46 @@ int run_evaluation(morap_ctx *c, const std::vector<int4> &pairs_in, cudaStream_t
     c->stats.h2d_bytes += (int64_t)((npair + chunks.size()) * sizeof(int4));
     c->stats.d2h_bytes += (int64_t)(npair * (2 * sizeof(double) + 1) + sizeof(LoopCtl));
     c->stats.kernel_launches += 3 + c->stats.eval_sweeps + c->stats.eval_sweeps / 6;
+    return MORAP_OK;
+}
+
+// Algorithm 4 for a list of (product, weight) pairs, in groups of at most
+// kEvalStates value slots (one device loop per group), so the device buffers
+// of an evaluation stay bounded however many pairs are asked for.
+constexpr size_t kEvalStates = size_t(1) << 27;
+
+int run_evaluation(morap_ctx *c, const std::vector<int4> &pairs, cudaStream_t s, std::vector<double> &rc,
+                   std::vector<double> &rp, int &not_conv) {
+    rc.clear();
+    rp.clear();
+    not_conv = 0;
+    int32_t sweeps = 0, npairs = 0;
+    int64_t updates = 0, bytes = 0;
+    double ms = 0.0;
+    size_t e0 = 0;
+    do {
+        size_t e1 = e0, states = 0;
+        while (e1 < pairs.size() && (e1 == e0 || states + c->h_prods[pairs[e1].x].n_nd + 1 <= kEvalStates))
+            states += c->h_prods[pairs[e1++].x].n_nd + 1;
+        std::vector<int4> group(pairs.begin() + e0, pairs.begin() + e1);
+        std::vector<double> grc, grp;
+        int nc = 0;
+        CKR(run_evaluation_group(c, group, s, grc, grp, nc));
+        rc.insert(rc.end(), grc.begin(), grc.end());
+        rp.insert(rp.end(), grp.begin(), grp.end());
+        not_conv += nc;
+        sweeps = std::max(sweeps, c->stats.eval_sweeps);
+        updates += c->stats.updates_eval;
+        bytes += c->stats.bytes_eval;
+        ms += c->stats.ms_eval;
+        npairs += c->stats.eval_pairs;
+        e0 = e1;
+    } while (e0 < pairs.size());
+    c->stats.eval_sweeps = sweeps;
+    c->stats.updates_eval = updates;
+    c->stats.bytes_eval = bytes;
+    c->stats.ms_eval = ms;
+    c->stats.eval_pairs = npairs;
     return MORAP_OK;
 }
 
@@ -945,6 +1093,8 @@ void morap_config_default(morap_config *cfg) {
     cfg->max_sweeps = 100000;
     cfg->precision = MORAP_PREC_MIXED;
     cfg->device = 0;
+    cfg->sweep_variant_fp32 = -1;
+    cfg->sweep_variant_fp64 = -1;
 }
 
 const char *morap_last_error(void) { return g_last_error.c_str(); }
@@ -964,6 +1114,9 @@ int morap_ctx_create(const morap_config *cfg, morap_ctx **out) {
         return fail(MORAP_EINVAL, "config: unknown precision mode");
     if (c.launch_mode != 0 && c.launch_mode != 1) return fail(MORAP_EINVAL, "config: unknown launch mode");
     if ((c.alloc == nullptr) != (c.free == nullptr)) return fail(MORAP_EINVAL, "config: alloc and free go together");
+    if (c.sweep_variant_fp32 < -1 || c.sweep_variant_fp32 >= sweep_variant_count(false) ||
+        c.sweep_variant_fp64 < -1 || c.sweep_variant_fp64 >= sweep_variant_count(true))
+        return fail(MORAP_EINVAL, "config: sweep_variant_* must be -1 (tuned) or a shape index");
     CK(cudaSetDevice(c.device));
     morap_ctx *ctx = new morap_ctx();
     ctx->cfg = c;

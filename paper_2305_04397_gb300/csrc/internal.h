@@ -163,8 +163,8 @@ struct EvalArgs {
     const uint32_t *state_sa;
     const uint32_t *sa_tr;
     const int32_t *col;
-    const double *p64;
-    const double *cost64;
+    const float2 *pdf;      // double-float probability per transition
+    const float2 *costdf;   // double-float cost per state-action
     const ProdDesc *prods;
     const uint8_t *policy;  // [state][Kp]
     int Kp;
@@ -176,13 +176,13 @@ struct EvalArgs {
     uint8_t *frozen;
     unsigned int *list[3];
     LoopCtl *ctl;
-    double2 *E[2];
+    float4 *E[2];    // (cost.h, cost.l, prob.h, prob.l) double-float values
     // compact scheduler rows of the evaluated pairs (built once per call):
     // for pair e with value offset off and n + 1 states (done slot n), slot j
     // of state s is at off * stride + j * (n + 1) + s
     int32_t *ecol;   // local successor (n = done slot for padding)
-    double *ep;      // probability (0 for padding)
-    double *ecost;   // cost of the scheduler's action, at off + s
+    float2 *ep;      // double-float probability (0 for padding)
+    float2 *ecost;   // double-float cost of the scheduler's action, at off + s
     int stride;      // slots per state: the longest action row of any agent
 };
 
@@ -203,8 +203,12 @@ int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, in
                          float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1, void *s);
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
                      size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s);
-int launch_sweep(bool fp64, int Kp, const SweepArgs &a, int pos, int grid, void *s);
-int sweep_blocks_per_sm(bool fp64, int Kp);
+// One sweep with kernel shape `variant` (0 .. sweep_variant_count - 1; all
+// shapes give bit-identical results, they differ only in speed).
+int launch_sweep(bool fp64, int Kp, int variant, const SweepArgs &a, int pos, int grid, void *s);
+int sweep_blocks_per_sm(bool fp64, int Kp, int variant);
+int sweep_variant_count(bool fp64);
+void sweep_variant_shape(bool fp64, int variant, int *vmax, int *d, int *minb);
 int eval_blocks_per_sm();
 int launch_loop_control(LoopCtl *ctl, unsigned long long handle, int next_idx, void *s);
 int launch_loop_control_host(LoopCtl *ctl, int next_idx, void *s);
@@ -214,7 +218,7 @@ int launch_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V64, con
                     int32_t *status_out, void *s);
 int launch_eval_sweep(const EvalArgs &a, int pos, int grid, void *s);
 int launch_eval_compact(const EvalArgs &a, int n_chunks, void *s);
-int launch_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const double2 *E, double *rc,
+int launch_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const float4 *E, double *rc,
                        double *rp, void *s);
 // plain baseline
 int launch_plain_spmv(const uint32_t *sa_tr, const int32_t *col, const double *p64, const double *cost64,

@@ -156,7 +156,7 @@ void morap_server_config_default(morap_server_config *cfg) {
     if (!cfg) return;
     std::memset(cfg, 0, sizeof(*cfg));
     cfg->max_batch = 64;
-    cfg->n_workers = 4;
+    cfg->n_workers = 8;
     cfg->eps = 1e-6;
     cfg->max_iter = 64;
 }

@@ -28,7 +28,9 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <array>
 #include <cstdint>
+#include <utility>
 
 #include "internal.h"
 
@@ -262,28 +264,34 @@ __device__ __forceinline__ void store_words(float *p, const float (&w)[NW]) {
     }
 }
 
-// Weights per lane (FP32 / double-float phase) and the minimum resident
-// blocks the register allocation is sized for.
-#ifndef MORAP_VMAX_F32
-#define MORAP_VMAX_F32 8
-#endif
-#ifndef MORAP_VMAX_DF
-#define MORAP_VMAX_DF 4
-#endif
-#ifndef MORAP_SWEEP_MIN_BLOCKS
-#define MORAP_SWEEP_MIN_BLOCKS 2
-#endif
-#ifndef MORAP_GATHER_D
-#define MORAP_GATHER_D 4
-#endif
-#ifndef MORAP_GATHER_D_WIDE
-#define MORAP_GATHER_D_WIDE 3
-#endif
+// Kernel shapes the tuner chooses from, per value format: VMAX weights per
+// lane (a lane owns VEC = min(Kp, VMAX) consecutive weights of a state), D
+// successor gathers in flight per action, and MINB resident blocks per SM
+// the register allocation is sized for.  Entry 0 is the default.  Every
+// shape performs the same operations in the same order per (state, weight),
+// so all of them give bit-identical results.
+template <class Ar>
+struct Variants;
+template <>
+struct Variants<ArithF32> {
+    static constexpr int N = 4;
+    static constexpr int vmax[N] = {8, 8, 8, 4};
+    static constexpr int d[N] = {3, 3, 2, 3};
+    static constexpr int minb[N] = {2, 2, 2, 2};
+    static constexpr int pipe[N] = {0, 1, 1, 1};  // actions software-pipelined
+};
+template <>
+struct Variants<ArithDF> {
+    static constexpr int N = 4;
+    static constexpr int vmax[N] = {4, 4, 4, 2};
+    static constexpr int d[N] = {3, 3, 2, 4};
+    static constexpr int minb[N] = {2, 2, 2, 2};
+    static constexpr int pipe[N] = {0, 1, 1, 1};
+};
 
-// Lanes per state and weights per lane for each (format, Kp).
-template <class Ar, int KP>
+// Lanes per state and weights per lane for each (format, Kp, VMAX).
+template <class Ar, int KP, int VMAX>
 struct Shape {
-    static constexpr int VMAX = Ar::WORDS == 1 ? MORAP_VMAX_F32 : MORAP_VMAX_DF;  // weights per lane
     static constexpr int VEC = KP < VMAX ? KP : VMAX;
     static constexpr int LPS = KP / VEC;                  // lanes per state (<= 32)
     static constexpr int SPW = 32 / LPS;                  // states per warp round
@@ -325,18 +333,17 @@ __device__ __forceinline__ Vec<T, VEC> vload(const T *p) {
 // once, coalesced, for all weights; each lane consumes its state's
 // transitions as one stream across the actions, issuing kGatherBatch
 // independent value gathers before it consumes them.
-template <class Ar, int KP>
+template <class Ar, int KP, int VMAX, int D>
 __device__ __forceinline__ void process_state(const SweepArgs &a, const typename Ar::View &vw, const uint32_t *ssa,
                                               uint32_t A0, uint32_t T0, int i, uint32_t u, bool pre,
                                               const typename Ar::W *__restrict__ sw, const unsigned int act_bits,
                                               const float *__restrict__ Vold, float *__restrict__ Vnew, int k0,
-                                              float (&rmax)[Shape<Ar, KP>::VEC]) {
+                                              float (&rmax)[Shape<Ar, KP, VMAX>::VEC]) {
     using Val = typename Ar::Val;
-    using SH = Shape<Ar, KP>;
+    using SH = Shape<Ar, KP, VMAX>;
     constexpr int VEC = SH::VEC;
     constexpr int NW = VEC * Ar::WORDS;
     constexpr int ROW = KP * Ar::WORDS;
-    constexpr int D = NW >= 8 ? MORAP_GATHER_D_WIDE : MORAP_GATHER_D;  // gathers in flight within one action
     const size_t row = (size_t)u * ROW + (size_t)k0 * Ar::WORDS;
     const uint32_t la0 = ssa[i] - A0, la1 = ssa[i + 1] - A0;
     Val best[VEC];
@@ -401,6 +408,113 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
     store_words<NW>(Vnew + row, yw);
 }
 
+// The same per-state computation with the actions software-pipelined: the
+// (successor, probability) slots of action a + 1 are read and their value
+// gathers issued before action a is reduced, so one gather round trip is
+// exposed per state instead of one per action.  Actions with more than D
+// transitions finish their remaining slots unpipelined.  Same operations in
+// the same order per (state, weight) as process_state.
+template <class Ar, int KP, int VMAX, int D>
+__device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typename Ar::View &vw,
+                                                   const uint32_t *ssa, uint32_t A0, uint32_t T0, int i, uint32_t u,
+                                                   bool pre, const typename Ar::W *__restrict__ sw,
+                                                   const unsigned int act_bits, const float *__restrict__ Vold,
+                                                   float *__restrict__ Vnew, int k0,
+                                                   float (&rmax)[Shape<Ar, KP, VMAX>::VEC]) {
+    using Val = typename Ar::Val;
+    using Prob = typename Ar::Prob;
+    using SH = Shape<Ar, KP, VMAX>;
+    constexpr int VEC = SH::VEC;
+    constexpr int NW = VEC * Ar::WORDS;
+    constexpr int ROW = KP * Ar::WORDS;
+    const float *__restrict__ vbase = Vold + (size_t)k0 * Ar::WORDS;
+    const size_t row = (size_t)u * ROW + (size_t)k0 * Ar::WORDS;
+    const uint32_t la0 = ssa[i] - A0, la1 = ssa[i + 1] - A0;
+    Val best[VEC];
+    uint32_t best_a[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+        best[v] = Ar::neg_inf();
+        best_a[v] = 0u;
+    }
+    struct Slots {
+        int32_t cl[D];
+        Prob pr[D];
+        float gw[D][NW];
+        uint32_t t0, t1;
+    };
+    // read slots t0 .. t0 + D - 1 of the current row and issue their gathers
+    auto fill = [&](Slots &S) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            if (S.t0 + j < S.t1) {
+                Ar::edge(vw, S.t0 + j, S.cl[j], S.pr[j]);
+            } else {
+                S.cl[j] = -1;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+            if (S.cl[j] >= 0) load_words<NW>(vbase + (size_t)S.cl[j] * ROW, S.gw[j]);
+    };
+    auto fetch = [&](uint32_t la, Slots &S) {
+        S.t0 = vw.str[la] - T0;
+        S.t1 = vw.str[la + 1] - T0;
+        fill(S);
+    };
+    auto reduce = [&](uint32_t la, Slots &S) {
+        Val acc[VEC];
+        {
+            const typename Ar::Cost c = Ar::cost(vw, la);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c, pre);
+        }
+        for (;;) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                if (S.cl[j] < 0) continue;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], S.pr[j], Ar::from_words(&S.gw[j][v * Ar::WORDS]));
+            }
+            if (S.t0 + D >= S.t1) break;
+            S.t0 += D;  // rows longer than D: the next slots, unpipelined
+            fill(S);
+        }
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            Ar::close(acc[v]);
+            const bool better = Ar::gt(acc[v], best[v]);
+            best[v] = better ? acc[v] : best[v];
+            best_a[v] = better ? la - la0 : best_a[v];
+        }
+    };
+    Slots A, B;
+    fetch(la0, A);
+    for (uint32_t la = la0;;) {
+        const bool more = la + 1 < la1;
+        if (more) fetch(la + 1, B);
+        reduce(la, A);
+        if (!more) break;
+        ++la;
+        const bool more2 = la + 1 < la1;
+        if (more2) fetch(la + 1, A);
+        reduce(la, B);
+        if (!more2) break;
+        ++la;
+    }
+    float yw[NW];
+    load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+        if (!((act_bits >> v) & 1u)) continue;
+        const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
+        rmax[v] = d > rmax[v] ? d : rmax[v];
+        if (d > Ar::record_threshold(best[v], a.eps1)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
+        Ar::to_words(best[v], &yw[v * Ar::WORDS]);
+    }
+    store_words<NW>(Vnew + row, yw);
+}
+
 // Work items are 128-state ranges of one product taken by whole warps
 // (dynamic scheduling, no block barriers), walked in batches of up to 32
 // states: the warp copies the batch's state starts, action-row starts, costs
@@ -408,9 +522,9 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
 // cp.async, then computes.  Inside a batch, LPS lanes share a state and each
 // lane owns VEC of the Kp weights, so a successor's value row is read once,
 // coalesced, for all weights.
-template <class Ar, int KP>
-__global__ void __launch_bounds__(kThreads, MORAP_SWEEP_MIN_BLOCKS) k_sweep(SweepArgs a, int pos) {
-    using SH = Shape<Ar, KP>;
+template <class Ar, int KP, int VMAX, int D, int MINB, int PIPE>
+__global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) {
+    using SH = Shape<Ar, KP, VMAX>;
     constexpr int VEC = SH::VEC, LPS = SH::LPS, SPW = SH::SPW;
     constexpr int NW = VEC * Ar::WORDS;
     constexpr int ROW = KP * Ar::WORDS;
@@ -524,8 +638,14 @@ __global__ void __launch_bounds__(kThreads, MORAP_SWEEP_MIN_BLOCKS) k_sweep(Swee
                 }
                 __syncwarp();
                 for (int i = grp; i < m; i += SPW)
-                    process_state<Ar, KP>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i, (uint32_t)(s0 + i) >= pd.pre_begin,
-                                          wsm + k0, act_bits, Vold, Vnew, k0, rmax);
+                    if constexpr (PIPE)
+                        process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                                                            (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits,
+                                                            Vold, Vnew, k0, rmax);
+                    else
+                        process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                                                       (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits, Vold,
+                                                       Vnew, k0, rmax);
                 __syncwarp();  // the next batch reuses the buffer
                 s0 += m;
             }
@@ -565,55 +685,60 @@ __global__ void __launch_bounds__(kThreads, MORAP_SWEEP_MIN_BLOCKS) k_sweep(Swee
 template <int KP>
 __global__ void __launch_bounds__(kThreads) k_finalize(SweepArgs a, int n_chunks, double tau, uint8_t *policy) {
     constexpr int VEC = KP < 2 ? KP : 2, LPS = KP / VEC, SPR = kThreads / LPS;
-    constexpr int MAXA = 32;  // actions scanned twice per state: first for the max, then for the choice
     const float2 *__restrict__ V = static_cast<const float2 *>(a.V[0]);  // double-float values
     const int k0 = (threadIdx.x % LPS) * VEC, slot = threadIdx.x / LPS;
+    const float ftau = (float)tau;
     for (int item = blockIdx.x; item < n_chunks; item += gridDim.x) {
         const int4 ch = a.chunks[item];
         const int p = ch.x;
         const ProdDesc pd = a.prods[p];
-        double2 w[VEC];
+        ArithDF::W w[VEC];
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) w[v] = a.w64[(size_t)p * KP + k0 + v];
+        for (int v = 0; v < VEC; ++v) w[v] = a.wdf[(size_t)p * KP + k0 + v];
         for (int s = ch.y + slot; s < ch.z; s += SPR) {
             const uint32_t u = pd.state_off + (uint32_t)s;
             const size_t row = (size_t)u * KP + k0;
             const bool pre = (uint32_t)s >= pd.pre_begin;
             const uint32_t a0 = a.state_sa[u], a1 = a.state_sa[u + 1];
-            double best[VEC], qrec[VEC];
+            DF best[VEC], qrec[VEC];
             uint8_t rec[VEC], pick[VEC], pick_loop[VEC];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
-                best[v] = -CUDART_INF;
+                best[v] = ArithDF::neg_inf();
                 rec[v] = a.a_rec[row + v];
-                qrec[v] = -CUDART_INF;
+                qrec[v] = ArithDF::neg_inf();
                 pick[v] = 0xFF;
                 pick_loop[v] = 0xFF;
             }
+            // Q within tau of the maximum, on the double-float values
+            auto near_max = [&](const DF &q, const DF &m) {
+                return __fadd_rn(__fadd_rn(q.h, -m.h), __fadd_rn(q.l, -m.l)) >= -ftau;
+            };
             for (int pass = 0; pass < 2; ++pass) {
                 for (uint32_t sa = a0; sa < a1; ++sa) {
-                    const double c = a.cost64[sa];
-                    double acc[VEC];
+                    const float2 cd = a.costdf[sa];
+                    DF acc[VEC];
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[v] = (pre ? w[v].y : 0.0) - w[v].x * c;
+                    for (int v = 0; v < VEC; ++v) acc[v] = ArithDF::reward(w[v], {cd.x, cd.y}, pre);
                     const uint32_t t0 = a.sa_tr[sa], t1 = a.sa_tr[sa + 1];
-                    bool self_loop = (t1 - t0 == 1) && ((uint32_t)a.col[t0] == u);
+                    const bool self_loop = (t1 - t0 == 1) && ((uint32_t)a.col[t0] == u);
                     for (uint32_t t = t0; t < t1; ++t) {
                         const int32_t cl = a.col[t];
-                        const double pr = a.p64[t];
+                        const float2 pr = a.pdf[t];
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
                             const float2 xv = V[(size_t)cl * KP + k0 + v];
-                            acc[v] = fma(pr, (double)xv.x + (double)xv.y, acc[v]);
+                            ArithDF::mac(acc[v], {pr.x, pr.y}, {xv.x, xv.y});
                         }
                     }
                     const uint8_t la = (uint8_t)(sa - a0);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
+                        acc[v] = df_norm(acc[v]);
                         if (pass == 0) {
-                            best[v] = acc[v] > best[v] ? acc[v] : best[v];
+                            best[v] = df_gt(acc[v], best[v]) ? acc[v] : best[v];
                             if (la == rec[v]) qrec[v] = acc[v];
-                        } else if (acc[v] >= best[v] - tau) {
+                        } else if (near_max(acc[v], best[v])) {
                             if (self_loop) {
                                 if (pick_loop[v] == 0xFF) pick_loop[v] = la;
                             } else if (pick[v] == 0xFF) {
@@ -624,15 +749,14 @@ __global__ void __launch_bounds__(kThreads) k_finalize(SweepArgs a, int n_chunks
                 }
                 bool all_kept = true;
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) all_kept = all_kept && (qrec[v] >= best[v] - tau);
+                for (int v = 0; v < VEC; ++v) all_kept = all_kept && near_max(qrec[v], best[v]);
                 if (all_kept) break;  // the second pass is only needed for a fallback
             }
 #pragma unroll
             for (int v = 0; v < VEC; ++v)
-                policy[row + v] = (qrec[v] >= best[v] - tau) ? rec[v] : (pick[v] != 0xFF ? pick[v] : pick_loop[v]);
+                policy[row + v] = near_max(qrec[v], best[v]) ? rec[v] : (pick[v] != 0xFF ? pick[v] : pick_loop[v]);
         }
     }
-    (void)MAXA;
 }
 
 // ------------------------------------------------------------- evaluation
@@ -653,15 +777,15 @@ __global__ void __launch_bounds__(kThreads) k_eval_compact(EvalArgs a, int n_chu
         const uint32_t u = pd.state_off + (uint32_t)s;
         const uint32_t sa = a.state_sa[u] + a.policy[(size_t)u * a.Kp + pr.y];
         const uint32_t t0 = a.sa_tr[sa], t1 = a.sa_tr[sa + 1];
-        a.ecost[off + s] = a.cost64[sa];
+        a.ecost[off + s] = a.costdf[sa];
         for (int j = 0; j < a.stride; ++j) {
             const size_t at = off * a.stride + (size_t)j * n1 + s;
             if (t0 + j < t1) {
                 a.ecol[at] = a.col[t0 + j] - (int32_t)pd.state_off;
-                a.ep[at] = a.p64[t0 + j];
+                a.ep[at] = a.pdf[t0 + j];
             } else {
                 a.ecol[at] = (int32_t)pd.n_nd;
-                a.ep[at] = 0.0;
+                a.ep[at] = make_float2(0.0f, 0.0f);
             }
         }
     }
@@ -669,8 +793,8 @@ __global__ void __launch_bounds__(kThreads) k_eval_compact(EvalArgs a, int n_chu
 
 __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
     const int cur = pos % 3, nxt = (pos + 1) % 3, far = (pos + 2) % 3;
-    const double2 *__restrict__ Eold = a.E[pos & 1];
-    double2 *__restrict__ Enew = a.E[(pos + 1) & 1];
+    const float4 *__restrict__ Eold = a.E[pos & 1];
+    float4 *__restrict__ Enew = a.E[(pos + 1) & 1];
     LoopCtl *ctl = a.ctl;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->cnt[far] = 0;
@@ -679,8 +803,12 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
     const unsigned int n_items = ctl->cnt[cur];
     const unsigned int sweep = ctl->sweep_base + pos;
     __shared__ unsigned int s_item;
-    __shared__ double s_red[kThreads / 32];
+    __shared__ float s_red[kThreads / 32];
     const int stride = a.stride;
+    // Moves below this fraction of a value are double-float rounding, not
+    // propagation: each of the stride + 1 accumulations adds at most a few
+    // units of 2^-48 relative error, so they are not counted as residual.
+    const float noise = (float)(stride + 1) * 2.8421709430404007e-14f; /* 2^-45 */
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&ctl->next[cur], 1u);
         __syncthreads();
@@ -709,22 +837,23 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
             else
                 a.frozen[e] = 1;
         }
-        double r = 0.0;
+        float r = 0.0f;
         const int s = ch.y + threadIdx.x;
         const size_t off = (size_t)pr.z;
         const uint32_t n1 = pd.n_nd + 1;
         if (s < ch.z) {
-            const double2 x = Eold[off + s];
-            double2 y = x;
+            const float4 x = Eold[off + s];
+            float4 y = x;
             if (active) {
-                double yc = -a.ecost[off + s];
-                double yp = ((uint32_t)s >= pd.pre_begin) ? 1.0 : 0.0;
+                const float2 cc = a.ecost[off + s];
+                DF yc = {-cc.x, -cc.y};
+                DF yp = {((uint32_t)s >= pd.pre_begin) ? 1.0f : 0.0f, 0.0f};
                 const size_t base = off * stride + s;
                 int j = 0;
                 for (; j + 4 <= stride; j += 4) {
                     int32_t c[4];
-                    double p[4];
-                    double2 v[4];
+                    float2 p[4];
+                    float4 v[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         c[q] = a.ecol[base + (size_t)(j + q) * n1];
@@ -734,30 +863,35 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
                     for (int q = 0; q < 4; ++q) v[q] = Eold[off + c[q]];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        yc = fma(p[q], v[q].x, yc);
-                        yp = fma(p[q], v[q].y, yp);
+                        ArithDF::mac(yc, {p[q].x, p[q].y}, {v[q].x, v[q].y});
+                        ArithDF::mac(yp, {p[q].x, p[q].y}, {v[q].z, v[q].w});
                     }
                 }
                 for (; j < stride; ++j) {
                     const int32_t c = a.ecol[base + (size_t)j * n1];
-                    const double p = a.ep[base + (size_t)j * n1];
-                    const double2 v = Eold[off + c];
-                    yc = fma(p, v.x, yc);
-                    yp = fma(p, v.y, yp);
+                    const float2 p = a.ep[base + (size_t)j * n1];
+                    const float4 v = Eold[off + c];
+                    ArithDF::mac(yc, {p.x, p.y}, {v.x, v.y});
+                    ArithDF::mac(yp, {p.x, p.y}, {v.z, v.w});
                 }
-                y = make_double2(yc, yp);
-                r = fmax(fabs(yc - x.x), fabs(yp - x.y));
+                yc = df_norm(yc);
+                yp = df_norm(yp);
+                y = make_float4(yc.h, yc.l, yp.h, yp.l);
+                float dc = ArithDF::diff(yc, {x.x, x.y}), dp = ArithDF::diff(yp, {x.z, x.w});
+                dc = dc > noise * fabsf(yc.h) ? dc : 0.0f;
+                dp = dp > noise * fabsf(yp.h) ? dp : 0.0f;
+                r = fmaxf(dc, dp);
             }
             Enew[off + s] = y;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x / 32] = r;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double mx = 0.0;
-            for (int wi = 0; wi < kThreads / 32; ++wi) mx = fmax(mx, s_red[wi]);
-            if (active && mx > 0.0) atomic_max_nonneg(a.res[cur] + e, mx);
+            float mx = 0.0f;
+            for (int wi = 0; wi < kThreads / 32; ++wi) mx = fmaxf(mx, s_red[wi]);
+            if (active && mx > 0.0f) atomic_max_nonneg(a.res[cur] + e, (double)mx);
             const unsigned long long n_s = (unsigned long long)(ch.z - ch.y);
             // values read + written (16 B each); when computing also the cost
             // (8) and every slot's successor and probability (4 + 8)
@@ -773,6 +907,15 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
 }
 
 // ------------------------------------------------------------- small kernels
+
+// The FP32 phase hands over to the double-float phase once a pair's residual
+// is at most 2^-MORAP_THR32_SHIFT of its largest possible value.  Its
+// round-down iterates increase monotonically to a fixed point of the rounded
+// operator, where the residual is exactly 0, so any shift terminates; the
+// shift only trades FP32 sweeps against double-float sweeps.
+#ifndef MORAP_THR32_SHIFT
+#define MORAP_THR32_SHIFT 20
+#endif
 
 __device__ __forceinline__ float2 to_df(double d) {
     const float h = __double2float_rn(d);
@@ -796,7 +939,7 @@ __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, in
         wdf[idx] = make_float4(a.x, a.y, b.x, b.y);
         // FP32 phase: stop once the residual is within a few ulps of the
         // largest possible value (values lie in [0, w_p]); FP64 phase: eps1.
-        thr32[idx] = fmax(eps1, wp * 9.5367431640625e-07 /* 2^-20 */);
+        thr32[idx] = fmax(eps1, ldexp(wp, -MORAP_THR32_SHIFT));
         thr64[idx] = eps1;
     }
 }
@@ -870,7 +1013,7 @@ __global__ void k_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V
     }
 }
 
-__global__ void k_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const double2 *E, double *rc,
+__global__ void k_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const float4 *E, double *rc,
                               double *rp) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_pairs; e += gridDim.x * blockDim.x) {
         const int4 pr = pairs[e];
@@ -879,9 +1022,9 @@ __global__ void k_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *pr
             rc[e] = 0.0;
             rp[e] = 0.0;
         } else {
-            const double2 v = E[(size_t)pr.z + pd.init_local];
-            rc[e] = v.x;
-            rp[e] = v.y;
+            const float4 v = E[(size_t)pr.z + pd.init_local];
+            rc[e] = (double)v.x + (double)v.y;
+            rp[e] = (double)v.z + (double)v.w;
         }
     }
 }
@@ -891,54 +1034,57 @@ constexpr int smem_of() {
     return (kThreads / 32) * (Ar::STAGE_BYTES + 64 * (int)sizeof(typename Ar::W));  // sized for the largest Kp
 }
 
+using SweepFn = void (*)(SweepArgs, int);
+
+template <class Ar, int KP, int... V>
+std::array<SweepFn, Variants<Ar>::N> sweep_row(std::integer_sequence<int, V...>) {
+    return {&k_sweep<Ar, KP, Variants<Ar>::vmax[V], Variants<Ar>::d[V], Variants<Ar>::minb[V],
+                     Variants<Ar>::pipe[V]>...};
+}
+
+// sweep_fn<Ar>(log2 Kp, variant)
 template <class Ar>
-int launch_sweep_t(int Kp, const SweepArgs &a, int pos, int grid, cudaStream_t s) {
-    constexpr int sm = smem_of<Ar>();
-    switch (Kp) {
-    case 1: k_sweep<Ar, 1><<<grid, kThreads, sm, s>>>(a, pos); break;
-    case 2: k_sweep<Ar, 2><<<grid, kThreads, sm, s>>>(a, pos); break;
-    case 4: k_sweep<Ar, 4><<<grid, kThreads, sm, s>>>(a, pos); break;
-    case 8: k_sweep<Ar, 8><<<grid, kThreads, sm, s>>>(a, pos); break;
-    case 16: k_sweep<Ar, 16><<<grid, kThreads, sm, s>>>(a, pos); break;
-    case 32: k_sweep<Ar, 32><<<grid, kThreads, sm, s>>>(a, pos); break;
-    case 64: k_sweep<Ar, 64><<<grid, kThreads, sm, s>>>(a, pos); break;
-    default: return (int)cudaErrorInvalidValue;
-    }
+SweepFn sweep_fn(int lg, int v) {
+    using Seq = std::make_integer_sequence<int, Variants<Ar>::N>;
+    static const std::array<std::array<SweepFn, Variants<Ar>::N>, 7> table = {
+        sweep_row<Ar, 1>(Seq{}),  sweep_row<Ar, 2>(Seq{}),  sweep_row<Ar, 4>(Seq{}), sweep_row<Ar, 8>(Seq{}),
+        sweep_row<Ar, 16>(Seq{}), sweep_row<Ar, 32>(Seq{}), sweep_row<Ar, 64>(Seq{})};
+    if (lg < 0 || lg > 6 || v < 0 || v >= Variants<Ar>::N) return nullptr;
+    return table[lg][v];
+}
+
+int log2_kp(int Kp) {
+    int l = 0;
+    while ((1 << l) < Kp) ++l;
+    return (1 << l) == Kp ? l : -1;
+}
+
+template <class Ar>
+int launch_sweep_t(int Kp, int variant, const SweepArgs &a, int pos, int grid, cudaStream_t s) {
+    const SweepFn f = sweep_fn<Ar>(log2_kp(Kp), variant);
+    if (!f) return (int)cudaErrorInvalidValue;
+    f<<<grid, kThreads, smem_of<Ar>(), s>>>(a, pos);
     return (int)cudaGetLastError();
 }
 
 template <class Ar>
 cudaError_t set_attr_t() {
-    constexpr int sm = smem_of<Ar>();
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep<Ar, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    return e;
+    for (int lg = 0; lg < 7; ++lg)
+        for (int v = 0; v < Variants<Ar>::N; ++v) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(sweep_fn<Ar>(lg, v), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of<Ar>());
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
 }
 
 }  // namespace
 
 template <class Ar>
-int blocks_per_sm_t(int Kp) {
+int blocks_per_sm_t(int Kp, int variant) {
+    const SweepFn f = sweep_fn<Ar>(log2_kp(Kp), variant);
     int n = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    constexpr int sm = smem_of<Ar>();
-    switch (Kp) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 1>, kThreads, sm); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 2>, kThreads, sm); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 4>, kThreads, sm); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 8>, kThreads, sm); break;
-    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 16>, kThreads, sm); break;
-    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 32>, kThreads, sm); break;
-    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<Ar, 64>, kThreads, sm); break;
-    default: break;
-    }
-    if (e != cudaSuccess) {
+    if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem_of<Ar>()) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -953,7 +1099,17 @@ int sweep_setup_attributes() {
 
 int sweep_smem_bytes(bool fp64) { return fp64 ? smem_of<ArithDF>() : smem_of<ArithF32>(); }
 
-int sweep_blocks_per_sm(bool fp64, int Kp) { return fp64 ? blocks_per_sm_t<ArithDF>(Kp) : blocks_per_sm_t<ArithF32>(Kp); }
+int sweep_blocks_per_sm(bool fp64, int Kp, int variant) {
+    return fp64 ? blocks_per_sm_t<ArithDF>(Kp, variant) : blocks_per_sm_t<ArithF32>(Kp, variant);
+}
+
+int sweep_variant_count(bool fp64) { return fp64 ? Variants<ArithDF>::N : Variants<ArithF32>::N; }
+
+void sweep_variant_shape(bool fp64, int variant, int *vmax, int *d, int *minb) {
+    *vmax = fp64 ? Variants<ArithDF>::vmax[variant] : Variants<ArithF32>::vmax[variant];
+    *d = fp64 ? Variants<ArithDF>::d[variant] : Variants<ArithF32>::d[variant];
+    *minb = fp64 ? Variants<ArithDF>::minb[variant] : Variants<ArithF32>::minb[variant];
+}
 
 int eval_blocks_per_sm() {
     int n = 0;
@@ -964,9 +1120,9 @@ int eval_blocks_per_sm() {
     return n > 0 ? n : 1;
 }
 
-int launch_sweep(bool fp64, int Kp, const SweepArgs &a, int pos, int grid, void *s) {
-    return fp64 ? launch_sweep_t<ArithDF>(Kp, a, pos, grid, (cudaStream_t)s)
-                : launch_sweep_t<ArithF32>(Kp, a, pos, grid, (cudaStream_t)s);
+int launch_sweep(bool fp64, int Kp, int variant, const SweepArgs &a, int pos, int grid, void *s) {
+    return fp64 ? launch_sweep_t<ArithDF>(Kp, variant, a, pos, grid, (cudaStream_t)s)
+                : launch_sweep_t<ArithF32>(Kp, variant, a, pos, grid, (cudaStream_t)s);
 }
 
 int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, void *sv) {
@@ -1039,7 +1195,7 @@ int launch_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V64, con
     return (int)cudaGetLastError();
 }
 
-int launch_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const double2 *E, double *rc,
+int launch_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const float4 *E, double *rc,
                        double *rp, void *s) {
     const int grid = (n_pairs + 255) / 256;
     if (grid == 0) return 0;

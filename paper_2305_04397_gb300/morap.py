@@ -46,6 +46,8 @@ class Config(ctypes.Structure):
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
+        ("sweep_variant_fp32", ctypes.c_int32),
+        ("sweep_variant_fp64", ctypes.c_int32),
     ]
 
 
@@ -64,7 +66,8 @@ class SolveStats(ctypes.Structure):
         ("ms_eval", ctypes.c_double), ("ms_host", ctypes.c_double), ("ms_total", ctypes.c_double),
         ("pairs_not_converged", ctypes.c_int32), ("eval_pairs", ctypes.c_int32),
         ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("variant_fp32", ctypes.c_int32), ("variant_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("ms_tune", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -473,7 +476,7 @@ def morap_plain_vi_noalloc(n_states, n_sa, state_sa, sa_tr, col, prob, cost, pre
 class Server:
     """Continuous-batching query server over built Contexts (morap_server_*)."""
 
-    def __init__(self, contexts, max_batch=64, n_workers=4, eps=1e-6, max_iter=64, hbm_budget=0):
+    def __init__(self, contexts, max_batch=64, n_workers=8, eps=1e-6, max_iter=64, hbm_budget=0):
         cfg = ServerConfig()
         lib().morap_server_config_default(ctypes.byref(cfg))
         cfg.max_batch, cfg.n_workers, cfg.eps, cfg.max_iter, cfg.hbm_budget = max_batch, n_workers, eps, max_iter, \

@@ -1,0 +1,72 @@
+"""Full-size parity on the two large batches, sampled: the 5000-product
+uneven batch (grids of side 16..64 with 1-8 Dirichlet successors, DFAs of
+2-8 locations, K = 64) and the 1000-product 128x128 batch (about 65k states
+per product, K = 32), each solved in one batch as the engine runs it.  A
+handful of (product, weight) pairs is recomputed by the oracle one by one;
+properties that hold at any size are checked on every output."""
+
+import numpy as np
+import pytest
+
+import instances as I
+from oracle import core as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2305_04397_gb300 import build
+
+    build.build()
+    from paper_2305_04397_gb300 import morap
+
+    return morap
+
+
+def _check(M, inst, n_sample, seed):
+    nI, nJ = len(inst.agents), len(inst.tasks)
+    ctx = M.Context()  # eps_vi = 1e-8: the parity setting
+    ctx.add(inst.agents, inst.tasks)
+    fp = ctx.build()
+    W = inst.weights
+    out = ctx.solve(W, evaluate=False)
+    st = ctx.stats()
+    assert out["code"] == M.OK and np.all(out["status"] == M.OK)
+    # every c lies between the value of doing nothing and w_p (values are
+    # scalarised costs <= 0 plus at most one probability weight)
+    wp = W[:, nI:][:, None, :]
+    assert np.all(out["c"] <= wp + 1e-12)
+    rng = np.random.default_rng(seed)
+    sample = [(int(rng.integers(nI)), int(rng.integers(nJ)), int(rng.integers(1, len(W)))) for _ in range(n_sample)]
+    # Algorithm 4 for the sampled pairs under the schedulers of this solve
+    # (the batch holds K <= 64 weights, so they are all still resident)
+    ev = M.morap_evaluate(ctx.h, [i * nJ + j for i, j, _ in sample], [k for _, _, k in sample])
+    for e, (i, j, k) in enumerate(sample):
+        r = O.solve_pair(O.Product(inst.agents[i], inst.tasks[j]), W[k][i], W[k][nI + j])
+        assert out["c"][k, i, j] == pytest.approx(r["c"], abs=TOL), (i, j, k)
+        assert ev["r_cost"][e] == pytest.approx(r["r_cost"], abs=TOL), (i, j, k)
+        assert ev["r_prob"][e] == pytest.approx(r["r_prob"], abs=TOL), (i, j, k)
+        # any size: probabilities in [0, 1], costs <= 0, w.r = c
+        assert -1e-12 <= ev["r_prob"][e] <= 1 + 1e-12 and ev["r_cost"][e] <= 1e-12
+        assert W[k][i] * ev["r_cost"][e] + W[k][nI + j] * ev["r_prob"][e] == pytest.approx(out["c"][k, i, j],
+                                                                                          abs=1e-6)
+    ctx.close()
+    return fp, st
+
+
+def test_uneven_5000_products_k64_sampled(M):
+    inst = I.config_uneven()
+    fp, st = _check(M, inst, n_sample=6, seed=1)
+    assert fp["n_trans"] > 5e8 and st["K"] == 64
+
+
+def test_large_1000_products_128x128_k32_sampled(M):
+    inst = I.config_large()
+    fp, st = _check(M, inst, n_sample=4, seed=2)
+    assert fp["n_states"] > 6e7 and st["K"] == 32

@@ -305,6 +305,26 @@ def test_host_driven_loop_matches_graph_loop(M, tiny):
     b.close()
 
 
+def test_every_kernel_shape_gives_identical_results(M, grid32):
+    """The tuner only picks among kernel shapes that do the same arithmetic
+    in the same order, so each forced shape must reproduce the tuned run
+    bit for bit (and the stats must name the shape used)."""
+    pair = (grid32.agents[:3], grid32.tasks[:5])
+    W = np.ascontiguousarray(grid32.weights[:8][:, [0, 1, 2, 10, 11, 12, 13, 14]])
+    ref_ctx = make_ctx(M, pair)
+    ref = ref_ctx.solve(W, evaluate=True)
+    st = ref_ctx.stats()
+    assert 0 <= st["variant_fp32"] < 4 and 0 <= st["variant_fp64"] < 4
+    ref_ctx.close()
+    for v in range(4):
+        ctx = make_ctx(M, pair, sweep_variant_fp32=v, sweep_variant_fp64=(v + 1) % 4)
+        out = ctx.solve(W, evaluate=True)
+        assert ctx.stats()["variant_fp32"] == v and ctx.stats()["variant_fp64"] == (v + 1) % 4
+        for key in ("c", "r_cost", "r_prob"):
+            assert np.array_equal(out[key], ref[key]), (v, key)
+        ctx.close()
+
+
 def test_batch_invariance(M, grid32):
     """Each pair runs exactly its own sweeps: a weight alone and inside the
     K = 16 batch gives bitwise-identical c and points."""
@@ -373,6 +393,12 @@ def test_invalid_inputs(M, tiny):
         ctx.solve(W)
     assert e.value.code == M.EINVAL
     ctx.close()
+    for field, val in (("sweep_variant_fp32", 4), ("sweep_variant_fp64", -2), ("launch_mode", 2)):
+        cfg = M.morap_config_default()
+        setattr(cfg, field, val)
+        with pytest.raises(M.MorapError) as e:
+            M.Context(cfg)
+        assert e.value.code == M.EINVAL, field
 
 
 def test_hbm_budget_refuses_before_allocating(M, grid32):
