@@ -82,9 +82,10 @@ typedef struct morap_config {
     morap_free_fn free;
     void *alloc_user;
     int32_t sweep_variant_fp32; /* kernel shape of the FP32 / double-float sweeps: -1 (default) =   */
-    int32_t sweep_variant_fp64; /* tuned: the first solve with a given padded batch size times the
-                                   first sweeps of every shape and keeps the fastest (instances with
-                                   fewer than 2^24 transition-weights per sweep use shape 0);
+    int32_t sweep_variant_fp64; /* tuned: the first solve at a given padded batch size runs each
+                                   phase's loop from the host with the shapes rotated body by body
+                                   and keeps the one that moved the most bytes per ms (instances
+                                   with fewer than 2^24 transition-weights per sweep use shape 0);
                                    >= 0 forces one (0 .. 3).  Every shape gives bit-identical
                                    results.                                                         */
 } morap_config;

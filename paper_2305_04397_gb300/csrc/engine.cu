@@ -316,69 +316,72 @@ int sweep_launch_grid(morap_ctx *c, bool fp64, int Kp, int v) {
     return std::max(1, (int)std::min<size_t>((size_t)sweep_grid(c, sweep_blocks_per_sm(fp64, Kp, v)), useful));
 }
 
-// The tuner: time the first sweeps from V = 0 on the batch's weights with each
-// kernel shape and keep the fastest.  Shapes give bit-identical values, so the
-// choice changes only the speed.  Leaves the phase's buffers dirty; the solve
-// initialises them afterwards.
-int tune_sweep_variant(morap_ctx *c, bool fp64, int Kp, cudaStream_t s, int &best_v) {
+// Build the loop graph of one phase for kernel shape v.
+int build_phase_graph(morap_ctx *c, LoopGraph &G, bool fp64, int Kp, int v) {
+    destroy_graph(G);
+    G.variant = v;
+    G.grid = sweep_launch_grid(c, fp64, Kp, v);
+    if (c->cfg.launch_mode != 0) return MORAP_OK;
     const SweepArgs a = fp64 ? c->args64 : c->args32;
-    const size_t nv = (size_t)c->TS * Kp, np = (size_t)c->P * Kp;
-    const unsigned int n_items = (unsigned int)c->h_chunks.size();
-    constexpr int kReps = 3;
-    float best = HUGE_VALF;
-    best_v = 0;
-    for (int v = 0; v < sweep_variant_count(fp64); ++v) {
-        const int grid = sweep_launch_grid(c, fp64, Kp, v);
-        CK(cudaMemsetAsync(a.V[0], 0, nv * (fp64 ? sizeof(float2) : sizeof(float)), s));
-        CK(cudaMemsetAsync(a.V[1], 0, nv * (fp64 ? sizeof(float2) : sizeof(float)), s));
-        CKL(launch_loop_init(a.ctl, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, 1u << 30, s));
-        CKL(launch_sweep(fp64, Kp, v, a, 0, grid, s));  // warm-up
-        CK(cudaEventRecord(c->ev[7], s));
-        for (int pos = 1; pos <= kReps; ++pos) CKL(launch_sweep(fp64, Kp, v, a, pos, grid, s));
-        CK(cudaEventRecord(c->ev[0], s));
-        CK(cudaEventSynchronize(c->ev[0]));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, c->ev[7], c->ev[0]));
-        if (ms < best) {
-            best = ms;
-            best_v = v;
-        }
-    }
-    return MORAP_OK;
+    const int grid = G.grid;
+    return build_loop_graph(c, G, a.ctl, [&](int pos, cudaStream_t st) {
+        return launch_sweep(fp64, Kp, v, a, pos, grid, st);
+    });
 }
 
-// Choose the kernel shapes for Kp (forced by the config, else tuned on the
-// current weights) and build the loop graphs with them.
-int prepare_loops(morap_ctx *c, int Kp, cudaStream_t s) {
-    LoopGraph *G[2] = {&c->g32[log2_of(Kp)], &c->g64[log2_of(Kp)]};
-    const bool need[2] = {c->V32[0] != nullptr, true};
-    if (G[1]->grid) return MORAP_OK;
-    CKL(sweep_setup_attributes());
-    const auto t0 = std::chrono::steady_clock::now();
-    for (int f = 0; f < 2; ++f) {
-        if (!need[f]) continue;
-        const bool fp64 = f == 1;
-        const int forced = fp64 ? c->cfg.sweep_variant_fp64 : c->cfg.sweep_variant_fp32;
-        int v = forced;
-        // tuning pays off only when a sweep is long enough for the shape to matter
-        const bool worth = (double)c->TT * (double)Kp >= (double)(1u << 24);
-        if (v < 0) {
-            if (worth)
-                CKR(tune_sweep_variant(c, fp64, Kp, s, v));
-            else
-                v = 0;
-        }
-        G[f]->variant = v;
-        G[f]->grid = sweep_launch_grid(c, fp64, Kp, v);
-        if (c->cfg.launch_mode == 0) {
-            const SweepArgs a = fp64 ? c->args64 : c->args32;
-            const int grid = G[f]->grid;
-            CKR(build_loop_graph(c, *G[f], a.ctl, [&](int pos, cudaStream_t st) {
-                return launch_sweep(fp64, Kp, v, a, pos, grid, st);
-            }));
-        }
+// The tuner.  The first solve of a phase at a given Kp runs its loop from the
+// host, body by body (six sweeps and the control kernel), rotating the kernel
+// shape from one body to the next, and times each body with CUDA events
+// against the algorithmic bytes it moved; the shape with the most bytes per
+// millisecond over the whole loop is kept and the phase's graph is built with
+// it.  Every shape does the same arithmetic, so the solve's results are those
+// of any single shape; only the first solve pays for the host round trips.
+int run_loop_tuning(morap_ctx *c, LoopGraph &G, bool fp64, int Kp, cudaStream_t s) {
+    const SweepArgs a = fp64 ? c->args64 : c->args32;
+    const int nvar = sweep_variant_count(fp64);
+    std::vector<double> ms(nvar, 0.0), bytes(nvar, 0.0);
+    CKR(stage_ctl(c));
+    unsigned long long prev_bytes = 0;
+    for (int body = 0;; ++body) {
+        const int v = body % nvar;
+        const int grid = sweep_launch_grid(c, fp64, Kp, v);
+        CK(cudaEventRecord(c->ev[7], s));
+        for (int pos = 0; pos < 6; ++pos) CKL(launch_sweep(fp64, Kp, v, a, pos, grid, s));
+        CK(cudaEventRecord(c->ev[5], s));
+        CKL(launch_loop_control_host(a.ctl, 0, s));
+        CK(cudaMemcpyAsync(c->h_ctl, a.ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->ev[7], c->ev[5]));
+        ms[v] += t;
+        bytes[v] += (double)(c->h_ctl->bytes - prev_bytes);
+        prev_bytes = c->h_ctl->bytes;
+        if (c->h_ctl->cnt[0] == 0 || c->h_ctl->sweep_base >= c->h_ctl->cap) break;
     }
-    c->ms_tune += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    int best = 0;
+    double best_rate = -1.0;
+    for (int v = 0; v < nvar; ++v)
+        if (ms[v] > 0.0 && bytes[v] / ms[v] > best_rate) {
+            best_rate = bytes[v] / ms[v];
+            best = v;
+        }
+    return build_phase_graph(c, G, fp64, Kp, best);
+}
+
+// Make the loop of one phase ready for Kp: the shape forced by the config,
+// shape 0 for instances whose sweeps are too short for the shape to matter,
+// otherwise (first solve at this Kp) the tuner decides inside the solve.
+// Returns through `tune` whether this solve must run the tuning loop.
+int prepare_phase(morap_ctx *c, bool fp64, int Kp, bool &tune) {
+    LoopGraph &G = fp64 ? c->g64[log2_of(Kp)] : c->g32[log2_of(Kp)];
+    tune = false;
+    if (G.variant >= 0) return MORAP_OK;
+    CKL(sweep_setup_attributes());
+    const int forced = fp64 ? c->cfg.sweep_variant_fp64 : c->cfg.sweep_variant_fp32;
+    const bool worth = (double)c->TT * (double)Kp >= (double)(1u << 24);
+    if (forced >= 0) return build_phase_graph(c, G, fp64, Kp, forced);
+    if (!worth) return build_phase_graph(c, G, fp64, Kp, 0);
+    tune = true;
     return MORAP_OK;
 }
 
@@ -569,7 +572,6 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     CK(cudaMemcpyAsync(c->d_W, c->h_stage, nW * sizeof(double), cudaMemcpyHostToDevice, s));
     CKL(launch_setup_weights(c->d_prods, c->P, c->nI, c->nJ, K, Kp, c->d_W, c->w32, c->w64, c->wdf, c->thr32,
                              c->thr64, c->cfg.eps_vi, s));
-    CKR(prepare_loops(c, Kp, s));
     const size_t nv = (size_t)c->TS * Kp;
     const unsigned int cap = (unsigned int)std::max(1, c->cfg.max_sweeps);
     const unsigned int n_items = (unsigned int)c->h_chunks.size();
@@ -580,8 +582,13 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         CK(cudaMemsetAsync(c->V32[0], 0, nv * sizeof(float), s));
         CK(cudaMemsetAsync(c->V32[1], 0, nv * sizeof(float), s));
         CKL(launch_loop_init(c->ctl + 0, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s));
+        bool tune = false;
+        CKR(prepare_phase(c, false, Kp, tune));
+        const auto t0 = std::chrono::steady_clock::now();
         CK(cudaEventRecord(c->ev[0], s));
-        {
+        if (tune) {
+            CKR(run_loop_tuning(c, c->g32[log2_of(Kp)], false, Kp, s));
+        } else {
             const SweepArgs a32 = c->args32;
             const LoopGraph &G = c->g32[log2_of(Kp)];
             const int grid = G.grid, v = G.variant;
@@ -590,6 +597,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
             }));
         }
         CK(cudaEventRecord(c->ev[1], s));
+        if (tune) c->ms_tune += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         CKL(launch_convert((const float *)c->V32[0], (float2 *)c->V64[0], (float2 *)c->V64[1], nv, s));
         launches += 2;
     } else {
@@ -597,8 +605,13 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         CK(cudaMemsetAsync(c->V64[1], 0, nv * sizeof(double), s));
     }
     CKL(launch_loop_init(c->ctl + 1, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s));
+    bool tune64 = false;
+    CKR(prepare_phase(c, true, Kp, tune64));
+    const auto t64 = std::chrono::steady_clock::now();
     CK(cudaEventRecord(c->ev[6], s));
-    {
+    if (tune64) {
+        CKR(run_loop_tuning(c, c->g64[log2_of(Kp)], true, Kp, s));
+    } else {
         const SweepArgs a64 = c->args64;
         const LoopGraph &G = c->g64[log2_of(Kp)];
         const int grid = G.grid, v = G.variant;
@@ -607,6 +620,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         }));
     }
     CK(cudaEventRecord(c->ev[2], s));
+    if (tune64) c->ms_tune += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t64).count();
     CKL(launch_finalize(Kp, c->args64, (int)n_items, c->cfg.tau_policy, c->policy, s));
     CKL(launch_gather_c(Kp, c->d_prods, c->P, (const float2 *)c->V64[0], c->frozen, c->d_c, c->d_status, s));
     CK(cudaEventRecord(c->ev[3], s));

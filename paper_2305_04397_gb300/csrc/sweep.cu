@@ -137,8 +137,11 @@ struct ArithF32 {
         c = e.x;
         p = __int_as_float(e.y);
     }
-    // rd(base - w_i' c) with w_i' >= w_i: one FMA, a lower bound of the reward
-    static __device__ __forceinline__ Val reward(W w, Cost c, bool pre) { return __fmaf_rd(w.x, c, pre ? w.y : 0.0f); }
+    // rd(-w_i' c) with w_i' >= w_i and c rounded up: a lower bound of the
+    // action's reward; the pre-sink weight (the same for every action of a
+    // state) is added once, after the maximum, by add_base
+    static __device__ __forceinline__ Val reward(W w, Cost c) { return __fmul_rd(w.x, c); }
+    static __device__ __forceinline__ Val add_base(Val v, W w, bool pre) { return pre ? __fadd_rd(v, w.y) : v; }
     static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) { acc = __fmaf_rd(p, v, acc); }
     static __device__ __forceinline__ void close(Val &) {}
     static __device__ __forceinline__ bool gt(Val a, Val b) { return a > b; }
@@ -204,11 +207,16 @@ struct ArithDF {
         const float2 q = v.p[lt];
         p = {q.x, q.y};
     }
-    static __device__ __forceinline__ Val reward(W w, Cost c, bool pre) {
-        const DF m = df_mul({w.x, w.y}, c);
-        const DF base = pre ? DF{w.z, w.w} : DF{0.0f, 0.0f};
-        return df_add(base, {-m.h, -m.l});
+    // -w_i c, left unnormalised (the accumulation that follows tolerates
+    // it); the pre-sink weight is added once per state by add_base
+    static __device__ __forceinline__ Val reward(W w, Cost c) {
+        const float m = __fmul_rn(w.x, c.h);
+        float e = __fmaf_rn(w.x, c.h, -m);
+        e = __fmaf_rn(w.x, c.l, e);
+        e = __fmaf_rn(w.y, c.h, e);
+        return {-m, -e};
     }
+    static __device__ __forceinline__ Val add_base(Val v, W w, bool pre) { return pre ? df_add({w.z, w.w}, v) : v; }
     // acc += p * v with the sum left unnormalised until the action closes
     static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) {
         const float ph = __fmul_rn(p.h, v.h);
@@ -362,7 +370,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
         {
             const typename Ar::Cost c = Ar::cost(vw, la);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c, pre);
+            for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c);
         }
         for (uint32_t base = t0; base < t1; base += D) {
             int32_t cl[D];
@@ -395,6 +403,8 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
         }
         t0 = t1;
     }
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) best[v] = Ar::add_base(best[v], sw[v], pre);
     float yw[NW];
     load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
 #pragma unroll
@@ -467,7 +477,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         {
             const typename Ar::Cost c = Ar::cost(vw, la);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c, pre);
+            for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c);
         }
         for (;;) {
 #pragma unroll
@@ -502,6 +512,8 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         if (!more2) break;
         ++la;
     }
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) best[v] = Ar::add_base(best[v], sw[v], pre);
     float yw[NW];
     load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
 #pragma unroll
@@ -698,8 +710,9 @@ __global__ void __launch_bounds__(kThreads) k_finalize(SweepArgs a, int n_chunks
         for (int s = ch.y + slot; s < ch.z; s += SPR) {
             const uint32_t u = pd.state_off + (uint32_t)s;
             const size_t row = (size_t)u * KP + k0;
-            const bool pre = (uint32_t)s >= pd.pre_begin;
             const uint32_t a0 = a.state_sa[u], a1 = a.state_sa[u + 1];
+            // Q without the state's pre-sink weight, which is the same for
+            // every action and cancels in every comparison below
             DF best[VEC], qrec[VEC];
             uint8_t rec[VEC], pick[VEC], pick_loop[VEC];
 #pragma unroll
@@ -719,7 +732,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(SweepArgs a, int n_chunks
                     const float2 cd = a.costdf[sa];
                     DF acc[VEC];
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[v] = ArithDF::reward(w[v], {cd.x, cd.y}, pre);
+                    for (int v = 0; v < VEC; ++v) acc[v] = ArithDF::reward(w[v], {cd.x, cd.y});
                     const uint32_t t0 = a.sa_tr[sa], t1 = a.sa_tr[sa + 1];
                     const bool self_loop = (t1 - t0 == 1) && ((uint32_t)a.col[t0] == u);
                     for (uint32_t t = t0; t < t1; ++t) {
@@ -914,7 +927,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
 // operator, where the residual is exactly 0, so any shift terminates; the
 // shift only trades FP32 sweeps against double-float sweeps.
 #ifndef MORAP_THR32_SHIFT
-#define MORAP_THR32_SHIFT 20
+#define MORAP_THR32_SHIFT 17
 #endif
 
 __device__ __forceinline__ float2 to_df(double d) {
