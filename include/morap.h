@@ -298,6 +298,16 @@ typedef struct morap_point_result {
     double *t_down;       /* caller-provided [|I|+|J|] or NULL                          */
     double *w_hist;       /* caller-provided [max_iter][|I|+|J|] or NULL                */
     double *r_hist;       /* caller-provided [max_iter][|I|+|J|] or NULL                */
+    double *lambda;       /* caller-provided [max_iter] or NULL: the synthesis — convex
+                             weights over the supporting points r_hist with
+                             sum_l lambda_l r_l >= t_up (>= t when feasible).  Running
+                             point l's assignment and schedulers with probability
+                             lambda_l achieves that vector in expectation (Sec. 3.3)  */
+    int32_t *assign_hist; /* caller-provided [max_iter][|J|] or NULL: the task
+                             assignment of each point (agent of task j, -1 for none);
+                             morap_query only.  A point's schedulers are those of
+                             morap_solve for its weight vector w_hist[l] (results are
+                             deterministic)                                          */
 } morap_point_result;
 
 /* Algorithm 1 for threshold t = (c, p) with norm ||v|| = sqrt(v^T M v)

@@ -230,6 +230,7 @@ void free_solve(morap_ctx *c) {
     dev_free_list(c, c->solve_allocs);
     c->Kp = 0;
     c->Kcap = 0;
+    c->last_K = 0;  // the schedulers of the last solve are gone
 }
 
 int log2_of(int Kp) {
@@ -447,6 +448,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a.frozen = c->frozen;
     a.a_rec = c->a_rec;
     a.eps1 = c->cfg.eps_vi;
+    a.eps1f = (float)c->cfg.eps_vi;
     a.P = c->P;
     SweepArgs a32 = a, a64 = a;
     a32.thr = c->thr32;
@@ -779,6 +781,40 @@ int run_evaluation(morap_ctx *c, const std::vector<int4> &pairs, cudaStream_t s,
     c->stats.eval_pairs = npairs;
     return MORAP_OK;
 }
+
+}  // namespace
+
+// Allocate, once, everything a batch of up to K weights needs (solve buffers,
+// evaluation buffers for K x |J| assigned pairs of the largest products) and
+// the loop graphs of every padded size up to K whose kernel shape needs no
+// tuning, so that later batches of varying size neither allocate nor free
+// (a device free synchronises the whole device).
+int morap::ctx_reserve(morap_ctx *c, int K) {
+    if (!c->built) return fail(MORAP_ESTATE, "reserve before build");
+    CK(cudaSetDevice(c->cfg.device));
+    const int Kp = next_pow2(std::max(1, std::min(K, 64)));
+    const int old_Kp = c->Kp;
+    const bool grow = Kp > c->Kcap;
+    CKR(ensure_solve(c, Kp));
+    size_t states = 0, chunks = 0;
+    for (int j = 0; j < c->nJ; ++j) {
+        uint32_t mx = 0;
+        for (int i = 0; i < c->nI; ++i) mx = std::max(mx, c->h_prods[(size_t)i * c->nJ + j].n_nd);
+        states += mx + 1;
+        chunks += (mx + kEvalChunk - 1) / kEvalChunk;
+    }
+    CKR(ensure_eval(c, (size_t)Kp * c->nJ, (size_t)Kp * chunks, (size_t)Kp * std::min<size_t>(states, kEvalStates)));
+    for (int kp = 1; kp <= Kp; kp *= 2)
+        for (int f = 0; f < 2; ++f) {
+            if (f == 0 && !c->V32[0]) continue;
+            bool tune = false;
+            CKR(prepare_phase(c, f == 1, kp, tune));  // shapes that need tuning are left to the first solve
+        }
+    if (!grow) c->Kp = old_Kp;
+    return MORAP_OK;
+}
+
+namespace {
 
 int supporting_batch(morap_ctx *c, int K, const double *W, cudaStream_t s, double *r_out, int32_t *assign_out,
                      double *c_out) {
@@ -1323,13 +1359,14 @@ int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, in
     Alg1 q;
     q.init(n, t, M, eps, max_iter);
     std::vector<double> r(n);
+    std::vector<int32_t> f(ctx->nJ);
     while (!q.done) {
-        const int rc = morap_supporting_points(ctx, 1, q.w.data(), stream, r.data(), nullptr, nullptr);
+        const int rc = morap_supporting_points(ctx, 1, q.w.data(), stream, r.data(), f.data(), nullptr);
         if (rc == MORAP_ENOTCONV)
             q.status = rc;
         else if (rc != MORAP_OK)
             return rc;
-        q.step(r.data());
+        q.step(r.data(), f.data(), ctx->nJ);
     }
     const int status = alg1_result(q, res);
     if (status != MORAP_OK) return fail(status, "query stopped before ||t_down - t_up|| <= eps");

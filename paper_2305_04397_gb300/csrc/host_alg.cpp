@@ -225,6 +225,49 @@ double inf_norm(const std::vector<double> &v) {
 
 }  // namespace
 
+// Solve the QP with the inequalities in `act` held as equalities (the KKT
+// system of the equality-constrained problem).  Accepts the point only if it
+// is feasible for every inequality and the multipliers of the held ones are
+// nonnegative, i.e. it is the exact optimum for that active set.
+bool qp_active_set_solve(int n, const double *G, const double *c, int m, const double *A, const double *b, int p,
+                         const double *E, const double *d, const std::vector<int> &act, double scale,
+                         double *x_out) {
+    const int na = (int)act.size(), N = n + na + p;
+    std::vector<double> K((size_t)N * N, 0.0), r(N, 0.0);
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) K[(size_t)i * N + j] = G[(size_t)i * n + j];
+        r[i] = -c[i];
+    }
+    for (int q = 0; q < na; ++q) {
+        const double *ak = A + (size_t)act[q] * n;
+        for (int j = 0; j < n; ++j) {
+            K[(size_t)(n + q) * N + j] = ak[j];
+            K[(size_t)j * N + (n + q)] = ak[j];
+        }
+        r[n + q] = b[act[q]];
+    }
+    for (int q = 0; q < p; ++q) {
+        for (int j = 0; j < n; ++j) {
+            K[(size_t)(n + na + q) * N + j] = E[(size_t)q * n + j];
+            K[(size_t)j * N + (n + na + q)] = E[(size_t)q * n + j];
+        }
+        r[n + na + q] = d[q];
+    }
+    std::vector<int> piv;
+    if (!lu_factor(N, K, piv)) return false;
+    lu_solve(N, K, piv, r.data());
+    const double ftol = 1e-12 * scale;
+    for (int q = 0; q < na; ++q)
+        if (r[n + q] < -ftol) return false;  // a held constraint wants to be released
+    for (int k = 0; k < m; ++k) {
+        double ax = 0.0;
+        for (int j = 0; j < n; ++j) ax += A[(size_t)k * n + j] * r[j];
+        if (ax > b[k] + ftol) return false;
+    }
+    std::copy(r.begin(), r.begin() + n, x_out);
+    return true;
+}
+
 int qp_solve(int n, const double *G, const double *c, int m, const double *A, const double *b, int p,
              const double *E, const double *d, double *x, double tol, int max_iter) {
     std::vector<double> s(m), z(m, 1.0), y(p, 0.0);
@@ -297,6 +340,16 @@ int qp_solve(int n, const double *G, const double *c, int m, const double *A, co
                                 : 0.0;
         const double res = std::max(inf_norm(rd), std::max(inf_norm(rp), inf_norm(re)));
         if (res <= tol * scale && mu <= 1e-3 * tol * scale) return 0;
+        // Near the optimum the active constraints are those whose slack has
+        // gone to zero while the multiplier has not: solve for them exactly
+        // (an interior point's x is only accurate to the square root of the
+        // duality gap, and the gap cannot shrink much below rounding).
+        if (m > 0 && res <= 1e-7 * scale && mu <= 1e-6 * scale) {
+            std::vector<int> act;
+            for (int k = 0; k < m; ++k)
+                if (z[k] > s[k]) act.push_back(k);
+            if (qp_active_set_solve(n, G, c, m, A, b, p, E, d, act, scale, x)) return 0;
+        }
         // K = [G + A' diag(z/s) A, E'; E, 0]
         std::fill(K.begin(), K.end(), 0.0);
         const int N = n + p;
@@ -364,7 +417,7 @@ int project_halfspaces(int n, int m, const double *t, const double *A, const dou
 
 // Algorithm 1, inner bound: argmin_x ||t - x||_M over x <= sum_l lam_l Phi_l,
 // lam >= 0, sum lam = 1 (variables x and lam).
-int project_down_hull(int n, int m, const double *t, const double *Phi, const double *M, double *x) {
+int project_down_hull(int n, int m, const double *t, const double *Phi, const double *M, double *x, double *lambda) {
     const int N = n + m;
     std::vector<double> G((size_t)N * N, 0.0), c(N, 0.0), v(N, 0.0);
     for (int i = 0; i < n; ++i)
@@ -390,6 +443,12 @@ int project_down_hull(int n, int m, const double *t, const double *Phi, const do
     }
     const int rc = qp_solve(N, G.data(), c.data(), mi, A.data(), b.data(), 1, E.data(), d.data(), v.data());
     for (int i = 0; i < n; ++i) x[i] = std::min(v[i], t[i]);
+    if (lambda) {
+        // the convex weights, cleaned of the solver's roundoff (>= 0, sum 1)
+        double sum = 0.0;
+        for (int l = 0; l < m; ++l) sum += (lambda[l] = std::max(v[n + l], 0.0));
+        for (int l = 0; l < m; ++l) lambda[l] = sum > 0.0 ? lambda[l] / sum : 1.0 / m;
+    }
     return rc;
 }
 
@@ -421,6 +480,8 @@ void Alg1::init(int n_obj, const double *t_in, const double *M_in, double eps_in
     b.clear();
     w_hist.clear();
     r_hist.clear();
+    f_hist.clear();
+    lambda.clear();
     moved = false;
     done = false;
     it = 0;
@@ -435,10 +496,14 @@ void Alg1::init(int n_obj, const double *t_in, const double *M_in, double eps_in
 // outer bound moves when w.r < w.t_down; the inner bound is re-projected;
 // then the loop test on ||t_down - t_up||_M, and the next direction
 // w = M (t - t_up) / ||M (t - t_up)||_1.
-void Alg1::step(const double *r) {
+void Alg1::step(const double *r, const int32_t *assign, int n_tasks) {
     const double *Mp = M.empty() ? nullptr : M.data();
     w_hist.insert(w_hist.end(), w.begin(), w.end());
     r_hist.insert(r_hist.end(), r, r + n);
+    if (assign && n_tasks > 0) {
+        f_tasks = n_tasks;
+        f_hist.insert(f_hist.end(), assign, assign + n_tasks);
+    }
     ++it;
     Phi.insert(Phi.end(), r, r + n);
     A.insert(A.end(), w.begin(), w.end());
@@ -452,7 +517,8 @@ void Alg1::step(const double *r) {
         project_halfspaces(n, (int)b.size(), t.data(), A.data(), b.data(), Mp, t_dn.data());
         moved = true;
     }
-    project_down_hull(n, it, t.data(), Phi.data(), Mp, t_up.data());
+    lambda.assign(it, 0.0);
+    project_down_hull(n, it, t.data(), Phi.data(), Mp, t_up.data(), lambda.data());
     std::vector<double> d(n);
     for (int i = 0; i < n; ++i) d[i] = t_dn[i] - t_up[i];
     dist = mnorm(n, d.data(), Mp);
@@ -487,6 +553,8 @@ int alg1_result(const Alg1 &q, morap_point_result *res) {
     if (res->t_down) std::copy(q.t_dn.begin(), q.t_dn.end(), res->t_down);
     if (res->w_hist) std::copy(q.w_hist.begin(), q.w_hist.end(), res->w_hist);
     if (res->r_hist) std::copy(q.r_hist.begin(), q.r_hist.end(), res->r_hist);
+    if (res->lambda) std::copy(q.lambda.begin(), q.lambda.end(), res->lambda);
+    if (res->assign_hist && !q.f_hist.empty()) std::copy(q.f_hist.begin(), q.f_hist.end(), res->assign_hist);
     return status;
 }
 

@@ -62,7 +62,9 @@ int qp_solve(int n, const double *G, const double *c, int m, const double *A, co
 
 int project_halfspaces(int n, int m, const double *t, const double *A, const double *b, const double *M,
                        double *z);
-int project_down_hull(int n, int m, const double *t, const double *Phi, const double *M, double *x);
+// lambda (nullable, [m]): convex weights of the points with x <= sum lambda_l Phi_l
+int project_down_hull(int n, int m, const double *t, const double *Phi, const double *M, double *x,
+                      double *lambda = nullptr);
 
 // ||v||_M = sqrt(v' M v); M row-major [n][n], NULL = identity.
 double mnorm(int n, const double *v, const double *M);
@@ -74,8 +76,11 @@ struct Alg1 {
     double eps = 1e-6, dist = HUGE_VAL;
     bool moved = false, done = false;
     std::vector<double> t, M, w, t_dn, t_up, Phi, A, b, w_hist, r_hist;
+    std::vector<double> lambda;  // convex weights of the points behind t_up (last projection)
+    std::vector<int32_t> f_hist;  // assignment of each point, [it][f_tasks], when the caller gives it
+    int f_tasks = 0;
     void init(int n_obj, const double *t_in, const double *M_in, double eps_in, int max_iter_in);
-    void step(const double *r);
+    void step(const double *r, const int32_t *assign = nullptr, int n_tasks = 0);
 };
 // Fill *res from a finished run; returns its status (ENOTCONV when it
 // stopped with ||t_down - t_up|| > eps).
@@ -156,6 +161,7 @@ struct SweepArgs {
     void *V[2];
     uint8_t *a_rec;
     double eps1;
+    float eps1f;  // eps1 rounded to FP32 (record tests in the kernels)
     int P;
 };
 
@@ -186,6 +192,9 @@ struct EvalArgs {
     int stride;      // slots per state: the longest action row of any agent
 };
 
+// Engine helpers the serving layer uses (engine.cu).
+int ctx_reserve(morap_ctx *c, int K);
+
 // ---------------------------------------------------------- kernel launchers
 // (defined in the .cu files; every launcher enqueues on `s` and returns the
 // cudaError_t of the launch as an int)
@@ -208,6 +217,7 @@ int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, un
 int launch_sweep(bool fp64, int Kp, int variant, const SweepArgs &a, int pos, int grid, void *s);
 int sweep_blocks_per_sm(bool fp64, int Kp, int variant);
 int sweep_variant_count(bool fp64);
+
 void sweep_variant_shape(bool fp64, int variant, int *vmax, int *d, int *minb);
 int eval_blocks_per_sm();
 int launch_loop_control(LoopCtl *ctl, unsigned long long handle, int next_idx, void *s);

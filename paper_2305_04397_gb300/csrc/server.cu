@@ -44,7 +44,7 @@ struct ServerQuery {
 
 struct morap_server {
     std::vector<morap_ctx *> inst;
-    std::vector<int> n_obj;
+    std::vector<int> n_obj, n_tasks;
     std::vector<int64_t> bytes_per_weight;
     std::vector<cudaStream_t> streams;
     std::vector<char> busy;
@@ -106,14 +106,16 @@ void worker_loop(morap_server *S) {
             S->ready[i].pop_front();
         }
         const int n = S->n_obj[i];
+        const int nJ = S->n_tasks[i];
         std::vector<double> W(batch.size() * n), R(batch.size() * n);
+        std::vector<int32_t> F(batch.size() * nJ);
         for (size_t b = 0; b < batch.size(); ++b) {
             const ServerQuery &q = S->queries[batch[b]];
             std::copy(q.ps.w.begin(), q.ps.w.end(), W.begin() + b * n);
         }
         lk.unlock();
         const int rc = morap_supporting_points(S->inst[i], (int32_t)batch.size(), W.data(), (void *)S->streams[i],
-                                               R.data(), nullptr, nullptr);
+                                               R.data(), F.data(), nullptr);
         lk.lock();
         S->batches += 1;
         S->batch_queries += (int64_t)batch.size();
@@ -128,7 +130,7 @@ void worker_loop(morap_server *S) {
                 Alg1 ps = q.ps;
                 if (rc == MORAP_ENOTCONV && ps.status == MORAP_OK) ps.status = rc;
                 lk.unlock();
-                ps.step(R.data() + b * n);
+                ps.step(R.data() + b * n, F.data() + b * nJ, nJ);
                 lk.lock();
                 q.ps = std::move(ps);
             }
@@ -192,9 +194,16 @@ int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const 
             ++p;
         }
         set_error("");
+        // reserve a full batch up front (when the admission budget allows it),
+        // so batches of varying size never allocate or free device memory
+        const int64_t bpw = states * (2 * 4 + 2 * 8 + 1 + 1);
+        int reserve = cfg.max_batch;
+        if (cfg.hbm_budget) reserve = (int)std::min<int64_t>(reserve, std::max<int64_t>(1, (int64_t)cfg.hbm_budget / bpw));
+        if (ctx_reserve(c, reserve) != MORAP_OK) set_error("");  // not fatal: buffers then grow on demand
         S->inst.push_back(c);
         S->n_obj.push_back(nI + nJ);
-        S->bytes_per_weight.push_back(states * (2 * 4 + 2 * 8 + 1 + 1));
+        S->n_tasks.push_back(nJ);
+        S->bytes_per_weight.push_back(bpw);
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             for (auto s : S->streams) cudaStreamDestroy(s);

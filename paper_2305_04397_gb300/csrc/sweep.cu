@@ -102,26 +102,33 @@ constexpr int kStageStates = 32;  // states per batch (at most; fewer when the r
 struct ArithF32 {
     using Val = float;
     static constexpr int AMAX = 192, EMAX = 448;
-    // ssa[kStageStates + 1] | str[AMAX + 1] | cost[AMAX] | edge[EMAX] (int2)
-    static constexpr int OFF_STR = 136, OFF_COST = OFF_STR + 4 * (AMAX + 2), OFF_EDGE = OFF_COST + 4 * AMAX;
-    static constexpr int STAGE_BYTES = OFF_EDGE + 8 * EMAX;
+    // ssa[kStageStates + 1] | str[AM + 1] | cost[AM] | edge[EM] (int2)
+    template <int AM, int EM>
+    struct Lay {
+        static constexpr int STR = 136, COST = STR + 4 * (AM + 2), EDGE = COST + 4 * AM, BYTES = EDGE + 8 * EM;
+    };
+    static constexpr int STAGE_BYTES = Lay<AMAX, EMAX>::BYTES;
     struct View {
         const uint32_t *str;
         const float *cost;
         const int2 *edge;
     };
+    template <int AM = AMAX, int EM = EMAX>
     static __device__ __forceinline__ View smem_view(unsigned char *b) {
-        return {reinterpret_cast<const uint32_t *>(b + OFF_STR), reinterpret_cast<const float *>(b + OFF_COST),
-                reinterpret_cast<const int2 *>(b + OFF_EDGE)};
+        using L = Lay<AM, EM>;
+        return {reinterpret_cast<const uint32_t *>(b + L::STR), reinterpret_cast<const float *>(b + L::COST),
+                reinterpret_cast<const int2 *>(b + L::EDGE)};
     }
     static __device__ __forceinline__ View global_view(const SweepArgs &a, uint32_t A0, uint32_t T0) {
         return {a.sa_tr + A0, a.cost32 + A0, a.cp32 + T0};
     }
+    template <int AM = AMAX, int EM = EMAX>
     static __device__ __forceinline__ void stage(const SweepArgs &a, unsigned char *b, uint32_t A0, uint32_t nA,
                                                  uint32_t T0, uint32_t nT, int lane) {
-        uint32_t *str = reinterpret_cast<uint32_t *>(b + OFF_STR);
-        float *cost = reinterpret_cast<float *>(b + OFF_COST);
-        int2 *edge = reinterpret_cast<int2 *>(b + OFF_EDGE);
+        using L = Lay<AM, EM>;
+        uint32_t *str = reinterpret_cast<uint32_t *>(b + L::STR);
+        float *cost = reinterpret_cast<float *>(b + L::COST);
+        int2 *edge = reinterpret_cast<int2 *>(b + L::EDGE);
         for (uint32_t i = lane; i <= nA; i += 32) cp_async4(str + i, a.sa_tr + A0 + i);
         for (uint32_t i = lane; i < nA; i += 32) cp_async4(cost + i, a.cost32 + A0 + i);
         for (uint32_t i = lane; i < nT; i += 32) cp_async8(edge + i, a.cp32 + T0 + i);
@@ -140,7 +147,10 @@ struct ArithF32 {
     // rd(-w_i' c) with w_i' >= w_i and c rounded up: a lower bound of the
     // action's reward; the pre-sink weight (the same for every action of a
     // state) is added once, after the maximum, by add_base
-    static __device__ __forceinline__ Val reward(W w, Cost c) { return __fmul_rd(w.x, c); }
+    using CW = float;  // the part of W the reward needs
+    static __device__ __forceinline__ CW cost_weight(W w) { return w.x; }
+    static __device__ __forceinline__ Val reward_cw(CW w, Cost c) { return __fmul_rd(w, c); }
+    static __device__ __forceinline__ Val reward(W w, Cost c) { return reward_cw(cost_weight(w), c); }
     static __device__ __forceinline__ Val add_base(Val v, W w, bool pre) { return pre ? __fadd_rd(v, w.y) : v; }
     static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) { acc = __fmaf_rd(p, v, acc); }
     static __device__ __forceinline__ void close(Val &) {}
@@ -154,38 +164,45 @@ struct ArithF32 {
     // eps1.  In FP32 a move of a few ulps is rounding, not propagation, so
     // this phase records only moves above 64 ulps of the new value (the
     // double-float phase that follows records with eps1 itself).
-    static __device__ __forceinline__ float record_threshold(Val y, double eps1) {
+    static __device__ __forceinline__ float record_threshold(Val y, float eps1) {
         const float rel = y * 7.62939453125e-06f; /* 2^-17 */
-        return rel > (float)eps1 ? rel : (float)eps1;
+        return rel > eps1 ? rel : eps1;
     }
 };
 
 struct ArithDF {
     using Val = DF;
     static constexpr int AMAX = 192, EMAX = 448;
-    // ssa | str[AMAX + 1] | cost[AMAX] (float2) | col[EMAX] | p[EMAX] (float2)
-    static constexpr int OFF_STR = 136, OFF_COST = OFF_STR + 4 * (AMAX + 2), OFF_COL = OFF_COST + 8 * AMAX,
-                         OFF_P = OFF_COL + 4 * EMAX;
-    static constexpr int STAGE_BYTES = OFF_P + 8 * EMAX;
+    // ssa | str[AM + 1] | cost[AM] (float2) | col[EM] | p[EM] (float2)
+    template <int AM, int EM>
+    struct Lay {
+        static constexpr int STR = 136, COST = STR + 4 * (AM + 2), COL = COST + 8 * AM, P = COL + 4 * EM,
+                             BYTES = P + 8 * EM;
+    };
+    static constexpr int STAGE_BYTES = Lay<AMAX, EMAX>::BYTES;
     struct View {
         const uint32_t *str;
         const float2 *cost;
         const int32_t *col;
         const float2 *p;
     };
+    template <int AM = AMAX, int EM = EMAX>
     static __device__ __forceinline__ View smem_view(unsigned char *b) {
-        return {reinterpret_cast<const uint32_t *>(b + OFF_STR), reinterpret_cast<const float2 *>(b + OFF_COST),
-                reinterpret_cast<const int32_t *>(b + OFF_COL), reinterpret_cast<const float2 *>(b + OFF_P)};
+        using L = Lay<AM, EM>;
+        return {reinterpret_cast<const uint32_t *>(b + L::STR), reinterpret_cast<const float2 *>(b + L::COST),
+                reinterpret_cast<const int32_t *>(b + L::COL), reinterpret_cast<const float2 *>(b + L::P)};
     }
     static __device__ __forceinline__ View global_view(const SweepArgs &a, uint32_t A0, uint32_t T0) {
         return {a.sa_tr + A0, a.costdf + A0, a.col + T0, a.pdf + T0};
     }
+    template <int AM = AMAX, int EM = EMAX>
     static __device__ __forceinline__ void stage(const SweepArgs &a, unsigned char *b, uint32_t A0, uint32_t nA,
                                                  uint32_t T0, uint32_t nT, int lane) {
-        uint32_t *str = reinterpret_cast<uint32_t *>(b + OFF_STR);
-        float2 *cost = reinterpret_cast<float2 *>(b + OFF_COST);
-        int32_t *col = reinterpret_cast<int32_t *>(b + OFF_COL);
-        float2 *p = reinterpret_cast<float2 *>(b + OFF_P);
+        using L = Lay<AM, EM>;
+        uint32_t *str = reinterpret_cast<uint32_t *>(b + L::STR);
+        float2 *cost = reinterpret_cast<float2 *>(b + L::COST);
+        int32_t *col = reinterpret_cast<int32_t *>(b + L::COL);
+        float2 *p = reinterpret_cast<float2 *>(b + L::P);
         for (uint32_t i = lane; i <= nA; i += 32) cp_async4(str + i, a.sa_tr + A0 + i);
         for (uint32_t i = lane; i < nA; i += 32) cp_async8(cost + i, a.costdf + A0 + i);
         for (uint32_t i = lane; i < nT; i += 32) {
@@ -209,13 +226,16 @@ struct ArithDF {
     }
     // -w_i c, left unnormalised (the accumulation that follows tolerates
     // it); the pre-sink weight is added once per state by add_base
-    static __device__ __forceinline__ Val reward(W w, Cost c) {
+    using CW = float2;  // w_i as (hi, lo)
+    static __device__ __forceinline__ CW cost_weight(W w) { return make_float2(w.x, w.y); }
+    static __device__ __forceinline__ Val reward_cw(CW w, Cost c) {
         const float m = __fmul_rn(w.x, c.h);
         float e = __fmaf_rn(w.x, c.h, -m);
         e = __fmaf_rn(w.x, c.l, e);
         e = __fmaf_rn(w.y, c.h, e);
         return {-m, -e};
     }
+    static __device__ __forceinline__ Val reward(W w, Cost c) { return reward_cw(cost_weight(w), c); }
     static __device__ __forceinline__ Val add_base(Val v, W w, bool pre) { return pre ? df_add({w.z, w.w}, v) : v; }
     // acc += p * v with the sum left unnormalised until the action closes
     static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) {
@@ -239,7 +259,7 @@ struct ArithDF {
         w[0] = v.h;
         w[1] = v.l;
     }
-    static __device__ __forceinline__ float record_threshold(Val, double eps1) { return (float)eps1; }
+    static __device__ __forceinline__ float record_threshold(Val, float eps1) { return eps1; }
 };
 
 // Load / store NW consecutive 32-bit words with the widest aligned accesses.
@@ -283,18 +303,18 @@ struct Variants;
 template <>
 struct Variants<ArithF32> {
     static constexpr int N = 4;
-    static constexpr int vmax[N] = {8, 8, 8, 4};
-    static constexpr int d[N] = {3, 3, 2, 3};
-    static constexpr int minb[N] = {2, 2, 2, 2};
-    static constexpr int pipe[N] = {0, 1, 1, 1};  // actions software-pipelined
+    static constexpr int vmax[N] = {8, 8, 4, 8};
+    static constexpr int d[N] = {3, 4, 4, 2};
+    static constexpr int minb[N] = {2, 2, 3, 2};
+    static constexpr int pipe[N] = {0, 0, 0, 1};  // actions software-pipelined
 };
 template <>
 struct Variants<ArithDF> {
     static constexpr int N = 4;
-    static constexpr int vmax[N] = {4, 4, 4, 2};
-    static constexpr int d[N] = {3, 3, 2, 4};
-    static constexpr int minb[N] = {2, 2, 2, 2};
-    static constexpr int pipe[N] = {0, 1, 1, 1};
+    static constexpr int vmax[N] = {4, 4, 2, 4};
+    static constexpr int d[N] = {3, 4, 4, 2};
+    static constexpr int minb[N] = {2, 2, 3, 2};
+    static constexpr int pipe[N] = {0, 0, 0, 1};
 };
 
 // Lanes per state and weights per lane for each (format, Kp, VMAX).
@@ -412,7 +432,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
         if (!((act_bits >> v) & 1u)) continue;
         const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
         rmax[v] = d > rmax[v] ? d : rmax[v];
-        if (d > Ar::record_threshold(best[v], a.eps1)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
+        if (d > Ar::record_threshold(best[v], a.eps1f)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
         Ar::to_words(best[v], &yw[v * Ar::WORDS]);
     }
     store_words<NW>(Vnew + row, yw);
@@ -521,7 +541,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         if (!((act_bits >> v) & 1u)) continue;
         const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
         rmax[v] = d > rmax[v] ? d : rmax[v];
-        if (d > Ar::record_threshold(best[v], a.eps1)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
+        if (d > Ar::record_threshold(best[v], a.eps1f)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
         Ar::to_words(best[v], &yw[v * Ar::WORDS]);
     }
     store_words<NW>(Vnew + row, yw);
@@ -1049,21 +1069,31 @@ constexpr int smem_of() {
 
 using SweepFn = void (*)(SweepArgs, int);
 
+struct SweepKernel {
+    SweepFn f;
+    int smem;  // dynamic shared memory per block
+};
+
+template <class Ar, int KP, int V>
+SweepKernel sweep_kernel() {
+    using VA = Variants<Ar>;
+    return {&k_sweep<Ar, KP, VA::vmax[V], VA::d[V], VA::minb[V], VA::pipe[V]>, smem_of<Ar>()};
+}
+
 template <class Ar, int KP, int... V>
-std::array<SweepFn, Variants<Ar>::N> sweep_row(std::integer_sequence<int, V...>) {
-    return {&k_sweep<Ar, KP, Variants<Ar>::vmax[V], Variants<Ar>::d[V], Variants<Ar>::minb[V],
-                     Variants<Ar>::pipe[V]>...};
+std::array<SweepKernel, Variants<Ar>::N> sweep_row(std::integer_sequence<int, V...>) {
+    return {sweep_kernel<Ar, KP, V>()...};
 }
 
 // sweep_fn<Ar>(log2 Kp, variant)
 template <class Ar>
-SweepFn sweep_fn(int lg, int v) {
+const SweepKernel *sweep_fn(int lg, int v) {
     using Seq = std::make_integer_sequence<int, Variants<Ar>::N>;
-    static const std::array<std::array<SweepFn, Variants<Ar>::N>, 7> table = {
+    static const std::array<std::array<SweepKernel, Variants<Ar>::N>, 7> table = {
         sweep_row<Ar, 1>(Seq{}),  sweep_row<Ar, 2>(Seq{}),  sweep_row<Ar, 4>(Seq{}), sweep_row<Ar, 8>(Seq{}),
         sweep_row<Ar, 16>(Seq{}), sweep_row<Ar, 32>(Seq{}), sweep_row<Ar, 64>(Seq{})};
     if (lg < 0 || lg > 6 || v < 0 || v >= Variants<Ar>::N) return nullptr;
-    return table[lg][v];
+    return &table[lg][v];
 }
 
 int log2_kp(int Kp) {
@@ -1074,9 +1104,9 @@ int log2_kp(int Kp) {
 
 template <class Ar>
 int launch_sweep_t(int Kp, int variant, const SweepArgs &a, int pos, int grid, cudaStream_t s) {
-    const SweepFn f = sweep_fn<Ar>(log2_kp(Kp), variant);
-    if (!f) return (int)cudaErrorInvalidValue;
-    f<<<grid, kThreads, smem_of<Ar>(), s>>>(a, pos);
+    const SweepKernel *k = sweep_fn<Ar>(log2_kp(Kp), variant);
+    if (!k) return (int)cudaErrorInvalidValue;
+    k->f<<<grid, kThreads, k->smem, s>>>(a, pos);
     return (int)cudaGetLastError();
 }
 
@@ -1084,8 +1114,8 @@ template <class Ar>
 cudaError_t set_attr_t() {
     for (int lg = 0; lg < 7; ++lg)
         for (int v = 0; v < Variants<Ar>::N; ++v) {
-            const cudaError_t e =
-                cudaFuncSetAttribute(sweep_fn<Ar>(lg, v), cudaFuncAttributeMaxDynamicSharedMemorySize, smem_of<Ar>());
+            const SweepKernel *k = sweep_fn<Ar>(lg, v);
+            const cudaError_t e = cudaFuncSetAttribute(k->f, cudaFuncAttributeMaxDynamicSharedMemorySize, k->smem);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -1095,9 +1125,9 @@ cudaError_t set_attr_t() {
 
 template <class Ar>
 int blocks_per_sm_t(int Kp, int variant) {
-    const SweepFn f = sweep_fn<Ar>(log2_kp(Kp), variant);
+    const SweepKernel *k = sweep_fn<Ar>(log2_kp(Kp), variant);
     int n = 0;
-    if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem_of<Ar>()) != cudaSuccess) {
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k->f, kThreads, k->smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -1117,6 +1147,8 @@ int sweep_blocks_per_sm(bool fp64, int Kp, int variant) {
 }
 
 int sweep_variant_count(bool fp64) { return fp64 ? Variants<ArithDF>::N : Variants<ArithF32>::N; }
+
+
 
 void sweep_variant_shape(bool fp64, int variant, int *vmax, int *d, int *minb) {
     *vmax = fp64 ? Variants<ArithDF>::vmax[variant] : Variants<ArithF32>::vmax[variant];

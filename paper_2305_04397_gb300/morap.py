@@ -94,6 +94,7 @@ class PointResult(ctypes.Structure):
         ("status", ctypes.c_int32), ("distance", ctypes.c_double),
         ("t_up", ctypes.POINTER(ctypes.c_double)), ("t_down", ctypes.POINTER(ctypes.c_double)),
         ("w_hist", ctypes.POINTER(ctypes.c_double)), ("r_hist", ctypes.POINTER(ctypes.c_double)),
+        ("lambda_", ctypes.POINTER(ctypes.c_double)), ("assign_hist", ctypes.POINTER(ctypes.c_int32)),
     ]
 
 
@@ -289,7 +290,7 @@ def morap_solve_plain(ctx, pair_product, pair_w, stream=None, evaluate=True):
             "updates": stats[2], "ms": stats[3], "code": code}
 
 
-def morap_query(ctx, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True):
+def morap_query(ctx, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True, n_tasks=None):
     t = _arr(t, np.float64)
     n = len(t)
     Mm = _arr(M, np.float64) if M is not None else None
@@ -302,14 +303,35 @@ def morap_query(ctx, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True):
     res.t_down = _ptr(t_dn, ctypes.c_double)
     res.w_hist = _ptr(wh, ctypes.c_double)
     res.r_hist = _ptr(rh, ctypes.c_double)
+    lam = np.zeros(max_iter)
+    n_tasks = n_tasks if n_tasks is not None else 0
+    fh = np.zeros((max_iter, max(n_tasks, 1)), np.int32)
+    res.lambda_ = _ptr(lam, ctypes.c_double)
+    res.assign_hist = _ptr(fh, ctypes.c_int32) if n_tasks else None
     code = lib().morap_query(ctx, _ptr(t, ctypes.c_double), _ptr(Mm, ctypes.c_double), float(eps), int(max_iter),
                              _stream(stream), ctypes.byref(res))
     if check and code not in (OK, ENOTCONV):
         _check(code)
     it = res.iterations
-    return {"feasible": bool(res.feasible), "iterations": it, "converged": bool(res.converged),
-            "distance": res.distance, "t_up": t_up, "t_down": t_dn, "w_hist": wh[:it], "r_hist": rh[:it],
-            "code": code}
+    out = {"feasible": bool(res.feasible), "iterations": it, "converged": bool(res.converged),
+           "distance": res.distance, "t_up": t_up, "t_down": t_dn, "w_hist": wh[:it], "r_hist": rh[:it],
+           "lambda": lam[:it], "code": code}
+    if n_tasks:
+        out["assign_hist"] = fh[:it]
+    return out
+
+
+def random_assignment(lam, assign_hist, n_agents):
+    """The synthesised random assignment: P[i][j] = probability that agent i
+    does task j = sum over the points l of lambda_l [assign_hist[l][j] == i]."""
+    lam = np.asarray(lam)
+    assign_hist = np.asarray(assign_hist)
+    P = np.zeros((n_agents, assign_hist.shape[1]))
+    for l, f in enumerate(assign_hist):
+        for j, i in enumerate(f):
+            if i >= 0:
+                P[i, j] += lam[l]
+    return P
 
 
 class Pareto:
@@ -345,13 +367,15 @@ class Pareto:
         res.t_down = _ptr(t_dn, ctypes.c_double)
         res.w_hist = _ptr(wh, ctypes.c_double)
         res.r_hist = _ptr(rh, ctypes.c_double)
+        lam = np.zeros(it)
+        res.lambda_ = _ptr(lam, ctypes.c_double)
         code = lib().morap_pareto_result(self.h, ctypes.byref(res))
         if code not in (OK, ENOTCONV):
             _check(code)
         k = res.iterations
         return {"feasible": bool(res.feasible), "iterations": k, "converged": bool(res.converged),
                 "distance": res.distance, "t_up": t_up, "t_down": t_dn, "w_hist": wh[:k], "r_hist": rh[:k],
-                "code": code}
+                "lambda": lam[:k], "code": code}
 
     def close(self):
         if self.h:
@@ -592,7 +616,10 @@ class Context:
         return morap_supporting_points(self.h, W, self.n_agents, self.n_tasks, stream, want_c, check)
 
     def query(self, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True):
-        return morap_query(self.h, t, M, eps, max_iter, stream, check)
+        """Algorithm 1 for threshold t; also returns the synthesis: `lambda`
+        (convex weights of the points) and `assign_hist` (each point's task
+        assignment); `random_assignment(...)` turns them into P[i][j]."""
+        return morap_query(self.h, t, M, eps, max_iter, stream, check, n_tasks=self.n_tasks)
 
     def stats(self):
         return morap_last_solve_stats(self.h)

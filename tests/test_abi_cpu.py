@@ -119,3 +119,31 @@ def test_task_preprocess_rejects_non_sink_accepting(M):
         M.morap_task_preprocess(2, 0, 1, delta, np.array([0, 1], np.uint8))
     assert e.value.code == M.EINVAL
     assert "not a sink" in str(e.value)
+
+
+def test_pareto_stepper_synthesis_on_a_known_set(M):
+    """Algorithm 1 fed from a known achievable set (the down-closure of the
+    convex hull of four points, supporting points found by enumeration): the
+    loop decides feasibility as the geometry says, and its convex weights
+    reproduce a point that dominates t_up (t itself when feasible)."""
+    pts = np.array([[-1.0, 0.2], [-2.0, 0.6], [-4.0, 0.9], [-3.0, 0.5]])
+
+    def support(w):
+        return pts[int(np.argmax(pts @ w))]
+
+    # (-3, 0.7) needs a mix: half of (-2, 0.6) and half of (-4, 0.9) gives (-3, 0.75)
+    for t, feasible in (([-2.5, 0.6], True), ([-3.0, 0.7], True), ([-2.5, 0.7], False), ([-3.5, 0.95], False)):
+        P = M.Pareto(t, eps=1e-9, max_iter=30)
+        while True:
+            w = P.next()
+            if w is None:
+                break
+            P.step(support(w))
+        res = P.result()
+        P.close()
+        lam = res["lambda"]
+        assert res["feasible"] == feasible
+        assert np.all(lam >= 0) and abs(lam.sum() - 1) < 1e-12
+        assert np.all(lam @ res["r_hist"] >= res["t_up"] - 1e-9)
+        if feasible:
+            assert np.all(lam @ res["r_hist"] >= np.array(t) - 1e-9)

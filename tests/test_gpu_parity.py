@@ -237,6 +237,20 @@ def test_query_matches_oracle_alg1(M, tiny, tiny_prods):
         # Lemma 6 on every direction the engine produced
         for w in got["w_hist"]:
             assert np.all(w >= 0) and abs(w.sum() - 1) < 1e-9
+        # the synthesis: a convex combination of the supporting points that
+        # dominates t_up (and t itself when t is feasible), and a random
+        # assignment in which no agent and no task is used more than once
+        lam, R, F = got["lambda"], got["r_hist"], got["assign_hist"]
+        assert np.all(lam >= 0) and abs(lam.sum() - 1) < 1e-12
+        assert np.all(lam @ R >= got["t_up"] - 1e-7)
+        if got["feasible"]:
+            assert np.all(lam @ R >= t - 1e-7)
+        P = M.random_assignment(lam, F, len(tiny.agents))
+        assert np.all(P.sum(axis=0) <= 1 + 1e-12) and np.all(P.sum(axis=1) <= 1 + 1e-12)
+        # each point is the supporting point of its weight under its assignment
+        for l in range(len(lam)):
+            r, f, _, _, _ = O.supporting_point(tiny_prods, got["w_hist"][l])
+            assert np.max(np.abs(R[l] - r)) < 1e-6
     ctx.close()
 
 
