@@ -247,10 +247,13 @@ def test_query_matches_oracle_alg1(M, tiny, tiny_prods):
             assert np.all(lam @ R >= t - 1e-7)
         P = M.random_assignment(lam, F, len(tiny.agents))
         assert np.all(P.sum(axis=0) <= 1 + 1e-12) and np.all(P.sum(axis=1) <= 1 + 1e-12)
-        # each point is the supporting point of its weight under its assignment
+        # each point is a supporting point of its weight: the scalarised value
+        # matches the oracle's (the point itself is unique only up to ties of
+        # the scalarised objective, which small weights make wide)
         for l in range(len(lam)):
-            r, f, _, _, _ = O.supporting_point(tiny_prods, got["w_hist"][l])
-            assert np.max(np.abs(R[l] - r)) < 1e-6
+            w = got["w_hist"][l]
+            r, f, _, _, _ = O.supporting_point(tiny_prods, w)
+            assert abs(w @ (R[l] - r)) < 1e-6
     ctx.close()
 
 
@@ -288,7 +291,8 @@ def test_grid32_full_size_sampled(M, grid32):
     rng = np.random.default_rng(0)
     sample = [(int(i), int(j)) for i, j in zip(rng.integers(0, nI, 5), rng.integers(0, nJ, 5))]
     sample += [(int(out["assign"][k][j]), j) for k, j in [(3, 0), (7, 5), (11, 19)] if out["assign"][k][j] >= 0]
-    for i, j in sample:
+    checked = 0
+    for n_s, (i, j) in enumerate(sample):
         p = O.Product(inst.agents[i], inst.tasks[j])
         for k in range(len(W)):
             r = O.solve_pair(p, W[k][i], W[k][nI + j])
@@ -296,6 +300,18 @@ def test_grid32_full_size_sampled(M, grid32):
             if out["assign"][k][j] == i:
                 assert out["r"][k][i] == pytest.approx(r["r_cost"], abs=TOL), (i, j, k)
                 assert out["r"][k][nI + j] == pytest.approx(r["r_prob"], abs=TOL), (i, j, k)
+            if n_s < 3 and k in (2, 9):
+                # the returned scheduler, wherever the oracle's action gap exceeds 1e-9
+                mu, _ = M.morap_last_policy(ctx.h, k, i * nJ + j)
+                q = O.q_values(p, r["rew"], r["x"])
+                for u in range(p.n - 1):
+                    qa = q[p.state_ptr[u]:p.state_ptr[u + 1]]
+                    m = r["mu"][u]
+                    others = np.delete(qa, m)
+                    if len(others) and qa[m] - others.max() > 1e-9:
+                        assert mu[u] == m, (i, j, k, u)
+                        checked += 1
+    assert checked > 1000
     # properties that hold at any size: probabilities in [0, 1], costs <= 0,
     # c consistent with w.r on the assigned products
     assert np.all(out["r"][:, nI:] >= -1e-12) and np.all(out["r"][:, nI:] <= 1 + 1e-12)
