@@ -88,6 +88,11 @@ typedef struct morap_config {
                                    with fewer than 2^24 transition-weights per sweep use shape 0);
                                    >= 0 forces one (0 .. 3).  Every shape gives bit-identical
                                    results.                                                         */
+    int32_t skip_unchanged;     /* 1 (default): a sweep does not recompute a work item none of whose
+                                   inputs changed in the previous sweep (the values it would write
+                                   are the ones already there, so results are bit-identical);
+                                   0: every sweep recomputes every item of an active product      */
+    int32_t reserved;
 } morap_config;
 
 typedef struct morap_ctx morap_ctx;
@@ -234,6 +239,10 @@ typedef struct morap_solve_stats {
     int32_t variant_fp64;
     int32_t reserved;
     double ms_tune;           /* host time the context has spent tuning shapes      */
+    int64_t skipped_fp32;     /* work-item sweeps skipped exactly (nothing they read had
+                                 changed; their values are reproduced bit for bit)     */
+    int64_t skipped_fp64;
+    int64_t work_items;       /* work items (128 states of one product) per full sweep */
 } morap_solve_stats;
 
 int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out);

@@ -86,6 +86,8 @@ struct morap_ctx {
     uint32_t TS = 0, TSA = 0, TT = 0;
     std::vector<ProdDesc> h_prods;
     std::vector<int4> h_chunks;
+    int32_t *in_items = nullptr;  // [items][kInItems] input items of each sweep work item
+    uint8_t *chg[3] = {};         // per item: changed in sweep n % 3
     ProdDesc *d_prods = nullptr;
     AgentDesc *d_agents = nullptr;
     TaskDesc *d_tasks = nullptr;
@@ -447,6 +449,9 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a.sweeps_pair = c->sweeps_pair;
     a.frozen = c->frozen;
     a.a_rec = c->a_rec;
+    a.in_items = c->in_items;
+    a.skip = c->cfg.skip_unchanged ? 1 : 0;
+    for (int q = 0; q < 3; ++q) a.chg[q] = c->chg[q];
     a.eps1 = c->cfg.eps_vi;
     a.eps1f = (float)c->cfg.eps_vi;
     a.P = c->P;
@@ -583,7 +588,8 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     if (mixed) {
         CK(cudaMemsetAsync(c->V32[0], 0, nv * sizeof(float), s));
         CK(cudaMemsetAsync(c->V32[1], 0, nv * sizeof(float), s));
-        CKL(launch_loop_init(c->ctl + 0, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s));
+        CKL(launch_loop_init(c->ctl + 0, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
+                             c->chg[2]));
         bool tune = false;
         CKR(prepare_phase(c, false, Kp, tune));
         const auto t0 = std::chrono::steady_clock::now();
@@ -606,7 +612,8 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         CK(cudaMemsetAsync(c->V64[0], 0, nv * sizeof(double), s));
         CK(cudaMemsetAsync(c->V64[1], 0, nv * sizeof(double), s));
     }
-    CKL(launch_loop_init(c->ctl + 1, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s));
+    CKL(launch_loop_init(c->ctl + 1, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
+                         c->chg[2]));
     bool tune64 = false;
     CKR(prepare_phase(c, true, Kp, tune64));
     const auto t64 = std::chrono::steady_clock::now();
@@ -641,11 +648,14 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     st.K = K;
     if (mixed) {
         st.fp32_sweeps = (int32_t)hctl[0].sweep_base;
+        st.skipped_fp32 = (int64_t)hctl[0].skipped;
         st.updates_fp32 = (int64_t)hctl[0].updates;
         st.bytes_fp32 = (int64_t)hctl[0].bytes;
         st.ms_fp32 = ms_between(c->ev[0], c->ev[1]);
     }
     st.fp64_sweeps = (int32_t)hctl[1].sweep_base;
+    st.skipped_fp64 = (int64_t)hctl[1].skipped;
+    st.work_items = (int64_t)n_items;
     st.updates_fp64 = (int64_t)hctl[1].updates;
     st.bytes_fp64 = (int64_t)hctl[1].bytes;
     st.ms_fp64 = ms_between(c->ev[6], c->ev[2]);
@@ -938,6 +948,7 @@ int run_construction(morap_ctx *c, cudaStream_t s) {
     CKL(launch_build(c->d_prods, c->P, c->d_ad, c->d_td, c->d_sp, c->d_sap, c->d_succ, c->d_prob, c->d_cost,
                      c->d_letters, c->d_nd, c->state_sa, c->state_tr, c->sa_tr, c->col, c->cp32, c->p64, c->pdf,
                      c->cost32, c->cost64, c->costdf, c->TS, c->TSA, c->TT, c->max_work, s));
+    CKL(launch_item_inputs(c->d_chunks, (int)c->h_chunks.size(), c->d_prods, c->state_tr, c->col, c->in_items, s));
     return MORAP_OK;
 }
 
@@ -1015,6 +1026,7 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
             pd.sa_off = (uint32_t)TSA;
             pd.tr_off = (uint32_t)TT;
             pd.letter_off = (uint32_t)letters;
+            pd.item_off = (uint32_t)chunks.size();
             TS += (uint64_t)pd.n_nd + 1;
             TSA += (uint64_t)t.Qn * a.SA;
             TT += (uint64_t)t.Qn * a.T;
@@ -1065,6 +1077,8 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         CKR(dev_alloc(c, L, &c->cost64, std::max<uint64_t>(TSA, 1) * 8));
         CKR(dev_alloc(c, L, &c->d_prods, P * sizeof(ProdDesc)));
         CKR(dev_alloc(c, L, &c->d_chunks, std::max<size_t>(chunks.size(), 1) * sizeof(int4)));
+        CKR(dev_alloc(c, L, &c->in_items, std::max<size_t>(chunks.size(), 1) * kInItems * sizeof(int32_t)));
+        for (int q = 0; q < 3; ++q) CKR(dev_alloc(c, L, &c->chg[q], std::max<size_t>(chunks.size(), 1)));
         CKR(dev_alloc(c, L, &c->d_ad, nI * sizeof(AgentDesc)));
         CKR(dev_alloc(c, L, &c->d_td, nJ * sizeof(TaskDesc)));
         CKR(dev_alloc(c, L, &c->d_sp, a_sp.size() * 4));
@@ -1145,6 +1159,7 @@ void morap_config_default(morap_config *cfg) {
     cfg->device = 0;
     cfg->sweep_variant_fp32 = -1;
     cfg->sweep_variant_fp64 = -1;
+    cfg->skip_unchanged = 1;
 }
 
 const char *morap_last_error(void) { return g_last_error.c_str(); }

@@ -97,6 +97,7 @@ struct ProdDesc {
     uint32_t S, SA, T;   // agent sizes
     int32_t Qn;
     uint32_t letter_off; // offset of this product's letter table (per agent state)
+    uint32_t item_off;   // index of the product's first sweep work item
 };
 
 struct AgentDesc {
@@ -124,7 +125,7 @@ struct LoopCtl {
     unsigned int sweep_base;
     unsigned int hit_cap;
     unsigned int cap;
-    unsigned int pad;
+    unsigned int skipped;  // work items a sweep skipped because none of their inputs changed
     unsigned long long updates;
     unsigned long long bytes;
 };
@@ -133,6 +134,7 @@ constexpr int kChunk = 128;      // states per (warp) work item of the optimisat
 constexpr int kEvalChunk = 256;  // states per work item of the evaluation sweeps
 constexpr int kThreads = 256;
 constexpr int kGatherBatch = 4;  // independent successor gathers a thread issues back to back
+constexpr int kInItems = 16;     // input items recorded per work item (more: always recomputed)
 int sweep_smem_bytes(bool fp64);
 int sweep_setup_attributes();
 
@@ -160,6 +162,14 @@ struct SweepArgs {
     LoopCtl *ctl;
     void *V[2];
     uint8_t *a_rec;
+    // Exact skipping: a work item whose states and successors all kept their
+    // values in the previous sweep would reproduce its values bit for bit,
+    // so it is not recomputed.  in_items[item][kInItems]: the other items
+    // holding successors of its states (-1 none, -2 too many: always
+    // recompute); chg[n % 3][item]: some value of the item changed in sweep n.
+    const int32_t *in_items;
+    uint8_t *chg[3];
+    int skip;  // 0: recompute every item (skipping disabled)
     double eps1;
     float eps1f;  // eps1 rounded to FP32 (record tests in the kernels)
     int P;
@@ -210,8 +220,12 @@ int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const Ta
 
 int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W,
                          float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1, void *s);
+int launch_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, const uint32_t *state_tr,
+                       const int32_t *col, int32_t *in_items, void *s);
+// chg_prev (nullable, [n_items]): set to 1 so that the first sweep recomputes every item
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
-                     size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s);
+                     size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s,
+                     uint8_t *chg_prev = nullptr);
 // One sweep with kernel shape `variant` (0 .. sweep_variant_count - 1; all
 // shapes give bit-identical results, they differ only in speed).
 int launch_sweep(bool fp64, int Kp, int variant, const SweepArgs &a, int pos, int grid, void *s);

@@ -366,7 +366,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
                                               uint32_t A0, uint32_t T0, int i, uint32_t u, bool pre,
                                               const typename Ar::W *__restrict__ sw, const unsigned int act_bits,
                                               const float *__restrict__ Vold, float *__restrict__ Vnew, int k0,
-                                              float (&rmax)[Shape<Ar, KP, VMAX>::VEC]) {
+                                              float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed) {
     using Val = typename Ar::Val;
     using SH = Shape<Ar, KP, VMAX>;
     constexpr int VEC = SH::VEC;
@@ -433,7 +433,13 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
         const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
         rmax[v] = d > rmax[v] ? d : rmax[v];
         if (d > Ar::record_threshold(best[v], a.eps1f)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
+        float before[Ar::WORDS];
+#pragma unroll
+        for (int q = 0; q < Ar::WORDS; ++q) before[q] = yw[v * Ar::WORDS + q];
         Ar::to_words(best[v], &yw[v * Ar::WORDS]);
+#pragma unroll
+        for (int q = 0; q < Ar::WORDS; ++q)
+            changed = changed || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
     }
     store_words<NW>(Vnew + row, yw);
 }
@@ -450,7 +456,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
                                                    bool pre, const typename Ar::W *__restrict__ sw,
                                                    const unsigned int act_bits, const float *__restrict__ Vold,
                                                    float *__restrict__ Vnew, int k0,
-                                                   float (&rmax)[Shape<Ar, KP, VMAX>::VEC]) {
+                                                   float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed) {
     using Val = typename Ar::Val;
     using Prob = typename Ar::Prob;
     using SH = Shape<Ar, KP, VMAX>;
@@ -542,7 +548,13 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
         rmax[v] = d > rmax[v] ? d : rmax[v];
         if (d > Ar::record_threshold(best[v], a.eps1f)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
+        float before[Ar::WORDS];
+#pragma unroll
+        for (int q = 0; q < Ar::WORDS; ++q) before[q] = yw[v * Ar::WORDS + q];
         Ar::to_words(best[v], &yw[v * Ar::WORDS]);
+#pragma unroll
+        for (int q = 0; q < Ar::WORDS; ++q)
+            changed = changed || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
     }
     store_words<NW>(Vnew + row, yw);
 }
@@ -623,6 +635,25 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                 else
                     a.frozen[pair0 + k] = 1;
             }
+        if (any_active && a.skip) {
+            // exact skipping: nothing this item reads changed in the previous
+            // sweep, so it would reproduce its values bit for bit (and both
+            // value buffers already hold them)
+            const int32_t in = lane < kInItems ? __ldg(a.in_items + (size_t)item * kInItems + lane) : -1;
+            const bool in_chg = (lane == 0 && a.chg[far][item]) || in == -2 || (in >= 0 && a.chg[far][in]);
+            if (!__any_sync(0xffffffffu, in_chg)) {
+                if (lane == 0) {
+                    a.chg[cur][item] = 0;
+                    atomicAdd(&ctl->skipped, 1u);
+                    // the sweep still updates these states (to the same values)
+                    const uint32_t tr0 = a.state_tr[pd.state_off + ch.y], tr1 = a.state_tr[pd.state_off + ch.z];
+                    atomicAdd(&ctl->updates, (unsigned long long)(tr1 - tr0) *
+                                                 (unsigned long long)(__popc(act_w[0]) + __popc(act_w[1])));
+                }
+                continue;
+            }
+        }
+        bool changed = false;
         unsigned int act_bits = 0u;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
@@ -673,14 +704,18 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                     if constexpr (PIPE)
                         process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
                                                             (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits,
-                                                            Vold, Vnew, k0, rmax);
+                                                            Vold, Vnew, k0, rmax, changed);
                     else
                         process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
                                                        (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits, Vold,
-                                                       Vnew, k0, rmax);
+                                                       Vnew, k0, rmax, changed);
                 __syncwarp();  // the next batch reuses the buffer
                 s0 += m;
             }
+        }
+        {
+            const bool any_chg = __any_sync(0xffffffffu, changed);
+            if (lane == 0) a.chg[cur][item] = any_chg ? 1 : 0;
         }
         // residual: lanes with the same li share weights
 #pragma unroll
@@ -979,9 +1014,12 @@ __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, in
 
 __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *r0,
                             unsigned long long *r1, unsigned long long *r2, size_t n_pairs, int32_t *sweeps_pair,
-                            uint8_t *frozen, unsigned int cap) {
+                            uint8_t *frozen, unsigned int cap, uint8_t *chg_prev) {
     const size_t gid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = gid; i < n_items; i += stride) list0[i] = (unsigned int)i;
+    for (size_t i = gid; i < n_items; i += stride) {
+        list0[i] = (unsigned int)i;
+        if (chg_prev) chg_prev[i] = 1;
+    }
     const unsigned long long inf_bits = (unsigned long long)__double_as_longlong(CUDART_INF);
     for (size_t i = gid; i < n_pairs; i += stride) {
         r0[i] = 0ull;
@@ -997,6 +1035,7 @@ __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_it
         ctl->sweep_base = 0;
         ctl->hit_cap = 0;
         ctl->cap = cap;
+        ctl->skipped = 0;
         ctl->updates = 0;
         ctl->bytes = 0;
     }
@@ -1208,11 +1247,66 @@ int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, in
 }
 
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
-                     size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s) {
+                     size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s,
+                     uint8_t *chg_prev) {
     const size_t n = n_items > n_pairs ? n_items : n_pairs;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     k_loop_init<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(ctl, list0, n_items, res[0], res[1], res[2],
-                                                                 n_pairs, sweeps_pair, frozen, cap);
+                                                                 n_pairs, sweeps_pair, frozen, cap, chg_prev);
+    return (int)cudaGetLastError();
+}
+
+// The input items of every work item: the items (of the same product) that
+// hold successors of its states.  One warp per item; duplicates are removed
+// with warp matching; more than kInItems distinct inputs mark the item as
+// always recomputed.
+__global__ void k_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, const uint32_t *state_tr,
+                              const int32_t *col, int32_t *in_items) {
+    __shared__ int32_t set[kThreads / 32][kInItems];
+    __shared__ int cnt[kThreads / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int item = blockIdx.x * (kThreads / 32) + w; item < n_items; item += gridDim.x * (kThreads / 32)) {
+        const int4 ch = chunks[item];
+        const ProdDesc pd = prods[ch.x];
+        if (lane == 0) cnt[w] = 0;
+        __syncwarp();
+        const uint32_t t0 = state_tr[pd.state_off + ch.y], t1 = state_tr[pd.state_off + ch.z];
+        for (uint32_t base = t0; base < t1; base += 32) {
+            // the set as the previous batches left it (they are complete: __syncwarp
+            // below); values inserted by this batch are distinct from each other
+            const int n_before = min(cnt[w], kInItems);
+            const uint32_t t = base + lane;
+            int v = -1;
+            if (t < t1) {
+                const uint32_t cl = (uint32_t)col[t] - pd.state_off;
+                if (cl < pd.n_nd) {
+                    const int it = (int)(pd.item_off + cl / kChunk);
+                    if (it != item) v = it;
+                }
+            }
+            const unsigned int same = __match_any_sync(0xffffffffu, v);
+            if (v >= 0 && (__ffs(same) - 1) == lane) {  // one lane per distinct value of this batch
+                bool present = false;
+                for (int q = 0; q < n_before; ++q) present = present || set[w][q] == v;
+                if (!present) {
+                    const int at = atomicAdd(&cnt[w], 1);
+                    if (at < kInItems) set[w][at] = v;
+                }
+            }
+            __syncwarp();
+        }
+        const int n = cnt[w];
+        if (lane < kInItems) in_items[(size_t)item * kInItems + lane] = n > kInItems ? -2 : (lane < n ? set[w][lane] : -1);
+        __syncwarp();
+    }
+}
+
+int launch_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, const uint32_t *state_tr,
+                       const int32_t *col, int32_t *in_items, void *s) {
+    if (n_items <= 0) return 0;
+    const int grid = (n_items + kThreads / 32 - 1) / (kThreads / 32);
+    k_item_inputs<<<grid < 65535 ? grid : 65535, kThreads, 0, (cudaStream_t)s>>>(chunks, n_items, prods, state_tr, col,
+                                                                              in_items);
     return (int)cudaGetLastError();
 }
 

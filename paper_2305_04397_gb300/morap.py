@@ -48,6 +48,8 @@ class Config(ctypes.Structure):
         ("alloc_user", ctypes.c_void_p),
         ("sweep_variant_fp32", ctypes.c_int32),
         ("sweep_variant_fp64", ctypes.c_int32),
+        ("skip_unchanged", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -68,6 +70,7 @@ class SolveStats(ctypes.Structure):
         ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int32),
         ("variant_fp32", ctypes.c_int32), ("variant_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("ms_tune", ctypes.c_double),
+        ("skipped_fp32", ctypes.c_int64), ("skipped_fp64", ctypes.c_int64), ("work_items", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -355,6 +355,29 @@ def test_every_kernel_shape_gives_identical_results(M, grid32):
         ctx.close()
 
 
+def test_skipping_unchanged_items_is_exact(M, grid32):
+    """A sweep skips work items none of whose inputs changed in the previous
+    sweep; the results must be those of recomputing everything, bit for bit,
+    and some items must actually have been skipped."""
+    pair = (grid32.agents[:3], grid32.tasks[:6])
+    W = np.ascontiguousarray(grid32.weights[:8][:, [0, 1, 2, 10, 11, 12, 13, 14, 15]])
+    on = make_ctx(M, pair)
+    off = make_ctx(M, pair, skip_unchanged=0)
+    a = on.solve(W, evaluate=True)
+    st_on = on.stats()
+    b = off.solve(W, evaluate=True)
+    st_off = off.stats()
+    for key in ("c", "r_cost", "r_prob"):
+        assert np.array_equal(a[key], b[key]), key
+    for k in range(len(W)):
+        for p in range(3 * 6):
+            assert np.array_equal(M.morap_last_policy(on.h, k, p)[0], M.morap_last_policy(off.h, k, p)[0])
+    assert st_on["fp32_sweeps"] == st_off["fp32_sweeps"] and st_on["fp64_sweeps"] == st_off["fp64_sweeps"]
+    assert st_on["skipped_fp32"] > 0 and st_off["skipped_fp32"] == 0 and st_off["skipped_fp64"] == 0
+    on.close()
+    off.close()
+
+
 def test_batch_invariance(M, grid32):
     """Each pair runs exactly its own sweeps: a weight alone and inside the
     K = 16 batch gives bitwise-identical c and points."""
