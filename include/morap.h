@@ -242,7 +242,7 @@ typedef struct morap_solve_stats {
     int64_t skipped_fp32;     /* work-item sweeps skipped exactly (nothing they read had
                                  changed; their values are reproduced bit for bit)     */
     int64_t skipped_fp64;
-    int64_t work_items;       /* work items (128 states of one product) per full sweep */
+    int64_t work_items;       /* work items (64 states of one product) per full sweep  */
 } morap_solve_stats;
 
 int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out);

@@ -130,7 +130,10 @@ struct LoopCtl {
     unsigned long long bytes;
 };
 
-constexpr int kChunk = 128;      // states per (warp) work item of the optimisation sweeps
+#ifndef MORAP_CHUNK
+#define MORAP_CHUNK 64
+#endif
+constexpr int kChunk = MORAP_CHUNK;  // states per (warp) work item of the optimisation sweeps
 constexpr int kEvalChunk = 256;  // states per work item of the evaluation sweeps
 constexpr int kThreads = 256;
 constexpr int kGatherBatch = 4;  // independent successor gathers a thread issues back to back

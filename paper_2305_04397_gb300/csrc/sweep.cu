@@ -351,7 +351,7 @@ __device__ __forceinline__ Vec<T, VEC> vload(const T *p) {
 
 // ------------------------------------------------------------- the sweep
 //
-// Work items are 128-state ranges of one product taken by whole warps
+// Work items are kChunk-state ranges of one product taken by whole warps
 // (dynamic scheduling, no block barriers).  A warp walks its item in
 // batches: it copies the batch's state starts, action-row starts, costs and
 // (successor, probability) stream into its own shared-memory buffer with
@@ -559,7 +559,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
     store_words<NW>(Vnew + row, yw);
 }
 
-// Work items are 128-state ranges of one product taken by whole warps
+// Work items are kChunk-state ranges of one product taken by whole warps
 // (dynamic scheduling, no block barriers), walked in batches of up to 32
 // states: the warp copies the batch's state starts, action-row starts, costs
 // and (successor, probability) stream into its own shared-memory buffer with
@@ -593,153 +593,174 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     uint32_t *ssa = reinterpret_cast<uint32_t *>(stage_buf);
     typename Ar::W *wsm = reinterpret_cast<typename Ar::W *>(warp_buf + Ar::STAGE_BYTES);  // the item's weights
 
+    // Work items are taken kGrab at a time, items kept for the next sweep are
+    // appended once per grab, and the statistics are summed per warp: the
+    // shared counters see a few atomics per warp instead of several per item.
+    constexpr int kGrab = 1;
+    unsigned long long w_updates = 0, w_bytes = 0;  // lane 0's running sums
+    unsigned int w_skipped = 0;
     for (;;) {
-        unsigned int it = 0;
-        if (lane == 0) it = atomicAdd(&ctl->next[cur], 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= n_items) break;
-        const unsigned int item = a.list[cur][it];
-        const int4 ch = a.chunks[item];
-        const int p = ch.x;
-        const size_t pair0 = (size_t)p * KP;
-        // activity of the product's weights from the previous sweep's residuals
-        unsigned int act_w[2] = {0u, 0u}, nz_w[2] = {0u, 0u};
-#pragma unroll
-        for (int h = 0; h < (KP + 31) / 32; ++h) {
-            const int k = lane + 32 * h;
-            bool act = false, nz = false;
-            if (k < KP) {
-                const double prev = as_double(res_prev[pair0 + k]);
-                act = prev > a.thr[pair0 + k];
-                nz = prev > 0.0;
-            }
-            act_w[h] = __ballot_sync(0xffffffffu, act);
-            nz_w[h] = __ballot_sync(0xffffffffu, nz);
-        }
-        const bool any_active = (act_w[0] | act_w[1]) != 0u;
-        if ((nz_w[0] | nz_w[1]) == 0u) {  // converged earlier and already copied: drop
-            if (ch.w)
-                for (int k = lane; k < KP; k += 32) a.frozen[pair0 + k] = 1;
-            continue;
-        }
-        const ProdDesc pd = a.prods[p];
-        if (lane == 0 && any_active) {
-            const unsigned int at = atomicAdd(&ctl->cnt[nxt], 1u);
-            a.list[nxt][at] = item;
-        }
-        if (ch.w)
-            for (int k = lane; k < KP; k += 32) {
-                res_next[pair0 + k] = 0ull;
-                if ((act_w[k >> 5] >> (k & 31)) & 1u)
-                    a.sweeps_pair[pair0 + k] = (int32_t)(sweep + 1);
-                else
-                    a.frozen[pair0 + k] = 1;
-            }
-        if (any_active && a.skip) {
-            // exact skipping: nothing this item reads changed in the previous
-            // sweep, so it would reproduce its values bit for bit (and both
-            // value buffers already hold them)
-            const int32_t in = lane < kInItems ? __ldg(a.in_items + (size_t)item * kInItems + lane) : -1;
-            const bool in_chg = (lane == 0 && a.chg[far][item]) || in == -2 || (in >= 0 && a.chg[far][in]);
-            if (!__any_sync(0xffffffffu, in_chg)) {
-                if (lane == 0) {
-                    a.chg[cur][item] = 0;
-                    atomicAdd(&ctl->skipped, 1u);
-                    // the sweep still updates these states (to the same values)
-                    const uint32_t tr0 = a.state_tr[pd.state_off + ch.y], tr1 = a.state_tr[pd.state_off + ch.z];
-                    atomicAdd(&ctl->updates, (unsigned long long)(tr1 - tr0) *
-                                                 (unsigned long long)(__popc(act_w[0]) + __popc(act_w[1])));
+        unsigned int it0 = 0;
+        if (lane == 0) it0 = atomicAdd(&ctl->next[cur], (unsigned int)kGrab);
+        it0 = __shfl_sync(0xffffffffu, it0, 0);
+        if (it0 >= n_items) break;
+        unsigned int keep_mask = 0u;  // grab slots whose items stay in the work list
+        for (int g = 0; g < kGrab; ++g) {
+            const unsigned int it = it0 + (unsigned int)g;
+            if (it >= n_items) break;
+            const unsigned int item = a.list[cur][it];
+            const int4 ch = a.chunks[item];
+            const int p = ch.x;
+            const size_t pair0 = (size_t)p * KP;
+            // activity of the product's weights from the previous sweep's residuals
+            unsigned int act_w[2] = {0u, 0u}, nz_w[2] = {0u, 0u};
+    #pragma unroll
+            for (int h = 0; h < (KP + 31) / 32; ++h) {
+                const int k = lane + 32 * h;
+                bool act = false, nz = false;
+                if (k < KP) {
+                    const double prev = as_double(res_prev[pair0 + k]);
+                    act = prev > a.thr[pair0 + k];
+                    nz = prev > 0.0;
                 }
+                act_w[h] = __ballot_sync(0xffffffffu, act);
+                nz_w[h] = __ballot_sync(0xffffffffu, nz);
+            }
+            const bool any_active = (act_w[0] | act_w[1]) != 0u;
+            if ((nz_w[0] | nz_w[1]) == 0u) {  // converged earlier and already copied: drop
+                if (ch.w)
+                    for (int k = lane; k < KP; k += 32) a.frozen[pair0 + k] = 1;
                 continue;
             }
-        }
-        bool changed = false;
-        unsigned int act_bits = 0u;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            const int k = k0 + v;
-            act_bits |= ((act_w[k >> 5] >> (k & 31)) & 1u) << v;
-        }
-        for (int k = lane; k < KP; k += 32) wsm[k] = Ar::weight(a, pair0 + k);
-        __syncwarp();
-        float rmax[VEC];
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) rmax[v] = 0.0f;
-
-        if (!any_active) {  // every weight of the product froze: copy its rows once
-            for (int s = ch.y + grp; s < ch.z; s += SPW) {
-                const size_t row = (size_t)(pd.state_off + (uint32_t)s) * ROW + (size_t)k0 * Ar::WORDS;
-                float yw[NW];
-                load_words<NW>(Vold + row, yw);
-                store_words<NW>(Vnew + row, yw);
-            }
-        } else {
-            for (int s0 = ch.y; s0 < ch.z;) {
-                const int m_max = min(kStageStates, ch.z - s0);
-                const uint32_t u0 = pd.state_off + (uint32_t)s0;
-                uint32_t my_sa = 0, my_tr = 0;
-                if (lane <= m_max) {
-                    my_sa = __ldg(a.state_sa + u0 + lane);
-                    my_tr = __ldg(a.state_tr + u0 + lane);
-                }
-                const uint32_t A0 = __shfl_sync(0xffffffffu, my_sa, 0);
-                const uint32_t T0 = __shfl_sync(0xffffffffu, my_tr, 0);
-                const bool fits = lane <= m_max && my_sa - A0 <= (uint32_t)Ar::AMAX && my_tr - T0 <= (uint32_t)Ar::EMAX;
-                int m = __popc(__ballot_sync(0xffffffffu, fits)) - 1;  // boundaries 0..m fit
-                const bool staged = m >= 1;
-                if (!staged) m = 1;  // one state too large for the buffer: read it from global memory
-                const uint32_t A1 = __shfl_sync(0xffffffffu, my_sa, m);
-                const uint32_t T1 = __shfl_sync(0xffffffffu, my_tr, m);
-                if (lane <= m) ssa[lane] = my_sa;
-                typename Ar::View vw;
-                if (staged) {
-                    Ar::stage(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
-                    cp_async_wait_all();
-                    vw = Ar::smem_view(stage_buf);
-                } else {
-                    vw = Ar::global_view(a, A0, T0);
-                }
-                __syncwarp();
-                for (int i = grp; i < m; i += SPW)
-                    if constexpr (PIPE)
-                        process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
-                                                            (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits,
-                                                            Vold, Vnew, k0, rmax, changed);
+            const ProdDesc pd = a.prods[p];
+            if (any_active) keep_mask |= 1u << g;
+            if (ch.w)
+                for (int k = lane; k < KP; k += 32) {
+                    res_next[pair0 + k] = 0ull;
+                    if ((act_w[k >> 5] >> (k & 31)) & 1u)
+                        a.sweeps_pair[pair0 + k] = (int32_t)(sweep + 1);
                     else
-                        process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
-                                                       (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits, Vold,
-                                                       Vnew, k0, rmax, changed);
-                __syncwarp();  // the next batch reuses the buffer
-                s0 += m;
+                        a.frozen[pair0 + k] = 1;
+                }
+            if (any_active && a.skip) {
+                // exact skipping: nothing this item reads changed in the previous
+                // sweep, so it would reproduce its values bit for bit (and both
+                // value buffers already hold them)
+                const int32_t in = lane < kInItems ? __ldg(a.in_items + (size_t)item * kInItems + lane) : -1;
+                const bool in_chg = (lane == 0 && a.chg[far][item]) || in == -2 || (in >= 0 && a.chg[far][in]);
+                if (!__any_sync(0xffffffffu, in_chg)) {
+                    if (lane == 0) {
+                        a.chg[cur][item] = 0;
+                        ++w_skipped;
+                        // the sweep still updates these states (to the same values)
+                        const uint32_t tr0 = a.state_tr[pd.state_off + ch.y], tr1 = a.state_tr[pd.state_off + ch.z];
+                        w_updates += (unsigned long long)(tr1 - tr0) *
+                                     (unsigned long long)(__popc(act_w[0]) + __popc(act_w[1]));
+                    }
+                    continue;
+                }
+            }
+            bool changed = false;
+            unsigned int act_bits = 0u;
+    #pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int k = k0 + v;
+                act_bits |= ((act_w[k >> 5] >> (k & 31)) & 1u) << v;
+            }
+            for (int k = lane; k < KP; k += 32) wsm[k] = Ar::weight(a, pair0 + k);
+            __syncwarp();
+            float rmax[VEC];
+    #pragma unroll
+            for (int v = 0; v < VEC; ++v) rmax[v] = 0.0f;
+
+            if (!any_active) {  // every weight of the product froze: copy its rows once
+                for (int s = ch.y + grp; s < ch.z; s += SPW) {
+                    const size_t row = (size_t)(pd.state_off + (uint32_t)s) * ROW + (size_t)k0 * Ar::WORDS;
+                    float yw[NW];
+                    load_words<NW>(Vold + row, yw);
+                    store_words<NW>(Vnew + row, yw);
+                }
+            } else {
+                for (int s0 = ch.y; s0 < ch.z;) {
+                    const int m_max = min(kStageStates, ch.z - s0);
+                    const uint32_t u0 = pd.state_off + (uint32_t)s0;
+                    uint32_t my_sa = 0, my_tr = 0;
+                    if (lane <= m_max) {
+                        my_sa = __ldg(a.state_sa + u0 + lane);
+                        my_tr = __ldg(a.state_tr + u0 + lane);
+                    }
+                    const uint32_t A0 = __shfl_sync(0xffffffffu, my_sa, 0);
+                    const uint32_t T0 = __shfl_sync(0xffffffffu, my_tr, 0);
+                    const bool fits =
+                        lane <= m_max && my_sa - A0 <= (uint32_t)Ar::AMAX && my_tr - T0 <= (uint32_t)Ar::EMAX;
+                    int m = __popc(__ballot_sync(0xffffffffu, fits)) - 1;  // boundaries 0..m fit
+                    const bool staged = m >= 1;
+                    if (!staged) m = 1;  // one state too large for the buffer: read it from global memory
+                    const uint32_t A1 = __shfl_sync(0xffffffffu, my_sa, m);
+                    const uint32_t T1 = __shfl_sync(0xffffffffu, my_tr, m);
+                    if (lane <= m) ssa[lane] = my_sa;
+                    typename Ar::View vw;
+                    if (staged) {
+                        Ar::stage(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
+                        cp_async_wait_all();
+                        vw = Ar::smem_view(stage_buf);
+                    } else {
+                        vw = Ar::global_view(a, A0, T0);
+                    }
+                    __syncwarp();
+                    for (int i = grp; i < m; i += SPW)
+                        if constexpr (PIPE)
+                            process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                                                                (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits,
+                                                                Vold, Vnew, k0, rmax, changed);
+                        else
+                            process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                                                           (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits, Vold,
+                                                           Vnew, k0, rmax, changed);
+                    __syncwarp();  // the next batch reuses the buffer
+                    s0 += m;
+                }
+            }
+            {
+                const bool any_chg = __any_sync(0xffffffffu, changed);
+                if (lane == 0) a.chg[cur][item] = any_chg ? 1 : 0;
+            }
+            // residual: lanes with the same li share weights
+    #pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                float r = rmax[v];
+    #pragma unroll
+                for (int off = LPS; off < 32; off <<= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
+                if (grp == 0 && any_active && r > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)r);
+            }
+            if (lane == 0) {
+                const uint32_t n_s = (uint32_t)(ch.z - ch.y);
+                const uint32_t u0 = pd.state_off + ch.y, u1 = pd.state_off + ch.z;
+                w_bytes += 2ull * n_s * ROW * 4;
+                if (any_active) {
+                    const uint32_t sa0 = a.state_sa[u0], sa1 = a.state_sa[u1];
+                    const uint32_t tr0 = a.state_tr[u0], tr1 = a.state_tr[u1];
+                    const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
+                    w_updates += (unsigned long long)(tr1 - tr0) * (unsigned long long)n_act;
+                    // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
+                    w_bytes += 8ull * (n_s + 1) + 4ull * (sa1 - sa0 + 1) + 4ull * Ar::WORDS * (sa1 - sa0) +
+                               4ull * (1 + Ar::WORDS) * (tr1 - tr0);
+                }
             }
         }
-        {
-            const bool any_chg = __any_sync(0xffffffffu, changed);
-            if (lane == 0) a.chg[cur][item] = any_chg ? 1 : 0;
+        // the grab's items that stay active, appended with one atomic
+        if (keep_mask) {
+            unsigned int at = 0;
+            if (lane == 0) at = atomicAdd(&ctl->cnt[nxt], (unsigned int)__popc(keep_mask));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (lane < kGrab && ((keep_mask >> lane) & 1u))
+                a.list[nxt][at + __popc(keep_mask & ((1u << lane) - 1u))] = a.list[cur][it0 + lane];
         }
-        // residual: lanes with the same li share weights
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            float r = rmax[v];
-#pragma unroll
-            for (int off = LPS; off < 32; off <<= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
-            if (grp == 0 && any_active && r > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)r);
-        }
-        if (lane == 0) {
-            const uint32_t n_s = (uint32_t)(ch.z - ch.y);
-            const uint32_t u0 = pd.state_off + ch.y, u1 = pd.state_off + ch.z;
-            unsigned long long bytes = 2ull * n_s * ROW * 4;
-            if (any_active) {
-                const uint32_t sa0 = a.state_sa[u0], sa1 = a.state_sa[u1];
-                const uint32_t tr0 = a.state_tr[u0], tr1 = a.state_tr[u1];
-                const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
-                atomicAdd(&ctl->updates, (unsigned long long)(tr1 - tr0) * (unsigned long long)n_act);
-                // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
-                bytes += 8ull * (n_s + 1) + 4ull * (sa1 - sa0 + 1) + 4ull * Ar::WORDS * (sa1 - sa0) +
-                         4ull * (1 + Ar::WORDS) * (tr1 - tr0);
-            }
-            atomicAdd(&ctl->bytes, bytes);
-        }
+    }
+    if (lane == 0) {
+        if (w_updates) atomicAdd(&ctl->updates, w_updates);
+        if (w_bytes) atomicAdd(&ctl->bytes, w_bytes);
+        if (w_skipped) atomicAdd(&ctl->skipped, w_skipped);
     }
 }
 
@@ -1296,7 +1317,8 @@ __global__ void k_item_inputs(const int4 *chunks, int n_items, const ProdDesc *p
             __syncwarp();
         }
         const int n = cnt[w];
-        if (lane < kInItems) in_items[(size_t)item * kInItems + lane] = n > kInItems ? -2 : (lane < n ? set[w][lane] : -1);
+        if (lane < kInItems)
+            in_items[(size_t)item * kInItems + lane] = n > kInItems ? -2 : (lane < n ? set[w][lane] : -1);
         __syncwarp();
     }
 }
