@@ -13,10 +13,11 @@
 // Thread mapping: LPS = Kp / VEC lanes share one state, lane l owns weights
 // [l*VEC, l*VEC+VEC) and loads them as one vector, so the value row of a
 // successor is one coalesced Kp-wide read and the CSR stream is read once for
-// all Kp weights.  A 256-thread block takes 512-state work items of one
-// product from the sweep's work list (dynamic scheduling); the item's
-// residuals are reduced with warp shuffles, then across warps in shared
-// memory, then with one 64-bit atomicMax per weight.
+// all Kp weights.  Each warp takes kChunk-state work items of one product
+// from the sweep's work list (dynamic scheduling, one item per atomic); an
+// item's residuals are reduced with warp shuffles and one 64-bit atomicMax
+// per weight.  Items none of whose inputs changed in the previous sweep are
+// skipped exactly (see SweepArgs::in_items).
 //
 // Work lists: L[n % 3] holds the items of sweep n.  An item is re-queued for
 // sweep n+1 when its product still had an active weight in sweep n.  Weight k

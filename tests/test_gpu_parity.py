@@ -378,6 +378,28 @@ def test_skipping_unchanged_items_is_exact(M, grid32):
     off.close()
 
 
+def test_skipping_with_scattered_successors(M):
+    """Random MDPs whose actions jump anywhere: most work items have more
+    input items than are recorded (so they are always recomputed), the rest
+    have few.  Skipping must still be exact, and the values must match the
+    oracle."""
+    agents = [I.random_tiny_agent(3, 40 + i, n_states=1500, n_actions=(1, 3), n_succ=(1, 3)) for i in range(2)]
+    tasks = [I.random_tiny_task(3, 50 + j, n_locs=3) for j in range(2)]
+    rng = np.random.default_rng(8)
+    W = rng.dirichlet(np.ones(4), size=4)
+    on = make_ctx(M, (agents, tasks))
+    off = make_ctx(M, (agents, tasks), skip_unchanged=0)
+    a = on.solve(W, evaluate=True)
+    b = off.solve(W, evaluate=True)
+    for key in ("c", "r_cost", "r_prob"):
+        assert np.array_equal(a[key], b[key]), key
+    for i, j, k in [(0, 0, 0), (1, 1, 2), (0, 1, 3)]:
+        r = O.solve_pair(O.Product(agents[i], tasks[j]), W[k][i], W[k][2 + j])
+        assert a["c"][k, i, j] == pytest.approx(r["c"], abs=TOL)
+    on.close()
+    off.close()
+
+
 def test_batch_invariance(M, grid32):
     """Each pair runs exactly its own sweeps: a weight alone and inside the
     K = 16 batch gives bitwise-identical c and points."""
