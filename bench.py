@@ -55,8 +55,8 @@ def make_workload(name, rank=0):
 # its DRAM bytes and its algorithmic bytes.  Valid only while the sweep source
 # is the one that was profiled (sha256 prefix) and the same shape runs.
 TRAFFIC_PROFILES = {
-    "grid32-10x20-K16": {"sweep_source": "7804018a5245b60f", "variant_fp32": 0,
-                         "dram_bytes": 147727872 + 27437568, "alg_bytes": 189.1e6},
+    "grid32-10x20-K16": {"sweep_source": "680dfc9607690144", "variant_fp32": 0,
+                         "dram_bytes": 147800320 + 28054784, "alg_bytes": 189.1e6},
 }
 
 

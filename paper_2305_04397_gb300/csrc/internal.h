@@ -136,7 +136,6 @@ struct LoopCtl {
 constexpr int kChunk = MORAP_CHUNK;  // states per (warp) work item of the optimisation sweeps
 constexpr int kEvalChunk = 256;  // states per work item of the evaluation sweeps
 constexpr int kThreads = 256;
-constexpr int kGatherBatch = 4;  // independent successor gathers a thread issues back to back
 constexpr int kInItems = 16;     // input items recorded per work item (more: always recomputed)
 int sweep_smem_bytes(bool fp64);
 int sweep_setup_attributes();

@@ -359,9 +359,8 @@ __device__ __forceinline__ Vec<T, VEC> vload(const T *p) {
 // cp.async (one coalesced round trip per batch instead of one per
 // transition), then computes.  Inside the batch, LPS lanes share a state and
 // each lane owns VEC of the Kp weights, so a successor's value row is read
-// once, coalesced, for all weights; each lane consumes its state's
-// transitions as one stream across the actions, issuing kGatherBatch
-// independent value gathers before it consumes them.
+// once, coalesced, for all weights.  Actions are the outer loop; within an
+// action a lane issues D independent value gathers before it consumes them.
 template <class Ar, int KP, int VMAX, int D>
 __device__ __forceinline__ void process_state(const SweepArgs &a, const typename Ar::View &vw, const uint32_t *ssa,
                                               uint32_t A0, uint32_t T0, int i, uint32_t u, bool pre,
