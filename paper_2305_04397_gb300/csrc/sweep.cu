@@ -681,14 +681,17 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                     store_words<NW>(Vnew + row, yw);
                 }
             } else {
+                // a batch's state boundaries are loaded while the previous
+                // batch is staged and computed
+                uint32_t nx_sa = 0, nx_tr = 0;
+                if (lane <= min(kStageStates, ch.z - ch.y)) {
+                    nx_sa = __ldg(a.state_sa + pd.state_off + (uint32_t)ch.y + lane);
+                    nx_tr = __ldg(a.state_tr + pd.state_off + (uint32_t)ch.y + lane);
+                }
                 for (int s0 = ch.y; s0 < ch.z;) {
                     const int m_max = min(kStageStates, ch.z - s0);
                     const uint32_t u0 = pd.state_off + (uint32_t)s0;
-                    uint32_t my_sa = 0, my_tr = 0;
-                    if (lane <= m_max) {
-                        my_sa = __ldg(a.state_sa + u0 + lane);
-                        my_tr = __ldg(a.state_tr + u0 + lane);
-                    }
+                    const uint32_t my_sa = nx_sa, my_tr = nx_tr;
                     const uint32_t A0 = __shfl_sync(0xffffffffu, my_sa, 0);
                     const uint32_t T0 = __shfl_sync(0xffffffffu, my_tr, 0);
                     const bool fits =
@@ -699,6 +702,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                     const uint32_t A1 = __shfl_sync(0xffffffffu, my_sa, m);
                     const uint32_t T1 = __shfl_sync(0xffffffffu, my_tr, m);
                     if (lane <= m) ssa[lane] = my_sa;
+                    if (s0 + m < ch.z && lane <= min(kStageStates, ch.z - (s0 + m))) {
+                        nx_sa = __ldg(a.state_sa + u0 + (uint32_t)m + lane);
+                        nx_tr = __ldg(a.state_tr + u0 + (uint32_t)m + lane);
+                    }
                     typename Ar::View vw;
                     if (staged) {
                         Ar::stage(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
