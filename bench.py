@@ -55,16 +55,18 @@ def make_workload(name, rank=0):
 # its DRAM bytes and its algorithmic bytes.  Valid only while the sweep source
 # is the one that was profiled (sha256 prefix) and the same shape runs.
 TRAFFIC_PROFILES = {
-    "grid32-10x20-K16": {"sweep_source": "680dfc9607690144", "variant_fp32": 0,
-                         "dram_bytes": 147800320 + 28054784, "alg_bytes": 189.1e6},
+    ("grid32-10x20-K16", "fp32"): {"sweep_source": "844741a58a766e19", "variant": 0,
+                                   "dram_bytes": 147796224 + 28456192, "alg_bytes": 189.1e6},
+    ("grid32-10x20-K16", "fp64"): {"sweep_source": "844741a58a766e19", "variant": 0,
+                                   "dram_bytes": 243567616 + 71100672, "alg_bytes": 324.8e6},
 }
 
 
-def _traffic(workload, variant, alg_bytes_per_launch):
+def _traffic(workload, phase, variant, alg_bytes_per_launch):
     import hashlib
 
-    prof = TRAFFIC_PROFILES.get(workload)
-    if prof is None or variant != prof["variant_fp32"]:
+    prof = TRAFFIC_PROFILES.get((workload, phase))
+    if prof is None or variant != prof["variant"]:
         return None
     with open(os.path.join(ROOT, "paper_2305_04397_gb300", "csrc", "sweep.cu"), "rb") as f:
         if hashlib.sha256(f.read()).hexdigest()[:16] != prof["sweep_source"]:
@@ -445,7 +447,8 @@ def run_engine(args):
         return st, h2d, st["d2h_bytes"]
 
     def timed(n, e2e):
-        tot = {"updates": 0, "bytes_fp32": 0, "ms_fp32": 0.0, "sweeps32": 0, "launches": 0, "h2d": 0, "d2h": 0,
+        tot = {"updates": 0, "bytes_fp32": 0, "ms_fp32": 0.0, "sweeps32": 0, "sweeps64": 0, "launches": 0, "h2d": 0,
+               "d2h": 0,
                "variant_fp32": -1, "variant_fp64": -1,
                "ms_fp64": 0.0, "ms_eval": 0.0, "bytes_fp64": 0, "bytes_eval": 0}
         _barrier(ws)
@@ -463,6 +466,7 @@ def run_engine(args):
             tot["bytes_eval"] += st["bytes_eval"]
             tot["ms_eval"] += st["ms_eval"]
             tot["sweeps32"] += st["fp32_sweeps"]
+            tot["sweeps64"] += st["fp64_sweeps"]
             tot["variant_fp32"], tot["variant_fp64"] = st["variant_fp32"], st["variant_fp64"]
             tot["launches"] += st["kernel_launches"] + 2  # + the two construction kernels
             tot["h2d"] += h2d
@@ -490,18 +494,26 @@ def run_engine(args):
     e2e_value = _reduce_sum(e2e["updates"], ws) / e2e_secs
 
     peak, peak_kind = _peaks()
-    achieved = dev["bytes_fp32"] / (dev["ms_fp32"] / 1e3) / 1e9 if dev["ms_fp32"] > 0 else None
-    bytes_per_sweep = dev["bytes_fp32"] / max(dev["sweeps32"], 1)
-    roofline = {"bound": "hbm",
-                "kernel": f"k_sweep<ArithF32,{len(W) if len(W) & (len(W) - 1) == 0 else 'Kp'}> shape "
-                          f"{dev['variant_fp32']} (FP32 round-down Bellman sweep, graph-launched loop)",
-                "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": _traffic(args.workload, dev["variant_fp32"], bytes_per_sweep),
-                "bytes_per_sweep": bytes_per_sweep,
-                "ms_per_sweep": dev["ms_fp32"] / max(dev["sweeps32"], 1),
-                "other_phases_GBps": {"df64_sweeps": dev["bytes_fp64"] / max(dev["ms_fp64"], 1e-9) / 1e6,
-                                      "evaluation": dev["bytes_eval"] / max(dev["ms_eval"], 1e-9) / 1e6}}
+
+    def phase_roofline(phase):
+        b, ms, n = (dev["bytes_fp32"], dev["ms_fp32"], dev["sweeps32"]) if phase == "fp32" else \
+            (dev["bytes_fp64"], dev["ms_fp64"], dev["sweeps64"])
+        ach = b / (ms / 1e3) / 1e9 if ms > 0 else None
+        per = b / max(n, 1)
+        v = dev["variant_fp32"] if phase == "fp32" else dev["variant_fp64"]
+        name = ("k_sweep<ArithF32,…> shape %d (FP32 round-down Bellman sweep)" if phase == "fp32" else
+                "k_sweep<ArithDF,…> shape %d (double-float Bellman sweep)") % v
+        return {"bound": "hbm", "kernel": name + ", graph-launched loop", "achieved": ach, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": (ach / peak) if ach else None,
+                "traffic": _traffic(args.workload, phase, v, per), "bytes_per_sweep": per,
+                "ms_per_sweep": ms / max(n, 1), "share_of_step": ms / dev["ms"]}
+
+    # the roofline object is the sweep loop with the largest share of the step
+    dominant = "fp64" if dev["ms_fp64"] >= dev["ms_fp32"] else "fp32"
+    roofline = phase_roofline(dominant)
+    roofline["other_phases"] = {("fp32_sweeps" if dominant == "fp64" else "df64_sweeps"):
+                                phase_roofline("fp32" if dominant == "fp64" else "fp64"),
+                                "evaluation_GBps": dev["bytes_eval"] / max(dev["ms_eval"], 1e-9) / 1e6}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
