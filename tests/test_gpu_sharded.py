@@ -72,3 +72,43 @@ def test_evaluate_errors(M):
     assert got["r_cost"][0] == full["r_cost"][1].reshape(-1)[1]
     assert got["r_prob"][1] == full["r_prob"][0].reshape(-1)[4]
     ctx.close()
+
+
+def test_sharded_driver_over_nccl_one_rank(M):
+    """The driver's collectives over a real NCCL process group (one rank on
+    this GPU): the points equal the unsharded context's bit for bit."""
+    import os
+    import socket
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2305_04397_gb300 import sharded as S
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("nccl", rank=0, world_size=1, device_id=torch.device("cuda", 0))
+    try:
+        g = I.config_grid32()
+        agents, tasks = g.agents[:3], g.tasks[:4]
+        W = np.ascontiguousarray(g.weights[:4][:, [0, 1, 2, 10, 11, 12, 13]])
+        W = W / W.sum(axis=1, keepdims=True)
+        parts = S.partition_agents(S.agent_loads(agents, tasks), 1)
+        shard = S.EngineShard(agents, tasks, parts[0])
+        sp = S.ShardedSupportingPoints(shard, parts, 3, 4, S.TorchComm(device=torch.device("cuda", 0)))
+        got = sp(W)
+        full = M.Context()
+        full.add(agents, tasks)
+        full.build()
+        ref = full.supporting_points(W)
+        assert np.array_equal(got["r"], ref["r"]) and np.array_equal(got["assign"], ref["assign"])
+        q = sp.query(np.array([-30.0, -30.0, -30.0, 0.5, 0.5, 0.5, 0.5]), eps=1e-6, max_iter=20)
+        q_ref = full.query(np.array([-30.0, -30.0, -30.0, 0.5, 0.5, 0.5, 0.5]), eps=1e-6, max_iter=20)
+        assert q["feasible"] == q_ref["feasible"] and q["iterations"] == q_ref["iterations"]
+        assert np.array_equal(q["t_up"], q_ref["t_up"])
+        shard.close()
+        full.close()
+    finally:
+        dist.destroy_process_group()
