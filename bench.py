@@ -57,7 +57,7 @@ def make_workload(name, rank=0):
 TRAFFIC_PROFILES = {
     ("grid32-10x20-K16", "fp32"): {"sweep_source": "844741a58a766e19", "variant": 0,
                                    "dram_bytes": 147796224 + 28456192, "alg_bytes": 189.1e6},
-    ("grid32-10x20-K16", "fp64"): {"sweep_source": "844741a58a766e19", "variant": 0,
+    ("grid32-10x20-K16", "df64"): {"sweep_source": "844741a58a766e19", "variant": 0,
                                    "dram_bytes": 243567616 + 71100672, "alg_bytes": 324.8e6},
 }
 
@@ -468,6 +468,7 @@ def run_engine(args):
             tot["sweeps32"] += st["fp32_sweeps"]
             tot["sweeps64"] += st["fp64_sweeps"]
             tot["variant_fp32"], tot["variant_fp64"] = st["variant_fp32"], st["variant_fp64"]
+            tot["polish"] = st["polish"]
             tot["launches"] += st["kernel_launches"] + 2  # + the two construction kernels
             tot["h2d"] += h2d
             tot["d2h"] += d2h
@@ -495,24 +496,27 @@ def run_engine(args):
 
     peak, peak_kind = _peaks()
 
+    # the second phase: the FP32 residual correction ("delta") or double-float sweeps ("df64")
+    polish = "delta" if dev.get("polish", 1) == 0 else "df64"
+    names = {"fp32": "k_sweep<ArithF32,…> shape %d (FP32 round-down Bellman sweep)",
+             "delta": "k_sweep<ArithDelta,…> shape %d (FP32 residual-correction sweep on a double-float table)",
+             "df64": "k_sweep<ArithDF,…> shape %d (double-float Bellman sweep)"}
+
     def phase_roofline(phase):
         b, ms, n = (dev["bytes_fp32"], dev["ms_fp32"], dev["sweeps32"]) if phase == "fp32" else \
             (dev["bytes_fp64"], dev["ms_fp64"], dev["sweeps64"])
         ach = b / (ms / 1e3) / 1e9 if ms > 0 else None
         per = b / max(n, 1)
         v = dev["variant_fp32"] if phase == "fp32" else dev["variant_fp64"]
-        name = ("k_sweep<ArithF32,…> shape %d (FP32 round-down Bellman sweep)" if phase == "fp32" else
-                "k_sweep<ArithDF,…> shape %d (double-float Bellman sweep)") % v
-        return {"bound": "hbm", "kernel": name + ", graph-launched loop", "achieved": ach, "peak": peak,
+        return {"bound": "hbm", "kernel": names[phase] % v + ", graph-launched loop", "achieved": ach, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": (ach / peak) if ach else None,
                 "traffic": _traffic(args.workload, phase, v, per), "bytes_per_sweep": per,
                 "ms_per_sweep": ms / max(n, 1), "share_of_step": ms / dev["ms"]}
 
     # the roofline object is the sweep loop with the largest share of the step
-    dominant = "fp64" if dev["ms_fp64"] >= dev["ms_fp32"] else "fp32"
+    dominant, other = (polish, "fp32") if dev["ms_fp64"] >= dev["ms_fp32"] else ("fp32", polish)
     roofline = phase_roofline(dominant)
-    roofline["other_phases"] = {("fp32_sweeps" if dominant == "fp64" else "df64_sweeps"):
-                                phase_roofline("fp32" if dominant == "fp64" else "fp64"),
+    roofline["other_phases"] = {other + "_sweeps": phase_roofline(other),
                                 "evaluation_GBps": dev["bytes_eval"] / max(dev["ms_eval"], 1e-9) / 1e6}
 
     line = {

@@ -92,7 +92,11 @@ typedef struct morap_config {
                                    inputs changed in the previous sweep (the values it would write
                                    are the ones already there, so results are bit-identical);
                                    0: every sweep recomputes every item of an active product      */
-    int32_t reserved;
+    int32_t polish;             /* the second phase of a mixed-precision solve: 0 (default) = FP32
+                                   residual correction on a double-float table (V = B + d with B
+                                   the FP32 phase's values, d iterated in FP32); 1 = the sweeps in
+                                   double-float on V itself.  0 holds one more value array in FP32
+                                   and a [state-action][Kp] FP32 table on the device.             */
 } morap_config;
 
 typedef struct morap_ctx morap_ctx;
@@ -215,7 +219,7 @@ int morap_supporting_points(morap_ctx *ctx, int32_t K, const double *W, void *st
 typedef struct morap_solve_stats {
     int32_t K;                /* weights in the batch                              */
     int32_t fp32_sweeps;      /* sweep launches of the FP32 phase (0 if unused)    */
-    int32_t fp64_sweeps;      /* sweep launches of the FP64 phase                   */
+    int32_t fp64_sweeps;      /* sweep launches of the second (polish) phase         */
     int32_t eval_sweeps;      /* sweep launches of the evaluation phase             */
     int64_t updates_fp32;     /* transition-updates: one (s,a,s') term for one weight in one sweep */
     int64_t updates_fp64;
@@ -237,7 +241,8 @@ typedef struct morap_solve_stats {
     int32_t kernel_launches;  /* kernels of this library the call launched          */
     int32_t variant_fp32;     /* kernel shapes the sweeps used (-1: phase not run)  */
     int32_t variant_fp64;
-    int32_t reserved;
+    int32_t polish;           /* the second phase's form: 0 = FP32 residual correction,
+                                 1 = double-float sweeps (always 1 without an FP32 phase) */
     double ms_tune;           /* host time the context has spent tuning shapes      */
     int64_t skipped_fp32;     /* work-item sweeps skipped exactly (nothing they read had
                                  changed; their values are reproduced bit for bit)     */

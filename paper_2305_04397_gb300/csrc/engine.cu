@@ -125,7 +125,11 @@ struct morap_ctx {
     unsigned long long *res[3] = {};
     unsigned int *list[3] = {};
     LoopCtl *ctl = nullptr;  // [3]: FP32, FP64, evaluation
-    LoopGraph g32[7], g64[7];  // per Kp = 1, 2, 4, ..., 64 (log2 index)
+    LoopGraph g32[7], g64[7];  // per Kp = 1, 2, 4, ..., 64 (log2 index); g64: the polish phase
+    int polish = kSweepDF;     // the polish kind of the current buffers (kSweepDF or kSweepDelta)
+    void *Vd[2] = {};          // residual-correction polish: the correction, double buffered
+    float *G = nullptr;        // residual-correction polish: [state-action][Kp] table
+    SweepArgs argsd{};
     int Kcap = 0;              // weights per product the solve buffers hold
     double ms_tune = 0.0;      // host time spent choosing kernel shapes (cumulative)
     SweepArgs args32{}, args64{};
@@ -229,6 +233,8 @@ void free_solve(morap_ctx *c) {
         c->g32[i].grid = c->g64[i].grid = 0;
         c->g32[i].variant = c->g64[i].variant = -1;
     }
+    c->Vd[0] = c->Vd[1] = nullptr;
+    c->G = nullptr;
     dev_free_list(c, c->solve_allocs);
     c->Kp = 0;
     c->Kcap = 0;
@@ -314,21 +320,26 @@ int run_loop(morap_ctx *c, LoopGraph &g, LoopCtl *ctl, cudaStream_t s, F &&launc
 
 // Blocks of a sweep launch with kernel shape v: every co-resident block, but
 // no more than one warp per work item needs.
-int sweep_launch_grid(morap_ctx *c, bool fp64, int Kp, int v) {
+int sweep_launch_grid(morap_ctx *c, int kind, int Kp, int v) {
     const size_t useful = (c->h_chunks.size() + kThreads / 32 - 1) / (kThreads / 32);
-    return std::max(1, (int)std::min<size_t>((size_t)sweep_grid(c, sweep_blocks_per_sm(fp64, Kp, v)), useful));
+    return std::max(1, (int)std::min<size_t>((size_t)sweep_grid(c, sweep_blocks_per_sm(kind, Kp, v)), useful));
 }
 
 // Build the loop graph of one phase for kernel shape v.
-int build_phase_graph(morap_ctx *c, LoopGraph &G, bool fp64, int Kp, int v) {
+// The arguments of a sweep kind (the polish kinds share the phase-2 control block).
+const SweepArgs &args_of(morap_ctx *c, int kind) {
+    return kind == kSweepF32 ? c->args32 : kind == kSweepDF ? c->args64 : c->argsd;
+}
+
+int build_phase_graph(morap_ctx *c, LoopGraph &G, int kind, int Kp, int v) {
     destroy_graph(G);
     G.variant = v;
-    G.grid = sweep_launch_grid(c, fp64, Kp, v);
+    G.grid = sweep_launch_grid(c, kind, Kp, v);
     if (c->cfg.launch_mode != 0) return MORAP_OK;
-    const SweepArgs a = fp64 ? c->args64 : c->args32;
+    const SweepArgs a = args_of(c, kind);
     const int grid = G.grid;
     return build_loop_graph(c, G, a.ctl, [&](int pos, cudaStream_t st) {
-        return launch_sweep(fp64, Kp, v, a, pos, grid, st);
+        return launch_sweep(kind, Kp, v, a, pos, grid, st);
     });
 }
 
@@ -339,17 +350,17 @@ int build_phase_graph(morap_ctx *c, LoopGraph &G, bool fp64, int Kp, int v) {
 // millisecond over the whole loop is kept and the phase's graph is built with
 // it.  Every shape does the same arithmetic, so the solve's results are those
 // of any single shape; only the first solve pays for the host round trips.
-int run_loop_tuning(morap_ctx *c, LoopGraph &G, bool fp64, int Kp, cudaStream_t s) {
-    const SweepArgs a = fp64 ? c->args64 : c->args32;
-    const int nvar = sweep_variant_count(fp64);
+int run_loop_tuning(morap_ctx *c, LoopGraph &G, int kind, int Kp, cudaStream_t s) {
+    const SweepArgs a = args_of(c, kind);
+    const int nvar = sweep_variant_count(kind);
     std::vector<double> ms(nvar, 0.0), bytes(nvar, 0.0);
     CKR(stage_ctl(c));
     unsigned long long prev_bytes = 0;
     for (int body = 0;; ++body) {
         const int v = body % nvar;
-        const int grid = sweep_launch_grid(c, fp64, Kp, v);
+        const int grid = sweep_launch_grid(c, kind, Kp, v);
         CK(cudaEventRecord(c->ev[7], s));
-        for (int pos = 0; pos < 6; ++pos) CKL(launch_sweep(fp64, Kp, v, a, pos, grid, s));
+        for (int pos = 0; pos < 6; ++pos) CKL(launch_sweep(kind, Kp, v, a, pos, grid, s));
         CK(cudaEventRecord(c->ev[5], s));
         CKL(launch_loop_control_host(a.ctl, 0, s));
         CK(cudaMemcpyAsync(c->h_ctl, a.ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
@@ -368,22 +379,22 @@ int run_loop_tuning(morap_ctx *c, LoopGraph &G, bool fp64, int Kp, cudaStream_t 
             best_rate = bytes[v] / ms[v];
             best = v;
         }
-    return build_phase_graph(c, G, fp64, Kp, best);
+    return build_phase_graph(c, G, kind, Kp, best);
 }
 
 // Make the loop of one phase ready for Kp: the shape forced by the config,
 // shape 0 for instances whose sweeps are too short for the shape to matter,
 // otherwise (first solve at this Kp) the tuner decides inside the solve.
 // Returns through `tune` whether this solve must run the tuning loop.
-int prepare_phase(morap_ctx *c, bool fp64, int Kp, bool &tune) {
-    LoopGraph &G = fp64 ? c->g64[log2_of(Kp)] : c->g32[log2_of(Kp)];
+int prepare_phase(morap_ctx *c, int kind, int Kp, bool &tune) {
+    LoopGraph &G = kind == kSweepF32 ? c->g32[log2_of(Kp)] : c->g64[log2_of(Kp)];
     tune = false;
     if (G.variant >= 0) return MORAP_OK;
     CKL(sweep_setup_attributes());
-    const int forced = fp64 ? c->cfg.sweep_variant_fp64 : c->cfg.sweep_variant_fp32;
+    const int forced = kind == kSweepF32 ? c->cfg.sweep_variant_fp32 : c->cfg.sweep_variant_fp64;
     const bool worth = (double)c->TT * (double)Kp >= (double)(1u << 24);
-    if (forced >= 0) return build_phase_graph(c, G, fp64, Kp, forced);
-    if (!worth) return build_phase_graph(c, G, fp64, Kp, 0);
+    if (forced >= 0) return build_phase_graph(c, G, kind, Kp, forced);
+    if (!worth) return build_phase_graph(c, G, kind, Kp, 0);
     tune = true;
     return MORAP_OK;
 }
@@ -406,6 +417,13 @@ int ensure_solve(morap_ctx *c, int Kp) {
     }
     CKR(dev_alloc(c, L, (double **)&c->V64[0], TS * Kp * sizeof(double)));
     CKR(dev_alloc(c, L, (double **)&c->V64[1], TS * Kp * sizeof(double)));
+    c->polish = kSweepDF;
+    if (c->V32[0] && c->cfg.polish == 0) {
+        c->polish = kSweepDelta;
+        CKR(dev_alloc(c, L, (float **)&c->Vd[0], TS * Kp * sizeof(float)));
+        CKR(dev_alloc(c, L, (float **)&c->Vd[1], TS * Kp * sizeof(float)));
+        CKR(dev_alloc(c, L, &c->G, std::max<size_t>(c->TSA, 1) * Kp * sizeof(float)));
+    }
     CKR(dev_alloc(c, L, &c->a_rec, TS * Kp));
     CKR(dev_alloc(c, L, &c->policy, TS * Kp));
     CKR(dev_alloc(c, L, &c->frozen, np));
@@ -466,6 +484,11 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a64.V[1] = c->V64[1];
     c->args32 = a32;
     c->args64 = a64;
+    SweepArgs ad = a64;  // the residual correction iterates d with the phase-2 control block
+    ad.V[0] = c->Vd[0];
+    ad.V[1] = c->Vd[1];
+    ad.G = c->G;
+    c->argsd = ad;
     return MORAP_OK;
 }
 
@@ -591,45 +614,57 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         CKL(launch_loop_init(c->ctl + 0, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
                              c->chg[2]));
         bool tune = false;
-        CKR(prepare_phase(c, false, Kp, tune));
+        CKR(prepare_phase(c, kSweepF32, Kp, tune));
         const auto t0 = std::chrono::steady_clock::now();
         CK(cudaEventRecord(c->ev[0], s));
         if (tune) {
-            CKR(run_loop_tuning(c, c->g32[log2_of(Kp)], false, Kp, s));
+            CKR(run_loop_tuning(c, c->g32[log2_of(Kp)], kSweepF32, Kp, s));
         } else {
             const SweepArgs a32 = c->args32;
             const LoopGraph &G = c->g32[log2_of(Kp)];
             const int grid = G.grid, v = G.variant;
             CKR(run_loop(c, c->g32[log2_of(Kp)], c->ctl + 0, s, [&](int pos, cudaStream_t st) {
-                return launch_sweep(false, Kp, v, a32, pos, grid, st);
+                return launch_sweep(kSweepF32, Kp, v, a32, pos, grid, st);
             }));
         }
         CK(cudaEventRecord(c->ev[1], s));
         if (tune) c->ms_tune += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        CKL(launch_convert((const float *)c->V32[0], (float2 *)c->V64[0], (float2 *)c->V64[1], nv, s));
+        if (c->polish == kSweepDelta) {
+            // the residual correction starts from d = 0 on the table of the FP32 result
+            CKL(launch_delta_table(Kp, c->args64, (int)n_items, (const float *)c->V32[0], c->G, s));
+            CK(cudaMemsetAsync(c->Vd[0], 0, nv * sizeof(float), s));
+            CK(cudaMemsetAsync(c->Vd[1], 0, nv * sizeof(float), s));
+        } else {
+            CKL(launch_convert((const float *)c->V32[0], (float2 *)c->V64[0], (float2 *)c->V64[1], nv, s));
+        }
         launches += 2;
     } else {
         CK(cudaMemsetAsync(c->V64[0], 0, nv * sizeof(double), s));
         CK(cudaMemsetAsync(c->V64[1], 0, nv * sizeof(double), s));
     }
+    const int pk = mixed ? c->polish : kSweepDF;  // the polish kind of this solve
     CKL(launch_loop_init(c->ctl + 1, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
                          c->chg[2]));
     bool tune64 = false;
-    CKR(prepare_phase(c, true, Kp, tune64));
+    CKR(prepare_phase(c, pk, Kp, tune64));
     const auto t64 = std::chrono::steady_clock::now();
     CK(cudaEventRecord(c->ev[6], s));
     if (tune64) {
-        CKR(run_loop_tuning(c, c->g64[log2_of(Kp)], true, Kp, s));
+        CKR(run_loop_tuning(c, c->g64[log2_of(Kp)], pk, Kp, s));
     } else {
-        const SweepArgs a64 = c->args64;
+        const SweepArgs a2 = args_of(c, pk);
         const LoopGraph &G = c->g64[log2_of(Kp)];
         const int grid = G.grid, v = G.variant;
         CKR(run_loop(c, c->g64[log2_of(Kp)], c->ctl + 1, s, [&](int pos, cudaStream_t st) {
-            return launch_sweep(true, Kp, v, a64, pos, grid, st);
+            return launch_sweep(pk, Kp, v, a2, pos, grid, st);
         }));
     }
     CK(cudaEventRecord(c->ev[2], s));
     if (tune64) c->ms_tune += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t64).count();
+    if (pk == kSweepDelta) {  // V = B + d, exactly, in double-float
+        CKL(launch_delta_combine((const float *)c->V32[0], (const float *)c->Vd[0], (float2 *)c->V64[0], nv, s));
+        launches += 1;
+    }
     CKL(launch_finalize(Kp, c->args64, (int)n_items, c->cfg.tau_policy, c->policy, s));
     CKL(launch_gather_c(Kp, c->d_prods, c->P, (const float2 *)c->V64[0], c->frozen, c->d_c, c->d_status, s));
     CK(cudaEventRecord(c->ev[3], s));
@@ -667,6 +702,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     st.kernel_launches = launches;
     st.variant_fp32 = mixed ? c->g32[log2_of(Kp)].variant : -1;
     st.variant_fp64 = c->g64[log2_of(Kp)].variant;
+    st.polish = pk == kSweepDelta ? 0 : 1;
     st.ms_tune = c->ms_tune;
     int bad = 0;
     for (int p = 0; p < c->P; ++p)
@@ -818,7 +854,8 @@ int morap::ctx_reserve(morap_ctx *c, int K) {
         for (int f = 0; f < 2; ++f) {
             if (f == 0 && !c->V32[0]) continue;
             bool tune = false;
-            CKR(prepare_phase(c, f == 1, kp, tune));  // shapes that need tuning are left to the first solve
+            CKR(prepare_phase(c, f == 1 ? (c->V32[0] ? c->polish : kSweepDF) : kSweepF32, kp, tune));  // shapes that
+            // need tuning are left to the first solve
         }
     if (!grow) c->Kp = old_Kp;
     return MORAP_OK;
@@ -1160,6 +1197,7 @@ void morap_config_default(morap_config *cfg) {
     cfg->sweep_variant_fp32 = -1;
     cfg->sweep_variant_fp64 = -1;
     cfg->skip_unchanged = 1;
+    cfg->polish = 0;
 }
 
 const char *morap_last_error(void) { return g_last_error.c_str(); }
@@ -1179,9 +1217,10 @@ int morap_ctx_create(const morap_config *cfg, morap_ctx **out) {
         return fail(MORAP_EINVAL, "config: unknown precision mode");
     if (c.launch_mode != 0 && c.launch_mode != 1) return fail(MORAP_EINVAL, "config: unknown launch mode");
     if ((c.alloc == nullptr) != (c.free == nullptr)) return fail(MORAP_EINVAL, "config: alloc and free go together");
-    if (c.sweep_variant_fp32 < -1 || c.sweep_variant_fp32 >= sweep_variant_count(false) ||
-        c.sweep_variant_fp64 < -1 || c.sweep_variant_fp64 >= sweep_variant_count(true))
+    if (c.sweep_variant_fp32 < -1 || c.sweep_variant_fp32 >= sweep_variant_count(kSweepF32) ||
+        c.sweep_variant_fp64 < -1 || c.sweep_variant_fp64 >= sweep_variant_count(kSweepDF))
         return fail(MORAP_EINVAL, "config: sweep_variant_* must be -1 (tuned) or a shape index");
+    if (c.polish != 0 && c.polish != 1) return fail(MORAP_EINVAL, "config: polish must be 0 or 1");
     CK(cudaSetDevice(c.device));
     morap_ctx *ctx = new morap_ctx();
     ctx->cfg = c;

@@ -137,7 +137,7 @@ constexpr int kChunk = MORAP_CHUNK;  // states per (warp) work item of the optim
 constexpr int kEvalChunk = 256;  // states per work item of the evaluation sweeps
 constexpr int kThreads = 256;
 constexpr int kInItems = 16;     // input items recorded per work item (more: always recomputed)
-int sweep_smem_bytes(bool fp64);
+int sweep_smem_bytes(int kind);
 int sweep_setup_attributes();
 
 struct SweepArgs {
@@ -172,6 +172,7 @@ struct SweepArgs {
     const int32_t *in_items;
     uint8_t *chg[3];
     int skip;  // 0: recompute every item (skipping disabled)
+    const float *G;  // residual-correction polish: [state-action][Kp] table (see ArithDelta)
     double eps1;
     float eps1f;  // eps1 rounded to FP32 (record tests in the kernels)
     int P;
@@ -228,16 +229,23 @@ int launch_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, c
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
                      size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s,
                      uint8_t *chg_prev = nullptr);
+// Sweep kinds: the FP32 round-down phase, the double-float polish, and the
+// polish as an FP32 residual correction on a double-float table.
+enum { kSweepF32 = 0, kSweepDF = 1, kSweepDelta = 2 };
 // One sweep with kernel shape `variant` (0 .. sweep_variant_count - 1; all
 // shapes give bit-identical results, they differ only in speed).
-int launch_sweep(bool fp64, int Kp, int variant, const SweepArgs &a, int pos, int grid, void *s);
-int sweep_blocks_per_sm(bool fp64, int Kp, int variant);
-int sweep_variant_count(bool fp64);
+int launch_sweep(int kind, int Kp, int variant, const SweepArgs &a, int pos, int grid, void *s);
+int sweep_blocks_per_sm(int kind, int Kp, int variant);
+int sweep_variant_count(int kind);
 
-void sweep_variant_shape(bool fp64, int variant, int *vmax, int *d, int *minb);
 int eval_blocks_per_sm();
 int launch_loop_control(LoopCtl *ctl, unsigned long long handle, int next_idx, void *s);
 int launch_loop_control_host(LoopCtl *ctl, int next_idx, void *s);
+// The residual-correction table G[sa][k] = r_a + sum p B(s') - B(s) (+ the
+// pre-sink weight) in double-float from the FP32 values B, rounded to FP32.
+int launch_delta_table(int Kp, const SweepArgs &a, int n_chunks, const float *B, float *G, void *s);
+// V = B + d as an exact double-float sum.
+int launch_delta_combine(const float *B, const float *d, float2 *V, size_t n, void *s);
 int launch_convert(const float *v32, float2 *vda, float2 *vdb, size_t n, void *s);
 int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, void *s);
 int launch_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V64, const uint8_t *frozen, double *c_out,

@@ -31,6 +31,7 @@
 
 #include <array>
 #include <cstdint>
+#include <type_traits>
 #include <utility>
 
 #include "internal.h"
@@ -293,6 +294,54 @@ __device__ __forceinline__ void store_words(float *p, const float (&w)[NW]) {
     }
 }
 
+// The polish phase as a residual correction (the default after an FP32
+// phase).  With B the certified FP32 lower bound the FP32 phase ends on and
+// V = B + d, the Bellman update of state s reads
+//   y(s) - B(s) = max_a [ G_a(s) + sum_s' p d(s') ],
+//   G_a(s)      = r_a(s) + sum_s' p B(s') - B(s),
+// so once G (one value per state-action row and weight) has been formed in
+// double-float from B and rounded to FP32, the correction d is iterated in
+// plain FP32 with one fused multiply-add per transition and weight.  d is of
+// the size of B's remaining error (about 1e-5 of the values), so FP32
+// carries it to about 1e-12; the winning G_a are of the same size.  d
+// starts at 0, the sweeps, freezes and records follow the paper's rule on d
+// (y - x is the same quantity in V and in d), and V = B + d is formed
+// exactly in double-float at the end.
+struct ArithDelta : ArithF32 {
+    using Prob = float;
+    // the rows' costs are inside G: only the row starts and the transitions are staged
+    template <int AM = AMAX, int EM = EMAX>
+    static __device__ __forceinline__ void stage(const SweepArgs &a, unsigned char *b, uint32_t A0, uint32_t nA,
+                                                 uint32_t T0, uint32_t nT, int lane) {
+        using L = Lay<AM, EM>;
+        uint32_t *str = reinterpret_cast<uint32_t *>(b + L::STR);
+        int2 *edge = reinterpret_cast<int2 *>(b + L::EDGE);
+        for (uint32_t i = lane; i <= nA; i += 32) cp_async4(str + i, a.sa_tr + A0 + i);
+        for (uint32_t i = lane; i < nT; i += 32) cp_async8(edge + i, a.cp32 + T0 + i);
+    }
+    static __device__ __forceinline__ Val add_base(Val v, W, bool) { return v; }  // inside G
+    static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) { acc = __fmaf_rn(p, v, acc); }
+    static __device__ __forceinline__ float record_threshold(Val, float eps1) { return eps1; }
+};
+
+// The value of action row la before its transitions are added: the
+// scalarised reward, or for the residual correction the row of G.
+template <class Ar, int KP, int VEC>
+__device__ __forceinline__ void init_action(const SweepArgs &a, const typename Ar::View &vw, uint32_t A0,
+                                            uint32_t la, int k0, const typename Ar::W *__restrict__ sw,
+                                            typename Ar::Val (&acc)[VEC]) {
+    if constexpr (std::is_same<Ar, ArithDelta>::value) {
+        float g[VEC];
+        load_words<VEC>(a.G + (size_t)(A0 + la) * KP + k0, g);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = g[v];
+    } else {
+        const typename Ar::Cost c = Ar::cost(vw, la);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c);
+    }
+}
+
 // Kernel shapes the tuner chooses from, per value format: VMAX weights per
 // lane (a lane owns VEC = min(Kp, VMAX) consecutive weights of a state), D
 // successor gathers in flight per action, and MINB resident blocks per SM
@@ -309,6 +358,8 @@ struct Variants<ArithF32> {
     static constexpr int minb[N] = {2, 2, 3, 2};
     static constexpr int pipe[N] = {0, 0, 0, 1};  // actions software-pipelined
 };
+template <>
+struct Variants<ArithDelta> : Variants<ArithF32> {};
 template <>
 struct Variants<ArithDF> {
     static constexpr int N = 4;
@@ -387,11 +438,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
     for (uint32_t la = la0; la < la1; ++la) {
         const uint32_t t1 = vw.str[la + 1] - T0;
         Val acc[VEC];
-        {
-            const typename Ar::Cost c = Ar::cost(vw, la);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c);
-        }
+        init_action<Ar, KP, VEC>(a, vw, A0, la, k0, sw, acc);
         for (uint32_t base = t0; base < t1; base += D) {
             int32_t cl[D];
             typename Ar::Prob pr[D];
@@ -500,11 +547,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
     };
     auto reduce = [&](uint32_t la, Slots &S) {
         Val acc[VEC];
-        {
-            const typename Ar::Cost c = Ar::cost(vw, la);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c);
-        }
+        init_action<Ar, KP, VEC>(a, vw, A0, la, k0, sw, acc);
         for (;;) {
 #pragma unroll
             for (int j = 0; j < D; ++j) {
@@ -750,8 +793,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                     const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
                     w_updates += (unsigned long long)(tr1 - tr0) * (unsigned long long)n_act;
                     // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
-                    w_bytes += 8ull * (n_s + 1) + 4ull * (sa1 - sa0 + 1) + 4ull * Ar::WORDS * (sa1 - sa0) +
-                               4ull * (1 + Ar::WORDS) * (tr1 - tr0);
+                    w_bytes += 8ull * (n_s + 1) + 4ull * (sa1 - sa0 + 1) + 4ull * (1 + Ar::WORDS) * (tr1 - tr0);
+                    // per row: its cost, or for the residual correction its row of G
+                    w_bytes += (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * (sa1 - sa0);
                 }
             }
         }
@@ -1087,6 +1131,48 @@ __global__ void k_loop_control_host(LoopCtl *ctl, int next_idx) {
     if (ctl->cnt[next_idx] > 0 && ctl->sweep_base >= ctl->cap) ctl->hit_cap = 1;
 }
 
+// The residual-correction table: G[sa][k] = -w_i c(sa) + sum_t p_t B(s'_t)
+// - B(s) (+ w_p at a pre-sink state) for every action row of every state,
+// formed in double-float from the FP32 values B and rounded once to FP32.
+// One thread per (state, weight); the threads of a state write its rows'
+// Kp weights as consecutive words.
+template <int KP>
+__global__ void __launch_bounds__(kThreads) k_delta_table(SweepArgs a, int n_chunks, const float *B, float *G) {
+    constexpr int SPR = kThreads / KP > 0 ? kThreads / KP : 1;
+    const int k = threadIdx.x % KP, slot = threadIdx.x / KP;
+    if (slot >= SPR) return;
+    for (int item = blockIdx.x; item < n_chunks; item += gridDim.x) {
+        const int4 ch = a.chunks[item];
+        const ProdDesc pd = a.prods[ch.x];
+        const ArithDF::W w = a.wdf[(size_t)ch.x * KP + k];
+        for (int s = ch.y + slot; s < ch.z; s += SPR) {
+            const uint32_t u = pd.state_off + (uint32_t)s;
+            const bool pre = (uint32_t)s >= pd.pre_begin;
+            const float bs = B[(size_t)u * KP + k];
+            const uint32_t a0 = a.state_sa[u], a1 = a.state_sa[u + 1];
+            for (uint32_t sa = a0; sa < a1; ++sa) {
+                const float2 cd = a.costdf[sa];
+                DF acc = ArithDF::reward(w, {cd.x, cd.y});
+                for (uint32_t t = a.sa_tr[sa], t1 = a.sa_tr[sa + 1]; t < t1; ++t) {
+                    const float2 pr = a.pdf[t];
+                    ArithDF::mac(acc, {pr.x, pr.y}, {B[(size_t)a.col[t] * KP + k], 0.0f});
+                }
+                acc = ArithDF::add_base(df_norm(acc), w, pre);
+                acc = df_add(acc, {-bs, 0.0f});
+                G[(size_t)sa * KP + k] = __fadd_rn(acc.h, acc.l);
+            }
+        }
+    }
+}
+
+// V = B + d as an unevaluated double-float sum (two_sum is exact).
+__global__ void k_delta_combine(const float *B, const float *d, float2 *V, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const DF v = two_sum(B[i], d[i]);
+        V[i] = make_float2(v.h, v.l);
+    }
+}
+
 __global__ void k_convert(const float *v32, float2 *a, float2 *b, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float2 v = make_float2(v32[i], 0.0f);
@@ -1204,24 +1290,27 @@ int blocks_per_sm_t(int Kp, int variant) {
 int sweep_setup_attributes() {
     cudaError_t e = set_attr_t<ArithF32>();
     if (e == cudaSuccess) e = set_attr_t<ArithDF>();
+    if (e == cudaSuccess) e = set_attr_t<ArithDelta>();
     return (int)e;
 }
 
-int sweep_smem_bytes(bool fp64) { return fp64 ? smem_of<ArithDF>() : smem_of<ArithF32>(); }
-
-int sweep_blocks_per_sm(bool fp64, int Kp, int variant) {
-    return fp64 ? blocks_per_sm_t<ArithDF>(Kp, variant) : blocks_per_sm_t<ArithF32>(Kp, variant);
+int sweep_smem_bytes(int kind) {
+    return kind == kSweepDF ? smem_of<ArithDF>() : kind == kSweepDelta ? smem_of<ArithDelta>() : smem_of<ArithF32>();
 }
 
-int sweep_variant_count(bool fp64) { return fp64 ? Variants<ArithDF>::N : Variants<ArithF32>::N; }
-
-
-
-void sweep_variant_shape(bool fp64, int variant, int *vmax, int *d, int *minb) {
-    *vmax = fp64 ? Variants<ArithDF>::vmax[variant] : Variants<ArithF32>::vmax[variant];
-    *d = fp64 ? Variants<ArithDF>::d[variant] : Variants<ArithF32>::d[variant];
-    *minb = fp64 ? Variants<ArithDF>::minb[variant] : Variants<ArithF32>::minb[variant];
+int sweep_blocks_per_sm(int kind, int Kp, int variant) {
+    return kind == kSweepDF      ? blocks_per_sm_t<ArithDF>(Kp, variant)
+           : kind == kSweepDelta ? blocks_per_sm_t<ArithDelta>(Kp, variant)
+                                 : blocks_per_sm_t<ArithF32>(Kp, variant);
 }
+
+int sweep_variant_count(int kind) {
+    return kind == kSweepDF ? Variants<ArithDF>::N : kind == kSweepDelta ? Variants<ArithDelta>::N : Variants<ArithF32>::N;
+}
+
+
+
+
 
 int eval_blocks_per_sm() {
     int n = 0;
@@ -1232,9 +1321,10 @@ int eval_blocks_per_sm() {
     return n > 0 ? n : 1;
 }
 
-int launch_sweep(bool fp64, int Kp, int variant, const SweepArgs &a, int pos, int grid, void *s) {
-    return fp64 ? launch_sweep_t<ArithDF>(Kp, variant, a, pos, grid, (cudaStream_t)s)
-                : launch_sweep_t<ArithF32>(Kp, variant, a, pos, grid, (cudaStream_t)s);
+int launch_sweep(int kind, int Kp, int variant, const SweepArgs &a, int pos, int grid, void *s) {
+    return kind == kSweepDF      ? launch_sweep_t<ArithDF>(Kp, variant, a, pos, grid, (cudaStream_t)s)
+           : kind == kSweepDelta ? launch_sweep_t<ArithDelta>(Kp, variant, a, pos, grid, (cudaStream_t)s)
+                                 : launch_sweep_t<ArithF32>(Kp, variant, a, pos, grid, (cudaStream_t)s);
 }
 
 int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, void *sv) {
@@ -1346,6 +1436,29 @@ int launch_loop_control(LoopCtl *ctl, unsigned long long handle, int next_idx, v
 
 int launch_loop_control_host(LoopCtl *ctl, int next_idx, void *s) {
     k_loop_control_host<<<1, 32, 0, (cudaStream_t)s>>>(ctl, next_idx);
+    return (int)cudaGetLastError();
+}
+
+int launch_delta_table(int Kp, const SweepArgs &a, int n_chunks, const float *B, float *G, void *sv) {
+    cudaStream_t s = (cudaStream_t)sv;
+    const int grid = n_chunks < 8192 ? n_chunks : 8192;
+    if (grid <= 0) return 0;
+    switch (Kp) {
+    case 1: k_delta_table<1><<<grid, kThreads, 0, s>>>(a, n_chunks, B, G); break;
+    case 2: k_delta_table<2><<<grid, kThreads, 0, s>>>(a, n_chunks, B, G); break;
+    case 4: k_delta_table<4><<<grid, kThreads, 0, s>>>(a, n_chunks, B, G); break;
+    case 8: k_delta_table<8><<<grid, kThreads, 0, s>>>(a, n_chunks, B, G); break;
+    case 16: k_delta_table<16><<<grid, kThreads, 0, s>>>(a, n_chunks, B, G); break;
+    case 32: k_delta_table<32><<<grid, kThreads, 0, s>>>(a, n_chunks, B, G); break;
+    case 64: k_delta_table<64><<<grid, kThreads, 0, s>>>(a, n_chunks, B, G); break;
+    default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_delta_combine(const float *B, const float *d, float2 *V, size_t n, void *s) {
+    const int grid = (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+    k_delta_combine<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(B, d, V, n);
     return (int)cudaGetLastError();
 }
 

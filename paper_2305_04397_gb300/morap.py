@@ -49,7 +49,7 @@ class Config(ctypes.Structure):
         ("sweep_variant_fp32", ctypes.c_int32),
         ("sweep_variant_fp64", ctypes.c_int32),
         ("skip_unchanged", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("polish", ctypes.c_int32),
     ]
 
 
@@ -68,7 +68,7 @@ class SolveStats(ctypes.Structure):
         ("ms_eval", ctypes.c_double), ("ms_host", ctypes.c_double), ("ms_total", ctypes.c_double),
         ("pairs_not_converged", ctypes.c_int32), ("eval_pairs", ctypes.c_int32),
         ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int32),
-        ("variant_fp32", ctypes.c_int32), ("variant_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("variant_fp32", ctypes.c_int32), ("variant_fp64", ctypes.c_int32), ("polish", ctypes.c_int32),
         ("ms_tune", ctypes.c_double),
         ("skipped_fp32", ctypes.c_int64), ("skipped_fp64", ctypes.c_int64), ("work_items", ctypes.c_int64),
     ]

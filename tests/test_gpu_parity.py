@@ -125,11 +125,11 @@ def _oracle_pairs(prods, W, nI, nJ):
     return c, rc, rp, res
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_solve_matches_oracle(M, tiny, tiny_prods, precision):
+@pytest.mark.parametrize("precision,polish", [(0, 0), (0, 1), (1, 1)])
+def test_solve_matches_oracle(M, tiny, tiny_prods, precision, polish):
     W = tiny_weights(tiny)
     nI, nJ = len(tiny.agents), len(tiny.tasks)
-    ctx = make_ctx(M, tiny, precision=precision)
+    ctx = make_ctx(M, tiny, precision=precision, polish=polish)
     out = ctx.solve(W)
     c, rc, rp, res = _oracle_pairs(tiny_prods, W, nI, nJ)
     assert np.all(out["status"] == 0)
@@ -164,9 +164,9 @@ def test_solve_matches_oracle(M, tiny, tiny_prods, precision):
     assert checked > 20
     st = ctx.stats()
     if precision == 0:
-        assert st["fp32_sweeps"] > 0
+        assert st["fp32_sweeps"] > 0 and st["polish"] == polish
     else:
-        assert st["fp32_sweeps"] == 0
+        assert st["fp32_sweeps"] == 0 and st["polish"] == 1
     ctx.close()
 
 
@@ -335,19 +335,21 @@ def test_host_driven_loop_matches_graph_loop(M, tiny):
     b.close()
 
 
-def test_every_kernel_shape_gives_identical_results(M, grid32):
+@pytest.mark.parametrize("polish", [0, 1])
+def test_every_kernel_shape_gives_identical_results(M, grid32, polish):
     """The tuner only picks among kernel shapes that do the same arithmetic
     in the same order, so each forced shape must reproduce the tuned run
-    bit for bit (and the stats must name the shape used)."""
+    bit for bit (and the stats must name the shape used), for both forms of
+    the second phase."""
     pair = (grid32.agents[:3], grid32.tasks[:5])
     W = np.ascontiguousarray(grid32.weights[:8][:, [0, 1, 2, 10, 11, 12, 13, 14]])
-    ref_ctx = make_ctx(M, pair)
+    ref_ctx = make_ctx(M, pair, polish=polish)
     ref = ref_ctx.solve(W, evaluate=True)
     st = ref_ctx.stats()
-    assert 0 <= st["variant_fp32"] < 4 and 0 <= st["variant_fp64"] < 4
+    assert 0 <= st["variant_fp32"] < 4 and 0 <= st["variant_fp64"] < 4 and st["polish"] == polish
     ref_ctx.close()
     for v in range(4):
-        ctx = make_ctx(M, pair, sweep_variant_fp32=v, sweep_variant_fp64=(v + 1) % 4)
+        ctx = make_ctx(M, pair, sweep_variant_fp32=v, sweep_variant_fp64=(v + 1) % 4, polish=polish)
         out = ctx.solve(W, evaluate=True)
         assert ctx.stats()["variant_fp32"] == v and ctx.stats()["variant_fp64"] == (v + 1) % 4
         for key in ("c", "r_cost", "r_prob"):
@@ -355,14 +357,15 @@ def test_every_kernel_shape_gives_identical_results(M, grid32):
         ctx.close()
 
 
-def test_skipping_unchanged_items_is_exact(M, grid32):
+@pytest.mark.parametrize("polish", [0, 1])
+def test_skipping_unchanged_items_is_exact(M, grid32, polish):
     """A sweep skips work items none of whose inputs changed in the previous
     sweep; the results must be those of recomputing everything, bit for bit,
     and some items must actually have been skipped."""
     pair = (grid32.agents[:3], grid32.tasks[:6])
     W = np.ascontiguousarray(grid32.weights[:8][:, [0, 1, 2, 10, 11, 12, 13, 14, 15]])
-    on = make_ctx(M, pair)
-    off = make_ctx(M, pair, skip_unchanged=0)
+    on = make_ctx(M, pair, polish=polish)
+    off = make_ctx(M, pair, skip_unchanged=0, polish=polish)
     a = on.solve(W, evaluate=True)
     st_on = on.stats()
     b = off.solve(W, evaluate=True)
@@ -398,6 +401,26 @@ def test_skipping_with_scattered_successors(M):
         assert a["c"][k, i, j] == pytest.approx(r["c"], abs=TOL)
     on.close()
     off.close()
+
+
+def test_polish_forms_agree_at_full_size(M, grid32):
+    """The FP32 residual correction on a double-float table and the
+    double-float sweeps converge to the same fixed point: on the benchmark's
+    batch (200 products, K = 16) the c values and points agree far inside
+    the 1e-6 tolerance, with the same assignments and the same sweep counts."""
+    inst = grid32
+    out, st = {}, {}
+    for polish in (0, 1):
+        ctx = make_ctx(M, inst, polish=polish)
+        out[polish] = ctx.supporting_points(inst.weights, want_c=True)
+        st[polish] = ctx.stats()
+        ctx.close()
+    assert st[0]["polish"] == 0 and st[1]["polish"] == 1
+    assert np.max(np.abs(out[0]["c"] - out[1]["c"])) < 1e-9
+    assert np.max(np.abs(out[0]["r"] - out[1]["r"])) < 1e-9
+    assert np.array_equal(out[0]["assign"], out[1]["assign"])
+    assert st[0]["fp32_sweeps"] == st[1]["fp32_sweeps"]
+    assert abs(st[0]["fp64_sweeps"] - st[1]["fp64_sweeps"]) <= 6
 
 
 def test_batch_invariance(M, grid32):
@@ -468,7 +491,7 @@ def test_invalid_inputs(M, tiny):
         ctx.solve(W)
     assert e.value.code == M.EINVAL
     ctx.close()
-    for field, val in (("sweep_variant_fp32", 4), ("sweep_variant_fp64", -2), ("launch_mode", 2)):
+    for field, val in (("sweep_variant_fp32", 4), ("sweep_variant_fp64", -2), ("launch_mode", 2), ("polish", 2)):
         cfg = M.morap_config_default()
         setattr(cfg, field, val)
         with pytest.raises(M.MorapError) as e:
