@@ -50,15 +50,15 @@ def make_workload(name, rank=0):
     return getattr(I, gen)(seed={"config_grid32": 1, "config_uneven": 2, "config_large": 3}[gen] + rank), eps
 
 
-# DRAM traffic of the top kernel from the committed ncu capture
-# (profiles/k_sweep_f32_<workload>.md): one full FP32 sweep of the tuned shape,
-# its DRAM bytes and its algorithmic bytes.  Valid only while the sweep source
-# is the one that was profiled (sha256 prefix) and the same shape runs.
+# DRAM traffic of the sweep kernels from the committed ncu captures
+# (profiles/k_sweep_{f32,delta}_<workload>.md): one full sweep of the tuned
+# shape, its DRAM bytes and its algorithmic bytes.  Valid only while the sweep
+# source is the one that was profiled (sha256 prefix) and the same shape runs.
 TRAFFIC_PROFILES = {
-    ("grid32-10x20-K16", "fp32"): {"sweep_source": "844741a58a766e19", "variant": 0,
-                                   "dram_bytes": 147796224 + 28456192, "alg_bytes": 189.1e6},
-    ("grid32-10x20-K16", "df64"): {"sweep_source": "844741a58a766e19", "variant": 0,
-                                   "dram_bytes": 243567616 + 71100672, "alg_bytes": 324.8e6},
+    ("grid32-10x20-K16", "fp32"): {"sweep_source": "cafc99478262e567", "variant": 0,
+                                   "dram_bytes": 147910912 + 28476160, "alg_bytes": 189.1e6},
+    ("grid32-10x20-K16", "delta"): {"sweep_source": "cafc99478262e567", "variant": 0,
+                                    "dram_bytes": 357808128 + 42351872, "alg_bytes": 394.1e6},
 }
 
 

@@ -87,6 +87,7 @@ struct morap_ctx {
     std::vector<ProdDesc> h_prods;
     std::vector<int4> h_chunks;
     int32_t *in_items = nullptr;  // [items][kInItems] input items of each sweep work item
+    uint2 *item_w = nullptr;      // [items] (transitions, rows) of each work item
     uint8_t *chg[3] = {};         // per item: changed in sweep n % 3
     ProdDesc *d_prods = nullptr;
     AgentDesc *d_agents = nullptr;
@@ -468,6 +469,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a.frozen = c->frozen;
     a.a_rec = c->a_rec;
     a.in_items = c->in_items;
+    a.item_w = c->item_w;
     a.skip = c->cfg.skip_unchanged ? 1 : 0;
     for (int q = 0; q < 3; ++q) a.chg[q] = c->chg[q];
     a.eps1 = c->cfg.eps_vi;
@@ -985,7 +987,8 @@ int run_construction(morap_ctx *c, cudaStream_t s) {
     CKL(launch_build(c->d_prods, c->P, c->d_ad, c->d_td, c->d_sp, c->d_sap, c->d_succ, c->d_prob, c->d_cost,
                      c->d_letters, c->d_nd, c->state_sa, c->state_tr, c->sa_tr, c->col, c->cp32, c->p64, c->pdf,
                      c->cost32, c->cost64, c->costdf, c->TS, c->TSA, c->TT, c->max_work, s));
-    CKL(launch_item_inputs(c->d_chunks, (int)c->h_chunks.size(), c->d_prods, c->state_tr, c->col, c->in_items, s));
+    CKL(launch_item_inputs(c->d_chunks, (int)c->h_chunks.size(), c->d_prods, c->state_tr, c->col, c->in_items, c->item_w,
+                                c->state_sa, s));
     return MORAP_OK;
 }
 
@@ -1115,6 +1118,7 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         CKR(dev_alloc(c, L, &c->d_prods, P * sizeof(ProdDesc)));
         CKR(dev_alloc(c, L, &c->d_chunks, std::max<size_t>(chunks.size(), 1) * sizeof(int4)));
         CKR(dev_alloc(c, L, &c->in_items, std::max<size_t>(chunks.size(), 1) * kInItems * sizeof(int32_t)));
+        CKR(dev_alloc(c, L, &c->item_w, std::max<size_t>(chunks.size(), 1) * sizeof(uint2)));
         for (int q = 0; q < 3; ++q) CKR(dev_alloc(c, L, &c->chg[q], std::max<size_t>(chunks.size(), 1)));
         CKR(dev_alloc(c, L, &c->d_ad, nI * sizeof(AgentDesc)));
         CKR(dev_alloc(c, L, &c->d_td, nJ * sizeof(TaskDesc)));

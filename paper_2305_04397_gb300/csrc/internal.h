@@ -170,6 +170,7 @@ struct SweepArgs {
     // holding successors of its states (-1 none, -2 too many: always
     // recompute); chg[n % 3][item]: some value of the item changed in sweep n.
     const int32_t *in_items;
+    const uint2 *item_w;  // (transitions, state-action rows) of each item, for the statistics
     uint8_t *chg[3];
     int skip;  // 0: recompute every item (skipping disabled)
     const float *G;  // residual-correction polish: [state-action][Kp] table (see ArithDelta)
@@ -224,7 +225,8 @@ int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const Ta
 int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W,
                          float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1, void *s);
 int launch_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, const uint32_t *state_tr,
-                       const int32_t *col, int32_t *in_items, void *s);
+                       const int32_t *col, int32_t *in_items, uint2 *item_w, const uint32_t *state_sa,
+                       void *s);
 // chg_prev (nullable, [n_items]): set to 1 so that the first sweep recomputes every item
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
                      size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s,

@@ -93,6 +93,12 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *g) {
 __device__ __forceinline__ void cp_async8(void *smem, const void *g) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(g));
 }
+// Ask L2 to fetch a contiguous range of global memory (a hint with no
+// completion and no effect on results).  Start and size must be multiples of
+// 16 bytes, and the range must lie inside one allocation.
+__device__ __forceinline__ void prefetch_l2(const void *g, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(g), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -627,6 +633,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         ctl->cnt[far] = 0;
         ctl->next[far] = 0;
     }
+    __shared__ struct {
+        unsigned long long updates, bytes;
+        unsigned int skipped;
+    } b_stats;
+    if (threadIdx.x == 0) b_stats.updates = b_stats.bytes = 0ull, b_stats.skipped = 0u;
+    __syncthreads();
     const unsigned int n_items = ctl->cnt[cur];
     const unsigned int sweep = ctl->sweep_base + pos;
     const int lane = threadIdx.x & 31;
@@ -636,182 +648,210 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     uint32_t *ssa = reinterpret_cast<uint32_t *>(stage_buf);
     typename Ar::W *wsm = reinterpret_cast<typename Ar::W *>(warp_buf + Ar::STAGE_BYTES);  // the item's weights
 
-    // Work items are taken kGrab at a time, items kept for the next sweep are
-    // appended once per grab, and the statistics are summed per warp: the
-    // shared counters see a few atomics per warp instead of several per item.
-    constexpr int kGrab = 1;
+    // The shared counters see few atomics: the statistics are summed per warp
+    // and per block, and items that stay in the work list are collected per
+    // warp (lane i holds the i-th) and appended 32 at a time.
     unsigned long long w_updates = 0, w_bytes = 0;  // lane 0's running sums
     unsigned int w_skipped = 0;
+    unsigned int kept = 0u;
+    int n_kept = 0;  // warp-uniform
+    auto flush_kept = [&]() {
+        unsigned int at = 0;
+        if (lane == 0) at = atomicAdd(&ctl->cnt[nxt], (unsigned int)n_kept);
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (lane < n_kept) a.list[nxt][at + lane] = kept;
+        n_kept = 0;
+    };
+    // Warp w of the grid takes list entry w without an atomic; later items
+    // are taken one at a time from a shared cursor that starts after those.
+    const unsigned int n_warps = gridDim.x * (kThreads / 32);
+    bool first = true;
     for (;;) {
-        unsigned int it0 = 0;
-        if (lane == 0) it0 = atomicAdd(&ctl->next[cur], (unsigned int)kGrab);
-        it0 = __shfl_sync(0xffffffffu, it0, 0);
-        if (it0 >= n_items) break;
-        unsigned int keep_mask = 0u;  // grab slots whose items stay in the work list
-        for (int g = 0; g < kGrab; ++g) {
-            const unsigned int it = it0 + (unsigned int)g;
-            if (it >= n_items) break;
-            const unsigned int item = a.list[cur][it];
-            const int4 ch = a.chunks[item];
-            const int p = ch.x;
-            const size_t pair0 = (size_t)p * KP;
-            // activity of the product's weights from the previous sweep's residuals
-            unsigned int act_w[2] = {0u, 0u}, nz_w[2] = {0u, 0u};
-    #pragma unroll
-            for (int h = 0; h < (KP + 31) / 32; ++h) {
-                const int k = lane + 32 * h;
-                bool act = false, nz = false;
-                if (k < KP) {
-                    const double prev = as_double(res_prev[pair0 + k]);
-                    act = prev > a.thr[pair0 + k];
-                    nz = prev > 0.0;
-                }
-                act_w[h] = __ballot_sync(0xffffffffu, act);
-                nz_w[h] = __ballot_sync(0xffffffffu, nz);
+        unsigned int it = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+        if (!first) {
+            if (lane == 0) it = n_warps + atomicAdd(&ctl->next[cur], 1u);
+            it = __shfl_sync(0xffffffffu, it, 0);
+        }
+        first = false;
+        if (it >= n_items) break;
+        const unsigned int item = a.list[cur][it];
+        // the exact-skip test's inputs (see below) depend only on the
+        // item: load them now, alongside the item's descriptor
+        bool in_chg = false;
+        uint2 iw = make_uint2(0u, 0u);  // lane 0: (transitions, rows) of the item
+        if (lane == 0) iw = __ldg(a.item_w + item);
+        if (a.skip) {
+            const int32_t in = lane < kInItems ? __ldg(a.in_items + (size_t)item * kInItems + lane) : -1;
+            in_chg = (lane == 0 && a.chg[far][item]) || in == -2 || (in >= 0 && a.chg[far][in]);
+        }
+        const int4 ch = a.chunks[item];
+        const int p = ch.x;
+        const size_t pair0 = (size_t)p * KP;
+        // activity of the product's weights from the previous sweep's residuals
+        unsigned int act_w[2] = {0u, 0u}, nz_w[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < (KP + 31) / 32; ++h) {
+            const int k = lane + 32 * h;
+            bool act = false, nz = false;
+            if (k < KP) {
+                const double prev = as_double(res_prev[pair0 + k]);
+                act = prev > a.thr[pair0 + k];
+                nz = prev > 0.0;
             }
-            const bool any_active = (act_w[0] | act_w[1]) != 0u;
-            if ((nz_w[0] | nz_w[1]) == 0u) {  // converged earlier and already copied: drop
-                if (ch.w)
-                    for (int k = lane; k < KP; k += 32) a.frozen[pair0 + k] = 1;
+            act_w[h] = __ballot_sync(0xffffffffu, act);
+            nz_w[h] = __ballot_sync(0xffffffffu, nz);
+        }
+        const bool any_active = (act_w[0] | act_w[1]) != 0u;
+        if ((nz_w[0] | nz_w[1]) == 0u) {  // converged earlier and already copied: drop
+            if (ch.w)
+                for (int k = lane; k < KP; k += 32) a.frozen[pair0 + k] = 1;
+            continue;
+        }
+        const ProdDesc pd = a.prods[p];
+        if (any_active) {
+            if (lane == n_kept) kept = item;
+            if (++n_kept == 32) flush_kept();
+        }
+        if (ch.w)
+            for (int k = lane; k < KP; k += 32) {
+                res_next[pair0 + k] = 0ull;
+                if ((act_w[k >> 5] >> (k & 31)) & 1u)
+                    a.sweeps_pair[pair0 + k] = (int32_t)(sweep + 1);
+                else
+                    a.frozen[pair0 + k] = 1;
+            }
+        if (any_active && a.skip) {
+            // exact skipping: nothing this item reads changed in the previous
+            // sweep, so it would reproduce its values bit for bit (and both
+            // value buffers already hold them)
+            if (!__any_sync(0xffffffffu, in_chg)) {
+                if (lane == 0) {
+                    a.chg[cur][item] = 0;
+                    ++w_skipped;
+                    // the sweep still updates these states (to the same values)
+                    w_updates += (unsigned long long)iw.x *
+                                 (unsigned long long)(__popc(act_w[0]) + __popc(act_w[1]));
+                }
                 continue;
             }
-            const ProdDesc pd = a.prods[p];
-            if (any_active) keep_mask |= 1u << g;
-            if (ch.w)
-                for (int k = lane; k < KP; k += 32) {
-                    res_next[pair0 + k] = 0ull;
-                    if ((act_w[k >> 5] >> (k & 31)) & 1u)
-                        a.sweeps_pair[pair0 + k] = (int32_t)(sweep + 1);
-                    else
-                        a.frozen[pair0 + k] = 1;
-                }
-            if (any_active && a.skip) {
-                // exact skipping: nothing this item reads changed in the previous
-                // sweep, so it would reproduce its values bit for bit (and both
-                // value buffers already hold them)
-                const int32_t in = lane < kInItems ? __ldg(a.in_items + (size_t)item * kInItems + lane) : -1;
-                const bool in_chg = (lane == 0 && a.chg[far][item]) || in == -2 || (in >= 0 && a.chg[far][in]);
-                if (!__any_sync(0xffffffffu, in_chg)) {
-                    if (lane == 0) {
-                        a.chg[cur][item] = 0;
-                        ++w_skipped;
-                        // the sweep still updates these states (to the same values)
-                        const uint32_t tr0 = a.state_tr[pd.state_off + ch.y], tr1 = a.state_tr[pd.state_off + ch.z];
-                        w_updates += (unsigned long long)(tr1 - tr0) *
-                                     (unsigned long long)(__popc(act_w[0]) + __popc(act_w[1]));
-                    }
-                    continue;
-                }
-            }
-            bool changed = false;
-            unsigned int act_bits = 0u;
-    #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                const int k = k0 + v;
-                act_bits |= ((act_w[k >> 5] >> (k & 31)) & 1u) << v;
-            }
-            for (int k = lane; k < KP; k += 32) wsm[k] = Ar::weight(a, pair0 + k);
-            __syncwarp();
-            float rmax[VEC];
-    #pragma unroll
-            for (int v = 0; v < VEC; ++v) rmax[v] = 0.0f;
+        }
+        bool changed = false;
+        unsigned int act_bits = 0u;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const int k = k0 + v;
+            act_bits |= ((act_w[k >> 5] >> (k & 31)) & 1u) << v;
+        }
+        for (int k = lane; k < KP; k += 32) wsm[k] = Ar::weight(a, pair0 + k);
+        __syncwarp();
+        float rmax[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) rmax[v] = 0.0f;
 
-            if (!any_active) {  // every weight of the product froze: copy its rows once
-                for (int s = ch.y + grp; s < ch.z; s += SPW) {
-                    const size_t row = (size_t)(pd.state_off + (uint32_t)s) * ROW + (size_t)k0 * Ar::WORDS;
-                    float yw[NW];
-                    load_words<NW>(Vold + row, yw);
-                    store_words<NW>(Vnew + row, yw);
-                }
-            } else {
-                // a batch's state boundaries are loaded while the previous
-                // batch is staged and computed
-                uint32_t nx_sa = 0, nx_tr = 0;
-                if (lane <= min(kStageStates, ch.z - ch.y)) {
-                    nx_sa = __ldg(a.state_sa + pd.state_off + (uint32_t)ch.y + lane);
-                    nx_tr = __ldg(a.state_tr + pd.state_off + (uint32_t)ch.y + lane);
-                }
-                for (int s0 = ch.y; s0 < ch.z;) {
-                    const int m_max = min(kStageStates, ch.z - s0);
-                    const uint32_t u0 = pd.state_off + (uint32_t)s0;
-                    const uint32_t my_sa = nx_sa, my_tr = nx_tr;
-                    const uint32_t A0 = __shfl_sync(0xffffffffu, my_sa, 0);
-                    const uint32_t T0 = __shfl_sync(0xffffffffu, my_tr, 0);
-                    const bool fits =
-                        lane <= m_max && my_sa - A0 <= (uint32_t)Ar::AMAX && my_tr - T0 <= (uint32_t)Ar::EMAX;
-                    int m = __popc(__ballot_sync(0xffffffffu, fits)) - 1;  // boundaries 0..m fit
-                    const bool staged = m >= 1;
-                    if (!staged) m = 1;  // one state too large for the buffer: read it from global memory
-                    const uint32_t A1 = __shfl_sync(0xffffffffu, my_sa, m);
-                    const uint32_t T1 = __shfl_sync(0xffffffffu, my_tr, m);
-                    if (lane <= m) ssa[lane] = my_sa;
-                    if (s0 + m < ch.z && lane <= min(kStageStates, ch.z - (s0 + m))) {
-                        nx_sa = __ldg(a.state_sa + u0 + (uint32_t)m + lane);
-                        nx_tr = __ldg(a.state_tr + u0 + (uint32_t)m + lane);
-                    }
-                    typename Ar::View vw;
-                    if (staged) {
-                        Ar::stage(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
-                        cp_async_wait_all();
-                        vw = Ar::smem_view(stage_buf);
-                    } else {
-                        vw = Ar::global_view(a, A0, T0);
-                    }
-                    __syncwarp();
-                    for (int i = grp; i < m; i += SPW)
-                        if constexpr (PIPE)
-                            process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
-                                                                (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits,
-                                                                Vold, Vnew, k0, rmax, changed);
-                        else
-                            process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
-                                                           (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits, Vold,
-                                                           Vnew, k0, rmax, changed);
-                    __syncwarp();  // the next batch reuses the buffer
-                    s0 += m;
-                }
+        if (!any_active) {  // every weight of the product froze: copy its rows once
+            for (int s = ch.y + grp; s < ch.z; s += SPW) {
+                const size_t row = (size_t)(pd.state_off + (uint32_t)s) * ROW + (size_t)k0 * Ar::WORDS;
+                float yw[NW];
+                load_words<NW>(Vold + row, yw);
+                store_words<NW>(Vnew + row, yw);
             }
-            {
-                const bool any_chg = __any_sync(0xffffffffu, changed);
-                if (lane == 0) a.chg[cur][item] = any_chg ? 1 : 0;
+        } else {
+            // a batch's state boundaries are loaded while the previous
+            // batch is staged and computed
+            uint32_t nx_sa = 0, nx_tr = 0;
+            if (lane <= min(kStageStates, ch.z - ch.y)) {
+                nx_sa = __ldg(a.state_sa + pd.state_off + (uint32_t)ch.y + lane);
+                nx_tr = __ldg(a.state_tr + pd.state_off + (uint32_t)ch.y + lane);
             }
-            // residual: lanes with the same li share weights
-    #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                float r = rmax[v];
-    #pragma unroll
-                for (int off = LPS; off < 32; off <<= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
-                if (grp == 0 && any_active && r > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)r);
-            }
-            if (lane == 0) {
-                const uint32_t n_s = (uint32_t)(ch.z - ch.y);
-                const uint32_t u0 = pd.state_off + ch.y, u1 = pd.state_off + ch.z;
-                w_bytes += 2ull * n_s * ROW * 4;
-                if (any_active) {
-                    const uint32_t sa0 = a.state_sa[u0], sa1 = a.state_sa[u1];
-                    const uint32_t tr0 = a.state_tr[u0], tr1 = a.state_tr[u1];
-                    const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
-                    w_updates += (unsigned long long)(tr1 - tr0) * (unsigned long long)n_act;
-                    // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
-                    w_bytes += 8ull * (n_s + 1) + 4ull * (sa1 - sa0 + 1) + 4ull * (1 + Ar::WORDS) * (tr1 - tr0);
-                    // per row: its cost, or for the residual correction its row of G
-                    w_bytes += (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * (sa1 - sa0);
+            for (int s0 = ch.y; s0 < ch.z;) {
+                const int m_max = min(kStageStates, ch.z - s0);
+                const uint32_t u0 = pd.state_off + (uint32_t)s0;
+                const uint32_t my_sa = nx_sa, my_tr = nx_tr;
+                const uint32_t A0 = __shfl_sync(0xffffffffu, my_sa, 0);
+                const uint32_t T0 = __shfl_sync(0xffffffffu, my_tr, 0);
+                const bool fits =
+                    lane <= m_max && my_sa - A0 <= (uint32_t)Ar::AMAX && my_tr - T0 <= (uint32_t)Ar::EMAX;
+                int m = __popc(__ballot_sync(0xffffffffu, fits)) - 1;  // boundaries 0..m fit
+                const bool staged = m >= 1;
+                if (!staged) m = 1;  // one state too large for the buffer: read it from global memory
+                const uint32_t A1 = __shfl_sync(0xffffffffu, my_sa, m);
+                const uint32_t T1 = __shfl_sync(0xffffffffu, my_tr, m);
+                if (lane <= m) ssa[lane] = my_sa;
+                if (s0 + m < ch.z && lane <= min(kStageStates, ch.z - (s0 + m))) {
+                    nx_sa = __ldg(a.state_sa + u0 + (uint32_t)m + lane);
+                    nx_tr = __ldg(a.state_tr + u0 + (uint32_t)m + lane);
                 }
+                typename Ar::View vw;
+#ifndef MORAP_PREFETCH_G
+#define MORAP_PREFETCH_G 1
+#endif
+#ifndef MORAP_PREFETCH_V
+#define MORAP_PREFETCH_V 0
+#endif
+                // the batch's rows of G (residual correction) are one
+                // contiguous range: start it towards L2 before staging
+                if constexpr (MORAP_PREFETCH_G && std::is_same<Ar, ArithDelta>::value && KP % 4 == 0)
+                    if (lane == 0 && A1 > A0) prefetch_l2(a.G + (size_t)A0 * KP, (A1 - A0) * (uint32_t)(KP * 4));
+                if constexpr (MORAP_PREFETCH_V && (ROW % 4) == 0)
+                    if (lane == 0) prefetch_l2(Vold + (size_t)u0 * ROW, (uint32_t)(m * ROW * 4));
+                if (staged) {
+                    Ar::stage(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
+                    cp_async_wait_all();
+                    vw = Ar::smem_view(stage_buf);
+                } else {
+                    vw = Ar::global_view(a, A0, T0);
+                }
+                __syncwarp();
+                for (int i = grp; i < m; i += SPW)
+                    if constexpr (PIPE)
+                        process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                                                            (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits,
+                                                            Vold, Vnew, k0, rmax, changed);
+                    else
+                        process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                                                       (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits, Vold,
+                                                       Vnew, k0, rmax, changed);
+                __syncwarp();  // the next batch reuses the buffer
+                s0 += m;
             }
         }
-        // the grab's items that stay active, appended with one atomic
-        if (keep_mask) {
-            unsigned int at = 0;
-            if (lane == 0) at = atomicAdd(&ctl->cnt[nxt], (unsigned int)__popc(keep_mask));
-            at = __shfl_sync(0xffffffffu, at, 0);
-            if (lane < kGrab && ((keep_mask >> lane) & 1u))
-                a.list[nxt][at + __popc(keep_mask & ((1u << lane) - 1u))] = a.list[cur][it0 + lane];
+        {
+            const bool any_chg = __any_sync(0xffffffffu, changed);
+            if (lane == 0) a.chg[cur][item] = any_chg ? 1 : 0;
+        }
+        // residual: lanes with the same li share weights
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            float r = rmax[v];
+#pragma unroll
+            for (int off = LPS; off < 32; off <<= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
+            if (grp == 0 && any_active && r > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)r);
+        }
+        if (lane == 0) {
+            const uint32_t n_s = (uint32_t)(ch.z - ch.y);
+            w_bytes += 2ull * n_s * ROW * 4;
+            if (any_active) {
+                const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
+                w_updates += (unsigned long long)iw.x * (unsigned long long)n_act;
+                // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
+                w_bytes += 8ull * (n_s + 1) + 4ull * (iw.y + 1) + 4ull * (1 + Ar::WORDS) * iw.x;
+                // per row: its cost, or for the residual correction its row of G
+                w_bytes += (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * iw.y;
+            }
         }
     }
+    if (n_kept) flush_kept();
+    // statistics: per block in shared memory, then one global atomic each
     if (lane == 0) {
-        if (w_updates) atomicAdd(&ctl->updates, w_updates);
-        if (w_bytes) atomicAdd(&ctl->bytes, w_bytes);
-        if (w_skipped) atomicAdd(&ctl->skipped, w_skipped);
+        if (w_updates) atomicAdd(&b_stats.updates, w_updates);
+        if (w_bytes) atomicAdd(&b_stats.bytes, w_bytes);
+        if (w_skipped) atomicAdd(&b_stats.skipped, w_skipped);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (b_stats.updates) atomicAdd(&ctl->updates, b_stats.updates);
+        if (b_stats.bytes) atomicAdd(&ctl->bytes, b_stats.bytes);
+        if (b_stats.skipped) atomicAdd(&ctl->skipped, b_stats.skipped);
     }
 }
 
@@ -1048,13 +1088,15 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
 
 // ------------------------------------------------------------- small kernels
 
-// The FP32 phase hands over to the double-float phase once a pair's residual
-// is at most 2^-MORAP_THR32_SHIFT of its largest possible value.  Its
+// The FP32 phase hands over to the polish phase once a pair's residual is
+// at most 2^-MORAP_THR32_SHIFT of its largest possible value.  Its
 // round-down iterates increase monotonically to a fixed point of the rounded
 // operator, where the residual is exactly 0, so any shift terminates; the
-// shift only trades FP32 sweeps against double-float sweeps.
+// shift only trades FP32 sweeps against polish sweeps (near its fixed point
+// the round-down iteration slows down, so a later hand-over costs more
+// sweeps in total).
 #ifndef MORAP_THR32_SHIFT
-#define MORAP_THR32_SHIFT 17
+#define MORAP_THR32_SHIFT 16
 #endif
 
 __device__ __forceinline__ float2 to_df(double d) {
@@ -1078,7 +1120,7 @@ __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, in
         const float2 a = to_df(wi), b = to_df(wp);
         wdf[idx] = make_float4(a.x, a.y, b.x, b.y);
         // FP32 phase: stop once the residual is within a few ulps of the
-        // largest possible value (values lie in [0, w_p]); FP64 phase: eps1.
+        // largest possible value (values lie in [0, w_p]); polish phase: eps1.
         thr32[idx] = fmax(eps1, ldexp(wp, -MORAP_THR32_SHIFT));
         thr64[idx] = eps1;
     }
@@ -1379,7 +1421,7 @@ int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, un
 // with warp matching; more than kInItems distinct inputs mark the item as
 // always recomputed.
 __global__ void k_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, const uint32_t *state_tr,
-                              const int32_t *col, int32_t *in_items) {
+                              const int32_t *col, int32_t *in_items, uint2 *item_w, const uint32_t *state_sa) {
     __shared__ int32_t set[kThreads / 32][kInItems];
     __shared__ int cnt[kThreads / 32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1389,6 +1431,7 @@ __global__ void k_item_inputs(const int4 *chunks, int n_items, const ProdDesc *p
         if (lane == 0) cnt[w] = 0;
         __syncwarp();
         const uint32_t t0 = state_tr[pd.state_off + ch.y], t1 = state_tr[pd.state_off + ch.z];
+        if (lane == 0) item_w[item] = make_uint2(t1 - t0, state_sa[pd.state_off + ch.z] - state_sa[pd.state_off + ch.y]);
         for (uint32_t base = t0; base < t1; base += 32) {
             // the set as the previous batches left it (they are complete: __syncwarp
             // below); values inserted by this batch are distinct from each other
@@ -1421,11 +1464,11 @@ __global__ void k_item_inputs(const int4 *chunks, int n_items, const ProdDesc *p
 }
 
 int launch_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, const uint32_t *state_tr,
-                       const int32_t *col, int32_t *in_items, void *s) {
+                       const int32_t *col, int32_t *in_items, uint2 *item_w, const uint32_t *state_sa, void *s) {
     if (n_items <= 0) return 0;
     const int grid = (n_items + kThreads / 32 - 1) / (kThreads / 32);
     k_item_inputs<<<grid < 65535 ? grid : 65535, kThreads, 0, (cudaStream_t)s>>>(chunks, n_items, prods, state_tr, col,
-                                                                              in_items);
+                                                                              in_items, item_w, state_sa);
     return (int)cudaGetLastError();
 }
 
