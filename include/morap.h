@@ -97,6 +97,11 @@ typedef struct morap_config {
                                    the FP32 phase's values, d iterated in FP32); 1 = the sweeps in
                                    double-float on V itself.  0 holds one more value array in FP32
                                    and a [state-action][Kp] FP32 table on the device.             */
+    int32_t eval_block;         /* 1 (default): Algorithm 4 evaluates each pair whose values fit in
+                                   one block's shared memory (n + 1 <= 7168 states) with one block
+                                   running all its sweeps in one launch; larger pairs, or all pairs
+                                   with 0, run the multi-launch sweep loop.  Same results.         */
+    int32_t reserved;
 } morap_config;
 
 typedef struct morap_ctx morap_ctx;

@@ -140,6 +140,8 @@ struct morap_ctx {
     size_t eval_cap_pairs = 0, eval_cap_chunks = 0, eval_cap_states = 0;
     float4 *E[2] = {};
     int4 *d_epairs = nullptr, *d_echunks = nullptr;
+    int *d_ebpairs = nullptr;  // pairs evaluated one block each (k_eval_block)
+    bool eval_block_ready = false;
     unsigned long long *eres[3] = {};
     unsigned int *elist[3] = {};
     int32_t *esweeps = nullptr;
@@ -507,6 +509,7 @@ int ensure_eval(morap_ctx *c, size_t n_pairs, size_t n_chunks, size_t n_states) 
     CKR(dev_alloc(c, L, &c->E[1], n_states * sizeof(float4)));
     CKR(dev_alloc(c, L, &c->d_epairs, n_pairs * sizeof(int4)));
     CKR(dev_alloc(c, L, &c->d_echunks, n_chunks * sizeof(int4)));
+    CKR(dev_alloc(c, L, &c->d_ebpairs, n_pairs * sizeof(int)));
     for (int i = 0; i < 3; ++i) {
         CKR(dev_alloc(c, L, &c->eres[i], n_pairs * sizeof(unsigned long long)));
         CKR(dev_alloc(c, L, &c->elist[i], n_chunks * sizeof(unsigned int)));
@@ -719,26 +722,50 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
 int run_evaluation_group(morap_ctx *c, const std::vector<int4> &pairs_in, cudaStream_t s, std::vector<double> &rc,
                          std::vector<double> &rp, int &not_conv) {
     std::vector<int4> pairs = pairs_in;
-    std::vector<int4> chunks;
+    // Pairs small enough for one block run all their sweeps in k_eval_block;
+    // the others go through the multi-launch loop over kEvalChunk-state
+    // items.  The loop's items come first in `chunks`, then those of the
+    // block pairs (every pair's rows are compacted).
+    std::vector<int4> chunks, bchunks;
+    std::vector<int> bpairs;
+    uint32_t bmax = 0;
     size_t off = 0;
     for (size_t e = 0; e < pairs.size(); ++e) {
         const ProdDesc &pd = c->h_prods[pairs[e].x];
         pairs[e].z = (int)off;
         off += pd.n_nd + 1;
+        const bool block = c->cfg.eval_block && pd.n_nd + 1 <= kEvalBlockStates;
+        if (block) {
+            bpairs.push_back((int)e);
+            bmax = std::max(bmax, pd.n_nd + 1);
+        }
         for (uint32_t b = 0; b < pd.n_nd; b += kEvalChunk)
-            chunks.push_back(make_int4((int)e, (int)b, (int)std::min<uint32_t>(pd.n_nd, b + kEvalChunk), b == 0));
+            (block ? bchunks : chunks)
+                .push_back(make_int4((int)e, (int)b, (int)std::min<uint32_t>(pd.n_nd, b + kEvalChunk), b == 0));
     }
+    const size_t n_loop = chunks.size();
+    chunks.insert(chunks.end(), bchunks.begin(), bchunks.end());
+    // largest pairs first: blocks start in index order, so the long ones do
+    // not end up in the last wave
+    std::stable_sort(bpairs.begin(), bpairs.end(), [&](int x, int y) {
+        return c->h_prods[pairs[x].x].n_nd > c->h_prods[pairs[y].x].n_nd;
+    });
     if (off > 0x7fffffffull) return fail(MORAP_ENOMEM, "evaluation batch too large");
     CKR(ensure_eval(c, pairs.size(), chunks.size(), off));
-    const size_t npair = pairs.size();
-    CKR(stage(c, std::max(npair * sizeof(int4) + chunks.size() * sizeof(int4), 2 * npair * sizeof(double) +
-                                                                                    npair * 4 + sizeof(LoopCtl) + 64)));
+    const size_t npair = pairs.size(), nb = bpairs.size();
+    const size_t up = npair * sizeof(int4) + chunks.size() * sizeof(int4) + nb * sizeof(int);
+    CKR(stage(c, std::max(up, 2 * npair * sizeof(double) + npair * 4 + sizeof(LoopCtl) + 64)));
     if (npair) {
-        std::memcpy(c->h_stage, pairs.data(), npair * sizeof(int4));
-        std::memcpy((char *)c->h_stage + npair * sizeof(int4), chunks.data(), chunks.size() * sizeof(int4));
-        CK(cudaMemcpyAsync(c->d_epairs, c->h_stage, npair * sizeof(int4), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(c->d_echunks, (char *)c->h_stage + npair * sizeof(int4), chunks.size() * sizeof(int4),
+        char *h = (char *)c->h_stage;
+        std::memcpy(h, pairs.data(), npair * sizeof(int4));
+        std::memcpy(h + npair * sizeof(int4), chunks.data(), chunks.size() * sizeof(int4));
+        std::memcpy(h + (npair + chunks.size()) * sizeof(int4), bpairs.data(), nb * sizeof(int));
+        CK(cudaMemcpyAsync(c->d_epairs, h, npair * sizeof(int4), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c->d_echunks, h + npair * sizeof(int4), chunks.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, s));
+        if (nb)
+            CK(cudaMemcpyAsync(c->d_ebpairs, h + (npair + chunks.size()) * sizeof(int4), nb * sizeof(int),
+                               cudaMemcpyHostToDevice, s));
     }
     CK(cudaMemsetAsync(c->E[0], 0, off * sizeof(float4), s));
     CK(cudaMemsetAsync(c->E[1], 0, off * sizeof(float4), s));
@@ -748,13 +775,23 @@ int run_evaluation_group(morap_ctx *c, const std::vector<int4> &pairs_in, cudaSt
         CKL(launch_eval_compact(ea, (int)chunks.size(), s));
     }
     const unsigned int cap = (unsigned int)std::max(1, c->cfg.max_sweeps);
-    CKL(launch_loop_init(c->ctl + 2, c->elist[0], (unsigned int)chunks.size(), c->eres, npair, c->esweeps,
-                         c->efrozen, cap, s));
+    CKL(launch_loop_init(c->ctl + 2, c->elist[0], (unsigned int)n_loop, c->eres, npair, c->esweeps, c->efrozen, cap,
+                         s));
     CK(cudaEventRecord(c->ev[4], s));
-    {
+    int launches = 3;
+    if (nb) {
+        // the loop checks its cap after every body of six sweeps
+        if (!c->eval_block_ready) {
+            CKL(eval_block_setup());
+            c->eval_block_ready = true;
+        }
+        CKL(launch_eval_block(c->eargs, c->d_ebpairs, (int)nb, bmax, (cap + 5) / 6 * 6, s));
+        launches += 1;
+    }
+    if (n_loop) {
         const EvalArgs ea = c->eargs;
         int rc = MORAP_OK;
-        LoopGraph *ge = eval_graph(c, chunks.size(), rc);
+        LoopGraph *ge = eval_graph(c, n_loop, rc);
         CKR(rc);
         const int grid = ge->grid;
         CKR(run_loop(c, *ge, c->ctl + 2, s, [&](int pos, cudaStream_t st) {
@@ -779,14 +816,15 @@ int run_evaluation_group(morap_ctx *c, const std::vector<int4> &pairs_in, cudaSt
     rp.assign(h + npair, h + 2 * npair);
     not_conv = 0;
     for (size_t e = 0; e < npair; ++e) not_conv += hf[e] == 0;
-    c->stats.eval_sweeps = (int32_t)hctl->sweep_base;
+    c->stats.eval_sweeps = (int32_t)std::max(n_loop ? hctl->sweep_base : 0u, hctl->block_sweeps);
     c->stats.updates_eval = (int64_t)hctl->updates;
     c->stats.bytes_eval = (int64_t)hctl->bytes;
     c->stats.ms_eval = ms_between(c->ev[4], c->ev[5]);
     c->stats.eval_pairs = (int32_t)npair;
     c->stats.h2d_bytes += (int64_t)((npair + chunks.size()) * sizeof(int4));
     c->stats.d2h_bytes += (int64_t)(npair * (2 * sizeof(double) + 1) + sizeof(LoopCtl));
-    c->stats.kernel_launches += 3 + c->stats.eval_sweeps + c->stats.eval_sweeps / 6;
+    if (n_loop) launches += (int)hctl->sweep_base + (int)hctl->sweep_base / 6;
+    c->stats.kernel_launches += launches;
     return MORAP_OK;
 }
 
@@ -1202,6 +1240,7 @@ void morap_config_default(morap_config *cfg) {
     cfg->sweep_variant_fp64 = -1;
     cfg->skip_unchanged = 1;
     cfg->polish = 0;
+    cfg->eval_block = 1;
 }
 
 const char *morap_last_error(void) { return g_last_error.c_str(); }
@@ -1225,6 +1264,7 @@ int morap_ctx_create(const morap_config *cfg, morap_ctx **out) {
         c.sweep_variant_fp64 < -1 || c.sweep_variant_fp64 >= sweep_variant_count(kSweepDF))
         return fail(MORAP_EINVAL, "config: sweep_variant_* must be -1 (tuned) or a shape index");
     if (c.polish != 0 && c.polish != 1) return fail(MORAP_EINVAL, "config: polish must be 0 or 1");
+    if (c.eval_block != 0 && c.eval_block != 1) return fail(MORAP_EINVAL, "config: eval_block must be 0 or 1");
     CK(cudaSetDevice(c.device));
     morap_ctx *ctx = new morap_ctx();
     ctx->cfg = c;

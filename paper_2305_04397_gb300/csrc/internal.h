@@ -126,6 +126,7 @@ struct LoopCtl {
     unsigned int hit_cap;
     unsigned int cap;
     unsigned int skipped;  // work items a sweep skipped because none of their inputs changed
+    unsigned int block_sweeps;  // most sweeps of a pair evaluated by one block (k_eval_block)
     unsigned long long updates;
     unsigned long long bytes;
 };
@@ -135,6 +136,11 @@ struct LoopCtl {
 #endif
 constexpr int kChunk = MORAP_CHUNK;  // states per (warp) work item of the optimisation sweeps
 constexpr int kEvalChunk = 256;  // states per work item of the evaluation sweeps
+// Pairs whose n + 1 values fit twice in kEvalBlockSmem bytes are evaluated by
+// one block each, all sweeps in one launch (k_eval_block).
+constexpr int kEvalBlockThreads = 1024;
+constexpr int kEvalBlockSmem = 224 * 1024;
+constexpr uint32_t kEvalBlockStates = kEvalBlockSmem / (2 * 16);
 constexpr int kThreads = 256;
 constexpr int kInItems = 16;     // input items recorded per work item (more: always recomputed)
 int sweep_smem_bytes(int kind);
@@ -252,6 +258,11 @@ int launch_convert(const float *v32, float2 *vda, float2 *vdb, size_t n, void *s
 int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, void *s);
 int launch_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V64, const uint8_t *frozen, double *c_out,
                     int32_t *status_out, void *s);
+int eval_block_setup();  // once per device: k_eval_block's shared-memory limit
+// Algorithm 4 for n_bpairs pairs (indices into a.pairs), one block each,
+// every sweep in one launch; max_states bounds their n + 1 values.
+int launch_eval_block(const EvalArgs &a, const int *bpairs, int n_bpairs, uint32_t max_states, unsigned int cap,
+                      void *s);
 int launch_eval_sweep(const EvalArgs &a, int pos, int grid, void *s);
 int launch_eval_compact(const EvalArgs &a, int n_chunks, void *s);
 int launch_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *prods, const float4 *E, double *rc,

@@ -989,8 +989,23 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
     // propagation: each of the stride + 1 accumulations adds at most a few
     // units of 2^-48 relative error, so they are not counted as residual.
     const float noise = (float)(stride + 1) * 2.8421709430404007e-14f; /* 2^-45 */
+    // Few atomics on the shared counters: block b takes list entry b first
+    // and later ones from a cursor that starts after gridDim.x; items that
+    // stay in the list are appended up to 32 at a time; the statistics are
+    // summed per block (thread 0's registers).
+    __shared__ unsigned int s_kept[32];
+    __shared__ int s_n_kept;
+    if (threadIdx.x == 0) s_n_kept = 0;
+    auto flush_kept = [&]() {  // thread 0
+        const unsigned int at = atomicAdd(&ctl->cnt[nxt], (unsigned int)s_n_kept);
+        for (int q = 0; q < s_n_kept; ++q) a.list[nxt][at + q] = s_kept[q];
+        s_n_kept = 0;
+    };
+    unsigned long long b_updates = 0, b_bytes = 0;
+    bool first = true;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctl->next[cur], 1u);
+        if (threadIdx.x == 0) s_item = first ? blockIdx.x : gridDim.x + atomicAdd(&ctl->next[cur], 1u);
+        first = false;
         __syncthreads();
         const unsigned int it = s_item;
         if (it >= n_items) break;
@@ -1007,8 +1022,8 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
         const int4 pr = a.pairs[e];
         const ProdDesc pd = a.prods[pr.x];
         if (threadIdx.x == 0 && active) {
-            const unsigned int at = atomicAdd(&ctl->cnt[nxt], 1u);
-            a.list[nxt][at] = item;
+            s_kept[s_n_kept++] = item;
+            if (s_n_kept == 32) flush_kept();
         }
         if (ch.w && threadIdx.x == 0) {
             a.res[nxt][e] = 0ull;
@@ -1075,14 +1090,152 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
             const unsigned long long n_s = (unsigned long long)(ch.z - ch.y);
             // values read + written (16 B each); when computing also the cost
             // (8) and every slot's successor and probability (4 + 8)
-            unsigned long long bytes = n_s * 32ull;
+            b_bytes += n_s * 32ull;
             if (active) {
-                bytes += n_s * (8ull + 12ull * (unsigned long long)stride);
-                atomicAdd(&ctl->updates, n_s * (unsigned long long)stride * 2ull);
+                b_bytes += n_s * (8ull + 12ull * (unsigned long long)stride);
+                b_updates += n_s * (unsigned long long)stride * 2ull;
             }
-            atomicAdd(&ctl->bytes, bytes);
         }
         __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (s_n_kept) flush_kept();
+        if (b_updates) atomicAdd(&ctl->updates, b_updates);
+        if (b_bytes) atomicAdd(&ctl->bytes, b_bytes);
+    }
+}
+
+// One state of Algorithm 4 for the block kernel: y from x = Eo[s], the
+// state's cost and its slots (successor, probability); returns the state's
+// residual contribution.  The operations and their order are those of
+// k_eval_sweep.
+template <int MS>
+__device__ __forceinline__ float eval_state(const float4 *Eo, float4 *En, uint32_t s, bool pre, float2 cc,
+                                            const int32_t (&c)[MS], const float2 (&p)[MS], int stride, float noise) {
+    const float4 x = Eo[s];
+    DF yc = {-cc.x, -cc.y};
+    DF yp = {pre ? 1.0f : 0.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < MS; ++j) {
+        if (j >= stride) break;
+        const float4 v = Eo[c[j]];
+        ArithDF::mac(yc, {p[j].x, p[j].y}, {v.x, v.y});
+        ArithDF::mac(yp, {p[j].x, p[j].y}, {v.z, v.w});
+    }
+    yc = df_norm(yc);
+    yp = df_norm(yp);
+    En[s] = make_float4(yc.h, yc.l, yp.h, yp.l);
+    float dc = ArithDF::diff(yc, {x.x, x.y}), dp = ArithDF::diff(yp, {x.z, x.w});
+    dc = dc > noise * fabsf(yc.h) ? dc : 0.0f;
+    dp = dp > noise * fabsf(yp.h) ? dp : 0.0f;
+    return fmaxf(dc, dp);
+}
+
+// Algorithm 4 for one pair per block with every sweep inside the kernel: the
+// pair's values live in shared memory (double buffered), its compact
+// scheduler rows are read from global memory, and one block barrier
+// separates sweeps.  Per state the same operations in the same order as
+// k_eval_sweep, the same residual (with the same noise floor) and the same
+// stopping rule: the pair stops after the first sweep whose residual is at
+// most thr, or at the sweep cap.  Used for pairs whose n + 1 values fit twice
+// in shared memory; it saves the launch and work-list overhead of hundreds
+// of short sweeps.  The final values go to E[0], where the gather reads them.
+// MS > 0: rows of at most MS slots, U states per thread loaded together so
+// that their loads overlap; MS = 0: any row length, one state at a time.
+template <int MS, int U>
+__global__ void __launch_bounds__(kEvalBlockThreads, 1) k_eval_block(EvalArgs a, const int *bpairs, unsigned int cap) {
+    extern __shared__ __align__(16) float4 sE[];
+    __shared__ float s_red[2][kEvalBlockThreads / 32];
+    const int e = bpairs[blockIdx.x];
+    const int4 pr = a.pairs[e];
+    const ProdDesc pd = a.prods[pr.x];
+    const uint32_t n = pd.n_nd, n1 = n + 1;
+    const size_t off = (size_t)pr.z;
+    const int stride = a.stride;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t s = threadIdx.x; s < 2 * n1; s += kEvalBlockThreads) sE[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const float noise = (float)(stride + 1) * 2.8421709430404007e-14f; /* 2^-45, as k_eval_sweep */
+    // float r > thr_f exactly when (double)r > thr
+    const float thr_f = __double2float_rd(a.thr);
+    unsigned int sweeps = 0;
+    bool converged = false;
+    while (sweeps < cap) {
+        const float4 *Eo = sE + (sweeps & 1) * n1;
+        float4 *En = sE + ((sweeps + 1) & 1) * n1;
+        float r = 0.0f;
+        if constexpr (MS > 0) {
+            for (uint32_t s0 = threadIdx.x; s0 < n; s0 += U * kEvalBlockThreads) {
+                float2 cc[U];
+                int32_t c[U][MS];
+                float2 p[U][MS];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const uint32_t s = s0 + u * kEvalBlockThreads;
+                    if (s < n) {
+                        cc[u] = a.ecost[off + s];
+                        const size_t base = off * stride + s;
+#pragma unroll
+                        for (int j = 0; j < MS; ++j)
+                            if (j < stride) {
+                                c[u][j] = a.ecol[base + (size_t)j * n1];
+                                p[u][j] = a.ep[base + (size_t)j * n1];
+                            }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const uint32_t s = s0 + u * kEvalBlockThreads;
+                    if (s < n) r = fmaxf(r, eval_state<MS>(Eo, En, s, s >= pd.pre_begin, cc[u], c[u], p[u], stride, noise));
+                }
+            }
+        } else {
+            for (uint32_t s = threadIdx.x; s < n; s += kEvalBlockThreads) {
+                const float4 x = Eo[s];
+                const float2 cc = a.ecost[off + s];
+                DF yc = {-cc.x, -cc.y};
+                DF yp = {(s >= pd.pre_begin) ? 1.0f : 0.0f, 0.0f};
+                const size_t base = off * stride + s;
+                for (int j = 0; j < stride; ++j) {
+                    const int32_t c = a.ecol[base + (size_t)j * n1];
+                    const float2 p = a.ep[base + (size_t)j * n1];
+                    const float4 v = Eo[c];
+                    ArithDF::mac(yc, {p.x, p.y}, {v.x, v.y});
+                    ArithDF::mac(yp, {p.x, p.y}, {v.z, v.w});
+                }
+                yc = df_norm(yc);
+                yp = df_norm(yp);
+                En[s] = make_float4(yc.h, yc.l, yp.h, yp.l);
+                float dc = ArithDF::diff(yc, {x.x, x.y}), dp = ArithDF::diff(yp, {x.z, x.w});
+                dc = dc > noise * fabsf(yc.h) ? dc : 0.0f;
+                dp = dp > noise * fabsf(yp.h) ? dp : 0.0f;
+                r = fmaxf(r, fmaxf(dc, dp));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if (lane == 0) s_red[sweeps & 1][warp] = r;
+        __syncthreads();  // also orders this sweep's En writes before the next sweep's reads
+        float mx = 0.0f;
+#pragma unroll 8
+        for (int w = 0; w < kEvalBlockThreads / 32; ++w) mx = fmaxf(mx, s_red[sweeps & 1][w]);
+        ++sweeps;
+        if (!(mx > thr_f)) {
+            converged = true;
+            break;
+        }
+    }
+    const float4 *Ef = sE + (sweeps & 1) * n1;
+    for (uint32_t s = threadIdx.x; s < n; s += kEvalBlockThreads) a.E[0][off + s] = Ef[s];
+    if (threadIdx.x == 0) {
+        a.frozen[e] = converged ? 1 : 0;
+        a.sweeps_pair[e] = (int32_t)sweeps;
+        // the scheduler's rows and costs are read once per sweep; the values
+        // stay in shared memory (written out once)
+        atomicAdd(&a.ctl->updates, (unsigned long long)sweeps * n * (unsigned long long)stride * 2ull);
+        atomicAdd(&a.ctl->bytes,
+                  (unsigned long long)sweeps * n * (8ull + 12ull * (unsigned long long)stride) + 16ull * n);
+        atomicMax(&a.ctl->block_sweeps, sweeps);
     }
 }
 
@@ -1150,6 +1303,7 @@ __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_it
         ctl->hit_cap = 0;
         ctl->cap = cap;
         ctl->skipped = 0;
+        ctl->block_sweeps = 0;
         ctl->updates = 0;
         ctl->bytes = 0;
     }
@@ -1334,6 +1488,30 @@ int sweep_setup_attributes() {
     if (e == cudaSuccess) e = set_attr_t<ArithDF>();
     if (e == cudaSuccess) e = set_attr_t<ArithDelta>();
     return (int)e;
+}
+
+int eval_block_setup() {
+    cudaError_t e = cudaFuncSetAttribute(k_eval_block<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kEvalBlockSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_eval_block<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEvalBlockSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_eval_block<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEvalBlockSmem);
+    return (int)e;
+}
+
+int launch_eval_block(const EvalArgs &a, const int *bpairs, int n_bpairs, uint32_t max_states, unsigned int cap,
+                      void *s) {
+    if (n_bpairs <= 0) return 0;
+    const size_t smem = 2ull * max_states * sizeof(float4);
+    if (smem > (size_t)kEvalBlockSmem) return (int)cudaErrorInvalidValue;
+    if (a.stride <= 4)
+        k_eval_block<4, 2><<<n_bpairs, kEvalBlockThreads, smem, (cudaStream_t)s>>>(a, bpairs, cap);
+    else if (a.stride <= 8)
+        k_eval_block<8, 1><<<n_bpairs, kEvalBlockThreads, smem, (cudaStream_t)s>>>(a, bpairs, cap);
+    else
+        k_eval_block<0, 1><<<n_bpairs, kEvalBlockThreads, smem, (cudaStream_t)s>>>(a, bpairs, cap);
+    return (int)cudaGetLastError();
 }
 
 int sweep_smem_bytes(int kind) {

@@ -50,6 +50,8 @@ class Config(ctypes.Structure):
         ("sweep_variant_fp64", ctypes.c_int32),
         ("skip_unchanged", ctypes.c_int32),
         ("polish", ctypes.c_int32),
+        ("eval_block", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
