@@ -55,10 +55,10 @@ def make_workload(name, rank=0):
 # shape, its DRAM bytes and its algorithmic bytes.  Valid only while the sweep
 # source is the one that was profiled (sha256 prefix) and the same shape runs.
 TRAFFIC_PROFILES = {
-    ("grid32-10x20-K16", "fp32"): {"sweep_source": "cafc99478262e567", "variant": 0,
-                                   "dram_bytes": 147910912 + 28476160, "alg_bytes": 189.1e6},
-    ("grid32-10x20-K16", "delta"): {"sweep_source": "cafc99478262e567", "variant": 0,
-                                    "dram_bytes": 357808128 + 42351872, "alg_bytes": 394.1e6},
+    ("grid32-10x20-K16", "fp32"): {"sweep_source": "04ab2e4d8ef70131", "variant": 0,
+                                   "dram_bytes": 148023808 + 28043264, "alg_bytes": 189.1e6},
+    ("grid32-10x20-K16", "delta"): {"sweep_source": "04ab2e4d8ef70131", "variant": 0,
+                                    "dram_bytes": 357817344 + 42246912, "alg_bytes": 394.1e6},
 }
 
 
