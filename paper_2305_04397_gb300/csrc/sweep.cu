@@ -1105,47 +1105,31 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
     }
 }
 
-// One state of Algorithm 4 for the block kernel: y from x = Eo[s], the
-// state's cost and its slots (successor, probability); returns the state's
-// residual contribution.  The operations and their order are those of
-// k_eval_sweep.
-template <int MS>
-__device__ __forceinline__ float eval_state(const float4 *Eo, float4 *En, uint32_t s, bool pre, float2 cc,
-                                            const int32_t (&c)[MS], const float2 (&p)[MS], int stride, float noise) {
-    const float4 x = Eo[s];
-    DF yc = {-cc.x, -cc.y};
-    DF yp = {pre ? 1.0f : 0.0f, 0.0f};
-#pragma unroll
-    for (int j = 0; j < MS; ++j) {
-        if (j >= stride) break;
-        const float4 v = Eo[c[j]];
-        ArithDF::mac(yc, {p[j].x, p[j].y}, {v.x, v.y});
-        ArithDF::mac(yp, {p[j].x, p[j].y}, {v.z, v.w});
-    }
-    yc = df_norm(yc);
-    yp = df_norm(yp);
-    En[s] = make_float4(yc.h, yc.l, yp.h, yp.l);
-    float dc = ArithDF::diff(yc, {x.x, x.y}), dp = ArithDF::diff(yp, {x.z, x.w});
-    dc = dc > noise * fabsf(yc.h) ? dc : 0.0f;
-    dp = dp > noise * fabsf(yp.h) ? dp : 0.0f;
-    return fmaxf(dc, dp);
-}
-
-// Algorithm 4 for one pair per block with every sweep inside the kernel: the
-// pair's values live in shared memory (double buffered), its compact
-// scheduler rows are read from global memory, and one block barrier
-// separates sweeps.  Per state the same operations in the same order as
-// k_eval_sweep, the same residual (with the same noise floor) and the same
-// stopping rule: the pair stops after the first sweep whose residual is at
-// most thr, or at the sweep cap.  Used for pairs whose n + 1 values fit twice
-// in shared memory; it saves the launch and work-list overhead of hundreds
-// of short sweeps.  The final values go to E[0], where the gather reads them.
-// MS > 0: rows of at most MS slots, U states per thread loaded together so
-// that their loads overlap; MS = 0: any row length, one state at a time.
+// Algorithm 4 for one pair per block, every sweep inside one launch, as an
+// FP32 iteration followed by an FP32 residual correction on a double-float
+// table (the same scheme as the optimisation's polish, for a fixed
+// scheduler, where it is exact algebra: E = B + d with d = G + P d):
+//   A. E <- r + P E from 0 in FP32 (round to nearest) until, for both
+//      objectives, the sweep's largest move is at most 2^-18 of its largest
+//      value; B = the result;
+//   B. G = r + P B - B per state in double-float, rounded to FP32;
+//   C. d <- G + P d from 0 in FP32 until the sweep's largest move is at most
+//      thr (moves below (slots + 1) * 2^-23 |y| are FP32 rounding noise and
+//      count as 0, the analogue of k_eval_sweep's double-float floor);
+//   D. E = B + d, exactly, as a double-float pair.
+// The values live in shared memory (four float2 arrays: A's two buffers,
+// of which the unused one holds G, and C's two), one block barrier
+// separates sweeps.  A sweep costs two FP32 multiply-adds per slot instead
+// of two double-float ones; the result agrees with the double-float loop
+// to ~1e-9 (FP32 carries d, which is ~2^-18 of the values, to ~2^-24 of
+// itself per sweep).  The final values go to E[0], where the gather reads
+// them.  MS > 0: rows of at most MS slots, U states per thread loaded
+// together so that their loads overlap; MS = 0: any row length.
 template <int MS, int U>
 __global__ void __launch_bounds__(kEvalBlockThreads, 1) k_eval_block(EvalArgs a, const int *bpairs, unsigned int cap) {
-    extern __shared__ __align__(16) float4 sE[];
-    __shared__ float s_red[2][kEvalBlockThreads / 32];
+    constexpr int NWARP = kEvalBlockThreads / 32;
+    extern __shared__ __align__(16) float2 sX[];
+    __shared__ float s_red[2][4][NWARP];
     const int e = bpairs[blockIdx.x];
     const int4 pr = a.pairs[e];
     const ProdDesc pd = a.prods[pr.x];
@@ -1153,88 +1137,184 @@ __global__ void __launch_bounds__(kEvalBlockThreads, 1) k_eval_block(EvalArgs a,
     const size_t off = (size_t)pr.z;
     const int stride = a.stride;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t s = threadIdx.x; s < 2 * n1; s += kEvalBlockThreads) sE[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // X(q): phase A's buffers (q = 0, 1); D(q): phase C's
+    auto X = [&](unsigned int q) { return sX + (q & 1u) * n1; };
+    auto D = [&](unsigned int q) { return sX + (2u + (q & 1u)) * n1; };
+    for (uint32_t s = threadIdx.x; s < 4 * n1; s += kEvalBlockThreads) sX[s] = make_float2(0.f, 0.f);
     __syncthreads();
-    const float noise = (float)(stride + 1) * 2.8421709430404007e-14f; /* 2^-45, as k_eval_sweep */
-    // float r > thr_f exactly when (double)r > thr
-    const float thr_f = __double2float_rd(a.thr);
-    unsigned int sweeps = 0;
-    bool converged = false;
-    while (sweeps < cap) {
-        const float4 *Eo = sE + (sweeps & 1) * n1;
-        float4 *En = sE + ((sweeps + 1) & 1) * n1;
-        float r = 0.0f;
+    const float noise = (float)(stride + 1) * 1.1920928955078125e-07f; /* 2^-23 */
+    const float thr_f = __double2float_rd(a.thr);  // float r > thr_f exactly when (double)r > thr
+    // block-wide maxima of up to four quantities; every warp reduces the
+    // per-warp values itself, so one barrier per sweep suffices
+    auto block_max4 = [&](float (&v)[4], int parity) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[q] = fmaxf(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+            if (lane == 0) s_red[parity][q][warp] = v[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float m = lane < NWARP ? s_red[parity][q][lane] : 0.0f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            v[q] = m;
+        }
+    };
+    // One FP32 sweep over the block's states: y = base(s) + sum_j p_j x(c_j)
+    // with base = (-cost, pre) (phase A, Gt == nullptr) or G(s) (phase C);
+    // m[0..1] = largest move per objective (phase C: beyond the noise
+    // floor), m[2..3] = largest |y| per objective.
+    auto sweep = [&](const float2 *Xo, float2 *Xn, const float2 *Gt, float (&m)[4]) {
+        m[0] = m[1] = m[2] = m[3] = 0.0f;
+        constexpr int MSX = MS > 0 ? MS : 1;
+        auto one = [&](uint32_t s, float2 base, const int32_t (&c)[MSX], const float2 (&p)[MSX]) {
+            float yc = base.x, yp = base.y;
+#pragma unroll
+            for (int j = 0; j < MSX; ++j) {
+                if (j >= stride) break;
+                const float2 v = Xo[c[j]];
+                yc = __fmaf_rn(p[j].x, v.x, yc);
+                yp = __fmaf_rn(p[j].x, v.y, yp);
+            }
+            const float2 x = Xo[s];
+            Xn[s] = make_float2(yc, yp);
+            float dc = fabsf(yc - x.x), dp = fabsf(yp - x.y);
+            if (Gt) {
+                dc = dc > noise * fabsf(yc) ? dc : 0.0f;
+                dp = dp > noise * fabsf(yp) ? dp : 0.0f;
+            }
+            m[0] = fmaxf(m[0], dc);
+            m[1] = fmaxf(m[1], dp);
+            m[2] = fmaxf(m[2], fabsf(yc));
+            m[3] = fmaxf(m[3], fabsf(yp));
+        };
         if constexpr (MS > 0) {
             for (uint32_t s0 = threadIdx.x; s0 < n; s0 += U * kEvalBlockThreads) {
-                float2 cc[U];
-                int32_t c[U][MS];
-                float2 p[U][MS];
+                float2 base[U];
+                int32_t c[U][MSX];
+                float2 p[U][MSX];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const uint32_t s = s0 + u * kEvalBlockThreads;
                     if (s < n) {
-                        cc[u] = a.ecost[off + s];
-                        const size_t base = off * stride + s;
+                        if (Gt) {
+                            base[u] = Gt[s];
+                        } else {
+                            base[u] = make_float2(-a.ecost[off + s].x, s >= pd.pre_begin ? 1.0f : 0.0f);
+                        }
+                        const size_t b0 = off * stride + s;
 #pragma unroll
                         for (int j = 0; j < MS; ++j)
                             if (j < stride) {
-                                c[u][j] = a.ecol[base + (size_t)j * n1];
-                                p[u][j] = a.ep[base + (size_t)j * n1];
+                                c[u][j] = a.ecol[b0 + (size_t)j * n1];
+                                p[u][j] = a.ep[b0 + (size_t)j * n1];
                             }
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const uint32_t s = s0 + u * kEvalBlockThreads;
-                    if (s < n) r = fmaxf(r, eval_state<MS>(Eo, En, s, s >= pd.pre_begin, cc[u], c[u], p[u], stride, noise));
+                    if (s < n) one(s, base[u], c[u], p[u]);
                 }
             }
         } else {
             for (uint32_t s = threadIdx.x; s < n; s += kEvalBlockThreads) {
-                const float4 x = Eo[s];
-                const float2 cc = a.ecost[off + s];
-                DF yc = {-cc.x, -cc.y};
-                DF yp = {(s >= pd.pre_begin) ? 1.0f : 0.0f, 0.0f};
-                const size_t base = off * stride + s;
+                const float2 base =
+                    Gt ? Gt[s] : make_float2(-a.ecost[off + s].x, s >= pd.pre_begin ? 1.0f : 0.0f);
+                const size_t b0 = off * stride + s;
+                float yc = base.x, yp = base.y;
                 for (int j = 0; j < stride; ++j) {
-                    const int32_t c = a.ecol[base + (size_t)j * n1];
-                    const float2 p = a.ep[base + (size_t)j * n1];
-                    const float4 v = Eo[c];
-                    ArithDF::mac(yc, {p.x, p.y}, {v.x, v.y});
-                    ArithDF::mac(yp, {p.x, p.y}, {v.z, v.w});
+                    const int32_t c = a.ecol[b0 + (size_t)j * n1];
+                    const float px = a.ep[b0 + (size_t)j * n1].x;
+                    const float2 v = Xo[c];
+                    yc = __fmaf_rn(px, v.x, yc);
+                    yp = __fmaf_rn(px, v.y, yp);
                 }
-                yc = df_norm(yc);
-                yp = df_norm(yp);
-                En[s] = make_float4(yc.h, yc.l, yp.h, yp.l);
-                float dc = ArithDF::diff(yc, {x.x, x.y}), dp = ArithDF::diff(yp, {x.z, x.w});
-                dc = dc > noise * fabsf(yc.h) ? dc : 0.0f;
-                dp = dp > noise * fabsf(yp.h) ? dp : 0.0f;
-                r = fmaxf(r, fmaxf(dc, dp));
+                const float2 x = Xo[s];
+                Xn[s] = make_float2(yc, yp);
+                float dc = fabsf(yc - x.x), dp = fabsf(yp - x.y);
+                if (Gt) {
+                    dc = dc > noise * fabsf(yc) ? dc : 0.0f;
+                    dp = dp > noise * fabsf(yp) ? dp : 0.0f;
+                }
+                m[0] = fmaxf(m[0], dc);
+                m[1] = fmaxf(m[1], dp);
+                m[2] = fmaxf(m[2], fabsf(yc));
+                m[3] = fmaxf(m[3], fabsf(yp));
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
-        if (lane == 0) s_red[sweeps & 1][warp] = r;
-        __syncthreads();  // also orders this sweep's En writes before the next sweep's reads
-        float mx = 0.0f;
-#pragma unroll 8
-        for (int w = 0; w < kEvalBlockThreads / 32; ++w) mx = fmaxf(mx, s_red[sweeps & 1][w]);
+    };
+    unsigned int sweeps = 0, sweeps_a = 0;
+    bool converged = false;
+    // A
+    for (;;) {
+        if (sweeps >= cap) break;
+        float m[4];
+        sweep(X(sweeps), X(sweeps + 1), nullptr, m);
+        block_max4(m, sweeps & 1);
         ++sweeps;
-        if (!(mx > thr_f)) {
-            converged = true;
-            break;
+        const float f = 3.814697265625e-06f; /* 2^-18 */
+        if (m[0] <= f * m[2] && m[1] <= f * m[3]) break;
+    }
+    sweeps_a = sweeps;
+    const float2 *B = X(sweeps);
+    float2 *G = X(sweeps + 1);
+    if (sweeps < cap) {
+        // B: the table in double-float
+        for (uint32_t s = threadIdx.x; s < n; s += kEvalBlockThreads) {
+            const float2 cc = a.ecost[off + s];
+            DF gc = {-cc.x, -cc.y};
+            DF gp = {s >= pd.pre_begin ? 1.0f : 0.0f, 0.0f};
+            const size_t b0 = off * stride + s;
+            for (int j = 0; j < stride; ++j) {
+                const int32_t c = a.ecol[b0 + (size_t)j * n1];
+                const float2 p = a.ep[b0 + (size_t)j * n1];
+                const float2 v = B[c];
+                ArithDF::mac(gc, {p.x, p.y}, {v.x, 0.0f});
+                ArithDF::mac(gp, {p.x, p.y}, {v.y, 0.0f});
+            }
+            const float2 b = B[s];
+            gc = df_add(df_norm(gc), {-b.x, 0.0f});
+            gp = df_add(df_norm(gp), {-b.y, 0.0f});
+            G[s] = make_float2(__fadd_rn(gc.h, gc.l), __fadd_rn(gp.h, gp.l));
+        }
+        __syncthreads();
+        // C
+        unsigned int k = 0;
+        while (sweeps < cap) {
+            float m[4];
+            sweep(D(k), D(k + 1), G, m);
+            block_max4(m, sweeps & 1);
+            ++sweeps;
+            ++k;
+            if (!(fmaxf(m[0], m[1]) > thr_f)) {
+                converged = true;
+                break;
+            }
+        }
+        // D: E = B + d
+        const float2 *d = D(k);
+        for (uint32_t s = threadIdx.x; s < n; s += kEvalBlockThreads) {
+            const float2 b = B[s], v = d[s];
+            const DF ec = two_sum(b.x, v.x), ep = two_sum(b.y, v.y);
+            a.E[0][off + s] = make_float4(ec.h, ec.l, ep.h, ep.l);
+        }
+    } else {
+        for (uint32_t s = threadIdx.x; s < n; s += kEvalBlockThreads) {
+            const float2 b = B[s];
+            a.E[0][off + s] = make_float4(b.x, 0.0f, b.y, 0.0f);
         }
     }
-    const float4 *Ef = sE + (sweeps & 1) * n1;
-    for (uint32_t s = threadIdx.x; s < n; s += kEvalBlockThreads) a.E[0][off + s] = Ef[s];
     if (threadIdx.x == 0) {
         a.frozen[e] = converged ? 1 : 0;
         a.sweeps_pair[e] = (int32_t)sweeps;
-        // the scheduler's rows and costs are read once per sweep; the values
-        // stay in shared memory (written out once)
+        // per sweep the scheduler's rows and costs are read once (the
+        // table pass reads them once more); the values stay in shared memory
+        const unsigned long long per = (unsigned long long)n * (8ull + 12ull * (unsigned long long)stride);
         atomicAdd(&a.ctl->updates, (unsigned long long)sweeps * n * (unsigned long long)stride * 2ull);
-        atomicAdd(&a.ctl->bytes,
-                  (unsigned long long)sweeps * n * (8ull + 12ull * (unsigned long long)stride) + 16ull * n);
+        atomicAdd(&a.ctl->bytes, (unsigned long long)(sweeps + (sweeps > sweeps_a ? 1 : 0)) * per + 16ull * n);
         atomicMax(&a.ctl->block_sweeps, sweeps);
     }
 }

@@ -423,11 +423,12 @@ def test_polish_forms_agree_at_full_size(M, grid32):
     assert abs(st[0]["fp64_sweeps"] - st[1]["fp64_sweeps"]) <= 6
 
 
-def test_block_evaluation_equals_sweep_loop(M, grid32):
-    """Algorithm 4 with one block per pair (every sweep in one launch, values
-    in shared memory) and with the multi-launch sweep loop: same operations
-    in the same order per state and the same stopping rule, so the points
-    are bitwise identical; the block path also needs far fewer launches."""
+def test_block_evaluation_matches_sweep_loop(M, grid32):
+    """Algorithm 4 with one block per pair (every sweep in one launch, FP32
+    with a residual correction on a double-float table) and with the
+    multi-launch double-float sweep loop: both stop at the same residual
+    rule, so the points agree far inside the 1e-6 tolerance; the block
+    path needs far fewer launches."""
     pair = (grid32.agents[:4], grid32.tasks[:8])
     W = np.ascontiguousarray(grid32.weights[:8][:, [0, 1, 2, 3, 10, 11, 12, 13, 14, 15, 16, 17]])
     out, st = {}, {}
@@ -436,20 +437,18 @@ def test_block_evaluation_equals_sweep_loop(M, grid32):
         out[eb] = ctx.solve(W, evaluate=True)
         st[eb] = ctx.stats()
         ctx.close()
-    for key in ("c", "r_cost", "r_prob"):
-        assert np.array_equal(out[0][key], out[1][key]), key
-    # the loop also counts the sweep that copies a converged pair and rounds
-    # up to its bodies of six sweeps; the transition-updates are the same
-    assert 0 < st[1]["eval_sweeps"] <= st[0]["eval_sweeps"]
-    assert st[1]["updates_eval"] == st[0]["updates_eval"]
+    assert np.array_equal(out[0]["c"], out[1]["c"])
+    for key in ("r_cost", "r_prob"):
+        assert np.max(np.abs(out[0][key] - out[1][key])) < 1e-8, key
+    assert out[1]["code"] == M.OK and st[1]["eval_sweeps"] > 0
     assert st[1]["kernel_launches"] < st[0]["kernel_launches"]
 
 
 @pytest.mark.parametrize("n_succ", [(1, 3), (5, 7), (9, 12)])
 def test_block_evaluation_any_row_length(M, n_succ):
     """The block evaluation has variants for rows of at most 4 and 8 slots
-    and a general one; each must reproduce the sweep loop bit for bit, and
-    the values must match the oracle."""
+    and a general one; each must agree with the sweep loop and match the
+    oracle."""
     agents = [I.random_tiny_agent(5, 60 + i, n_states=400, n_actions=(1, 3), n_succ=n_succ) for i in range(2)]
     tasks = [I.random_tiny_task(5, 70 + j, n_locs=3) for j in range(2)]
     W = np.random.default_rng(9).dirichlet(np.ones(4), size=3)
@@ -458,8 +457,9 @@ def test_block_evaluation_any_row_length(M, n_succ):
         ctx = make_ctx(M, (agents, tasks), eval_block=eb)
         out[eb] = ctx.solve(W, evaluate=True)
         ctx.close()
-    for key in ("c", "r_cost", "r_prob"):
-        assert np.array_equal(out[0][key], out[1][key]), key
+    assert out[1]["code"] == M.OK
+    for key in ("r_cost", "r_prob"):
+        assert np.max(np.abs(out[0][key] - out[1][key])) < 1e-8, key
     for i, j, k in [(0, 0, 0), (1, 1, 2)]:
         r = O.solve_pair(O.Product(agents[i], tasks[j]), W[k][i], W[k][2 + j])
         assert out[1]["r_cost"][k, i, j] == pytest.approx(r["r_cost"], abs=TOL)
