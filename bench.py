@@ -53,24 +53,31 @@ def make_workload(name, rank=0):
 # DRAM traffic of the sweep kernels from the committed ncu captures
 # (profiles/k_sweep_{f32,delta}_<workload>.md): one full sweep of the tuned
 # shape, its DRAM bytes and its algorithmic bytes.  Valid only while the sweep
-# source is the one that was profiled (sha256 prefix) and the same shape runs.
+# kernels' source (sweep.cu up to its finalisation section; sha256 prefix) is
+# the one that was profiled and the same shape runs.
 TRAFFIC_PROFILES = {
-    ("grid32-10x20-K16", "fp32"): {"sweep_source": "04ab2e4d8ef70131", "variant": 0,
+    ("grid32-10x20-K16", "fp32"): {"sweep_source": "e2905b93cc8e783e", "variant": 0,
                                    "dram_bytes": 148023808 + 28043264, "alg_bytes": 189.1e6},
-    ("grid32-10x20-K16", "delta"): {"sweep_source": "04ab2e4d8ef70131", "variant": 0,
+    ("grid32-10x20-K16", "delta"): {"sweep_source": "e2905b93cc8e783e", "variant": 0,
                                     "dram_bytes": 357817344 + 42246912, "alg_bytes": 394.1e6},
 }
+SWEEP_SECTION_END = "// -------------------------------------------------------------- finalise"
+
+
+def _sweep_source_hash():
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_2305_04397_gb300", "csrc", "sweep.cu"), encoding="utf-8") as f:
+        text = f.read()
+    return hashlib.sha256(text[: text.index(SWEEP_SECTION_END)].encode()).hexdigest()[:16]
 
 
 def _traffic(workload, phase, variant, alg_bytes_per_launch):
-    import hashlib
-
     prof = TRAFFIC_PROFILES.get((workload, phase))
     if prof is None or variant != prof["variant"]:
         return None
-    with open(os.path.join(ROOT, "paper_2305_04397_gb300", "csrc", "sweep.cu"), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest()[:16] != prof["sweep_source"]:
-            return None
+    if _sweep_source_hash() != prof["sweep_source"]:
+        return None
     # the capture is a fully active sweep; the loop's average launch moves
     # fewer bytes, and DRAM traffic scales with the bytes a launch must move
     return prof["dram_bytes"] / prof["alg_bytes"] * alg_bytes_per_launch

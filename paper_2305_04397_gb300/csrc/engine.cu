@@ -396,6 +396,8 @@ int prepare_phase(morap_ctx *c, int kind, int Kp, bool &tune) {
     CKL(sweep_setup_attributes());
     const int forced = kind == kSweepF32 ? c->cfg.sweep_variant_fp32 : c->cfg.sweep_variant_fp64;
     const bool worth = (double)c->TT * (double)Kp >= (double)(1u << 24);
+    if (forced >= sweep_variant_count(kind))
+        return fail(MORAP_EINVAL, "config: sweep_variant_fp64 is not a shape of this polish form");
     if (forced >= 0) return build_phase_graph(c, G, kind, Kp, forced);
     if (!worth) return build_phase_graph(c, G, kind, Kp, 0);
     tune = true;
@@ -1261,7 +1263,8 @@ int morap_ctx_create(const morap_config *cfg, morap_ctx **out) {
     if (c.launch_mode != 0 && c.launch_mode != 1) return fail(MORAP_EINVAL, "config: unknown launch mode");
     if ((c.alloc == nullptr) != (c.free == nullptr)) return fail(MORAP_EINVAL, "config: alloc and free go together");
     if (c.sweep_variant_fp32 < -1 || c.sweep_variant_fp32 >= sweep_variant_count(kSweepF32) ||
-        c.sweep_variant_fp64 < -1 || c.sweep_variant_fp64 >= sweep_variant_count(kSweepDF))
+        c.sweep_variant_fp64 < -1 ||
+        c.sweep_variant_fp64 >= std::max(sweep_variant_count(kSweepDF), sweep_variant_count(kSweepDelta)))
         return fail(MORAP_EINVAL, "config: sweep_variant_* must be -1 (tuned) or a shape index");
     if (c.polish != 0 && c.polish != 1) return fail(MORAP_EINVAL, "config: polish must be 0 or 1");
     if (c.eval_block != 0 && c.eval_block != 1) return fail(MORAP_EINVAL, "config: eval_block must be 0 or 1");
