@@ -340,6 +340,17 @@ typedef struct morap_point_result {
 int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, int32_t max_iter, void *stream,
                 morap_point_result *res);
 
+/* Algorithm 1 in the verification-only setting (Sec. 5, Experiment 2): the
+ * outer-bound projection is replaced by a stop, so the loop ends with
+ * feasible = 0 at the first supporting point with w.r < w.t (t is separated
+ * from the achievable set by that hyperplane), or with feasible = 1 once
+ * ||t - t_up|| <= eps.  It runs the same directions and points as
+ * morap_query up to that point (t_down stays t), so the verdict is
+ * morap_query's and it never needs more iterations.  converged = 1 when
+ * the verdict is final.  Same arguments and errors as morap_query. */
+int morap_verify(morap_ctx *ctx, const double *t, const double *M, double eps, int32_t max_iter, void *stream,
+                 morap_point_result *res);
+
 /* Algorithm 1 with the supporting points supplied by the caller, one at a
  * time: for drivers that compute them elsewhere (products sharded over
  * several devices or processes, another solver).  morap_query is this loop
@@ -359,6 +370,13 @@ int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, in
 typedef struct morap_pareto morap_pareto;
 int morap_pareto_create(int32_t n, const double *t, const double *M, double eps, int32_t max_iter,
                         morap_pareto **out);
+/* As morap_pareto_create with a mode: MORAP_PARETO_SYNTHESIS (Algorithm 1,
+ * what morap_pareto_create makes) or MORAP_PARETO_VERIFY (the
+ * verification-only loop of morap_verify).  Errors: EINVAL. */
+#define MORAP_PARETO_SYNTHESIS 0
+#define MORAP_PARETO_VERIFY 1
+int morap_pareto_create_mode(int32_t n, const double *t, const double *M, double eps, int32_t max_iter,
+                             int32_t mode, morap_pareto **out);
 int morap_pareto_next(const morap_pareto *ps, double *w_out, int32_t *done);
 int morap_pareto_step(morap_pareto *ps, const double *r, int32_t solve_status);
 int morap_pareto_result(const morap_pareto *ps, morap_point_result *res);

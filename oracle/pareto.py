@@ -73,9 +73,13 @@ def project_down_hull(t, Phi, M):
     return np.minimum(x, t)
 
 
-def alg1(supporting_point, t, M=None, eps=1e-6, max_iter=64):
+def alg1(supporting_point, t, M=None, eps=1e-6, max_iter=64, verify_only=False):
     """Algorithm 1.  supporting_point(w) -> r.  Returns a dict with the
-    verdict (t_dn == t, Cor. (ii)), t_up, t_dn and the (w, r) history."""
+    verdict (t_dn == t, Cor. (ii)), t_up, t_dn and the (w, r) history.
+
+    verify_only: the verification-only setting of Sec. 5 (Experiment 2),
+    where the outer-bound update is replaced by a break: the loop stops, with
+    the verdict "not achievable", at the first point with w.r < w.t_dn."""
     t = np.asarray(t, np.float64)
     n = len(t)
     M = np.eye(n) if M is None else np.asarray(M, np.float64)
@@ -93,6 +97,11 @@ def alg1(supporting_point, t, M=None, eps=1e-6, max_iter=64):
         Phi.append(r)
         Lam.append((w.copy(), r))
         if w @ r < w @ t_dn:
+            if verify_only:
+                hist.append({"w": w.copy(), "r": r, "t_up": t_up, "t_dn": t_dn.copy()})
+                t_up = t_up if t_up is not None else np.full(n, -np.inf)
+                return {"feasible": False, "t_up": t_up, "t_dn": t_dn, "iterations": it, "history": hist,
+                        "converged": True, "decided": True}
             A = np.array([wl for wl, _ in Lam])
             b = np.array([wl @ rl for wl, rl in Lam])
             t_dn = project_halfspaces(t, A, b, M)

@@ -1448,9 +1448,9 @@ int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out) {
     return MORAP_OK;
 }
 
-int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, int32_t max_iter, void *stream,
-                morap_point_result *res) {
-    API_BEGIN
+namespace {
+int run_query(morap_ctx *ctx, const double *t, const double *M, double eps, int32_t max_iter, void *stream,
+              morap_point_result *res, bool verify_only) {
     if (!ctx || !t || !res) return fail(MORAP_EINVAL, "null argument");
     if (!ctx->built) return fail(MORAP_ESTATE, "query before build");
     if (!(eps >= 0) || max_iter < 1) return fail(MORAP_EINVAL, "eps >= 0 and max_iter >= 1 required");
@@ -1458,7 +1458,7 @@ int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, in
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(t[i])) return fail(MORAP_EINVAL, "threshold entries must be finite");
     Alg1 q;
-    q.init(n, t, M, eps, max_iter);
+    q.init(n, t, M, eps, max_iter, verify_only);
     std::vector<double> r(n);
     std::vector<int32_t> f(ctx->nJ);
     while (!q.done) {
@@ -1472,6 +1472,20 @@ int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, in
     const int status = alg1_result(q, res);
     if (status != MORAP_OK) return fail(status, "query stopped before ||t_down - t_up|| <= eps");
     return MORAP_OK;
+}
+}  // namespace
+
+int morap_query(morap_ctx *ctx, const double *t, const double *M, double eps, int32_t max_iter, void *stream,
+                morap_point_result *res) {
+    API_BEGIN
+    return run_query(ctx, t, M, eps, max_iter, stream, res, false);
+    API_END
+}
+
+int morap_verify(morap_ctx *ctx, const double *t, const double *M, double eps, int32_t max_iter, void *stream,
+                 morap_point_result *res) {
+    API_BEGIN
+    return run_query(ctx, t, M, eps, max_iter, stream, res, true);
     API_END
 }
 
@@ -1479,18 +1493,25 @@ struct morap_pareto {
     Alg1 q;
 };
 
-int morap_pareto_create(int32_t n, const double *t, const double *M, double eps, int32_t max_iter,
-                        morap_pareto **out) {
+int morap_pareto_create_mode(int32_t n, const double *t, const double *M, double eps, int32_t max_iter,
+                             int32_t mode, morap_pareto **out) {
     API_BEGIN
+    if (mode != MORAP_PARETO_SYNTHESIS && mode != MORAP_PARETO_VERIFY)
+        return fail(MORAP_EINVAL, "pareto_create: unknown mode");
     if (!t || !out || n < 1) return fail(MORAP_EINVAL, "pareto_create: n >= 1, t and out required");
     if (!(eps >= 0) || max_iter < 1) return fail(MORAP_EINVAL, "eps >= 0 and max_iter >= 1 required");
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(t[i])) return fail(MORAP_EINVAL, "threshold entries must be finite");
     auto *ps = new morap_pareto();
-    ps->q.init(n, t, M, eps, max_iter);
+    ps->q.init(n, t, M, eps, max_iter, mode == MORAP_PARETO_VERIFY);
     *out = ps;
     return MORAP_OK;
     API_END
+}
+
+int morap_pareto_create(int32_t n, const double *t, const double *M, double eps, int32_t max_iter,
+                        morap_pareto **out) {
+    return morap_pareto_create_mode(n, t, M, eps, max_iter, MORAP_PARETO_SYNTHESIS, out);
 }
 
 int morap_pareto_next(const morap_pareto *ps, double *w_out, int32_t *done) {

@@ -464,7 +464,10 @@ double mnorm(int n, const double *v, const double *M) {
     return std::sqrt(std::max(acc, 0.0));
 }
 
-void Alg1::init(int n_obj, const double *t_in, const double *M_in, double eps_in, int max_iter_in) {
+void Alg1::init(int n_obj, const double *t_in, const double *M_in, double eps_in, int max_iter_in,
+                bool verify_only_in) {
+    verify_only = verify_only_in;
+    decided = false;
     n = n_obj;
     t.assign(t_in, t_in + n);
     if (M_in)
@@ -514,8 +517,15 @@ void Alg1::step(const double *r, const int32_t *assign, int n_tasks) {
     }
     b.push_back(wr);
     if (wr < wt) {
-        project_halfspaces(n, (int)b.size(), t.data(), A.data(), b.data(), Mp, t_dn.data());
         moved = true;
+        if (verify_only) {
+            // the paper's verification-only loop breaks here, before the
+            // outer bound is projected: t is separated from the achievable set
+            decided = true;
+            done = true;
+            return;
+        }
+        project_halfspaces(n, (int)b.size(), t.data(), A.data(), b.data(), Mp, t_dn.data());
     }
     lambda.assign(it, 0.0);
     project_down_hull(n, it, t.data(), Phi.data(), Mp, t_up.data(), lambda.data());
@@ -542,7 +552,7 @@ void Alg1::step(const double *r, const int32_t *assign, int n_tasks) {
 
 int alg1_result(const Alg1 &q, morap_point_result *res) {
     int status = q.status;
-    const bool converged = q.dist <= q.eps;
+    const bool converged = q.dist <= q.eps || q.decided;
     if (!converged && status == MORAP_OK) status = MORAP_ENOTCONV;
     res->feasible = q.moved ? 0 : 1;
     res->iterations = q.it;

@@ -75,11 +75,15 @@ struct Alg1 {
     int n = 0, it = 0, max_iter = 64, status = 0;
     double eps = 1e-6, dist = HUGE_VAL;
     bool moved = false, done = false;
+    // verification only (Sec. 5, Exp. 2): the first supporting hyperplane
+    // that separates t ends the loop with the verdict "not achievable"
+    bool verify_only = false, decided = false;
     std::vector<double> t, M, w, t_dn, t_up, Phi, A, b, w_hist, r_hist;
     std::vector<double> lambda;  // convex weights of the points behind t_up (last projection)
     std::vector<int32_t> f_hist;  // assignment of each point, [it][f_tasks], when the caller gives it
     int f_tasks = 0;
-    void init(int n_obj, const double *t_in, const double *M_in, double eps_in, int max_iter_in);
+    void init(int n_obj, const double *t_in, const double *M_in, double eps_in, int max_iter_in,
+              bool verify_only_in = false);
     void step(const double *r, const int32_t *assign = nullptr, int n_tasks = 0);
 };
 // Fill *res from a finished run; returns its status (ENOTCONV when it

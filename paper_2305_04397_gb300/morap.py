@@ -126,11 +126,14 @@ _SIGS = {
     "morap_last_solve_stats": (ctypes.c_int, [_P, ctypes.POINTER(SolveStats)]),
     "morap_solve_plain": (ctypes.c_int, [_P, ctypes.c_int32, _I32P, _DP, _P, _DP, _DP, _DP, _DP]),
     "morap_query": (ctypes.c_int, [_P, _DP, _DP, ctypes.c_double, ctypes.c_int32, _P, ctypes.POINTER(PointResult)]),
+    "morap_verify": (ctypes.c_int, [_P, _DP, _DP, ctypes.c_double, ctypes.c_int32, _P, ctypes.POINTER(PointResult)]),
     "morap_assign_max": (ctypes.c_int, [ctypes.c_int32, _DP, _I32P]),
     "morap_assign_tasks": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _DP, _I32P]),
     "morap_evaluate": (ctypes.c_int, [_P, ctypes.c_int32, _I32P, _I32P, _P, _DP, _DP]),
     "morap_pareto_create": (ctypes.c_int, [ctypes.c_int32, _DP, _DP, ctypes.c_double, ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_void_p)]),
+    "morap_pareto_create_mode": (ctypes.c_int, [ctypes.c_int32, _DP, _DP, ctypes.c_double, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "morap_pareto_next": (ctypes.c_int, [_P, _DP, _I32P]),
     "morap_pareto_step": (ctypes.c_int, [_P, _DP, ctypes.c_int32]),
     "morap_pareto_result": (ctypes.c_int, [_P, ctypes.POINTER(PointResult)]),
@@ -295,7 +298,9 @@ def morap_solve_plain(ctx, pair_product, pair_w, stream=None, evaluate=True):
             "updates": stats[2], "ms": stats[3], "code": code}
 
 
-def morap_query(ctx, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True, n_tasks=None):
+def morap_query(ctx, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True, n_tasks=None, verify_only=False):
+    """Algorithm 1 (morap_query), or with verify_only=True the
+    verification-only loop (morap_verify): a yes/no answer for t."""
     t = _arr(t, np.float64)
     n = len(t)
     Mm = _arr(M, np.float64) if M is not None else None
@@ -313,8 +318,9 @@ def morap_query(ctx, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True, 
     fh = np.zeros((max_iter, max(n_tasks, 1)), np.int32)
     res.lambda_ = _ptr(lam, ctypes.c_double)
     res.assign_hist = _ptr(fh, ctypes.c_int32) if n_tasks else None
-    code = lib().morap_query(ctx, _ptr(t, ctypes.c_double), _ptr(Mm, ctypes.c_double), float(eps), int(max_iter),
-                             _stream(stream), ctypes.byref(res))
+    fn = lib().morap_verify if verify_only else lib().morap_query
+    code = fn(ctx, _ptr(t, ctypes.c_double), _ptr(Mm, ctypes.c_double), float(eps), int(max_iter), _stream(stream),
+              ctypes.byref(res))
     if check and code not in (OK, ENOTCONV):
         _check(code)
     it = res.iterations
@@ -342,14 +348,15 @@ def random_assignment(lam, assign_hist, n_agents):
 class Pareto:
     """Algorithm 1 fed one supporting point at a time (morap_pareto_*)."""
 
-    def __init__(self, t, M=None, eps=1e-6, max_iter=64):
+    def __init__(self, t, M=None, eps=1e-6, max_iter=64, verify_only=False):
         self.t = _arr(t, np.float64)
         self.n = len(self.t)
         self.max_iter = int(max_iter)
         Mm = _arr(M, np.float64) if M is not None else None
         h = ctypes.c_void_p()
-        _check(lib().morap_pareto_create(self.n, _ptr(self.t, ctypes.c_double), _ptr(Mm, ctypes.c_double),
-                                         float(eps), self.max_iter, ctypes.byref(h)))
+        _check(lib().morap_pareto_create_mode(self.n, _ptr(self.t, ctypes.c_double), _ptr(Mm, ctypes.c_double),
+                                              float(eps), self.max_iter, 1 if verify_only else 0,
+                                              ctypes.byref(h)))
         self.h = h
 
     def next(self):
@@ -625,6 +632,10 @@ class Context:
         (convex weights of the points) and `assign_hist` (each point's task
         assignment); `random_assignment(...)` turns them into P[i][j]."""
         return morap_query(self.h, t, M, eps, max_iter, stream, check, n_tasks=self.n_tasks)
+
+    def verify(self, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True):
+        """The verification-only loop (Sec. 5, Exp. 2): is t achievable?"""
+        return morap_query(self.h, t, M, eps, max_iter, stream, check, n_tasks=self.n_tasks, verify_only=True)
 
     def stats(self):
         return morap_last_solve_stats(self.h)

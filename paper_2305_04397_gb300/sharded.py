@@ -180,15 +180,18 @@ class ShardedSupportingPoints:
         code = M.ENOTCONV if tot[0, -1] > 0 else M.OK
         return {"r": tot[:, :-1], "assign": assign, "c": C, "code": code}
 
-    def query(self, t, Mnorm=None, eps=1e-6, max_iter=64) -> dict:
-        """Algorithm 1 for threshold t with these supporting points; every rank
-        runs the same loop on the same numbers."""
-        return run_alg1(lambda w: self(w[None, :]), t, Mnorm, eps, max_iter)
+    def query(self, t, Mnorm=None, eps=1e-6, max_iter=64, verify_only=False) -> dict:
+        """Algorithm 1 for threshold t with these supporting points (or its
+        verification-only form); every rank runs the same loop on the same
+        numbers."""
+        return run_alg1(lambda w: self(w[None, :]), t, Mnorm, eps, max_iter, verify_only)
 
 
-def run_alg1(supporting_point: Callable[[np.ndarray], dict], t, Mnorm=None, eps=1e-6, max_iter=64) -> dict:
-    """Algorithm 1 through morap_pareto_*, with supporting_point(w) -> {"r": [1][n], "code"}."""
-    P = M.Pareto(t, Mnorm, eps, max_iter)
+def run_alg1(supporting_point: Callable[[np.ndarray], dict], t, Mnorm=None, eps=1e-6, max_iter=64,
+             verify_only=False) -> dict:
+    """Algorithm 1 (or its verification-only form) through morap_pareto_*,
+    with supporting_point(w) -> {"r": [1][n], "code"}."""
+    P = M.Pareto(t, Mnorm, eps, max_iter, verify_only)
     try:
         while True:
             w = P.next()

@@ -149,3 +149,36 @@ def test_pareto_stepper_synthesis_on_a_known_set(M):
         assert np.all(lam @ res["r_hist"] >= res["t_up"] - 1e-9)
         if feasible:
             assert np.all(lam @ res["r_hist"] >= np.array(t) - 1e-9)
+
+
+def test_pareto_stepper_verification_only(M):
+    """The verification-only stepper on the same known set: the verdicts of
+    the full loop, never more points, and its points a prefix of the full
+    loop's; the oracle's verification-only loop gives the same run."""
+    from oracle import pareto as OP
+
+    pts = np.array([[-1.0, 0.2], [-2.0, 0.6], [-4.0, 0.9], [-3.0, 0.5]])
+
+    def support(w):
+        return pts[int(np.argmax(pts @ w))]
+
+    def run(t, verify_only):
+        P = M.Pareto(t, eps=1e-9, max_iter=30, verify_only=verify_only)
+        while True:
+            w = P.next()
+            if w is None:
+                break
+            P.step(support(w))
+        res = P.result()
+        P.close()
+        return res
+
+    for t, feasible in (([-2.5, 0.6], True), ([-3.0, 0.7], True), ([-2.5, 0.7], False), ([-3.5, 0.95], False)):
+        full, ver = run(t, False), run(t, True)
+        assert ver["feasible"] == full["feasible"] == feasible and ver["converged"]
+        assert ver["iterations"] <= full["iterations"]
+        assert np.array_equal(ver["r_hist"], full["r_hist"][: ver["iterations"]])
+        ref = OP.alg1(support, np.array(t), eps=1e-9, max_iter=30, verify_only=True)
+        assert ref["feasible"] == feasible and ref["iterations"] == ver["iterations"]
+        if not feasible:
+            assert np.array_equal(ver["t_down"], np.array(t))  # the outer bound is never projected

@@ -257,6 +257,23 @@ def test_query_matches_oracle_alg1(M, tiny, tiny_prods):
     ctx.close()
 
 
+def test_verify_matches_query_and_oracle(M, tiny, tiny_prods):
+    """The verification-only loop (Sec. 5, Exp. 2) through the C-ABI: the
+    verdict of morap_query and of the oracle's verification-only loop, in no
+    more iterations, with the same directions as the full loop up to its
+    stop."""
+    ctx = make_ctx(M, tiny)
+    for t in [tiny.thresholds[0], np.array([-12.0, -12.0, 0.6, 0.6, 0.6]), np.array([-1.0, -1.0, 0.2, 0.2, 0.2])]:
+        full = ctx.query(t, eps=1e-6, max_iter=40)
+        ver = ctx.verify(t, eps=1e-6, max_iter=40)
+        supp = lambda w: O.supporting_point(tiny_prods, w)[0]
+        want = OP.alg1(supp, t, eps=1e-6, max_iter=40, verify_only=True)
+        assert ver["feasible"] == full["feasible"] == want["feasible"] and ver["converged"]
+        assert ver["iterations"] <= full["iterations"] and ver["iterations"] == want["iterations"]
+        assert np.array_equal(ver["w_hist"], full["w_hist"][: ver["iterations"]])
+    ctx.close()
+
+
 def test_query_fig2(M):
     ctx = make_ctx(M, ([I.fig2_agent()], [I.fig2_task()]))
     prods = [[O.Product(I.fig2_agent(), I.fig2_task())]]

@@ -209,3 +209,39 @@ def test_alg1_theorem3_on_enumerable_instances(seed):
         assert np.linalg.norm(res["t_dn"] - x_true) < 1e-5
         feasible_true = dist < 1e-9
         assert res["feasible"] == feasible_true
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_alg1_verification_only_matches_full_loop(seed):
+    """The verification-only loop (Sec. 5, Exp. 2: the outer-bound update
+    replaced by a break) follows the full loop's directions and points until
+    the first separating hyperplane, so its verdict is the full loop's and
+    the true one (t inside the achievable set, by enumeration), and its run
+    is a prefix of the full run."""
+    prods = _tiny_instance(seed)
+    pts = _achievable_points(prods)
+    rng = np.random.default_rng(100 + seed)
+    supp = lambda w: C.supporting_point(prods, w, eps1=1e-12)[0]
+    for _ in range(4):
+        t = pts.max(axis=0) + rng.uniform(-0.6, 0.3, size=4)
+        full = P.alg1(supp, t, eps=1e-7)
+        ver = P.alg1(supp, t, eps=1e-7, verify_only=True)
+        truth = np.linalg.norm(t - P.project_down_hull(t, pts, np.eye(4))) < 1e-9
+        assert ver["feasible"] == full["feasible"] == truth
+        assert ver["iterations"] <= full["iterations"]
+        for hv, hf in zip(ver["history"], full["history"]):
+            assert np.array_equal(hv["w"], hf["w"]) and np.array_equal(hv["r"], hf["r"])
+        if not truth:
+            h = ver["history"][-1]
+            assert h["w"] @ h["r"] < h["w"] @ t  # the separating hyperplane
+            assert np.all(pts @ h["w"] <= h["w"] @ h["r"] + 1e-8)
+
+
+def test_alg1_verification_only_fig2():
+    prods = [[C.Product(I.fig2_agent(), I.fig2_task())]]
+    supp = lambda w: C.supporting_point(prods, w, eps1=1e-12)[0]
+    # t_u of Fig. 2 is not achievable: the second direction separates it
+    res = P.alg1(supp, np.array([-1.8, 0.9]), eps=1e-7, verify_only=True)
+    assert not res["feasible"] and res["iterations"] == 2
+    res = P.alg1(supp, np.array([-3.0, 0.5]), eps=1e-7, verify_only=True)
+    assert res["feasible"]

@@ -70,9 +70,10 @@ def _rank_main(rank, world, port, out_dir):
         sp = S.ShardedSupportingPoints(shard, parts, nI, nJ, S.TorchComm())
         out = sp(inst.weights[:3])
         q = sp.query(inst.thresholds[0], eps=1e-6, max_iter=12)
+        v = sp.query(inst.thresholds[0], eps=1e-6, max_iter=12, verify_only=True)
         np.savez(os.path.join(out_dir, f"rank{rank}.npz"), r=out["r"], assign=out["assign"], c=out["c"],
                  t_up=q["t_up"], t_down=q["t_down"], it=q["iterations"], feasible=q["feasible"],
-                 w_hist=q["w_hist"])
+                 w_hist=q["w_hist"], v_feasible=v["feasible"], v_it=v["iterations"])
     finally:
         dist.destroy_process_group()
 
@@ -121,6 +122,9 @@ def test_sharded_world2_gloo_matches_unsharded_oracle(oracle_lib):
         assert np.array_equal(res[0]["assign"][k], np.where(f < len(inst.agents), f, -1))
         assert np.max(np.abs(res[0]["r"][k] - r)) < 1e-12
     ref = OP.alg1(lambda w: O.supporting_point(prods, w)[0], inst.thresholds[0], eps=1e-6, max_iter=12)
+    ver = OP.alg1(lambda w: O.supporting_point(prods, w)[0], inst.thresholds[0], eps=1e-6, max_iter=12,
+                  verify_only=True)
+    assert bool(res[0]["v_feasible"]) == ver["feasible"] and int(res[0]["v_it"]) == ver["iterations"]
     assert int(res[0]["it"]) == ref["iterations"]
     assert bool(res[0]["feasible"]) == ref["feasible"]
     assert np.max(np.abs(res[0]["t_up"] - ref["t_up"])) < 1e-6
