@@ -14,6 +14,10 @@ Contents, each following the passage cited in its docstring:
              brute force over simple schedulers, Algorithm 2 with the
              assignment step (scipy's linear_sum_assignment)
   pareto.py  Algorithm 1 and its two projections (scipy SLSQP)
+  lp.py      the MORAP problem as one linear program (occupation measures,
+             Lemma 2 for the random assignment) and a hand-written dense
+             simplex: a second decision of "is t achievable?" for tiny
+             instances
 
 Every function is pinned by tests/test_oracle_*.py against closed forms,
 brute force, exact linear solves, invariants of Sec. 3 (Lemmas 6-7, Thm 3)

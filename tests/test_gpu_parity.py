@@ -274,6 +274,29 @@ def test_verify_matches_query_and_oracle(M, tiny, tiny_prods):
     ctx.close()
 
 
+def test_query_verdicts_match_the_lp_oracle(M, tiny, tiny_prods):
+    """The engine's Algorithm 1 verdicts (full and verification-only)
+    against the LP formulation of MORAP solved by the oracle's simplex,
+    which shares nothing with value iteration or Algorithm 1."""
+    from oracle import lp as L
+
+    ctx = make_ctx(M, tiny)
+    rng = np.random.default_rng(17)
+    ts = [np.array([-12.0, -12.0, 0.6, 0.6, 0.6]), np.array([-1.0, -1.0, 0.2, 0.2, 0.2])]
+    ts += [np.concatenate([-rng.uniform(2, 14, 2), rng.uniform(0.1, 0.95, 3)]) for _ in range(4)]
+    seen = set()
+    for t in ts:
+        full = ctx.query(t, eps=1e-7, max_iter=60)
+        if not full["feasible"] and np.linalg.norm(full["t_down"] - t) < 1e-4:
+            continue  # too close to the boundary to call
+        ok, _ = L.morap_feasible(tiny_prods, t)
+        assert full["feasible"] == ok, t
+        assert ctx.verify(t, eps=1e-7, max_iter=60)["feasible"] == ok, t
+        seen.add(ok)
+    assert seen == {True, False}
+    ctx.close()
+
+
 def test_query_fig2(M):
     ctx = make_ctx(M, ([I.fig2_agent()], [I.fig2_task()]))
     prods = [[O.Product(I.fig2_agent(), I.fig2_task())]]
