@@ -101,7 +101,14 @@ typedef struct morap_config {
                                    one block's shared memory (n + 1 <= 7168 states) with one block
                                    running all its sweeps in one launch; larger pairs, or all pairs
                                    with 0, run the multi-launch sweep loop.  Same results.         */
-    int32_t reserved;
+    int32_t in_place;           /* 0 (default): Algorithm 3's sweeps are synchronous (Jacobi: each
+                                   sweep reads the previous sweep's values only), so results do not
+                                   depend on scheduling, kernel shape or batch; 1: values are
+                                   updated in place, as the paper's printed loop does (a sweep may
+                                   read values already updated in the same sweep, in an order set
+                                   by the GPU's scheduling).  Same fixed point and stopping rule;
+                                   usually fewer sweeps; results reproducible only to the
+                                   tolerance.  Algorithm 4 stays synchronous.                       */
 } morap_config;
 
 typedef struct morap_ctx morap_ctx;

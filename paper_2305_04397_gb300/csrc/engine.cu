@@ -495,6 +495,11 @@ int ensure_solve(morap_ctx *c, int Kp) {
     ad.V[1] = c->Vd[1];
     ad.G = c->G;
     c->argsd = ad;
+    if (c->cfg.in_place) {  // one value array per phase: a sweep reads what it has already written
+        c->args32.V[1] = c->args32.V[0];
+        c->args64.V[1] = c->args64.V[0];
+        c->argsd.V[1] = c->argsd.V[0];
+    }
     return MORAP_OK;
 }
 
@@ -1243,6 +1248,7 @@ void morap_config_default(morap_config *cfg) {
     cfg->skip_unchanged = 1;
     cfg->polish = 0;
     cfg->eval_block = 1;
+    cfg->in_place = 0;
 }
 
 const char *morap_last_error(void) { return g_last_error.c_str(); }
@@ -1268,6 +1274,7 @@ int morap_ctx_create(const morap_config *cfg, morap_ctx **out) {
         return fail(MORAP_EINVAL, "config: sweep_variant_* must be -1 (tuned) or a shape index");
     if (c.polish != 0 && c.polish != 1) return fail(MORAP_EINVAL, "config: polish must be 0 or 1");
     if (c.eval_block != 0 && c.eval_block != 1) return fail(MORAP_EINVAL, "config: eval_block must be 0 or 1");
+    if (c.in_place != 0 && c.in_place != 1) return fail(MORAP_EINVAL, "config: in_place must be 0 or 1");
     CK(cudaSetDevice(c.device));
     morap_ctx *ctx = new morap_ctx();
     ctx->cfg = c;

@@ -51,7 +51,7 @@ class Config(ctypes.Structure):
         ("skip_unchanged", ctypes.c_int32),
         ("polish", ctypes.c_int32),
         ("eval_block", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("in_place", ctypes.c_int32),
     ]
 
 

@@ -50,7 +50,7 @@ def test_config_default(M):
     cfg = M.morap_config_default()
     assert cfg.eps_vi == 1e-8 and cfg.eps_eval == 1e-11 and cfg.tau_policy == 1e-9
     assert cfg.precision == M.PREC_MIXED and cfg.max_sweeps == 100000
-    assert cfg.polish == 0 and cfg.skip_unchanged == 1 and cfg.eval_block == 1
+    assert cfg.polish == 0 and cfg.skip_unchanged == 1 and cfg.eval_block == 1 and cfg.in_place == 0
     assert cfg.sweep_variant_fp32 == -1 and cfg.sweep_variant_fp64 == -1
 
 

@@ -506,6 +506,36 @@ def test_block_evaluation_any_row_length(M, n_succ):
         assert out[1]["r_prob"][k, i, j] == pytest.approx(r["r_prob"], abs=TOL)
 
 
+def test_in_place_sweeps(M, grid32):
+    """Algorithm 3 with values updated in place (the paper's printed loop)
+    reaches the same fixed point as the synchronous sweeps, within the
+    stopping error, in no more sweeps.  The recorded actions follow another
+    trajectory, so where near-ties exist the returned scheduler may be
+    another optimal one: its points agree in the scalarised value w.r = c,
+    and the values match the oracle."""
+    pair = (grid32.agents[:3], grid32.tasks[:6])
+    W = np.ascontiguousarray(grid32.weights[:8][:, [0, 1, 2, 10, 11, 12, 13, 14, 15]])
+    out, st = {}, {}
+    for ip in (0, 1):
+        ctx = make_ctx(M, pair, in_place=ip)
+        out[ip] = ctx.solve(W, evaluate=True)
+        st[ip] = ctx.stats()
+        ctx.close()
+    assert out[1]["code"] == M.OK
+    # both stop at the same residual rule, each within its stopping error of
+    # the fixed point
+    assert np.max(np.abs(out[1]["c"] - out[0]["c"])) < TOL
+    wc = W[:, :3][:, :, None]
+    wp = W[:, 3:][:, None, :]
+    for ip in (0, 1):
+        assert np.max(np.abs(wc * out[ip]["r_cost"] + wp * out[ip]["r_prob"] - out[ip]["c"])) < TOL
+    assert st[1]["fp32_sweeps"] + st[1]["fp64_sweeps"] <= st[0]["fp32_sweeps"] + st[0]["fp64_sweeps"]
+    for i, j, k in [(0, 1, 2), (2, 5, 6)]:
+        # the oracle converged far tighter than the rule, as the reference point
+        r = O.solve_pair(O.Product(pair[0][i], pair[1][j]), W[k][i], W[k][3 + j], eps1=1e-12)
+        assert out[1]["c"][k, i, j] == pytest.approx(r["c"], abs=TOL)
+
+
 def test_batch_invariance(M, grid32):
     """Each pair runs exactly its own sweeps: a weight alone and inside the
     K = 16 batch gives bitwise-identical c and points."""
@@ -575,7 +605,7 @@ def test_invalid_inputs(M, tiny):
     assert e.value.code == M.EINVAL
     ctx.close()
     for field, val in (("sweep_variant_fp32", 4), ("sweep_variant_fp64", -2), ("launch_mode", 2), ("polish", 2),
-                       ("eval_block", 3)):
+                       ("eval_block", 3), ("in_place", 2)):
         cfg = M.morap_config_default()
         setattr(cfg, field, val)
         with pytest.raises(M.MorapError) as e:
