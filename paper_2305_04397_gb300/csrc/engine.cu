@@ -475,6 +475,9 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a.in_items = c->in_items;
     a.item_w = c->item_w;
     a.skip = c->cfg.skip_unchanged ? 1 : 0;
+    // instances with many more work items than resident warps keep their
+    // lists in order (their values do not fit in L2; see k_sweep)
+    a.keep_batch = c->h_chunks.size() >= (size_t)16 * 16 * std::max(1, c->sm_count) ? 1 : 4;
     for (int q = 0; q < 3; ++q) a.chg[q] = c->chg[q];
     a.eps1 = c->cfg.eps_vi;
     a.eps1f = (float)c->cfg.eps_vi;

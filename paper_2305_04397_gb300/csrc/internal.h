@@ -183,6 +183,7 @@ struct SweepArgs {
     const uint2 *item_w;  // (transitions, state-action rows) of each item, for the statistics
     uint8_t *chg[3];
     int skip;  // 0: recompute every item (skipping disabled)
+    int keep_batch;  // kept items appended per atomic (1 keeps the list's order; 1..32)
     const float *G;  // residual-correction polish: [state-action][Kp] table (see ArithDelta)
     double eps1;
     float eps1f;  // eps1 rounded to FP32 (record tests in the kernels)

@@ -650,7 +650,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
 
     // The shared counters see few atomics: the statistics are summed per warp
     // and per block, and items that stay in the work list are collected per
-    // warp (lane i holds the i-th) and appended 32 at a time.
+    // warp (lane i holds the i-th) and appended a.keep_batch at a time.
+    // Large instances append each item at once instead (keep_batch = 1):
+    // then the next list keeps the order of this one (neighbouring items stay
+    // neighbours), which keeps the value gathers of concurrent warps close
+    // together when the values do not fit in L2; batches would interleave
+    // the warps' items from one sweep to the next.
     unsigned long long w_updates = 0, w_bytes = 0;  // lane 0's running sums
     unsigned int w_skipped = 0;
     unsigned int kept = 0u;
@@ -665,6 +670,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     // Warp w of the grid takes list entry w without an atomic; later items
     // are taken one at a time from a shared cursor that starts after those.
     const unsigned int n_warps = gridDim.x * (kThreads / 32);
+    const int keep_batch = a.keep_batch;
     bool first = true;
     for (;;) {
         unsigned int it = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
@@ -710,7 +716,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         const ProdDesc pd = a.prods[p];
         if (any_active) {
             if (lane == n_kept) kept = item;
-            if (++n_kept == 32) flush_kept();
+            if (++n_kept == keep_batch) flush_kept();
         }
         if (ch.w)
             for (int k = lane; k < KP; k += 32) {
