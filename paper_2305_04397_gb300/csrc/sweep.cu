@@ -788,18 +788,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                     nx_tr = __ldg(a.state_tr + u0 + (uint32_t)m + lane);
                 }
                 typename Ar::View vw;
-#ifndef MORAP_PREFETCH_G
-#define MORAP_PREFETCH_G 1
-#endif
-#ifndef MORAP_PREFETCH_V
-#define MORAP_PREFETCH_V 0
-#endif
                 // the batch's rows of G (residual correction) are one
                 // contiguous range: start it towards L2 before staging
-                if constexpr (MORAP_PREFETCH_G && std::is_same<Ar, ArithDelta>::value && KP % 4 == 0)
+                if constexpr (std::is_same<Ar, ArithDelta>::value && KP % 4 == 0)
                     if (lane == 0 && A1 > A0) prefetch_l2(a.G + (size_t)A0 * KP, (A1 - A0) * (uint32_t)(KP * 4));
-                if constexpr (MORAP_PREFETCH_V && (ROW % 4) == 0)
-                    if (lane == 0) prefetch_l2(Vold + (size_t)u0 * ROW, (uint32_t)(m * ROW * 4));
                 if (staged) {
                     Ar::stage(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
                     cp_async_wait_all();
