@@ -26,9 +26,9 @@ By Lemma 2 (Birkhoff) the doubly substochastic matrices mu are exactly the
 marginals of random assignments of the padded square problem, so the system
 describes the achievable set of Def. 1.
 
-t is achievable iff this system has a solution.  Zero-reward end components other than self-loops are not
-modelled (the function checks that there are none); the instances used have
-zero cost only on "stay".
+t is achievable iff this system has a solution.  Zero-reward end
+components other than self-loops are not modelled (the function checks that
+there are none); the instances used have zero cost only on "stay".
 
 The simplex is phase 1 of the textbook tableau method on A x = b, x >= 0,
 b >= 0, with artificial variables: Dantzig's entering rule and the minimum
