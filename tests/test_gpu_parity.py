@@ -506,7 +506,8 @@ def test_block_evaluation_any_row_length(M, n_succ):
         assert out[1]["r_prob"][k, i, j] == pytest.approx(r["r_prob"], abs=TOL)
 
 
-def test_in_place_sweeps(M, grid32):
+@pytest.mark.parametrize("polish", [0, 1])
+def test_in_place_sweeps(M, grid32, polish):
     """Algorithm 3 with values updated in place (the paper's printed loop)
     reaches the same fixed point as the synchronous sweeps, within the
     stopping error, in no more sweeps.  The recorded actions follow another
@@ -517,7 +518,7 @@ def test_in_place_sweeps(M, grid32):
     W = np.ascontiguousarray(grid32.weights[:8][:, [0, 1, 2, 10, 11, 12, 13, 14, 15]])
     out, st = {}, {}
     for ip in (0, 1):
-        ctx = make_ctx(M, pair, in_place=ip)
+        ctx = make_ctx(M, pair, in_place=ip, polish=polish)
         out[ip] = ctx.solve(W, evaluate=True)
         st[ip] = ctx.stats()
         ctx.close()
