@@ -77,14 +77,6 @@ __device__ __forceinline__ DF df_add(DF x, DF y) {
     return fast_two_sum(s.h, s.l);
 }
 
-__device__ __forceinline__ DF df_mul(DF x, DF y) {
-    const float p = __fmul_rn(x.h, y.h);
-    float e = __fmaf_rn(x.h, y.h, -p);
-    e = __fmaf_rn(x.h, y.l, e);
-    e = __fmaf_rn(x.l, y.h, e);
-    return fast_two_sum(p, e);
-}
-
 __device__ __forceinline__ bool df_gt(DF a, DF b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
 
 __device__ __forceinline__ void cp_async4(void *smem, const void *g) {
@@ -164,7 +156,6 @@ struct ArithF32 {
     static __device__ __forceinline__ void close(Val &) {}
     static __device__ __forceinline__ bool gt(Val a, Val b) { return a > b; }
     static __device__ __forceinline__ Val neg_inf() { return -CUDART_INF_F; }
-    static __device__ __forceinline__ Val zero() { return 0.0f; }
     static __device__ __forceinline__ float diff(Val y, Val x) { return fabsf(y - x); }
     static __device__ __forceinline__ Val from_words(const float *w) { return w[0]; }
     static __device__ __forceinline__ void to_words(Val v, float *w) { w[0] = v; }
@@ -258,7 +249,6 @@ struct ArithDF {
     static __device__ __forceinline__ void close(Val &v) { v = df_norm(v); }
     static __device__ __forceinline__ bool gt(Val a, Val b) { return df_gt(a, b); }
     static __device__ __forceinline__ Val neg_inf() { return {-CUDART_INF_F, 0.0f}; }
-    static __device__ __forceinline__ Val zero() { return {0.0f, 0.0f}; }
     static __device__ __forceinline__ float diff(Val y, Val x) {
         return fabsf(__fadd_rn(__fadd_rn(y.h, -x.h), __fadd_rn(y.l, -x.l)));
     }
