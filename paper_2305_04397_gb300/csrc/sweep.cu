@@ -422,11 +422,14 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
     const size_t row = (size_t)u * ROW + (size_t)k0 * Ar::WORDS;
     const uint32_t la0 = ssa[i] - A0, la1 = ssa[i + 1] - A0;
     Val best[VEC];
-    uint32_t best_a[VEC];
+    // the maximising actions; one byte per weight for Kp >= 32, where the
+    // registers it saves avoid spills (smaller Kp run faster unpacked)
+    constexpr int PACK = KP >= 32 ? 4 : 1;
+    uint32_t best_a[(VEC + PACK - 1) / PACK];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
         best[v] = Ar::neg_inf();
-        best_a[v] = 0u;
+        if (v % PACK == 0) best_a[v / PACK] = 0u;
     }
     uint32_t t0 = vw.str[la0] - T0;
     // Actions are the outer loop: every lane closes an action at the same
@@ -462,7 +465,12 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
             Ar::close(acc[v]);
             const bool better = Ar::gt(acc[v], best[v]);
             best[v] = better ? acc[v] : best[v];
-            best_a[v] = better ? la - la0 : best_a[v];
+            if constexpr (PACK == 1) {
+                best_a[v] = better ? la - la0 : best_a[v];
+            } else if (better) {
+                const int sh = 8 * (v % PACK);
+                best_a[v / PACK] = (best_a[v / PACK] & ~(0xFFu << sh)) | ((la - la0) << sh);
+            }
         }
         t0 = t1;
     }
@@ -475,7 +483,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
         if (!((act_bits >> v) & 1u)) continue;
         const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
         rmax[v] = d > rmax[v] ? d : rmax[v];
-        if (d > Ar::record_threshold(best[v], a.eps1f)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
+        if (d > Ar::record_threshold(best[v], a.eps1f)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)(best_a[v / PACK] >> (8 * (v % PACK)));
         float before[Ar::WORDS];
 #pragma unroll
         for (int q = 0; q < Ar::WORDS; ++q) before[q] = yw[v * Ar::WORDS + q];
@@ -510,11 +518,14 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
     const size_t row = (size_t)u * ROW + (size_t)k0 * Ar::WORDS;
     const uint32_t la0 = ssa[i] - A0, la1 = ssa[i + 1] - A0;
     Val best[VEC];
-    uint32_t best_a[VEC];
+    // the maximising actions; one byte per weight for Kp >= 32, where the
+    // registers it saves avoid spills (smaller Kp run faster unpacked)
+    constexpr int PACK = KP >= 32 ? 4 : 1;
+    uint32_t best_a[(VEC + PACK - 1) / PACK];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
         best[v] = Ar::neg_inf();
-        best_a[v] = 0u;
+        if (v % PACK == 0) best_a[v / PACK] = 0u;
     }
     struct Slots {
         int32_t cl[D];
@@ -560,7 +571,12 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
             Ar::close(acc[v]);
             const bool better = Ar::gt(acc[v], best[v]);
             best[v] = better ? acc[v] : best[v];
-            best_a[v] = better ? la - la0 : best_a[v];
+            if constexpr (PACK == 1) {
+                best_a[v] = better ? la - la0 : best_a[v];
+            } else if (better) {
+                const int sh = 8 * (v % PACK);
+                best_a[v / PACK] = (best_a[v / PACK] & ~(0xFFu << sh)) | ((la - la0) << sh);
+            }
         }
     };
     Slots A, B;
@@ -586,7 +602,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         if (!((act_bits >> v) & 1u)) continue;
         const float d = Ar::diff(best[v], Ar::from_words(&yw[v * Ar::WORDS]));
         rmax[v] = d > rmax[v] ? d : rmax[v];
-        if (d > Ar::record_threshold(best[v], a.eps1f)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)best_a[v];
+        if (d > Ar::record_threshold(best[v], a.eps1f)) a.a_rec[(size_t)u * KP + k0 + v] = (uint8_t)(best_a[v / PACK] >> (8 * (v % PACK)));
         float before[Ar::WORDS];
 #pragma unroll
         for (int q = 0; q < Ar::WORDS; ++q) before[q] = yw[v * Ar::WORDS + q];
