@@ -56,9 +56,9 @@ def make_workload(name, rank=0):
 # kernels' source (sweep.cu up to its finalisation section; sha256 prefix) is
 # the one that was profiled and the same shape runs.
 TRAFFIC_PROFILES = {
-    ("grid32-10x20-K16", "fp32"): {"sweep_source": "bf7a6a1738cd12f5", "variant": 0,
+    ("grid32-10x20-K16", "fp32"): {"sweep_source": "496f3d6de3cb2b6f", "variant": 0,
                                    "dram_bytes": 148030976 + 28169728, "alg_bytes": 189.1e6},
-    ("grid32-10x20-K16", "delta"): {"sweep_source": "bf7a6a1738cd12f5", "variant": 0,
+    ("grid32-10x20-K16", "delta"): {"sweep_source": "496f3d6de3cb2b6f", "variant": 0,
                                     "dram_bytes": 357863424 + 42290432, "alg_bytes": 394.1e6},
 }
 SWEEP_SECTION_END = "// -------------------------------------------------------------- finalise"

@@ -6,7 +6,8 @@
 // Data layout (HBM):
 //   values  V[state][Kp]   (Kp = weights padded to a power of two), double
 //                          buffered; a sweep reads V[n % 2] and writes
-//                          V[(n + 1) % 2] (synchronous sweeps, as the oracle)
+//                          V[(n + 1) % 2] (synchronous sweeps, as the oracle;
+//                          with in-place sweeps both are one array)
 //   a_rec   [state][Kp]    uint8 local action recorded by Algorithm 3
 //   CSR     state_sa[state+1] -> sa_tr[sa+1] -> col[t], p[t]
 //
@@ -14,9 +15,9 @@
 // [l*VEC, l*VEC+VEC) and loads them as one vector, so the value row of a
 // successor is one coalesced Kp-wide read and the CSR stream is read once for
 // all Kp weights.  Each warp takes kChunk-state work items of one product
-// from the sweep's work list (dynamic scheduling, one item per atomic); an
-// item's residuals are reduced with warp shuffles and one 64-bit atomicMax
-// per weight.  Items none of whose inputs changed in the previous sweep are
+// from the sweep's work list (its first without an atomic, then one item per
+// atomic); an item's residuals are reduced with warp shuffles and one 64-bit
+// atomicMax per weight.  Items none of whose inputs changed in the previous sweep are
 // skipped exactly (see SweepArgs::in_items).
 //
 // Work lists: L[n % 3] holds the items of sweep n.  An item is re-queued for
