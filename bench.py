@@ -53,23 +53,29 @@ def make_workload(name, rank=0):
 # DRAM traffic of the sweep kernels from the committed ncu captures
 # (profiles/k_sweep_{f32,delta}_<workload>.md): one full sweep of the tuned
 # shape, its DRAM bytes and its algorithmic bytes.  Valid only while the sweep
-# kernels' source (sweep.cu up to its finalisation section; sha256 prefix) is
-# the one that was profiled and the same shape runs.
+# kernels' code (sweep.cu up to its finalisation section, comments removed;
+# sha256 prefix) is the one that was profiled and the same shape runs.
 TRAFFIC_PROFILES = {
-    ("grid32-10x20-K16", "fp32"): {"sweep_source": "496f3d6de3cb2b6f", "variant": 0,
+    ("grid32-10x20-K16", "fp32"): {"sweep_source": "7ab7d883e47baafd", "variant": 0,
                                    "dram_bytes": 148030976 + 28169728, "alg_bytes": 189.1e6},
-    ("grid32-10x20-K16", "delta"): {"sweep_source": "496f3d6de3cb2b6f", "variant": 0,
+    ("grid32-10x20-K16", "delta"): {"sweep_source": "7ab7d883e47baafd", "variant": 0,
                                     "dram_bytes": 357863424 + 42290432, "alg_bytes": 394.1e6},
 }
 SWEEP_SECTION_END = "// -------------------------------------------------------------- finalise"
 
 
 def _sweep_source_hash():
+    """sha256 prefix of the sweep kernels' code (sweep.cu up to its
+    finalisation section) with comments and whitespace removed, so that a
+    comment edit does not invalidate the profiled constants."""
     import hashlib
+    import re
 
     with open(os.path.join(ROOT, "paper_2305_04397_gb300", "csrc", "sweep.cu"), encoding="utf-8") as f:
         text = f.read()
-    return hashlib.sha256(text[: text.index(SWEEP_SECTION_END)].encode()).hexdigest()[:16]
+    code = re.sub(r"//[^\n]*", "", text[: text.index(SWEEP_SECTION_END)])
+    code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
+    return hashlib.sha256("".join(code.split()).encode()).hexdigest()[:16]
 
 
 def _traffic(workload, phase, variant, alg_bytes_per_launch):
