@@ -441,6 +441,8 @@ def run_engine(args):
     cfg.device = local
     cfg.launch_mode = args.launch_mode
     cfg.eps_vi = eps_vi
+    cfg.polish = args.polish
+    cfg.in_place = 1 if args.in_place else 0
     ctx = M.Context(cfg)
     ctx.add(inst.agents, inst.tasks)
     fp = ctx.build(stream)
@@ -538,6 +540,8 @@ def run_engine(args):
         "dtype": "f32+df64", "data": "synthetic",
         "config": {"workload": args.workload, "products": nI * nJ, "K": len(W), "states": fp["n_states"],
                    "transitions": fp["n_trans"], "eps_vi": cfg.eps_vi, "eps_eval": cfg.eps_eval,
+                   "polish": ["fp32 residual correction", "double-float"][cfg.polish],
+                   "sweeps": "in place" if cfg.in_place else "synchronous",
                    "l2": "per-step working set (CSR + FP32/FP64 value buffers) exceeds the 129 MB L2; no flush",
                    "parallelism": f"{ws} independent instance(s), one per GPU"},
         "roofline": roofline,
@@ -595,6 +599,9 @@ def main():
     ap.add_argument("--launch-mode", type=int, default=0,
                     help="0: sweep loops as CUDA graphs with a device-side while node; 1: host-driven bodies "
                          "(same kernels; lets ncu list the kernels inside the loops)")
+    ap.add_argument("--polish", type=int, choices=[0, 1], default=0,
+                    help="second phase: 0 FP32 residual correction (default), 1 double-float sweeps")
+    ap.add_argument("--in-place", action="store_true", help="in-place (Gauss-Seidel order) sweeps")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--plain-pairs", type=int, default=6)
