@@ -1278,6 +1278,8 @@ int morap_ctx_create(const morap_config *cfg, morap_ctx **out) {
     if (c.polish != 0 && c.polish != 1) return fail(MORAP_EINVAL, "config: polish must be 0 or 1");
     if (c.eval_block != 0 && c.eval_block != 1) return fail(MORAP_EINVAL, "config: eval_block must be 0 or 1");
     if (c.in_place != 0 && c.in_place != 1) return fail(MORAP_EINVAL, "config: in_place must be 0 or 1");
+    if (c.skip_unchanged != 0 && c.skip_unchanged != 1)
+        return fail(MORAP_EINVAL, "config: skip_unchanged must be 0 or 1");
     CK(cudaSetDevice(c.device));
     morap_ctx *ctx = new morap_ctx();
     ctx->cfg = c;

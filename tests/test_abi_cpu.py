@@ -54,6 +54,18 @@ def test_config_default(M):
     assert cfg.sweep_variant_fp32 == -1 and cfg.sweep_variant_fp64 == -1
 
 
+@pytest.mark.parametrize("field,val", [("polish", 2), ("in_place", 2), ("eval_block", 3), ("skip_unchanged", 2),
+                                       ("launch_mode", 2), ("sweep_variant_fp32", 9), ("sweep_variant_fp64", -2),
+                                       ("precision", 7), ("max_sweeps", 0)])
+def test_config_validation_needs_no_device(M, field, val):
+    """Invalid configurations are refused (EINVAL) before any CUDA call."""
+    cfg = M.morap_config_default()
+    setattr(cfg, field, val)
+    with pytest.raises(M.MorapError) as e:
+        M.morap_ctx_create(cfg)
+    assert e.value.code == M.EINVAL, field
+
+
 @pytest.mark.parametrize("n", [1, 2, 4, 6, 7])
 def test_assignment_vs_brute_force(M, n):
     rng = np.random.default_rng(10 + n)
