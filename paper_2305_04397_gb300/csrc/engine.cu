@@ -825,7 +825,9 @@ int run_evaluation_group(morap_ctx *c, const std::vector<int4> &pairs_in, cudaSt
     rc.assign(h, h + npair);
     rp.assign(h + npair, h + 2 * npair);
     not_conv = 0;
-    for (size_t e = 0; e < npair; ++e) not_conv += hf[e] == 0;
+    // a pair whose task is done in its initial state has no states to
+    // evaluate (its values are 0): nothing can fail to converge there
+    for (size_t e = 0; e < npair; ++e) not_conv += hf[e] == 0 && c->h_prods[pairs[e].x].n_nd > 0;
     c->stats.eval_sweeps = (int32_t)std::max(n_loop ? hctl->sweep_base : 0u, hctl->block_sweeps);
     c->stats.updates_eval = (int64_t)hctl->updates;
     c->stats.bytes_eval = (int64_t)hctl->bytes;
