@@ -277,16 +277,15 @@ int morap_solve_plain(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_produ
 
 /* Allocation-free plain value iteration for one product and one weight
  * vector (the paper has no counterpart: this is an interface for callers).
- * Some callers may not allocate device memory: code that records a CUDA
- * graph (a cudaMalloc inside a stream capture breaks the capture), hosts
- * that hand every byte of the GPU to their own memory pool and treat any
- * outside cudaMalloc as a leak or a deadlock risk, and real-time loops that
- * forbid allocation after start-up.  This call allocates nothing (no
- * cudaMalloc, cudaFree, pinned host memory or allocating library routine):
- * the caller passes the inputs and outputs, and the scratch it needs (second
- * value buffer, state-action values, recorded actions, residual word) lives
- * in one static device array of about 6.3 MB that every GPU which loads this
- * library holds until the process exits.
+ * Some callers may not allocate device memory: hosts that hand every byte
+ * of the GPU to their own memory pool and treat any outside cudaMalloc as a
+ * leak or a deadlock risk, and real-time loops that forbid allocation after
+ * start-up.  This call allocates nothing (no cudaMalloc, cudaFree, pinned
+ * host memory or allocating library routine): the caller passes the inputs
+ * and outputs, and the scratch it needs (second value buffer, state-action
+ * values, recorded actions, residual and round words) lives in one static
+ * device array of about 6.3 MB that every GPU which loads this library
+ * holds until the process exits.
  *   Limits: n_states <= 131071 (plus the done slot) and n_sa <= 655360;
  *   larger products are rejected with MORAP_EINVAL.
  *   Inputs (device memory, the product's CSR with local indices, e.g. as
@@ -299,13 +298,18 @@ int morap_solve_plain(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_produ
  *   scheduler), *c_out and *sweeps_out (host, either may be NULL).
  *   The computation is morap_solve_plain's: Algorithm 3 in FP64 from 0 with
  *   a host convergence check after every sweep, then the scheduler reading.
- * The call is synchronous on `stream`.  The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call on a
- * device shares the one array and clears what must start at zero; calls
- * that overlap on the GPU (other threads or streams) race on it.
- * Errors: EINVAL (sizes over the limits, bad arguments), ENOTCONV (sweep cap
- * reached; outputs hold the last iterate), ECUDA. */
+ * The call is synchronous: it waits on `stream` after every sweep and reads
+ * the residual on the host, so it cannot run inside a stream capture (a
+ * capturing stream is refused with MORAP_EINVAL before anything is
+ * enqueued).  The stream and every buffer must belong to the current
+ * device (MORAP_EINVAL otherwise), because the scratch used is the current
+ * device's copy of the array.  The first call on each device looks up that
+ * copy's address (cudaGetSymbolAddress) with the device current.  Every
+ * call on a device shares the one array and clears what must start at
+ * zero; calls that overlap on the GPU (other threads or streams) race on it.
+ * Errors: EINVAL (sizes over the limits, bad arguments, wrong device,
+ * capturing stream), ENOTCONV (sweep cap reached; outputs hold the last
+ * iterate), ECUDA. */
 int morap_plain_vi_noalloc(int32_t n_states, int32_t n_sa, const uint32_t *state_sa, const uint32_t *sa_tr,
                            const int32_t *col, const double *prob, const double *cost, int32_t pre_begin,
                            int32_t init_state, double w_cost, double w_prob, double eps, double tau,
@@ -440,6 +444,18 @@ int morap_server_stats(morap_server *server, morap_serving_stats *stats);
 /* ------------------------------------------------ host-side building blocks
  * These run on the CPU only (no device needed) and are what morap_query and
  * morap_supporting_points use. */
+
+/* The synthesised random assignment (Sec. 3.3, the synthesis after
+ * Algorithm 1; Lemma 2): running point l's deterministic assignment f_l with
+ * probability lambda_l assigns agent i to task j with probability
+ *   P_out[i][j] = sum_l lambda_l [f_l(j) = i]      ([n_agents][n_tasks]).
+ * lambda[n_points] and assign_hist[n_points][n_tasks] are what
+ * morap_query returns in morap_point_result (lambda, assign_hist; -1 marks
+ * a task no agent does).  With the lambda of a query (sum 1) P is doubly
+ * substochastic.  Host-only.  Errors: EINVAL (null pointer, negative or
+ * non-finite lambda, agent index out of range). */
+int morap_random_assignment(int32_t n_points, int32_t n_agents, int32_t n_tasks, const double *lambda,
+                            const int32_t *assign_hist, double *P_out);
 
 /* Hungarian assignment: f_out[j] = the row assigned to column j maximising
  * sum_j C[f(j)][j] for a square C [n][n] (row-major, rows = agents). */

@@ -21,6 +21,7 @@ from .gen import (  # noqa: F401
     fig2_task,
     corridor_agent,
     chain_agent,
+    tie_drift_agent,
     random_tiny_agent,
     random_tiny_task,
     weight_vectors,

@@ -287,6 +287,30 @@ def fig2_task():
     return Task(3, 0, 2, np.array([0, 1], np.int32), delta.reshape(-1), np.array([0, 1, 0], np.uint8), {"kind": "fig2"})
 
 
+def tie_drift_agent(delta=5e-9, s=0.5, s_far=1e-3):
+    """Seven states built so that Algorithm 3's recorded action goes stale
+    and two states tie.  From A (state 0, the start) the goal G (AP 0) is
+    reached by X (one move, then G with 1 - delta, a dead end T otherwise) or
+    by Y (a move that reaches G with probability s per try); B (state 1) can
+    go to A or to X, and A to B.  Y's value overtakes X's only once its
+    per-sweep increments are below 1e-8, while a far state Z (G with s_far
+    per try) keeps the sweeps going, so A and B keep "go to X" recorded, and
+    on the final values A -> B, B -> A and A -> Y all tie at probability 1.
+    Every move costs 1; action 0 of every state is a free stay."""
+    A, B, X, Y, Z, Gs, T = range(7)
+    rows = [
+        [(0.0, {A: 1.0}), (1.0, {B: 1.0}), (1.0, {X: 1.0}), (1.0, {Y: 1.0})],
+        [(0.0, {B: 1.0}), (1.0, {A: 1.0}), (1.0, {X: 1.0})],
+        [(0.0, {X: 1.0}), (1.0, {Gs: 1.0 - delta, T: delta})],
+        [(0.0, {Y: 1.0}), (1.0, {Gs: s, Y: 1.0 - s})],
+        [(0.0, {Z: 1.0}), (1.0, {Gs: s_far, Z: 1.0 - s_far})],
+        [(0.0, {Gs: 1.0})],
+        [(0.0, {T: 1.0})],
+    ]
+    labels = [[], [], [], [], [], [0], []]
+    return _pack_agent(rows, labels, A, {"kind": "tie_drift"})
+
+
 def sequence_task(target_aps, avoid_ap=None):
     """'Visit target_aps[0], then target_aps[1], ...' optionally with 'and never
     enter the region labelled avoid_ap before finishing' (a trap).

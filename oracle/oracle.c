@@ -127,10 +127,21 @@ int orc_alg3(int n, const int *state_ptr, const int *sa_ptr, const int *col, con
 }
 
 /* The scheduler returned for Algorithm 3.  On the final values x, keep the
- * recorded action when its Q-value is within tau of the maximum.  Otherwise
- * take the lowest-index action within tau of the maximum that is not a
- * self-loop (an action whose only successor is u itself); only when every
- * such action is a self-loop take the lowest-index one.  (At a fixed point a
+ * recorded action when its Q-value is within tau of the maximum; such
+ * states, and the absorbing DONE state, are "anchored".  A state whose
+ * recorded action fell more than tau behind (its value kept drifting by
+ * steps below eps after the last record) takes an action within tau of the
+ * maximum that is not a self-loop (an action whose only successor is u
+ * itself) and reaches, with positive probability, a state other than u that
+ * is already anchored: in rounds, each round deciding every remaining state
+ * from the anchors of the rounds before it (lowest-index such action), and
+ * anchoring the states it decided.  The levels so formed lead every decided
+ * state to an anchor with probability one, so two states that tie can never
+ * send the run back and forth between themselves forever (with a zero
+ * weight on the cost every move is free, and "go to the neighbour" ties
+ * with the maximum in a region of equal values).  States no round decides
+ * take the lowest-index non-self-loop action within tau of the maximum, and
+ * a self-loop only when nothing else is within tau.  (At a fixed point a
  * zero-reward self-loop always ties with the maximum, so preferring it would
  * return "stay forever" in states where the value came from moving.) */
 static int is_self_loop(int u, int a, const int *sa_ptr, const int *col)
@@ -138,26 +149,72 @@ static int is_self_loop(int u, int a, const int *sa_ptr, const int *col)
     return sa_ptr[a + 1] - sa_ptr[a] == 1 && col[sa_ptr[a]] == u;
 }
 
+static double max_q(int u, const int *state_ptr, const int *sa_ptr, const int *col, const double *prob,
+                    const double *rew, const double *x)
+{
+    double best = q_value(state_ptr[u], sa_ptr, col, prob, rew, x);
+    for (int a = state_ptr[u] + 1; a < state_ptr[u + 1]; ++a) {
+        const double qa = q_value(a, sa_ptr, col, prob, rew, x);
+        if (qa > best)
+            best = qa;
+    }
+    return best;
+}
+
 void orc_finalise_policy(int n, const int *state_ptr, const int *sa_ptr, const int *col, const double *prob,
                          const double *rew, const double *x, const int *a_rec, double tau, int *mu)
 {
+    /* anchored[u]: 1 from the start, r + 1 once decided in round r, 0 while undecided */
+    int *anchored = (int *)calloc((size_t)n, sizeof(int));
+    int undecided = 0;
     for (int u = 0; u < n; ++u) {
         const int a0 = state_ptr[u], a1 = state_ptr[u + 1];
+        mu[u] = 0;
         if (a0 == a1) {
-            mu[u] = 0;
+            anchored[u] = 1;
             continue;
         }
-        double best = q_value(a0, sa_ptr, col, prob, rew, x);
-        for (int a = a0 + 1; a < a1; ++a) {
-            const double qa = q_value(a, sa_ptr, col, prob, rew, x);
-            if (qa > best)
-                best = qa;
-        }
-        const double q_rec = q_value(a0 + a_rec[u], sa_ptr, col, prob, rew, x);
-        if (q_rec >= best - tau) {
+        const double best = max_q(u, state_ptr, sa_ptr, col, prob, rew, x);
+        if (q_value(a0 + a_rec[u], sa_ptr, col, prob, rew, x) >= best - tau) {
             mu[u] = a_rec[u];
-            continue;
+            anchored[u] = 1;
+        } else {
+            ++undecided;
         }
+    }
+    /* at most 254 rounds: the engine stamps the round in a byte; states still
+     * undecided after them take the plain fallback below */
+    for (int round = 1; undecided > 0 && round <= 254; ++round) {
+        int decided = 0;
+        for (int u = 0; u < n; ++u) {
+            if (anchored[u])
+                continue;
+            const int a0 = state_ptr[u], a1 = state_ptr[u + 1];
+            const double best = max_q(u, state_ptr, sa_ptr, col, prob, rew, x);
+            for (int a = a0; a < a1 && !anchored[u]; ++a) {
+                if (q_value(a, sa_ptr, col, prob, rew, x) < best - tau || is_self_loop(u, a, sa_ptr, col))
+                    continue;
+                for (int t = sa_ptr[a]; t < sa_ptr[a + 1]; ++t) {
+                    const int v = col[t];
+                    /* anchored before this round: 1 (from the start) or decided in an earlier round */
+                    if (prob[t] > 0.0 && v != u && anchored[v] >= 1 && anchored[v] <= round) {
+                        mu[u] = a - a0;
+                        anchored[u] = round + 1;
+                        ++decided;
+                        break;
+                    }
+                }
+            }
+        }
+        undecided -= decided;
+        if (decided == 0)
+            break;
+    }
+    for (int u = 0; u < n && undecided > 0; ++u) {
+        if (anchored[u])
+            continue;
+        const int a0 = state_ptr[u], a1 = state_ptr[u + 1];
+        const double best = max_q(u, state_ptr, sa_ptr, col, prob, rew, x);
         int pick = -1, pick_loop = -1;
         for (int a = a0; a < a1; ++a) {
             if (q_value(a, sa_ptr, col, prob, rew, x) < best - tau)
@@ -171,6 +228,7 @@ void orc_finalise_policy(int n, const int *state_ptr, const int *sa_ptr, const i
         }
         mu[u] = pick >= 0 ? pick : pick_loop;
     }
+    free(anchored);
 }
 
 /* Algorithm 4: y_u = rew(u, mu(u)) + sum P(u, mu(u), u') x_u' from x = 0

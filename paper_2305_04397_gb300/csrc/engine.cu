@@ -691,6 +691,17 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     CK(cudaMemcpyAsync(hs, c->d_status, np * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hctl, c->ctl, 2 * sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    // The scheduler's anchoring rounds, only when some recorded action was
+    // not kept (rare: its value drifted by steps below eps1 after the record).
+    for (int round = 1, pending = (int)hctl[1].undecided; pending > 0 && round <= kAnchorRounds; ++round) {
+        CK(cudaMemsetAsync(&c->ctl[1].decided, 0, sizeof(unsigned int), s));
+        CKL(launch_anchor(Kp, c->args64, (int)n_items, c->cfg.tau_policy, c->policy, round, s));
+        CK(cudaMemcpyAsync(&hctl[1].decided, &c->ctl[1].decided, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ++launches;
+        if (hctl[1].decided == 0) break;
+        pending -= (int)hctl[1].decided;
+    }
     h_c.assign(hc, hc + np);
     h_status.assign(hs, hs + np);
     morap_solve_stats &st = c->stats;
@@ -1630,8 +1641,8 @@ int morap_solve_plain(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_produ
             sweeps_vi += sw;
             CKL(launch_plain_spmv(ctx->sa_tr, ctx->col, ctx->p64, ctx->cost64, pd.sa_off, n_sa, wi, wp, pre_sa,
                                   pd.state_off, xc, q, s));
-            CKL(launch_plain_finalize(ctx->state_sa, ctx->sa_tr, ctx->col, pd.state_off, n, pd.sa_off, q, a_rec,
-                                      ctx->cfg.tau_policy, mu, s));
+            CKL(plain_finalize(ctx->state_sa, ctx->sa_tr, ctx->col, ctx->p64, pd.state_off, n, pd.sa_off, q, a_rec,
+                               ctx->cfg.tau_policy, mu, dres + 1, s));
             double cval = 0.0;
             if ((uint32_t)pd.init_local < n) CK(cudaMemcpyAsync(&cval, xc + pd.init_local, 8, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
@@ -1700,6 +1711,32 @@ int morap_assign_tasks(int32_t n_agents, int32_t n_tasks, int32_t K, const doubl
     if ((size_t)n_agents * n_tasks * K > 0 && (!c || !assign_out)) return fail(MORAP_EINVAL, "null argument");
     for (int k = 0; k < K; ++k)
         assign_tasks(n_agents, n_tasks, c + (size_t)k * n_agents * n_tasks, assign_out + (size_t)k * n_tasks);
+    return MORAP_OK;
+    API_END
+}
+
+int morap_random_assignment(int32_t n_points, int32_t n_agents, int32_t n_tasks, const double *lambda,
+                            const int32_t *assign_hist, double *P_out) {
+    API_BEGIN
+    if (n_points < 0 || n_agents < 0 || n_tasks < 0) return fail(MORAP_EINVAL, "negative size");
+    if ((size_t)n_agents * n_tasks > 0 && !P_out) return fail(MORAP_EINVAL, "null argument");
+    if (n_points > 0 && n_tasks > 0 && (!lambda || !assign_hist)) return fail(MORAP_EINVAL, "null argument");
+    for (int l = 0; l < n_points; ++l) {
+        if (!(lambda[l] >= 0.0) || !std::isfinite(lambda[l]))
+            return fail(MORAP_EINVAL, "lambda[" + std::to_string(l) + "] is not a finite weight >= 0");
+        for (int j = 0; j < n_tasks; ++j) {
+            const int32_t i = assign_hist[(size_t)l * n_tasks + j];
+            if (i < -1 || i >= n_agents)
+                return fail(MORAP_EINVAL, "assign_hist[" + std::to_string(l) + "][" + std::to_string(j) +
+                                              "] is not an agent index or -1");
+        }
+    }
+    std::fill(P_out, P_out + (size_t)n_agents * n_tasks, 0.0);
+    for (int l = 0; l < n_points; ++l)
+        for (int j = 0; j < n_tasks; ++j) {
+            const int32_t i = assign_hist[(size_t)l * n_tasks + j];
+            if (i >= 0) P_out[(size_t)i * n_tasks + j] += lambda[l];
+        }
     return MORAP_OK;
     API_END
 }

@@ -442,7 +442,14 @@ int project_down_hull(int n, int m, const double *t, const double *Phi, const do
         v[i] = std::min(t[i], hull) - 1.0;
     }
     const int rc = qp_solve(N, G.data(), c.data(), mi, A.data(), b.data(), 1, E.data(), d.data(), v.data());
-    for (int i = 0; i < n; ++i) x[i] = std::min(v[i], t[i]);
+    // With a diagonal metric the projection never exceeds t in any objective
+    // (x_i = min(t_i, (Phi' lam)_i)), so clipping removes only roundoff; with a
+    // general metric it may exceed t and is returned as solved.
+    bool diagonal = true;
+    for (int i = 0; M && i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (i != j && M[(size_t)i * n + j] != 0.0) diagonal = false;
+    for (int i = 0; i < n; ++i) x[i] = diagonal ? std::min(v[i], t[i]) : v[i];
     if (lambda) {
         // the convex weights, cleaned of the solver's roundoff (>= 0, sum 1)
         double sum = 0.0;

@@ -133,6 +133,8 @@ struct LoopCtl {
     unsigned int block_sweeps;  // most sweeps of a pair evaluated by one block (k_eval_block)
     unsigned long long updates;
     unsigned long long bytes;
+    unsigned int undecided;  // scheduler states whose recorded action is not kept (k_finalize)
+    unsigned int decided;    // states one anchoring round decided (k_anchor)
 };
 
 #ifndef MORAP_CHUNK
@@ -146,6 +148,10 @@ constexpr int kEvalBlockThreads = 1024;
 constexpr int kEvalBlockSmem = 224 * 1024;
 constexpr uint32_t kEvalBlockStates = kEvalBlockSmem / (2 * 16);
 constexpr int kThreads = 256;
+// Rounds of the scheduler's anchoring step (a state decided in round r is
+// stamped r + 1 in a byte): states still undecided after them keep the
+// lowest-index near-maximiser that is not a self-loop.
+constexpr int kAnchorRounds = 254;
 constexpr int kInItems = 16;     // input items recorded per work item (more: always recomputed)
 int sweep_smem_bytes(int kind);
 int sweep_setup_attributes();
@@ -260,7 +266,12 @@ int launch_delta_table(int Kp, const SweepArgs &a, int n_chunks, const float *B,
 // V = B + d as an exact double-float sum.
 int launch_delta_combine(const float *B, const float *d, float2 *V, size_t n, void *s);
 int launch_convert(const float *v32, float2 *vda, float2 *vdb, size_t n, void *s);
+// The returned scheduler (a.a_rec is consumed: it becomes the anchoring
+// flags; a.ctl->undecided counts the states the anchoring rounds decide).
 int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, void *s);
+// One anchoring round over every undecided (state, weight); a.ctl->decided
+// counts the states it decided.
+int launch_anchor(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, int round, void *s);
 int launch_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V64, const uint8_t *frozen, double *c_out,
                     int32_t *status_out, void *s);
 int eval_block_setup();  // once per device: k_eval_block's shared-memory limit
@@ -279,9 +290,13 @@ int launch_plain_spmv(const uint32_t *sa_tr, const int32_t *col, const double *p
 int launch_plain_reduce(const uint32_t *state_sa, uint32_t state_off, uint32_t n_states, uint32_t sa_begin,
                         const double *q, const double *x, double *y, int32_t *a_rec, double eps,
                         unsigned long long *res, void *s);
-int launch_plain_finalize(const uint32_t *state_sa, const uint32_t *sa_tr, const int32_t *col, uint32_t state_off,
-                          uint32_t n_states, uint32_t sa_begin, const double *q, const int32_t *a_rec, double tau,
-                          int32_t *mu, void *s);
+// The returned scheduler of the plain path from the Q values q of the final
+// iterate: kept recorded actions, then the anchoring rounds (at most
+// kAnchorRounds).  a_rec is consumed (it becomes the anchor flags); counter
+// is one device word of scratch.  Synchronises the stream.
+int plain_finalize(const uint32_t *state_sa, const uint32_t *sa_tr, const int32_t *col, const double *p64,
+                   uint32_t state_off, uint32_t n_states, uint32_t sa_begin, const double *q, int32_t *a_rec,
+                   double tau, int32_t *mu, unsigned long long *counter, void *s);
 int launch_plain_eval(const uint32_t *state_sa, const uint32_t *sa_tr, const int32_t *col, const double *p64,
                       const double *cost64, uint32_t state_off, uint32_t n_states, uint32_t pre_begin,
                       const int32_t *mu, int objective, const double *x, double *y, unsigned long long *res,

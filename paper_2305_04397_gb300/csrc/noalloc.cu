@@ -3,7 +3,9 @@
 // Its scratch (the second value buffer, the state-action values, the
 // recorded actions and the residual word) lives in one file-scope static
 // device array, so the call itself never allocates device or pinned host
-// memory.  It runs the same kernels as morap_solve_plain.
+// memory.  It runs the same kernels as morap_solve_plain, including the
+// scheduler's anchoring rounds (its one extra scratch word is the round
+// counter next to the residual word).
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -70,6 +72,39 @@ extern "C" int morap_plain_vi_noalloc(int32_t n_states, int32_t n_sa, const uint
         return fail(MORAP_EINVAL, "noalloc: init_state / pre_begin out of range");
     if (!(eps > 0) || !(tau >= 0) || max_sweeps < 1 || !(w_cost >= 0) || !(w_prob >= 0))
         return fail(MORAP_EINVAL, "noalloc: eps > 0, tau >= 0, max_sweeps >= 1, weights >= 0 required");
+    cudaStream_t s = (cudaStream_t)stream;
+    // The call waits on the stream after every sweep, so it cannot be part of
+    // a stream capture: refuse one before touching the stream.
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &capturing);
+    if (ce != cudaSuccess) return fail(MORAP_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+    if (capturing != cudaStreamCaptureStatusNone)
+        return fail(MORAP_EINVAL, "noalloc: the stream is being captured (the call is synchronous)");
+    // The scratch is the current device's copy of the array: the stream and
+    // every buffer must belong to that device too.
+    int dev = -1;
+    if ((ce = cudaGetDevice(&dev)) != cudaSuccess)
+        return fail(MORAP_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+    if (s) {
+        int sdev = -1;
+        if ((ce = cudaStreamGetDevice(s, &sdev)) != cudaSuccess)
+            return fail(MORAP_ECUDA, std::string("cudaStreamGetDevice: ") + cudaGetErrorString(ce));
+        if (sdev != dev)
+            return fail(MORAP_EINVAL, "noalloc: the stream belongs to device " + std::to_string(sdev) +
+                                          ", the current device is " + std::to_string(dev));
+    }
+    const void *bufs[] = {state_sa, sa_tr, col, prob, cost, values, policy};
+    const char *names[] = {"state_sa", "sa_tr", "col", "prob", "cost", "values", "policy"};
+    for (int i = 0; i < 7; ++i) {
+        cudaPointerAttributes at{};
+        if ((ce = cudaPointerGetAttributes(&at, bufs[i])) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MORAP_EINVAL, std::string("noalloc: ") + names[i] + " is not a device address");
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+            return fail(MORAP_EINVAL, std::string("noalloc: ") + names[i] + " is not memory of the current device (" +
+                                          std::to_string(dev) + ")");
+    }
     unsigned char *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc != MORAP_OK) return rc;
@@ -77,7 +112,6 @@ extern "C" int morap_plain_vi_noalloc(int32_t n_states, int32_t n_sa, const uint
     double *q = reinterpret_cast<double *>(scratch + kOffQ);
     int32_t *a_rec = reinterpret_cast<int32_t *>(scratch + kOffRec);
     unsigned long long *dres = reinterpret_cast<unsigned long long *>(scratch + kOffRes);
-    cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = (uint32_t)n_states;
     // the scratch keeps the previous call's contents: clear what must start at 0
 #define NA_CK(call)                                                                                   \
@@ -121,7 +155,7 @@ extern "C" int morap_plain_vi_noalloc(int32_t n_states, int32_t n_sa, const uint
     if (xc != values) NA_CK(cudaMemcpyAsync(values, xc, sizeof(double) * (n + 1), cudaMemcpyDeviceToDevice, s));
     NA_CKL(launch_plain_spmv(sa_tr, col, prob, cost, 0u, (uint32_t)n_sa, w_cost, w_prob, pre_sa_begin, 0u, values, q,
                              s));
-    NA_CKL(launch_plain_finalize(state_sa, sa_tr, col, 0u, n, 0u, q, a_rec, tau, policy, s));
+    NA_CKL(plain_finalize(state_sa, sa_tr, col, prob, 0u, n, 0u, q, a_rec, tau, policy, dres + 1, s));
     double c = 0.0;
     if ((uint32_t)init_state < n) NA_CK(cudaMemcpyAsync(&c, values + init_state, sizeof(c), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));

@@ -862,10 +862,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
 
 // -------------------------------------------------------------- finalise
 // The returned scheduler: keep the recorded action when its Q-value on the
-// final FP64 values is within tau of the maximum; otherwise the lowest-index
-// action within tau of the maximum that is not a self-loop (a zero-reward
-// self-loop ties with the maximum at any fixed point), and only if every
-// such action is a self-loop the lowest-index one.
+// final FP64 values is within tau of the maximum (the state is "anchored");
+// otherwise, provisionally, the lowest-index action within tau of the
+// maximum that is not a self-loop (a zero-reward self-loop ties with the
+// maximum at any fixed point), and only if every such action is a self-loop
+// the lowest-index one.  a_rec is consumed: it becomes the anchoring flag
+// (1 anchored, 0 undecided), and the undecided (state, weight) entries are
+// counted in ctl->undecided for the anchoring rounds (k_anchor).
 template <int KP>
 __global__ void __launch_bounds__(kThreads) k_finalize(SweepArgs a, int n_chunks, double tau, uint8_t *policy) {
     constexpr int VEC = KP < 2 ? KP : 2, LPS = KP / VEC, SPR = kThreads / LPS;
@@ -937,11 +940,87 @@ __global__ void __launch_bounds__(kThreads) k_finalize(SweepArgs a, int n_chunks
                 for (int v = 0; v < VEC; ++v) all_kept = all_kept && near_max(qrec[v], best[v]);
                 if (all_kept) break;  // the second pass is only needed for a fallback
             }
+            unsigned int undecided = 0;
 #pragma unroll
-            for (int v = 0; v < VEC; ++v)
-                policy[row + v] = near_max(qrec[v], best[v]) ? rec[v] : (pick[v] != 0xFF ? pick[v] : pick_loop[v]);
+            for (int v = 0; v < VEC; ++v) {
+                const bool kept = near_max(qrec[v], best[v]);
+                policy[row + v] = kept ? rec[v] : (pick[v] != 0xFF ? pick[v] : pick_loop[v]);
+                a.a_rec[row + v] = kept ? 1 : 0;
+                undecided += kept ? 0u : 1u;
+            }
+            if (undecided) atomicAdd(&a.ctl->undecided, undecided);
         }
     }
+}
+
+// One anchoring round of the returned scheduler.  With a zero weight on the
+// cost every move is free, so in a region of equal values "go to the
+// neighbour" ties with the maximum and two undecided neighbours could send
+// the run between them forever.  An undecided (state, weight) therefore
+// takes the lowest-index action within tau of the maximum that is not a
+// self-loop and reaches, with positive probability, another state anchored
+// before this round: flag 1, or decided in an earlier round r' (flag
+// r' + 1); the done slot is always anchored.  Decided entries get flag
+// round + 1, which this round's readers treat as not yet anchored, so the
+// result does not depend on the order in which threads run.  Each decided
+// state reaches an anchor with positive probability through states of
+// lower rounds, so the scheduler reaches the kept recorded actions (or the
+// done slot) with probability one.  One thread per (state, weight).
+template <int KP>
+__global__ void __launch_bounds__(kThreads) k_anchor(SweepArgs a, int n_chunks, double tau, uint8_t *policy,
+                                                      int round) {
+    constexpr int SPR = kThreads / KP;
+    const float2 *__restrict__ V = static_cast<const float2 *>(a.V[0]);  // double-float values
+    const int k = threadIdx.x % KP, slot = threadIdx.x / KP;
+    const float ftau = (float)tau;
+    unsigned int decided = 0;
+    for (int item = blockIdx.x; item < n_chunks; item += gridDim.x) {
+        const int4 ch = a.chunks[item];
+        const ProdDesc pd = a.prods[ch.x];
+        const uint32_t done_slot = pd.state_off + pd.n_nd;
+        const ArithDF::W w = a.wdf[(size_t)ch.x * KP + k];
+        for (int s = ch.y + slot; s < ch.z; s += SPR) {
+            const uint32_t u = pd.state_off + (uint32_t)s;
+            const size_t row = (size_t)u * KP + k;
+            if (a.a_rec[row] != 0) continue;
+            const uint32_t a0 = a.state_sa[u], a1 = a.state_sa[u + 1];
+            auto q_of = [&](uint32_t sa) {
+                const float2 cd = a.costdf[sa];
+                DF acc = ArithDF::reward(w, {cd.x, cd.y});
+                for (uint32_t t = a.sa_tr[sa]; t < a.sa_tr[sa + 1]; ++t) {
+                    const float2 pr = a.pdf[t];
+                    const float2 xv = V[(size_t)a.col[t] * KP + k];
+                    ArithDF::mac(acc, {pr.x, pr.y}, {xv.x, xv.y});
+                }
+                return df_norm(acc);
+            };
+            DF best = ArithDF::neg_inf();
+            for (uint32_t sa = a0; sa < a1; ++sa) {
+                const DF q = q_of(sa);
+                best = df_gt(q, best) ? q : best;
+            }
+            for (uint32_t sa = a0; sa < a1; ++sa) {
+                const uint32_t t0 = a.sa_tr[sa], t1 = a.sa_tr[sa + 1];
+                if (t1 - t0 == 1 && (uint32_t)a.col[t0] == u) continue;  // self-loop
+                const DF q = q_of(sa);
+                if (!(__fadd_rn(__fadd_rn(q.h, -best.h), __fadd_rn(q.l, -best.l)) >= -ftau)) continue;
+                bool hit = false;
+                for (uint32_t t = t0; t < t1 && !hit; ++t) {
+                    const uint32_t v = (uint32_t)a.col[t];
+                    if (!(a.pdf[t].x > 0.0f) || v == u) continue;
+                    const int f = v == done_slot ? 1 : (int)a.a_rec[(size_t)v * KP + k];
+                    hit = f >= 1 && f <= round;
+                }
+                if (hit) {
+                    policy[row] = (uint8_t)(sa - a0);
+                    a.a_rec[row] = (uint8_t)(round + 1);
+                    ++decided;
+                    break;
+                }
+            }
+        }
+    }
+    if (decided) atomicAdd(&a.ctl->decided, decided);
 }
 
 // ------------------------------------------------------------- evaluation
@@ -1391,6 +1470,8 @@ __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_it
         ctl->block_sweeps = 0;
         ctl->updates = 0;
         ctl->bytes = 0;
+        ctl->undecided = 0;
+        ctl->decided = 0;
     }
 }
 
@@ -1644,6 +1725,23 @@ int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_
     case 16: k_finalize<16><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy); break;
     case 32: k_finalize<32><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy); break;
     case 64: k_finalize<64><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy); break;
+    default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_anchor(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, int round, void *sv) {
+    cudaStream_t s = (cudaStream_t)sv;
+    const int grid = n_chunks < 8192 ? n_chunks : 8192;
+    if (grid <= 0) return 0;
+    switch (Kp) {
+    case 1: k_anchor<1><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy, round); break;
+    case 2: k_anchor<2><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy, round); break;
+    case 4: k_anchor<4><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy, round); break;
+    case 8: k_anchor<8><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy, round); break;
+    case 16: k_anchor<16><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy, round); break;
+    case 32: k_anchor<32><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy, round); break;
+    case 64: k_anchor<64><<<grid, kThreads, 0, s>>>(a, n_chunks, tau, policy, round); break;
     default: return (int)cudaErrorInvalidValue;
     }
     return (int)cudaGetLastError();

@@ -129,6 +129,7 @@ _SIGS = {
     "morap_verify": (ctypes.c_int, [_P, _DP, _DP, ctypes.c_double, ctypes.c_int32, _P, ctypes.POINTER(PointResult)]),
     "morap_assign_max": (ctypes.c_int, [ctypes.c_int32, _DP, _I32P]),
     "morap_assign_tasks": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _DP, _I32P]),
+    "morap_random_assignment": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _DP, _I32P, _DP]),
     "morap_evaluate": (ctypes.c_int, [_P, ctypes.c_int32, _I32P, _I32P, _P, _DP, _DP]),
     "morap_pareto_create": (ctypes.c_int, [ctypes.c_int32, _DP, _DP, ctypes.c_double, ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_void_p)]),
@@ -333,15 +334,15 @@ def morap_query(ctx, t, M=None, eps=1e-6, max_iter=64, stream=None, check=True, 
 
 
 def random_assignment(lam, assign_hist, n_agents):
-    """The synthesised random assignment: P[i][j] = probability that agent i
-    does task j = sum over the points l of lambda_l [assign_hist[l][j] == i]."""
-    lam = np.asarray(lam)
-    assign_hist = np.asarray(assign_hist)
-    P = np.zeros((n_agents, assign_hist.shape[1]))
-    for l, f in enumerate(assign_hist):
-        for j, i in enumerate(f):
-            if i >= 0:
-                P[i, j] += lam[l]
+    """The synthesised random assignment (morap_random_assignment):
+    P[i][j] = probability that agent i does task j."""
+    lam = _arr(lam, np.float64)
+    F = _arr(assign_hist, np.int32)
+    F = F.reshape(len(lam), -1) if F.size else np.zeros((len(lam), 0), np.int32)
+    n_tasks = F.shape[1]
+    P = np.zeros((n_agents, n_tasks))
+    _check(lib().morap_random_assignment(len(lam), int(n_agents), n_tasks, _ptr(lam, ctypes.c_double),
+                                         _ptr(F, ctypes.c_int32), _ptr(P, ctypes.c_double)))
     return P
 
 

@@ -87,31 +87,76 @@ def test_assignment_large_vs_oracle(M):
 
 
 def test_halfspace_projection_vs_oracle(M):
+    """The engine's outer-bound projection (interior point with an exact
+    active-set finish) against the oracle's least-distance program, to
+    1e-10, for the identity and a general metric."""
     rng = np.random.default_rng(2)
-    for n, m in [(2, 1), (3, 3), (5, 6), (8, 10)]:
-        Wt = rng.dirichlet(np.ones(n), size=m)
-        R = rng.normal(size=(m, n))
-        b = np.einsum("ij,ij->i", Wt, R)
-        t = R.max(axis=0) + rng.uniform(0.1, 1.0, size=n)
-        A = rng.normal(size=(n, n))
-        Mm = A @ A.T + n * np.eye(n)
-        for MM in (None, Mm):
-            z = M.morap_project_halfspaces(t, Wt, b, MM)
-            zo = P.project_halfspaces(t, Wt, b, np.eye(n) if MM is None else MM)
-            assert np.all(Wt @ z <= b + 1e-9)
-            assert np.max(np.abs(z - zo)) < 1e-6
+    for n, m in [(2, 1), (3, 3), (5, 6), (8, 10), (25, 40)]:
+        for _ in range(3):
+            Wt = rng.dirichlet(np.ones(n), size=m)
+            R = rng.normal(size=(m, n))
+            b = np.einsum("ij,ij->i", Wt, R)
+            t = R.max(axis=0) + rng.uniform(0.1, 1.0, size=n)
+            A = rng.normal(size=(n, n))
+            Mm = A @ A.T + n * np.eye(n)
+            for MM in (None, Mm):
+                z = M.morap_project_halfspaces(t, Wt, b, MM)
+                zo = P.project_halfspaces(t, Wt, b, np.eye(n) if MM is None else MM)
+                assert np.all(Wt @ z <= b + 1e-9)
+                assert np.max(np.abs(z - zo)) < 1e-10, (n, m)
 
 
-def test_down_hull_projection_vs_oracle_and_scan(M):
+def test_down_hull_projection_vs_oracle(M):
+    """The engine's inner-bound projection against the oracle's minimum-norm
+    point (Wolfe's algorithm), to 1e-10, for the identity and a general
+    metric; t inside, on and outside the down-closure."""
     rng = np.random.default_rng(3)
-    for n, m in [(2, 1), (2, 3), (3, 4), (5, 6), (6, 9)]:
-        Phi = np.column_stack([-rng.uniform(1, 5, size=(m, max(n // 2, 1))),
-                               rng.uniform(0, 1, size=(m, n - max(n // 2, 1)))])
-        t = Phi.max(axis=0) + rng.uniform(-0.5, 0.5, size=n)
-        x = M.morap_project_down_hull(t, Phi)
-        xo = P.project_down_hull(t, Phi, np.eye(n))
-        assert np.linalg.norm(t - x) == pytest.approx(np.linalg.norm(t - xo), abs=1e-7)
-        assert np.max(np.abs(x - xo)) < 1e-5
+    for n, m in [(2, 1), (2, 3), (3, 4), (5, 6), (6, 9), (20, 30)]:
+        for _ in range(3):
+            Phi = np.column_stack([-rng.uniform(1, 5, size=(m, max(n // 2, 1))),
+                                   rng.uniform(0, 1, size=(m, n - max(n // 2, 1)))])
+            A = rng.normal(size=(n, n))
+            for t, MM in ((Phi.max(axis=0) + rng.uniform(-0.5, 0.5, size=n), None),
+                          (Phi.max(axis=0) + rng.uniform(-0.5, 0.5, size=n), A @ A.T + n * np.eye(n)),
+                          (Phi[0] - 0.01, None), (Phi.mean(axis=0), None)):
+                x = M.morap_project_down_hull(t, Phi, MM)
+                xo = P.project_down_hull(t, Phi, np.eye(n) if MM is None else MM)
+                assert np.max(np.abs(x - xo)) < 1e-10, (n, m)
+
+
+def test_random_assignment_by_hand(M):
+    """Three points with weights 0.5 / 0.3 / 0.2 over two agents and three
+    tasks (-1: no agent): P[i][j] sums the weights of the points that give
+    task j to agent i (Sec. 3.3, the synthesis)."""
+    lam = np.array([0.5, 0.3, 0.2])
+    F = np.array([[0, 1, -1], [1, -1, 0], [0, 1, -1]], np.int32)
+    P = M.random_assignment(lam, F, 2)
+    want = np.array([[0.7, 0.0, 0.3], [0.3, 0.7, 0.0]])
+    assert np.max(np.abs(P - want)) < 1e-15
+    with pytest.raises(M.MorapError) as e:
+        M.random_assignment(lam, np.array([[0, 2, -1]] * 3, np.int32), 2)
+    assert e.value.code == M.EINVAL
+    with pytest.raises(M.MorapError) as e:
+        M.random_assignment(np.array([0.5, -0.1, 0.6]), F, 2)
+    assert e.value.code == M.EINVAL
+
+
+def test_random_assignment_is_doubly_substochastic(M):
+    """Convex weights over partial permutations (each agent does at most one
+    task, each task at most one agent) give row and column sums <= 1; with
+    as many agents as tasks and full permutations, exactly 1 (Birkhoff)."""
+    rng = np.random.default_rng(11)
+    for nI, nJ in [(3, 5), (4, 4), (6, 2)]:
+        m = 7
+        lam = rng.dirichlet(np.ones(m))
+        F = np.full((m, nJ), -1, np.int32)
+        for l in range(m):
+            perm = rng.permutation(max(nI, nJ))
+            F[l] = [perm[j] if perm[j] < nI else -1 for j in range(nJ)]
+        P = M.random_assignment(lam, F, nI)
+        assert np.all(P >= 0) and np.all(P.sum(axis=0) <= 1 + 1e-12) and np.all(P.sum(axis=1) <= 1 + 1e-12)
+        if nI == nJ:
+            assert np.max(np.abs(P.sum(axis=0) - 1)) < 1e-12 and np.max(np.abs(P.sum(axis=1) - 1)) < 1e-12
 
 
 def test_task_preprocess_vs_oracle(M):

@@ -229,11 +229,19 @@ def test_query_matches_oracle_alg1(M, tiny, tiny_prods):
     ctx = make_ctx(M, tiny)
     for t in [tiny.thresholds[0], np.array([-12.0, -12.0, 0.6, 0.6, 0.6]), np.array([-1.0, -1.0, 0.2, 0.2, 0.2])]:
         got = ctx.query(t, eps=1e-6, max_iter=40)
-        supp = lambda w: O.supporting_point(tiny_prods, w)[0]
+        f_oracle = []
+
+        def supp(w):
+            r, f, _, _, _ = O.supporting_point(tiny_prods, w)
+            f_oracle.append([int(i) if i < len(tiny.agents) else -1 for i in f])
+            return r
+
         want = OP.alg1(supp, t, eps=1e-6, max_iter=40)
         assert got["feasible"] == want["feasible"]
-        assert np.max(np.abs(got["t_down"] - want["t_dn"])) < 1e-4
-        assert np.max(np.abs(got["t_up"] - want["t_up"])) < 1e-4
+        assert got["iterations"] == want["iterations"]
+        assert np.max(np.abs(got["t_down"] - want["t_dn"])) < TOL
+        assert np.max(np.abs(got["t_up"] - want["t_up"])) < TOL
+        assert np.max(np.abs(got["w_hist"] - np.array([h["w"] for h in want["history"]]))) < TOL
         # Lemma 6 on every direction the engine produced
         for w in got["w_hist"]:
             assert np.all(w >= 0) and abs(w.sum() - 1) < 1e-9
@@ -247,6 +255,23 @@ def test_query_matches_oracle_alg1(M, tiny, tiny_prods):
             assert np.all(lam @ R >= t - 1e-7)
         P = M.random_assignment(lam, F, len(tiny.agents))
         assert np.all(P.sum(axis=0) <= 1 + 1e-12) and np.all(P.sum(axis=1) <= 1 + 1e-12)
+        # the same random assignment from the oracle's run: its convex weights
+        # (the exact projection's) and its assignments, summed here.  Where
+        # the two Hungarian steps broke a tie differently (e.g. w = e_1, where
+        # every agent but the first has c = 0 on every task) the points must
+        # be the same and that point is left out of the comparison.
+        assert np.max(np.abs(lam - want["lambda"])) < TOL
+        same = np.array([np.array_equal(F[l], f_oracle[l]) for l in range(len(lam))])
+        for l in np.flatnonzero(~same):
+            assert np.max(np.abs(R[l] - want["history"][l]["r"])) < TOL
+        P_oracle = np.zeros_like(P)
+        for l, f in enumerate(f_oracle):
+            for j, i in enumerate(f):
+                if i >= 0 and same[l]:
+                    P_oracle[i, j] += want["lambda"][l]
+        P_same = M.random_assignment(np.where(same, lam, 0.0), F, len(tiny.agents))
+        assert np.max(np.abs(P_same - P_oracle)) < TOL
+        assert same.sum() >= 1
         # each point is a supporting point of its weight: the scalarised value
         # matches the oracle's (the point itself is unique only up to ties of
         # the scalarised objective, which small weights make wide)
@@ -304,8 +329,63 @@ def test_query_fig2(M):
     for t in ([-1.8, 0.9], [-3.0, 0.5], [-2.5, 0.7]):
         got = ctx.query(np.array(t), eps=1e-7)
         want = OP.alg1(supp, np.array(t), eps=1e-7)
-        assert got["feasible"] == want["feasible"]
-        assert np.max(np.abs(got["t_down"] - want["t_dn"])) < 1e-5
+        assert got["feasible"] == want["feasible"] and got["iterations"] == want["iterations"]
+        assert np.max(np.abs(got["t_down"] - want["t_dn"])) < TOL
+        assert np.max(np.abs(got["t_up"] - want["t_up"])) < TOL
+    ctx.close()
+
+
+def test_query_grid32_subinstance_matches_oracle_alg1(M):
+    """Algorithm 1 on a 3-agent x 4-task sub-instance of the 32x32 grid batch
+    (12 products of ~3.5k states): for a threshold the loop finds
+    achievable and one it does not, the engine's verdict, iteration count,
+    directions and both bounds t_down and t_up equal the oracle's Algorithm
+    1 (fed by the oracle's Algorithm 2) to 1e-6."""
+    inst = I.config_grid32()
+    agents, tasks = inst.agents[:3], inst.tasks[:4]
+    prods = O.products(agents, tasks)
+    ctx = make_ctx(M, (agents, tasks))
+    supp = lambda w: O.supporting_point(prods, w)[0]
+    seen = set()
+    for t in (np.array([-150.0, -150.0, -150.0, 0.3, 0.3, 0.3, 0.0]),
+              np.array([-30.0, -30.0, -30.0, 0.95, 0.95, 0.95, 0.95])):
+        got = ctx.query(t, eps=1e-6, max_iter=40)
+        want = OP.alg1(supp, t, eps=1e-6, max_iter=40)
+        assert got["feasible"] == want["feasible"] and got["iterations"] == want["iterations"]
+        assert np.max(np.abs(got["w_hist"] - np.array([h["w"] for h in want["history"]]))) < TOL
+        assert np.max(np.abs(got["r_hist"] - np.array([h["r"] for h in want["history"]]))) < TOL
+        assert np.max(np.abs(got["t_down"] - want["t_dn"])) < TOL
+        assert np.max(np.abs(got["t_up"] - want["t_up"])) < TOL
+        seen.add(bool(got["feasible"]))
+    assert seen == {True, False}
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,polish", [(0, 0), (0, 1), (1, 1)])
+def test_tie_fallback_anchoring_matches_oracle(M, precision, polish):
+    """A recorded action that went stale with a zero weight on the cost:
+    on the final values "go to the neighbour" ties at two states, and the
+    plain lowest-index fallback would send the run between them forever.
+    The engine's scheduler (batched and plain paths) must reach the goal with
+    the optimal probability, c and r as the oracle's."""
+    a, t = I.tie_drift_agent(), I.sequence_task([0])
+    p = O.Product(a, t)
+    ctx = make_ctx(M, ([a], [t]), precision=precision, polish=polish)
+    W = np.array([[0.0, 1.0], [0.0, 0.25], [0.01, 0.99]])
+    out = ctx.solve(W)
+    assert np.all(out["status"] == 0)
+    for k, w in enumerate(W):
+        r = O.solve_pair(p, w[0], w[1])
+        assert out["c"][k, 0, 0] == pytest.approx(r["c"], abs=TOL)
+        assert out["r_prob"][k, 0, 0] == pytest.approx(r["r_prob"], abs=TOL)
+        assert out["r_prob"][k, 0, 0] == pytest.approx(1.0, abs=TOL)
+        if w[0] > 0:
+            assert out["r_cost"][k, 0, 0] == pytest.approx(r["r_cost"], abs=TOL)
+        assert w[0] * out["r_cost"][k, 0, 0] + w[1] * out["r_prob"][k, 0, 0] == pytest.approx(out["c"][k, 0, 0],
+                                                                                            abs=TOL)
+    plain = M.morap_solve_plain(ctx.h, [0, 0], [(0.0, 1.0), (0.0, 0.25)])
+    assert np.max(np.abs(plain["r_prob"] - 1.0)) < TOL
+    assert np.max(np.abs(plain["c"] - out["c"][:2, 0, 0])) < TOL
     ctx.close()
 
 

@@ -1,8 +1,11 @@
 """Pins for the oracle's assignment step, projections and Algorithm 1 (CPU).
 
 Assignment: brute force over all permutations.  Projections: closed forms
-(one half-space, one dominating point), a 1-D scan over segments in 2-D, and
-the KKT conditions in higher dimension.  Algorithm 1: Thm 3 / Cor. on
+(one half-space, one dominating point, one LDP constraint), KKT certificates
+that characterise each projection completely (to 1e-10, general metric M),
+brute force over every active set in 2-4 dimensions, the non-negative least
+squares step against brute force over supports, and a 1-D scan over
+segments in 2-D.  Algorithm 1: Thm 3 / Cor. on
 instances whose achievable set C is enumerable (all permutations x all
 simple schedulers), and Lemma 6 on every direction it produces.
 """
@@ -50,44 +53,221 @@ def test_pad_square_dummy_agents():
 
 
 # ---------------------------------------------------------------- projections
+#
+# Both projections are pinned to 1e-10 by conditions that characterise the
+# answer completely (KKT certificates and brute force over every active
+# set), and to closed forms where one exists.
+
+
+def _rand_spd(rng, n):
+    A = rng.normal(size=(n, n))
+    return A @ A.T + n * np.eye(n)
+
+
+def _nnls_brute(E, f):
+    """min ||E u - f|| over u >= 0 by trying every support: the answer is the
+    unconstrained least-squares solution on some support whose coordinates
+    are positive and whose gradient is <= 0 off the support."""
+    m = E.shape[1]
+    best = None
+    for k in range(m + 1):
+        for S in itertools.combinations(range(m), k):
+            u = np.zeros(m)
+            if S:
+                u[list(S)] = np.linalg.lstsq(E[:, list(S)], f, rcond=None)[0]
+                if np.any(u[list(S)] <= 0):
+                    continue
+            g = E.T @ (f - E @ u)
+            off = [j for j in range(m) if j not in S]
+            if off and np.max(g[off]) > 1e-10:
+                continue
+            val = np.linalg.norm(E @ u - f)
+            if best is None or val < best[0] - 1e-12:
+                best = (val, u)
+    return best
+
+
+def test_nnls_kkt_and_brute_force():
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        n, m = rng.integers(2, 6), rng.integers(1, 7)
+        E = rng.normal(size=(n, m))
+        f = rng.normal(size=n)
+        u = P.nnls(E, f)
+        g = E.T @ (f - E @ u)
+        assert np.all(u >= 0)
+        assert np.all(g <= 1e-12)
+        assert np.all(np.abs(g[u > 0]) <= 1e-12)
+        val, ub = _nnls_brute(E, f)
+        assert np.linalg.norm(E @ u - f) == pytest.approx(val, abs=1e-12)
+        assert np.max(np.abs(E @ u - E @ ub)) < 1e-10  # the fitted vector is unique
+
+
+def test_ldp_closed_form():
+    """One constraint g.x >= h with h > 0: x = h g / |g|^2; h <= 0: x = 0;
+    inconsistent constraints are reported."""
+    rng = np.random.default_rng(6)
+    for _ in range(10):
+        g = rng.normal(size=4)
+        h = rng.uniform(0.1, 2.0)
+        x = P.ldp(g[None, :], np.array([h]))
+        assert np.max(np.abs(x - h * g / (g @ g))) < 1e-13
+        assert np.max(np.abs(P.ldp(g[None, :], np.array([-h])))) < 1e-15
+    g = np.array([[1.0, 0.0], [-1.0, 0.0]])
+    assert P.ldp(g, np.array([1.0, 1.0])) is None  # x0 >= 1 and -x0 >= 1
 
 
 def test_halfspace_projection_closed_form():
     rng = np.random.default_rng(0)
     for _ in range(10):
         n = 4
-        A = rng.normal(size=(n, n))
-        M = A @ A.T + n * np.eye(n)
+        M = _rand_spd(rng, n)
         w = rng.dirichlet(np.ones(n))
         t = rng.normal(size=n)
         b = w @ t - 0.7
         z = P.project_halfspaces(t, w[None, :], np.array([b]), M)
         Minv_w = np.linalg.solve(M, w)
         want = t - (w @ t - b) / (w @ Minv_w) * Minv_w
-        assert np.max(np.abs(z - want)) < 1e-7
+        assert np.max(np.abs(z - want)) < 1e-12
+
+
+def _halfspace_instance(rng, n, m):
+    Wt = rng.dirichlet(np.ones(n), size=m)
+    R = rng.normal(size=(m, n))
+    b = np.einsum("ij,ij->i", Wt, R)
+    t = R.max(axis=0) + rng.uniform(0.1, 1.0, size=n)
+    return Wt, b, t
 
 
 def test_halfspace_projection_kkt():
+    """z is feasible and M(t - z) = A_act^T mu with mu >= 0 on the active
+    rows (the KKT conditions of a strictly convex QP: they fix z)."""
     rng = np.random.default_rng(1)
-    for _ in range(10):
-        n, m = 5, 6
-        Wt = rng.dirichlet(np.ones(n), size=m)
-        R = rng.normal(size=(m, n))
-        b = np.einsum("ij,ij->i", Wt, R)
-        t = R.max(axis=0) + rng.uniform(0.1, 1.0, size=n)
-        M = np.eye(n)
-        z = P.project_halfspaces(t, Wt, b, M)
-        assert np.all(Wt @ z <= b + 1e-8)
-        act = np.abs(Wt @ z - b) < 1e-6
-        mu, res = nnls(Wt[act].T, M @ (t - z))
-        assert res < 1e-6
+    for n, m in [(3, 2), (5, 6), (8, 12), (20, 30)]:
+        for _ in range(4):
+            Wt, b, t = _halfspace_instance(rng, n, m)
+            M = _rand_spd(rng, n) if n <= 8 else np.eye(n)
+            z = P.project_halfspaces(t, Wt, b, M)
+            assert np.all(Wt @ z <= b + 1e-10)
+            act = np.abs(Wt @ z - b) < 1e-9
+            mu, res = nnls(Wt[act].T, M @ (t - z))
+            assert res < 1e-10
+
+
+def test_halfspace_projection_brute_force_active_sets():
+    """Every subset S of at most n rows: z_S = argmin ||t - z||_M on
+    A_S z = b_S (a KKT solve); the projection is the z_S that is feasible with
+    non-negative multipliers, unique for a strictly convex objective."""
+    rng = np.random.default_rng(3)
+    for n, m in [(2, 3), (3, 4), (4, 6), (3, 7)]:
+        for _ in range(5):
+            Wt, b, t = _halfspace_instance(rng, n, m)
+            M = _rand_spd(rng, n)
+            Minv = np.linalg.inv(M)
+            found = []
+            for k in range(0, n + 1):
+                for S in itertools.combinations(range(m), k):
+                    S = list(S)
+                    if S:
+                        AS = Wt[S]
+                        K = AS @ Minv @ AS.T
+                        if np.linalg.matrix_rank(K) < len(S):
+                            continue
+                        mu = np.linalg.solve(K, AS @ t - b[S])
+                        if np.any(mu < -1e-12):
+                            continue
+                        z = t - Minv @ AS.T @ mu
+                    else:
+                        z = t.copy()
+                    if np.all(Wt @ z <= b + 1e-11):
+                        found.append(z)
+            assert found
+            z = P.project_halfspaces(t, Wt, b, M)
+            for zb in found:
+                assert np.max(np.abs(z - zb)) < 1e-10
+
+
+def _down_hull_certificate(t, Phi, M, x, lam):
+    """x solves min ||t - x||_M over down(conv Phi) iff x <= Phi^T lam for some
+    lam on the simplex, g = M (t - x) >= 0, and max_k g.phi_k <= g.x (the
+    variational inequality over the generators: the points and the rays -e_i)."""
+    g = M @ (t - x)
+    sg = max(1.0, np.abs(g).max())  # tolerances relative to the scale of g and Phi
+    sp = max(1.0, np.abs(Phi).max())
+    assert np.all(lam >= -1e-15) and abs(lam.sum() - 1) < 1e-12
+    assert np.all(x <= Phi.T @ lam + 1e-12 * sp)
+    assert np.all(g >= -1e-12 * sg)
+    assert np.max(Phi @ g) <= g @ x + 1e-10 * sg * sp
 
 
 def test_down_hull_single_point_is_componentwise_min():
     t = np.array([-1.0, 0.9, 0.3])
     r = np.array([-2.0, 0.5, 0.8])
     x = P.project_down_hull(t, r[None, :], np.eye(3))
-    assert np.max(np.abs(x - np.minimum(t, r))) < 1e-8
+    assert np.max(np.abs(x - np.minimum(t, r))) < 1e-15
+
+
+def test_down_hull_inside_returns_t():
+    pts = np.array([[-1.0, 0.8], [-3.0, 0.95]])
+    for t in ([-2.0, 0.8], [-1.5, 0.5], [-1.0, 0.8]):
+        x = P.project_down_hull(np.array(t), pts, np.eye(2))
+        assert np.max(np.abs(x - np.array(t))) < 1e-15
+
+
+def _hull_instance(rng, n, m):
+    Phi = np.column_stack([-rng.uniform(1, 5, size=(m, max(n // 2, 1))),
+                           rng.uniform(0, 1, size=(m, n - max(n // 2, 1)))])
+    t = Phi.max(axis=0) + rng.uniform(-0.5, 0.5, size=n)
+    return Phi, t
+
+
+def test_down_hull_certificate_general_metric():
+    rng = np.random.default_rng(4)
+    for n, m in [(2, 1), (2, 5), (3, 4), (5, 8), (9, 20), (30, 40)]:
+        for _ in range(4):
+            Phi, t = _hull_instance(rng, n, m)
+            M = _rand_spd(rng, n) if n <= 9 else np.eye(n)
+            x, lam = P.project_down_hull(t, Phi, M, return_lambda=True)
+            _down_hull_certificate(t, Phi, M, x, lam)
+
+
+def test_down_hull_brute_force_active_sets():
+    """2-3 dimensions: every corral of at most n + 1 generators (points of Phi
+    and the rays -e_i, at least one point): its affine minimiser, kept when
+    its coefficients are non-negative and no generator improves on it.  The
+    minimum-norm point is unique, so every kept candidate must be the
+    oracle's projection (in y = R(x - t) coordinates, M = R^T R)."""
+    rng = np.random.default_rng(8)
+    for n, m in [(2, 3), (2, 5), (3, 4), (3, 5)]:
+        for _ in range(4):
+            Phi, t = _hull_instance(rng, n, m)
+            M = _rand_spd(rng, n)
+            R = np.linalg.cholesky(M).T
+            gens = np.vstack([(Phi - t) @ R.T, -R.T])
+            is_pt = np.arange(m + n) < m
+            found = []
+            for k in range(1, n + 2):
+                for S in itertools.combinations(range(m + n), k):
+                    S = list(S)
+                    e = is_pt[S].astype(float)
+                    if e.sum() == 0:
+                        continue
+                    Gs = gens[S]
+                    K = np.block([[Gs @ Gs.T, e[:, None]], [e[None, :], np.zeros((1, 1))]])
+                    if np.linalg.matrix_rank(K) < k + 1:
+                        continue
+                    c = np.linalg.solve(K, np.r_[np.zeros(k), 1.0])[:k]
+                    if np.any(c < -1e-12):
+                        continue
+                    y = c @ Gs
+                    test = gens @ y - np.where(is_pt, y @ y, 0.0)
+                    if np.min(test) < -1e-10:
+                        continue
+                    found.append(t + np.linalg.solve(R, y))
+            assert found
+            x = P.project_down_hull(t, Phi, M)
+            for xb in found:
+                assert np.max(np.abs(x - xb)) < 1e-10
 
 
 def _proj_down_2d_scan(t, pts):
@@ -122,8 +302,32 @@ def test_down_hull_2d_scan():
         t = np.array([-rng.uniform(0.5, 3), rng.uniform(0.3, 1.2)])
         d, x_scan = _proj_down_2d_scan(t, pts)
         x = P.project_down_hull(t, pts, np.eye(2))
-        assert np.linalg.norm(t - x) == pytest.approx(d, abs=1e-6)
-        assert np.max(np.abs(x - x_scan)) < 1e-4
+        assert np.linalg.norm(t - x) == pytest.approx(d, abs=1e-12)
+        assert np.max(np.abs(x - x_scan)) < 1e-6  # the scan's own resolution
+
+
+def test_planted_mistakes_are_caught():
+    """The certificates reject plausible wrong answers: a projection onto
+    conv Phi alone (the rays of the down-closure dropped) and one in the
+    Euclidean metric for a non-identity M."""
+    rng = np.random.default_rng(9)
+    Phi, _ = _hull_instance(rng, 3, 4)
+    t = Phi.max(axis=0) + np.array([-10.0, 0.3, 0.3])  # far below every point in objective 0
+    y, lam, _ = P.min_norm_point(Phi - t)
+    with pytest.raises(AssertionError):
+        _down_hull_certificate(t, Phi, np.eye(3), t + y, lam)
+    # a point whose projection lies inside the segment between two points,
+    # where the metric moves it
+    Phi = np.array([[-1.0, 0.2], [-3.0, 0.9]])
+    t = np.array([-1.5, 0.8])
+    M = np.array([[1.0, 0.6], [0.6, 2.0]])
+    x_e, lam_e = P.project_down_hull(t, Phi, np.eye(2), return_lambda=True)
+    x, lam = P.project_down_hull(t, Phi, M, return_lambda=True)
+    assert np.max(np.abs(x - x_e)) > 1e-3
+    with pytest.raises(AssertionError):
+        _down_hull_certificate(t, Phi, M, x_e, lam_e)
+    _down_hull_certificate(t, Phi, M, x, lam)
+    _down_hull_certificate(t, Phi, np.eye(2), x_e, lam_e)
 
 
 # ---------------------------------------------------------------- Algorithm 1

@@ -252,6 +252,31 @@ def test_finalise_fallback_prefers_moving_over_self_loop():
     assert v[p.init] == pytest.approx(1.0, abs=1e-12)
 
 
+def test_tie_fallback_never_returns_a_two_state_cycle():
+    """Zero weight on the cost (every move is free) and a stale recorded
+    action: on the final values A -> B, B -> A and A -> Y all tie, and the
+    lowest-index near-maximiser of A and of B would send the run between A
+    and B forever (probability 0 instead of 1).  The returned scheduler
+    must reach the goal with the optimal probability: the exact value of the
+    scheduler (dense solve) equals c, which is 1."""
+    a = I.tie_drift_agent()
+    p = C.Product(a, I.sequence_task([0]))
+    r = C.solve_pair(p, 0.0, 1.0, exact_eval=True)
+    q = C.q_values(p, r["rew"], r["x"])
+    A, B = p.init, p.init + 1
+    qa = q[p.state_ptr[A]:p.state_ptr[A + 1]]
+    assert qa[r["a_rec"][A]] < qa.max() - 1e-9  # the fallback branch is taken at A
+    assert r["c"] == pytest.approx(1.0, abs=1e-9)
+    assert r["r_prob"] == pytest.approx(r["c"], abs=1e-9)
+    assert r["mu"][A] == 3 and r["mu"][B] == 1  # A -> Y, B -> A (and on to Y)
+    # the planted mistake: lowest-index non-self-loop near-maximiser without
+    # the anchoring rounds returns the A <-> B cycle, which this pin rejects
+    mu_bad = r["mu"].copy()
+    mu_bad[A], mu_bad[B] = 1, 1
+    v_bad = C.exact_policy_values(p, p.reward_prob(), mu_bad)
+    assert v_bad[A] == pytest.approx(0.0, abs=1e-12)
+
+
 # ---------------------------------------------------------------- DFA and product
 
 
