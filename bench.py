@@ -50,11 +50,12 @@ def make_workload(name, rank=0):
     return getattr(I, gen)(seed={"config_grid32": 1, "config_uneven": 2, "config_large": 3}[gen] + rank), eps
 
 
-# DRAM traffic of the sweep kernels from the committed ncu captures
-# (profiles/k_sweep_{f32,delta}_<workload>.md): one full sweep of the tuned
-# shape, its DRAM bytes and its algorithmic bytes.  Valid only while the sweep
-# kernels' code (sweep.cu up to its finalisation section, comments removed;
-# sha256 prefix) is the one that was profiled and the same shape runs.
+# DRAM traffic of one fully active sweep of each sweep kernel (tuned shape)
+# from an ncu capture of the workload (dram__bytes_read.sum +
+# dram__bytes_write.sum), with that sweep's algorithmic bytes.  Valid only
+# while the sweep kernels' code (sweep.cu up to its finalisation section,
+# comments removed; sha256 prefix) is the one that was profiled and the same
+# shape runs; otherwise the bench reports traffic as null.
 TRAFFIC_PROFILES = {
     ("grid32-10x20-K16", "fp32"): {"sweep_source": "7ab7d883e47baafd", "variant": 0,
                                    "dram_bytes": 148030976 + 28169728, "alg_bytes": 189.1e6},
@@ -226,14 +227,18 @@ def _oracle_sample(inst, budget_s, seed=0, eps1=1e-8):
 
 def _oracle_worker(job):
     """One host process of the parallel oracle sample: solve the given
-    (product, weight) pairs one by one until the budget is spent."""
+    (product, weight) pairs one by one until the budget is spent (only
+    solve_pair is timed); for each pair also the oracle's Algorithm 4 on the
+    engine's scheduler and the states where the two schedulers differ
+    although the oracle's action gap exceeds 1e-9 (untimed)."""
     import numpy as np
 
     from oracle import core as O
 
     pairs, eps1, budget_s = job
     updates, done, solve_s = 0, 0, 0.0
-    for agent, task, wi, wp in pairs:
+    results = []
+    for p, k, agent, task, wi, wp, loc, mu_engine in pairs:
         prod = O.Product(agent, task)
         t0 = time.perf_counter()
         r = O.solve_pair(prod, wi, wp, eps1=eps1)
@@ -242,16 +247,22 @@ def _oracle_worker(job):
         t_mu = int(np.sum(prod.sa_ptr[a + 1] - prod.sa_ptr[a]))
         updates += r["sweeps"] * prod.n_trans + (r["eval_sweeps"][0] + r["eval_sweeps"][1]) * t_mu
         done += 1
+        if mu_engine is not None:
+            idx = O.states_from_locations(prod, loc)
+            mu = np.zeros(prod.n, np.int32)
+            mu[idx[:-1]] = mu_engine[: len(idx) - 1]
+            results.append((p, k, O.scheduler_check(prod, wi, wp, mu, eps1=eps1, r=r)))
         if solve_s > budget_s:
             break
-    return updates, done, solve_s
+    return updates, done, solve_s, results
 
 
-def _oracle_sample_parallel(inst, budget_s, eps1=1e-8, seed=0, procs=None):
+def _oracle_sample_parallel(inst, budget_s, eps1=1e-8, seed=0, procs=None, engine=None):
     """The oracle as it stands, one independent pair per process on every
     host core (spawned processes; each solves pairs of a seeded shuffle until
-    its budget is spent).  Returns (updates/s over the slowest process's
-    solver time, pairs, processes)."""
+    its budget is spent).  engine(p, k) -> (locations, scheduler) of the
+    engine's solve of the same pair, or None.  Returns (updates/s over the
+    slowest process's solver time, pairs, processes, per-pair checks)."""
     import multiprocessing as mp
 
     import numpy as np
@@ -267,13 +278,46 @@ def _oracle_sample_parallel(inst, budget_s, eps1=1e-8, seed=0, procs=None):
         for idx in order[q * per:(q + 1) * per]:
             pp, k = divmod(int(idx), len(W))
             i, j = divmod(pp, nJ)
-            chunk.append((inst.agents[i], inst.tasks[j], float(W[k][i]), float(W[k][nI + j])))
+            loc, mu = engine(pp, k) if engine is not None else (None, None)
+            chunk.append((pp, k, inst.agents[i], inst.tasks[j], float(W[k][i]), float(W[k][nI + j]), loc, mu))
         jobs.append((chunk, eps1, budget_s))
     with mp.get_context("spawn").Pool(procs) as pool:
         res = pool.map(_oracle_worker, jobs)
-    updates = sum(u for u, _, _ in res)
-    secs = max(t for _, _, t in res)
-    return updates / secs, sum(d for _, d, _ in res), procs
+    updates = sum(r[0] for r in res)
+    secs = max(r[2] for r in res)
+    return updates / secs, sum(r[1] for r in res), procs, [x for r in res for x in r[3]]
+
+
+def _parity(results, full, W, nI, nJ):
+    """The engine against the oracle on the oracle's sample of the benched
+    batch.  c and the scalarised value w.r are unique; r_cost and r_prob are
+    unique only where the optimal scheduler is (a near-tie in w.r can trade
+    cost against probability), so each objective is compared with the
+    oracle's Algorithm 4 on the engine's own scheduler, and the schedulers
+    are compared wherever the oracle's action gap exceeds 1e-9."""
+    dc, dw, drc, drp, drc_own = [], [], [], [], []
+    gap_states = gap_mismatch = 0
+    for p, k, r in results:
+        i, j = divmod(p, nJ)
+        wi, wp = W[k][i], W[k][nI + j]
+        rc, rp = full["r_cost"][k, i, j], full["r_prob"][k, i, j]
+        dc.append(abs(full["c"][k, i, j] - r["c"]))
+        dw.append(abs(wi * rc + wp * rp - r["c"]))
+        drc.append(abs(rc - r["mu_r_cost"]))
+        drp.append(abs(rp - r["mu_r_prob"]))
+        if wi > 0 and wp > 0:
+            drc_own.append(max(abs(rc - r["r_cost"]), abs(rp - r["r_prob"])))
+        gap_states += r["gap_states"]
+        gap_mismatch += r["gap_mismatch"]
+    return {"reference": "FP64 C oracle (Algorithm 3 to eps_vi, scheduler, Algorithm 4 to 1e-11)",
+            "pairs": len(dc), "tolerance": 1e-6, "max_abs_c": max(dc, default=None),
+            "max_abs_w_dot_r": max(dw, default=None),
+            "max_abs_r_cost": max(drc, default=None), "max_abs_r_prob": max(drp, default=None),
+            "objectives_of": "the engine's scheduler, evaluated by the oracle's Algorithm 4",
+            "policy_states_checked": gap_states, "policy_mismatches": gap_mismatch,
+            "max_abs_r_vs_oracle_scheduler": max(drc_own, default=None),
+            "note": "the last figure compares with the oracle's own scheduler; it differs from 0 only where "
+                    "two schedulers tie within 1e-9 in w.r"}
 
 
 def run_reference(args):
@@ -431,8 +475,11 @@ def run_engine(args):
     _barrier(ws)
     from paper_2305_04397_gb300 import morap as M
 
-    # weak scaling: every rank solves its own instance of the workload
-    inst, eps_vi = make_workload(args.workload, rank)
+    strong = args.scaling == "strong"
+    # weak scaling: every rank solves its own instance of the workload;
+    # strong scaling: the products of one instance are dealt to the ranks
+    # (sharded Algorithm 2: all-gather of c, replicated assignment, all-reduce of r)
+    inst, eps_vi = make_workload(args.workload, 0 if strong else rank)
     nI, nJ = len(inst.agents), len(inst.tasks)
     W = np.ascontiguousarray(inst.weights)
     t_point = inst.thresholds[0]
@@ -443,16 +490,34 @@ def run_engine(args):
     cfg.eps_vi = eps_vi
     cfg.polish = args.polish
     cfg.in_place = 1 if args.in_place else 0
-    ctx = M.Context(cfg)
-    ctx.add(inst.agents, inst.tasks)
-    fp = ctx.build(stream)
+    if strong:
+        from paper_2305_04397_gb300 import sharded as S
+
+        parts = S.partition_products(S.product_loads(inst.agents, inst.tasks), ws)
+        shard = S.EngineShard(inst.agents, inst.tasks, parts[rank], cfg, stream)
+        ctx = shard.ctx
+        fp = ctx.build(stream)
+
+        class _Local:  # one rank: the collectives are the identity
+            def all_gather(self, a):
+                return [a]
+
+            def all_reduce_sum(self, a):
+                return a
+
+        comm = S.TorchComm(device=torch.device("cuda", local)) if ws > 1 else _Local()
+        sharded = S.ShardedSupportingPoints(shard, parts, nI, nJ, comm)
+    else:
+        ctx = M.Context(cfg)
+        ctx.add(inst.agents, inst.tasks)
+        fp = ctx.build(stream)
 
     def step(e2e=False):
         if e2e:
             f = ctx.build(stream)  # host arrays -> device, then construction
         else:
             ctx.rebuild(stream)  # construction from the resident arrays
-        out = ctx.supporting_points(W, stream)
+        out = sharded(W) if strong else ctx.supporting_points(W, stream)
         st = ctx.stats()
         r = out["r"]
         b = np.einsum("kn,kn->k", W, r)
@@ -463,7 +528,7 @@ def run_engine(args):
 
     def timed(n, e2e):
         tot = {"updates": 0, "bytes_fp32": 0, "ms_fp32": 0.0, "sweeps32": 0, "sweeps64": 0, "launches": 0, "h2d": 0,
-               "d2h": 0,
+               "d2h": 0, "skipped32": 0, "computed32": 0, "skipped64": 0, "computed64": 0, "anchored": 0,
                "variant_fp32": -1, "variant_fp64": -1,
                "ms_fp64": 0.0, "ms_eval": 0.0, "bytes_fp64": 0, "bytes_eval": 0}
         _barrier(ws)
@@ -482,6 +547,11 @@ def run_engine(args):
             tot["ms_eval"] += st["ms_eval"]
             tot["sweeps32"] += st["fp32_sweeps"]
             tot["sweeps64"] += st["fp64_sweeps"]
+            tot["skipped32"] += st["skipped_fp32"]
+            tot["computed32"] += st["computed_fp32"]
+            tot["skipped64"] += st["skipped_fp64"]
+            tot["computed64"] += st["computed_fp64"]
+            tot["anchored"] += st["anchored_states"]
             tot["variant_fp32"], tot["variant_fp64"] = st["variant_fp32"], st["variant_fp64"]
             tot["polish"] = st["polish"]
             tot["launches"] += st["kernel_launches"] + 2  # + the two construction kernels
@@ -536,21 +606,37 @@ def run_engine(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
         "dtype": "f32+df64", "data": "synthetic",
         "config": {"workload": args.workload, "products": nI * nJ, "K": len(W), "states": fp["n_states"],
                    "transitions": fp["n_trans"], "eps_vi": cfg.eps_vi, "eps_eval": cfg.eps_eval,
                    "polish": ["fp32 residual correction", "double-float"][cfg.polish],
                    "sweeps": "in place" if cfg.in_place else "synchronous",
                    "l2": "per-step working set (CSR + FP32/FP64 value buffers) exceeds the 129 MB L2; no flush",
-                   "parallelism": f"{ws} independent instance(s), one per GPU"},
+                   "parallelism": (f"one instance, its products dealt to {ws} GPU(s) (LPT on transitions x "
+                                   f"expected sweeps; all-gather of c, all-reduce of r per batch)") if strong
+                   else f"{ws} independent instance(s), one per GPU"},
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"] // args.steps,
                 "d2h_bytes_per_step": e2e["d2h"] // args.steps, "ms_per_step": e2e_secs * 1e3 / args.steps},
         "gpu_launches": dev["launches"],
+        "updates_counted": "executed only: work items a sweep skips exactly (nothing they read changed) and "
+                           "evaluation padding slots count neither as updates nor as bytes",
+        "skipped_share": {"fp32": dev["skipped32"] / max(dev["skipped32"] + dev["computed32"], 1),
+                          "polish": dev["skipped64"] / max(dev["skipped64"] + dev["computed64"], 1)},
+        "anchored_states_per_step": dev["anchored"] / args.steps,
         "launch_mode": args.launch_mode,
         "clocks": clocks,
     }
+    if strong:  # the plain, oracle and serving legs need the whole instance on one context
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        shard.close()
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return 0
     if rank == 0 and not args.no_plain:
         # plain per-model FP64 GPU VI on a sample of the same pairs
         rng = np.random.default_rng(0)
@@ -570,11 +656,22 @@ def run_engine(args):
             "speedup_time_to_solution": alg2_ms / (secs * 1e3 / args.steps),
         }
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, pairs, procs = _oracle_sample_parallel(inst, args.cpu_budget, eps1=eps_vi)
+        # every pair of the benched batch evaluated by the engine (outside the
+        # timed region), for the per-objective comparison with the oracle
+        full = ctx.solve(W, stream)
+        locs = {}
+
+        def engine_pair(p, k):
+            if p not in locs:
+                locs[p] = M.morap_product_locations(ctx.h, p)
+            return locs[p], M.morap_last_policy(ctx.h, k, p)[0]
+
+        v, pairs, procs, results = _oracle_sample_parallel(inst, args.cpu_budget, eps1=eps_vi, engine=engine_pair)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
                                 "sample": f"{pairs} (product, weight) pairs of the workload in a seeded order, one per "
                                           f"process on {procs} host cores, ~{args.cpu_budget:.0f} s of FP64 C oracle "
                                           f"work per process (Algorithm 3 + both Algorithm 4 evaluations per pair)"}
+        line["parity"] = _parity(results, full, W, nI, nJ)
     ctx.close()
     if rank == 0 and not args.no_serving:
         line["serving"] = run_serving(M, args)
@@ -602,6 +699,9 @@ def main():
     ap.add_argument("--polish", type=int, choices=[0, 1], default=0,
                     help="second phase: 0 FP32 residual correction (default), 1 double-float sweeps")
     ap.add_argument("--in-place", action="store_true", help="in-place (Gauss-Seidel order) sweeps")
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="weak (default): one instance per GPU; strong: the products of one instance dealt to the "
+                         "GPUs by the sharded Algorithm 2 driver")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--plain-pairs", type=int, default=6)

@@ -162,6 +162,19 @@ int morap_add_agent(morap_ctx *ctx, int32_t n_states, int32_t s0, const int32_t 
 int morap_add_task(morap_ctx *ctx, int32_t n_locs, int32_t q0, int32_t n_ap, const int32_t *ap_ids,
                    const int32_t *delta, const uint8_t *accepting, int32_t *task_id);
 
+/* Restrict the context to a list of products (before morap_build): only
+ * M_{agent[e]} (x) A_{task[e]} for e = 0 .. n_pairs-1 is built, and product p
+ * of the context is the p-th pair of the list (without a list, product p is
+ * i * |J| + j for every agent i and task j).  For drivers that spread the
+ * independent products of one instance over several devices (Sec. 3.2: the
+ * products share nothing until the assignment), one device's share per
+ * context.  A context with a list answers morap_solve (c_out[K][n_pairs],
+ * the list's order) and morap_evaluate; morap_supporting_points and
+ * morap_query need every pair (ESTATE).
+ * Errors: EINVAL (negative index, a pair listed twice; an agent or task not
+ * added is reported by morap_build), ESTATE after build. */
+int morap_select_pairs(morap_ctx *ctx, int32_t n_pairs, const int32_t *agent, const int32_t *task);
+
 typedef struct morap_footprint {
     int64_t n_products;   /* |I| * |J|                                        */
     int64_t n_states;     /* product states over all products (done slots included) */
@@ -192,6 +205,8 @@ int morap_rebuild(morap_ctx *ctx, void *stream);
  * cost and probability of EVERY product under its returned scheduler.
  *   W[K][|I|+|J|]           weight vectors (entries >= 0)
  *   c_out[K][|I|][|J|]      c_ij = optimal scalarised value at (s_i0, q_j0)
+ *                           ([K][n_pairs] in list order for a context with
+ *                           morap_select_pairs)
  *   rcost_out, rprob_out    same layout: E[rho_i] and E[rho_{|I|+j}] under
  *                           the returned scheduler (may be NULL to skip
  *                           Algorithm 4)
@@ -233,9 +248,10 @@ typedef struct morap_solve_stats {
     int32_t fp32_sweeps;      /* sweep launches of the FP32 phase (0 if unused)    */
     int32_t fp64_sweeps;      /* sweep launches of the second (polish) phase         */
     int32_t eval_sweeps;      /* sweep launches of the evaluation phase             */
-    int64_t updates_fp32;     /* transition-updates: one (s,a,s') term for one weight in one sweep */
+    int64_t updates_fp32;     /* transition-updates executed: one (s,a,s') term for one weight in one
+                                 sweep (work items skipped exactly are not counted)   */
     int64_t updates_fp64;
-    int64_t updates_eval;     /* one (s, mu(s), s') term for one objective pair      */
+    int64_t updates_eval;     /* one (s, mu(s), s') term for one objective (cost or probability) */
     int64_t bytes_fp32;       /* algorithmic bytes the sweeps had to move           */
     int64_t bytes_fp64;
     int64_t bytes_eval;
@@ -260,6 +276,10 @@ typedef struct morap_solve_stats {
                                  changed; their values are reproduced bit for bit)     */
     int64_t skipped_fp64;
     int64_t work_items;       /* work items (64 states of one product) per full sweep  */
+    int64_t computed_fp32;    /* work-item sweeps computed (skipped ones excluded)   */
+    int64_t computed_fp64;
+    int64_t anchored_states;  /* (state, weight) entries whose recorded action was not kept and
+                                 that the scheduler's anchoring rounds decided          */
 } morap_solve_stats;
 
 int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out);

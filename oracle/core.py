@@ -176,6 +176,80 @@ def solve_pair(prod, w_cost, w_prob, eps1=1e-8, eps_eval=1e-11, tau=1e-9, max_sw
     }
 
 
+def states_from_locations(prod, loc):
+    """Oracle state index of each state of a product whose states are listed
+    as pl * S + s over a list `loc` of non-done DFA locations (pl-th entry =
+    the location), followed by one done state: for reading a scheduler
+    computed on another layout of the same product."""
+    S = prod.S
+    pos = prod.dfa["nd_pos"]
+    out = np.empty(len(loc) * S + 1, np.int64)
+    for pl, q in enumerate(loc):
+        out[pl * S:(pl + 1) * S] = int(pos[q]) * S + np.arange(S)
+    out[-1] = prod.done
+    return out
+
+
+def scheduler_check(prod, w_cost, w_prob, mu, eps1=1e-8, eps_eval=1e-11, tau_gap=1e-9, r=None):
+    """For a scheduler mu given in oracle state order: Algorithm 4 of its cost
+    and probability (an exact solve when the product has at most 512
+    states), and the number of states where the oracle's own scheduler has
+    an action gap above tau_gap on its final values and mu differs from it.
+    r: the oracle's solve_pair result for this pair, when already computed."""
+    if r is None:
+        r = solve_pair(prod, w_cost, w_prob, eps1=eps1, eps_eval=eps_eval)
+    mu = np.asarray(mu, np.int32)
+    if prod.n <= 512:
+        vc = exact_policy_values(prod, prod.reward_cost(), mu)[prod.init]
+        vp = exact_policy_values(prod, prod.reward_prob(), mu)[prod.init]
+    else:
+        vc = alg4(prod, prod.reward_cost(), mu, eps_eval, max_sweeps=1_000_000)[0][prod.init]
+        vp = alg4(prod, prod.reward_prob(), mu, eps_eval, max_sweeps=1_000_000)[0][prod.init]
+    # the action gap of the oracle's choice at every state (vectorised over rows)
+    q = q_values(prod, r["rew"], r["x"])
+    counts = np.diff(prod.state_ptr[: prod.n])
+    states = np.repeat(np.arange(prod.n - 1), counts[: prod.n - 1])
+    chosen = prod.state_ptr[: prod.n - 1] + r["mu"][: prod.n - 1]
+    q_other = q.copy()
+    q_other[chosen] = -np.inf
+    best_other = np.full(prod.n - 1, -np.inf)
+    np.maximum.at(best_other, states, q_other[: len(states)])
+    gap = q[chosen] - best_other
+    sel = gap > tau_gap
+    checked = int(sel.sum())
+    mismatch = int(np.sum(mu[: prod.n - 1][sel] != r["mu"][: prod.n - 1][sel]))
+    return {"c": r["c"], "r_cost": r["r_cost"], "r_prob": r["r_prob"], "mu_r_cost": float(vc), "mu_r_prob": float(vp),
+            "gap_states": checked, "gap_mismatch": mismatch}
+
+
+def solve_pair_job(job):
+    """One (agent, task, w_cost, w_prob, eps1[, loc, mu]) job, for process
+    pools of the tests (spawned processes; the product is rebuilt in the
+    worker).  Without a scheduler: (c, r_cost, r_prob) of solve_pair.  With
+    another layout's location list `loc` and a scheduler `mu` on that
+    layout: scheduler_check of mu."""
+    agent, task, w_cost, w_prob, eps1 = job[:5]
+    prod = Product(agent, task)
+    if len(job) == 5:
+        r = solve_pair(prod, w_cost, w_prob, eps1=eps1)
+        return r["c"], r["r_cost"], r["r_prob"]
+    loc, mu_other = job[5], np.asarray(job[6])
+    idx = states_from_locations(prod, loc)
+    mu = np.zeros(prod.n, np.int32)
+    mu[idx[:-1]] = mu_other[: len(idx) - 1]
+    return scheduler_check(prod, w_cost, w_prob, mu, eps1=eps1)
+
+
+def solve_pairs_pooled(jobs, procs=None):
+    """solve_pair_job over many jobs on every host core (spawn context, so
+    it is safe in a process that already uses a GPU)."""
+    import multiprocessing as mp
+
+    procs = procs or len(os.sched_getaffinity(0))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(solve_pair_job, jobs, chunksize=max(1, len(jobs) // (4 * procs)))
+
+
 # ----------------------------------------------------------------------------
 # exact values of a fixed scheduler and brute force over schedulers
 

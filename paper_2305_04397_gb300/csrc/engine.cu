@@ -83,6 +83,9 @@ struct morap_ctx {
 
     // products
     int P = 0, nI = 0, nJ = 0;
+    // morap_select_pairs: the (agent, task) of each product to build, in
+    // order; empty = every agent x task pair, product p = i * |J| + j
+    std::vector<int32_t> sel_agent, sel_task;
     uint32_t TS = 0, TSA = 0, TT = 0;
     std::vector<ProdDesc> h_prods;
     std::vector<int4> h_chunks;
@@ -146,6 +149,7 @@ struct morap_ctx {
     unsigned int *elist[3] = {};
     int32_t *esweeps = nullptr;
     uint8_t *efrozen = nullptr;
+    uint32_t *item_tmu = nullptr, *pair_tmu = nullptr;  // scheduler transitions per eval item / pair
     double *d_rc = nullptr, *d_rp = nullptr;
     int32_t *ecol = nullptr;
     float2 *ep = nullptr, *ecost = nullptr;
@@ -531,6 +535,8 @@ int ensure_eval(morap_ctx *c, size_t n_pairs, size_t n_chunks, size_t n_states) 
     CKR(dev_alloc(c, L, &c->ecol, n_states * (size_t)c->max_row * sizeof(int32_t)));
     CKR(dev_alloc(c, L, &c->ep, n_states * (size_t)c->max_row * sizeof(float2)));
     CKR(dev_alloc(c, L, &c->ecost, n_states * sizeof(float2)));
+    CKR(dev_alloc(c, L, &c->item_tmu, n_chunks * sizeof(uint32_t)));
+    CKR(dev_alloc(c, L, &c->pair_tmu, n_pairs * sizeof(uint32_t)));
     c->eval_cap_pairs = n_pairs;
     c->eval_cap_chunks = n_chunks;
     c->eval_cap_states = n_states;
@@ -552,6 +558,8 @@ int ensure_eval(morap_ctx *c, size_t n_pairs, size_t n_chunks, size_t n_states) 
     }
     e.sweeps_pair = c->esweeps;
     e.frozen = c->efrozen;
+    e.item_tmu = c->item_tmu;
+    e.pair_tmu = c->pair_tmu;
     e.ctl = c->ctl + 2;
     e.E[0] = c->E[0];
     e.E[1] = c->E[1];
@@ -710,12 +718,15 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     if (mixed) {
         st.fp32_sweeps = (int32_t)hctl[0].sweep_base;
         st.skipped_fp32 = (int64_t)hctl[0].skipped;
+        st.computed_fp32 = (int64_t)hctl[0].computed;
         st.updates_fp32 = (int64_t)hctl[0].updates;
         st.bytes_fp32 = (int64_t)hctl[0].bytes;
         st.ms_fp32 = ms_between(c->ev[0], c->ev[1]);
     }
     st.fp64_sweeps = (int32_t)hctl[1].sweep_base;
     st.skipped_fp64 = (int64_t)hctl[1].skipped;
+    st.computed_fp64 = (int64_t)hctl[1].computed;
+    st.anchored_states = (int64_t)hctl[1].undecided;
     st.work_items = (int64_t)n_items;
     st.updates_fp64 = (int64_t)hctl[1].updates;
     st.bytes_fp64 = (int64_t)hctl[1].bytes;
@@ -790,6 +801,8 @@ int run_evaluation_group(morap_ctx *c, const std::vector<int4> &pairs_in, cudaSt
     }
     CK(cudaMemsetAsync(c->E[0], 0, off * sizeof(float4), s));
     CK(cudaMemsetAsync(c->E[1], 0, off * sizeof(float4), s));
+    CK(cudaMemsetAsync(c->item_tmu, 0, chunks.size() * sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(c->pair_tmu, 0, std::max<size_t>(npair, 1) * sizeof(uint32_t), s));
     {
         EvalArgs ea = c->eargs;  // the scheduler layout of the last solve
         ea.Kp = c->Kp;
@@ -836,8 +849,9 @@ int run_evaluation_group(morap_ctx *c, const std::vector<int4> &pairs_in, cudaSt
     rc.assign(h, h + npair);
     rp.assign(h + npair, h + 2 * npair);
     not_conv = 0;
-    // a pair whose task is done in its initial state has no states to
-    // evaluate (its values are 0): nothing can fail to converge there
+    // a product without non-done states (every location of its task is
+    // done) has nothing to evaluate (its values are 0): nothing can fail to
+    // converge there
     for (size_t e = 0; e < npair; ++e) not_conv += hf[e] == 0 && c->h_prods[pairs[e].x].n_nd > 0;
     c->stats.eval_sweeps = (int32_t)std::max(n_loop ? hctl->sweep_base : 0u, hctl->block_sweeps);
     c->stats.updates_eval = (int64_t)hctl->updates;
@@ -1055,7 +1069,12 @@ int run_construction(morap_ctx *c, cudaStream_t s) {
 
 int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
     if (c->agents.empty() || c->tasks.empty()) return fail(MORAP_ESTATE, "build: add at least one agent and one task");
-    const int nI = (int)c->agents.size(), nJ = (int)c->tasks.size(), P = nI * nJ;
+    const int nI = (int)c->agents.size(), nJ = (int)c->tasks.size();
+    const bool selected = !c->sel_agent.empty();
+    const int P = selected ? (int)c->sel_agent.size() : nI * nJ;
+    for (size_t e = 0; e < c->sel_agent.size(); ++e)
+        if (c->sel_agent[e] >= nI || c->sel_task[e] >= nJ)
+            return fail(MORAP_EINVAL, "build: selected pair " + std::to_string(e) + " names an agent or task not added");
     // host-side descriptors
     std::vector<AgentDesc> ad(nI);
     std::vector<int32_t> a_sp, a_sap, a_succ, a_lp, a_la;
@@ -1109,9 +1128,9 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
     std::vector<ProdDesc> prods(P);
     std::vector<int4> chunks;
     uint64_t TS = 0, TSA = 0, TT = 0, letters = 0, max_work = 1;
-    for (int i = 0; i < nI; ++i)
-        for (int j = 0; j < nJ; ++j) {
-            ProdDesc &pd = prods[i * nJ + j];
+    for (int p = 0; p < P; ++p) {
+            const int i = selected ? c->sel_agent[p] : p / nJ, j = selected ? c->sel_task[p] : p % nJ;
+            ProdDesc &pd = prods[p];
             const AgentDesc &a = ad[i];
             const TaskDesc &t = td[j];
             pd.agent = i;
@@ -1136,7 +1155,7 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
             if (TS >= 0x7fffffffull || TSA >= 0xffffffffull || TT >= 0xffffffffull)
                 return fail(MORAP_ENOMEM, "products exceed the 32-bit index range of one context");
             for (uint32_t b = 0; b < pd.n_nd; b += kChunk)
-                chunks.push_back(make_int4(i * nJ + j, (int)b, (int)std::min<uint32_t>(pd.n_nd, b + kChunk), b == 0));
+                chunks.push_back(make_int4(p, (int)b, (int)std::min<uint32_t>(pd.n_nd, b + kChunk), b == 0));
         }
     // Same layout as the resident one: refill in place and keep the solve
     // buffers and their graphs.
@@ -1357,6 +1376,24 @@ int morap_add_task(morap_ctx *ctx, int32_t n_locs, int32_t q0, int32_t n_ap, con
     API_END
 }
 
+int morap_select_pairs(morap_ctx *ctx, int32_t n_pairs, const int32_t *agent, const int32_t *task) {
+    API_BEGIN
+    if (!ctx) return fail(MORAP_EINVAL, "ctx is NULL");
+    if (ctx->built) return fail(MORAP_ESTATE, "select_pairs after build");
+    if (n_pairs < 0 || (n_pairs > 0 && (!agent || !task))) return fail(MORAP_EINVAL, "bad argument");
+    std::vector<int64_t> keys((size_t)n_pairs);
+    for (int e = 0; e < n_pairs; ++e) {
+        if (agent[e] < 0 || task[e] < 0) return fail(MORAP_EINVAL, "negative agent or task index");
+        keys[e] = ((int64_t)agent[e] << 32) | (int64_t)task[e];
+    }
+    std::sort(keys.begin(), keys.end());
+    if (std::adjacent_find(keys.begin(), keys.end()) != keys.end()) return fail(MORAP_EINVAL, "a pair is listed twice");
+    ctx->sel_agent.assign(agent, agent + n_pairs);
+    ctx->sel_task.assign(task, task + n_pairs);
+    return MORAP_OK;
+    API_END
+}
+
 int morap_build(morap_ctx *ctx, void *stream, morap_footprint *fp) {
     API_BEGIN
     if (!ctx) return fail(MORAP_EINVAL, "ctx is NULL");
@@ -1448,6 +1485,8 @@ int morap_supporting_points(morap_ctx *ctx, int32_t K, const double *W, void *st
     API_BEGIN
     if (!ctx || !W || !r_out) return fail(MORAP_EINVAL, "null argument");
     if (!ctx->built) return fail(MORAP_ESTATE, "supporting_points before build");
+    if (!ctx->sel_agent.empty())
+        return fail(MORAP_ESTATE, "supporting_points needs every agent x task product (the context has a pair list)");
     if (K < 1) return fail(MORAP_EINVAL, "K must be >= 1");
     CK(cudaSetDevice(ctx->cfg.device));
     CKR(check_weights(ctx, K, W));

@@ -135,6 +135,7 @@ struct LoopCtl {
     unsigned long long bytes;
     unsigned int undecided;  // scheduler states whose recorded action is not kept (k_finalize)
     unsigned int decided;    // states one anchoring round decided (k_anchor)
+    unsigned int computed;   // work items a sweep computed (not skipped)
 };
 
 #ifndef MORAP_CHUNK
@@ -221,6 +222,10 @@ struct EvalArgs {
     float2 *ep;      // double-float probability (0 for padding)
     float2 *ecost;   // double-float cost of the scheduler's action, at off + s
     int stride;      // slots per state: the longest action row of any agent
+    // transitions of the scheduler's rows (padding excluded) per evaluation
+    // work item and per pair, summed by k_eval_compact (zeroed before it)
+    uint32_t *item_tmu;
+    uint32_t *pair_tmu;
 };
 
 // Engine helpers the serving layer uses (engine.cu).

@@ -642,9 +642,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     }
     __shared__ struct {
         unsigned long long updates, bytes;
-        unsigned int skipped;
+        unsigned int skipped, computed;
     } b_stats;
-    if (threadIdx.x == 0) b_stats.updates = b_stats.bytes = 0ull, b_stats.skipped = 0u;
+    if (threadIdx.x == 0) b_stats.updates = b_stats.bytes = 0ull, b_stats.skipped = b_stats.computed = 0u;
     __syncthreads();
     const unsigned int n_items = ctl->cnt[cur];
     const unsigned int sweep = ctl->sweep_base + pos;
@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     // together when the values do not fit in L2; batches would interleave
     // the warps' items from one sweep to the next.
     unsigned long long w_updates = 0, w_bytes = 0;  // lane 0's running sums
-    unsigned int w_skipped = 0;
+    unsigned int w_skipped = 0, w_computed = 0;
     unsigned int kept = 0u;
     int n_kept = 0;  // warp-uniform
     auto flush_kept = [&]() {
@@ -738,12 +738,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             // sweep, so it would reproduce its values bit for bit (and both
             // value buffers already hold them)
             if (!__any_sync(0xffffffffu, in_chg)) {
-                if (lane == 0) {
+                if (lane == 0) {  // no update executed and no byte moved
                     a.chg[cur][item] = 0;
                     ++w_skipped;
-                    // the sweep still updates these states (to the same values)
-                    w_updates += (unsigned long long)iw.x *
-                                 (unsigned long long)(__popc(act_w[0]) + __popc(act_w[1]));
                 }
                 continue;
             }
@@ -837,6 +834,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             w_bytes += 2ull * n_s * ROW * 4;
             if (any_active) {
                 const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
+                ++w_computed;
                 w_updates += (unsigned long long)iw.x * (unsigned long long)n_act;
                 // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
                 w_bytes += 8ull * (n_s + 1) + 4ull * (iw.y + 1) + 4ull * (1 + Ar::WORDS) * iw.x;
@@ -851,12 +849,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         if (w_updates) atomicAdd(&b_stats.updates, w_updates);
         if (w_bytes) atomicAdd(&b_stats.bytes, w_bytes);
         if (w_skipped) atomicAdd(&b_stats.skipped, w_skipped);
+        if (w_computed) atomicAdd(&b_stats.computed, w_computed);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         if (b_stats.updates) atomicAdd(&ctl->updates, b_stats.updates);
         if (b_stats.bytes) atomicAdd(&ctl->bytes, b_stats.bytes);
         if (b_stats.skipped) atomicAdd(&ctl->skipped, b_stats.skipped);
+        if (b_stats.computed) atomicAdd(&ctl->computed, b_stats.computed);
     }
 }
 
@@ -1041,6 +1041,8 @@ __global__ void __launch_bounds__(kThreads) k_eval_compact(EvalArgs a, int n_chu
         const uint32_t u = pd.state_off + (uint32_t)s;
         const uint32_t sa = a.state_sa[u] + a.policy[(size_t)u * a.Kp + pr.y];
         const uint32_t t0 = a.sa_tr[sa], t1 = a.sa_tr[sa + 1];
+        atomicAdd(&a.item_tmu[item], t1 - t0);  // the scheduler's transitions, for the statistics
+        atomicAdd(&a.pair_tmu[ch.x], t1 - t0);
         a.ecost[off + s] = a.costdf[sa];
         for (int j = 0; j < a.stride; ++j) {
             const size_t at = off * a.stride + (size_t)j * n1 + s;
@@ -1173,11 +1175,14 @@ __global__ void __launch_bounds__(kThreads) k_eval_sweep(EvalArgs a, int pos) {
             if (active && mx > 0.0f) atomic_max_nonneg(a.res[cur] + e, (double)mx);
             const unsigned long long n_s = (unsigned long long)(ch.z - ch.y);
             // values read + written (16 B each); when computing also the cost
-            // (8) and every slot's successor and probability (4 + 8)
+            // (8) and the successor and probability (4 + 8) of each of the
+            // scheduler's transitions (padding slots are not algorithmic);
+            // updates: one term per transition and objective
             b_bytes += n_s * 32ull;
             if (active) {
-                b_bytes += n_s * (8ull + 12ull * (unsigned long long)stride);
-                b_updates += n_s * (unsigned long long)stride * 2ull;
+                const unsigned long long tm = a.item_tmu[item];
+                b_bytes += n_s * 8ull + 12ull * tm;
+                b_updates += tm * 2ull;
             }
         }
         __syncthreads();
@@ -1394,10 +1399,12 @@ __global__ void __launch_bounds__(kEvalBlockThreads, 1) k_eval_block(EvalArgs a,
     if (threadIdx.x == 0) {
         a.frozen[e] = converged ? 1 : 0;
         a.sweeps_pair[e] = (int32_t)sweeps;
-        // per sweep the scheduler's rows and costs are read once (the
-        // table pass reads them once more); the values stay in shared memory
-        const unsigned long long per = (unsigned long long)n * (8ull + 12ull * (unsigned long long)stride);
-        atomicAdd(&a.ctl->updates, (unsigned long long)sweeps * n * (unsigned long long)stride * 2ull);
+        // per sweep the scheduler's transitions and costs are read once (the
+        // table pass reads them once more); the values stay in shared memory.
+        // Padding slots count neither as bytes nor as updates.
+        const unsigned long long tm = a.pair_tmu[e];
+        const unsigned long long per = (unsigned long long)n * 8ull + 12ull * tm;
+        atomicAdd(&a.ctl->updates, (unsigned long long)sweeps * tm * 2ull);
         atomicAdd(&a.ctl->bytes, (unsigned long long)(sweeps + (sweeps > sweeps_a ? 1 : 0)) * per + 16ull * n);
         atomicMax(&a.ctl->block_sweeps, sweeps);
     }
@@ -1472,6 +1479,7 @@ __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_it
         ctl->bytes = 0;
         ctl->undecided = 0;
         ctl->decided = 0;
+        ctl->computed = 0;
     }
 }
 

@@ -73,6 +73,7 @@ class SolveStats(ctypes.Structure):
         ("variant_fp32", ctypes.c_int32), ("variant_fp64", ctypes.c_int32), ("polish", ctypes.c_int32),
         ("ms_tune", ctypes.c_double),
         ("skipped_fp32", ctypes.c_int64), ("skipped_fp64", ctypes.c_int64), ("work_items", ctypes.c_int64),
+        ("computed_fp32", ctypes.c_int64), ("computed_fp64", ctypes.c_int64), ("anchored_states", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -129,6 +130,7 @@ _SIGS = {
     "morap_verify": (ctypes.c_int, [_P, _DP, _DP, ctypes.c_double, ctypes.c_int32, _P, ctypes.POINTER(PointResult)]),
     "morap_assign_max": (ctypes.c_int, [ctypes.c_int32, _DP, _I32P]),
     "morap_assign_tasks": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _DP, _I32P]),
+    "morap_select_pairs": (ctypes.c_int, [_P, ctypes.c_int32, _I32P, _I32P]),
     "morap_random_assignment": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _DP, _I32P, _DP]),
     "morap_evaluate": (ctypes.c_int, [_P, ctypes.c_int32, _I32P, _I32P, _P, _DP, _DP]),
     "morap_pareto_create": (ctypes.c_int, [ctypes.c_int32, _DP, _DP, ctypes.c_double, ctypes.c_int32,
@@ -247,14 +249,25 @@ def morap_rebuild(ctx, stream=None):
     return _check(lib().morap_rebuild(ctx, _stream(stream)))
 
 
-def morap_solve(ctx, W, n_agents, n_tasks, stream=None, evaluate=True, check=True):
+def morap_select_pairs(ctx, agent, task):
+    a = _arr(agent, np.int32)
+    t = _arr(task, np.int32)
+    if a.shape != t.shape:
+        raise ValueError("agent and task lists differ in length")
+    return _check(lib().morap_select_pairs(ctx, len(a), _ptr(a, ctypes.c_int32), _ptr(t, ctypes.c_int32)))
+
+
+def morap_solve(ctx, W, n_agents, n_tasks, stream=None, evaluate=True, check=True, n_pairs=None):
+    """c, r_cost, r_prob and status as [K][|I|][|J|] arrays, or [K][n_pairs]
+    for a context restricted by morap_select_pairs."""
     W = _arr(np.atleast_2d(W), np.float64)
     K = W.shape[0]
-    P = n_agents * n_tasks
-    c = np.zeros((K, n_agents, n_tasks))
+    shape = (K, n_pairs) if n_pairs is not None else (K, n_agents, n_tasks)
+    P = int(np.prod(shape[1:]))
+    c = np.zeros(shape)
     rc = np.zeros_like(c) if evaluate else None
     rp = np.zeros_like(c) if evaluate else None
-    st = np.zeros((K, n_agents, n_tasks), np.int32)
+    st = np.zeros(shape, np.int32)
     code = lib().morap_solve(ctx, K, _ptr(W, ctypes.c_double), _stream(stream), _ptr(c, ctypes.c_double),
                              _ptr(rc, ctypes.c_double), _ptr(rp, ctypes.c_double), _ptr(st, ctypes.c_int32))
     if check and code != ENOTCONV:
@@ -487,6 +500,15 @@ def morap_product_download(ctx, p):
             "prob": prob[: info["n_trans"]], "cost": cost[: info["n_sa"]], "loc": loc[: info["Qn"]]}
 
 
+def morap_product_locations(ctx, p):
+    """The DFA location of each product location of product p (the state
+    layout u = pl * S + s), without copying the CSR."""
+    info = morap_product_info(ctx, p)
+    loc = np.zeros(max(info["Qn"], 1), np.int32)
+    _check(lib().morap_product_download(ctx, int(p), None, None, None, None, None, _ptr(loc, ctypes.c_int32)))
+    return loc[: info["Qn"]]
+
+
 def morap_last_policy(ctx, k, p):
     info = morap_product_info(ctx, p)
     mu = np.zeros(info["n_states"], np.uint8)
@@ -606,6 +628,7 @@ class Context:
         self.h = morap_ctx_create(self.cfg)
         self.n_agents = 0
         self.n_tasks = 0
+        self.n_pairs = None  # set by select_pairs
 
     def add(self, agents, tasks):
         for a in agents:
@@ -616,6 +639,13 @@ class Context:
             self.n_tasks += 1
         return self
 
+    def select_pairs(self, pairs):
+        """Build only these (agent, task) products, in this order (before build)."""
+        pairs = list(pairs)
+        morap_select_pairs(self.h, [i for i, _ in pairs], [j for _, j in pairs])
+        self.n_pairs = len(pairs)
+        return self
+
     def build(self, stream=None):
         return morap_build(self.h, stream)
 
@@ -623,7 +653,7 @@ class Context:
         return morap_rebuild(self.h, stream)
 
     def solve(self, W, stream=None, evaluate=True, check=True):
-        return morap_solve(self.h, W, self.n_agents, self.n_tasks, stream, evaluate, check)
+        return morap_solve(self.h, W, self.n_agents, self.n_tasks, stream, evaluate, check, self.n_pairs)
 
     def supporting_points(self, W, stream=None, want_c=False, check=True):
         return morap_supporting_points(self.h, W, self.n_agents, self.n_tasks, stream, want_c, check)

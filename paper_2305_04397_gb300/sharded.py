@@ -1,10 +1,11 @@
 """Algorithm 2 (and the Algorithm 1 loop on top of it) with the products of
 one instance sharded over several processes, one GPU each.
 
-The |I| x |J| product MDPs are independent until the assignment (Sec. 3.2):
-agent i's products with every task go to one rank, chosen by a greedy
-longest-processing-time rule on the agents' transition counts.  A batch of
-K weight vectors then runs as
+The |I| x |J| product MDPs are independent until the assignment (Sec. 3.2),
+so each product is a unit of work: products are dealt to ranks by a greedy
+longest-processing-time rule on an estimate of their work (transitions x
+expected sweeps), and each rank builds only its own products
+(morap_select_pairs).  A batch of K weight vectors then runs as
 
   1. Algorithm 3 on every product the rank owns (morap_solve, no Algorithm 4);
   2. an all-gather of the c values, so that every rank holds c[K][|I|][|J|];
@@ -25,6 +26,7 @@ the host).  The per-rank work is behind a small shard interface
 
 from __future__ import annotations
 
+import math
 from typing import Callable, Sequence
 
 import numpy as np
@@ -32,82 +34,85 @@ import numpy as np
 from . import morap as M
 
 
-def partition_agents(loads: Sequence[float], world: int) -> list[list[int]]:
-    """Deal agents to `world` ranks: heaviest first, each to the rank with the
-    least load so far (lowest rank on ties).  Deterministic, so every rank
-    computes the same partition.  Returns the sorted agent ids per rank."""
+def product_loads(agents, tasks) -> np.ndarray:
+    """Work estimate per product [|I|][|J|]: its transitions (the agent's
+    transitions once per location of the task) times the sweeps value
+    iteration needs, estimated as the longest expected path: the task's
+    location count (targets visited in sequence) times the square root of
+    the agent's state count (the side of a grid)."""
+    L = np.zeros((len(agents), len(tasks)))
+    for i, a in enumerate(agents):
+        for j, t in enumerate(tasks):
+            L[i, j] = float(len(a.succ)) * int(t.n_locs) * int(t.n_locs) * math.sqrt(int(a.n_states))
+    return L
+
+
+def partition_products(loads, world: int) -> list[list[tuple[int, int]]]:
+    """Deal products (i, j) to `world` ranks: heaviest first, each to the rank
+    with the least load so far (lowest rank on ties).  Deterministic, so
+    every rank computes the same partition.  Returns each rank's pairs in
+    (i, j) order."""
     if world < 1:
         raise ValueError("world must be >= 1")
-    order = sorted(range(len(loads)), key=lambda i: (-float(loads[i]), i))
+    loads = np.asarray(loads, np.float64)
+    nI, nJ = loads.shape
+    order = sorted(((i, j) for i in range(nI) for j in range(nJ)), key=lambda ij: (-loads[ij], ij))
     total = [0.0] * world
-    parts: list[list[int]] = [[] for _ in range(world)]
-    for i in order:
+    parts: list[list[tuple[int, int]]] = [[] for _ in range(world)]
+    for ij in order:
         r = min(range(world), key=lambda q: (total[q], q))
-        parts[r].append(i)
-        total[r] += float(loads[i])
+        parts[r].append(ij)
+        total[r] += float(loads[ij])
     return [sorted(p) for p in parts]
 
 
-def agent_loads(agents, tasks) -> list[float]:
-    """Work estimate per agent: its transitions times the summed location
-    counts of the tasks (its products' transition count up to the trap and
-    done pruning)."""
-    locs = sum(int(t.n_locs) for t in tasks)
-    return [float(len(a.succ)) * locs for a in agents]
-
-
-def sub_weights(W: np.ndarray, agent_ids: Sequence[int], n_agents: int) -> np.ndarray:
-    """The columns of W[K][|I|+|J|] that a shard with `agent_ids` uses."""
-    W = np.atleast_2d(np.asarray(W, np.float64))
-    cols = list(agent_ids) + list(range(n_agents, W.shape[1]))
-    return np.ascontiguousarray(W[:, cols])
-
-
-def assemble_c(parts: Sequence[np.ndarray], ids_by_rank: Sequence[Sequence[int]], n_agents: int) -> np.ndarray:
-    """c[K][|I|][|J|] from the per-rank blocks c_r[K][rows_r][|J|] (blocks may be
-    padded with extra rows beyond len(ids_by_rank[r]))."""
-    K, _, nJ = parts[0].shape
-    C = np.zeros((K, n_agents, nJ))
-    for part, ids in zip(parts, ids_by_rank):
-        for row, i in enumerate(ids):
-            C[:, i, :] = part[:, row, :]
+def assemble_c(parts: Sequence[np.ndarray], pairs_by_rank: Sequence[Sequence[tuple[int, int]]], n_agents: int,
+               n_tasks: int) -> np.ndarray:
+    """c[K][|I|][|J|] from the per-rank blocks c_r[K][n_r] (value e of rank r
+    is product pairs_by_rank[r][e]; blocks may be padded beyond n_r)."""
+    K = parts[0].shape[0]
+    C = np.zeros((K, n_agents, n_tasks))
+    for part, pairs in zip(parts, pairs_by_rank):
+        for e, (i, j) in enumerate(pairs):
+            C[:, i, j] = part[:, e]
     return C
 
 
-def owned_pairs(assign: np.ndarray, agent_ids: Sequence[int], n_tasks: int):
+def owned_pairs(assign: np.ndarray, pairs: Sequence[tuple[int, int]]):
     """(local product index, weight index, agent, task) of the assigned pairs
-    a shard owns; local product index = local agent row * |J| + j."""
-    row = {i: r for r, i in enumerate(agent_ids)}
+    a shard owns; the local index is the pair's position in `pairs`."""
+    pos = {tuple(ij): e for e, ij in enumerate(pairs)}
     out = []
     for k in range(assign.shape[0]):
-        for j in range(n_tasks):
+        for j in range(assign.shape[1]):
             i = int(assign[k, j])
-            if i >= 0 and i in row:
-                out.append((row[i] * n_tasks + j, k, i, j))
+            if i >= 0 and (i, j) in pos:
+                out.append((pos[(i, j)], k, i, j))
     return out
 
 
 class EngineShard:
-    """The products of some agents with every task, on this process's GPU."""
+    """Some products of one instance, on this process's GPU: a context with
+    every agent and task, restricted to the shard's pairs."""
 
-    def __init__(self, agents, tasks, agent_ids: Sequence[int], cfg=None, stream=None):
-        self.agent_ids = list(agent_ids)
+    def __init__(self, agents, tasks, pairs: Sequence[tuple[int, int]], cfg=None, stream=None):
+        self.pairs = [tuple(p) for p in pairs]
         self.n_agents = len(agents)
         self.n_tasks = len(tasks)
         self.stream = stream
         self.ctx = None
-        if self.agent_ids:
+        if self.pairs:
             self.ctx = M.Context(cfg)
-            self.ctx.add([agents[i] for i in self.agent_ids], tasks)
+            self.ctx.add(agents, tasks)
+            self.ctx.select_pairs(self.pairs)
             self.ctx.build(stream)
 
     def optimise(self, W: np.ndarray):
-        """Algorithm 3 for the shard's products: (c[K][rows][|J|], not_converged)."""
+        """Algorithm 3 for the shard's products: (c[K][n_pairs], not_converged)."""
         K = np.atleast_2d(W).shape[0]
         if self.ctx is None:
-            return np.zeros((K, 0, self.n_tasks)), False
-        out = M.morap_solve(self.ctx.h, sub_weights(W, self.agent_ids, self.n_agents), len(self.agent_ids),
-                            self.n_tasks, self.stream, evaluate=False)
+            return np.zeros((K, 0)), False
+        out = self.ctx.solve(W, self.stream, evaluate=False)
         return out["c"], out["code"] == M.ENOTCONV
 
     def evaluate(self, assign: np.ndarray):
@@ -115,7 +120,7 @@ class EngineShard:
         with only those entries set, not_converged)."""
         K = assign.shape[0]
         r = np.zeros((K, self.n_agents + self.n_tasks))
-        pairs = owned_pairs(assign, self.agent_ids, self.n_tasks)
+        pairs = owned_pairs(assign, self.pairs)
         if not pairs:
             return r, False
         ev = M.morap_evaluate(self.ctx.h, [p for p, _, _, _ in pairs], [k for _, k, _, _ in pairs], self.stream)
@@ -123,6 +128,9 @@ class EngineShard:
             r[k, i] = ev["r_cost"][e]
             r[k, self.n_agents + j] = ev["r_prob"][e]
         return r, ev["code"] == M.ENOTCONV
+
+    def stats(self):
+        return self.ctx.stats() if self.ctx is not None else None
 
     def close(self):
         if self.ctx is not None:
@@ -155,22 +163,23 @@ class TorchComm:
 
 class ShardedSupportingPoints:
     """Algorithm 2 over a sharded instance: this rank's shard plus the
-    collectives.  `ids_by_rank` is the partition every rank agreed on."""
+    collectives.  `pairs_by_rank` is the partition every rank agreed on."""
 
-    def __init__(self, shard, ids_by_rank: Sequence[Sequence[int]], n_agents: int, n_tasks: int, comm):
+    def __init__(self, shard, pairs_by_rank: Sequence[Sequence[tuple[int, int]]], n_agents: int, n_tasks: int,
+                 comm):
         self.shard = shard
-        self.ids_by_rank = [list(x) for x in ids_by_rank]
+        self.pairs_by_rank = [[tuple(p) for p in x] for x in pairs_by_rank]
         self.n_agents, self.n_tasks = n_agents, n_tasks
         self.comm = comm
-        self.rows = max(1, max(len(x) for x in self.ids_by_rank))
+        self.width = max(1, max(len(x) for x in self.pairs_by_rank))
 
     def __call__(self, W: np.ndarray) -> dict:
         W = np.atleast_2d(np.asarray(W, np.float64))
         K = W.shape[0]
         c, nc1 = self.shard.optimise(W)
-        block = np.zeros((K, self.rows, self.n_tasks))
-        block[:, : c.shape[1], :] = c
-        C = assemble_c(self.comm.all_gather(block), self.ids_by_rank, self.n_agents)
+        block = np.zeros((K, self.width))
+        block[:, : c.shape[1]] = c
+        C = assemble_c(self.comm.all_gather(block), self.pairs_by_rank, self.n_agents, self.n_tasks)
         assign = M.morap_assign_tasks(C)
         r_part, nc2 = self.shard.evaluate(assign)
         flags = np.zeros((K, self.n_agents + self.n_tasks + 1))

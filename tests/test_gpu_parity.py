@@ -389,6 +389,30 @@ def test_tie_fallback_anchoring_matches_oracle(M, precision, polish):
     ctx.close()
 
 
+@pytest.mark.parametrize("eval_block", [0, 1])
+def test_tasks_done_at_the_start(M, eval_block):
+    """A task whose initial location is accepting (every location done: the
+    product has no non-done state) and one whose initial location is a trap
+    (the product has non-done states the run never enters): every pair
+    converges and c, r_cost and r_prob are 0, as in the oracle."""
+    t_acc = I.Task(1, 0, 1, np.array([0], np.int32), np.array([0, 0], np.int32), np.array([1], np.uint8), {})
+    delta = np.array([[0, 0], [1, 2], [2, 2]], np.int32).reshape(-1)
+    t_trap = I.Task(3, 0, 1, np.array([0], np.int32), delta, np.array([0, 0, 1], np.uint8), {})
+    a = I.grid_agent(4, 4, 0.1, (0, 0))
+    ctx = make_ctx(M, ([a], [t_acc, t_trap, I.sequence_task([I.GRID_AP(3, 3)])]), eval_block=eval_block)
+    W = np.array([[0.3, 0.7, 0.0, 0.0], [0.2, 0.0, 0.4, 0.4]])
+    out = ctx.solve(W)
+    assert np.all(out["status"] == 0)
+    for j, t in enumerate((t_acc, t_trap)):
+        r = O.solve_pair(O.Product(a, t), 0.3, 0.7)
+        assert r["c"] == r["r_cost"] == r["r_prob"] == 0.0
+        assert np.all(out["c"][:, 0, j] == 0.0) and np.all(out["r_cost"][:, 0, j] == 0.0)
+        assert np.all(out["r_prob"][:, 0, j] == 0.0)
+    sp = ctx.supporting_points(W)
+    assert sp["r"][:, 1:3].max() == 0.0 and ctx.stats()["pairs_not_converged"] == 0
+    ctx.close()
+
+
 # ------------------------------------------------------------- full size
 
 
@@ -439,6 +463,23 @@ def test_grid32_full_size_sampled(M, grid32):
     for k, w in enumerate(W):
         tot = sum(out["c"][k, out["assign"][k][j], j] for j in range(nJ) if out["assign"][k][j] >= 0)
         assert w @ out["r"][k] == pytest.approx(tot, abs=1e-5)
+    ctx.close()
+
+
+def test_grid32_every_c_matches_oracle(M, grid32):
+    """Every c of the benchmark's batch (200 products x 16 weights, one
+    supporting-point batch as the benchmark launches it) against the
+    oracle, one pair per host process."""
+    inst = grid32
+    nI, nJ = len(inst.agents), len(inst.tasks)
+    ctx = make_ctx(M, inst)
+    W = inst.weights
+    out = ctx.supporting_points(W, want_c=True)
+    jobs = [(inst.agents[i], inst.tasks[j], float(W[k][i]), float(W[k][nI + j]), 1e-8)
+            for k in range(len(W)) for i in range(nI) for j in range(nJ)]
+    want = np.array([c for c, _, _ in O.solve_pairs_pooled(jobs)]).reshape(len(W), nI, nJ)
+    err = np.abs(out["c"] - want)
+    assert err.max() < TOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
     ctx.close()
 
 

@@ -1,5 +1,6 @@
-"""The sharded driver's per-rank steps on one GPU: two shards (agents split
-by the partition rule), their c blocks assembled, the assignment taken once,
+"""The sharded driver's per-rank steps on one GPU: two shards (products
+dealt by the partition rule, each a context restricted to its pairs), their
+c blocks assembled, the assignment taken once,
 Algorithm 4 run per shard on the pairs it owns.  The result must be
 bit-identical to one context holding every product (per-pair results do not
 depend on the batch), and morap_evaluate must reject what it cannot do."""
@@ -37,12 +38,15 @@ def test_two_shards_equal_one_context_bitwise(M):
     full.add(agents, tasks)
     full.build()
     ref = full.supporting_points(W, want_c=True)
-    parts = S.partition_agents(S.agent_loads(agents, tasks), 2)
+    parts = S.partition_products(S.product_loads(agents, tasks), 2)
     assert all(parts)
-    shards = [S.EngineShard(agents, tasks, ids) for ids in parts]
+    shards = [S.EngineShard(agents, tasks, pairs) for pairs in parts]
     blocks = [s.optimise(W)[0] for s in shards]
-    C = S.assemble_c(blocks, parts, nI)
+    C = S.assemble_c(blocks, parts, nI, nJ)
     assert np.array_equal(C, ref["c"].reshape(C.shape))
+    with pytest.raises(M.MorapError) as e:  # a context with a pair list has no assignment step
+        shards[0].ctx.supporting_points(W)
+    assert e.value.code == M.ESTATE
     assign = M.morap_assign_tasks(C)
     assert np.array_equal(assign, ref["assign"])
     r = sum(s.evaluate(assign)[0] for s in shards)
@@ -95,7 +99,7 @@ def test_sharded_driver_over_nccl_one_rank(M):
         agents, tasks = g.agents[:3], g.tasks[:4]
         W = np.ascontiguousarray(g.weights[:4][:, [0, 1, 2, 10, 11, 12, 13]])
         W = W / W.sum(axis=1, keepdims=True)
-        parts = S.partition_agents(S.agent_loads(agents, tasks), 1)
+        parts = S.partition_products(S.product_loads(agents, tasks), 1)
         shard = S.EngineShard(agents, tasks, parts[0])
         sp = S.ShardedSupportingPoints(shard, parts, 3, 4, S.TorchComm(device=torch.device("cuda", 0)))
         got = sp(W)

@@ -1,7 +1,8 @@
-"""The multi-process path (products of one instance sharded by agent over
-ranks, Algorithm 2's c values all-gathered, the assignment replicated, the
-r vectors summed) on CPU: world_size-2 gloo ranks whose per-rank solver is
-the oracle.  The sharded supporting points and the Algorithm 1 loop built on
+"""The multi-process path (products of one instance dealt to ranks one by
+one, Algorithm 2's c values all-gathered, the assignment replicated, the r
+vectors summed) on CPU: world_size-2 and -3 gloo ranks (the latter with
+ranks holding different numbers of products) whose per-rank solver is the
+oracle.  The sharded supporting points and the Algorithm 1 loop built on
 them must equal the oracle's unsharded ones on every rank."""
 
 import os
@@ -19,33 +20,32 @@ class OracleShard:
     """Per-rank work of the sharded driver done by the oracle (one FP64 CPU
     solve per product and weight)."""
 
-    def __init__(self, agents, tasks, agent_ids):
+    def __init__(self, agents, tasks, pairs):
         from oracle import core as O
 
         self.O = O
         self.agents, self.tasks = agents, tasks
-        self.agent_ids = list(agent_ids)
+        self.pairs = [tuple(p) for p in pairs]
         self.n_agents, self.n_tasks = len(agents), len(tasks)
-        self.prods = {(i, j): O.Product(agents[i], tasks[j]) for i in self.agent_ids for j in range(self.n_tasks)}
+        self.prods = {(i, j): O.Product(agents[i], tasks[j]) for i, j in self.pairs}
         self.last = {}
 
     def optimise(self, W):
         W = np.atleast_2d(W)
         K, nI = W.shape[0], self.n_agents
-        c = np.zeros((K, len(self.agent_ids), self.n_tasks))
+        c = np.zeros((K, len(self.pairs)))
         self.last = {}
         for k in range(K):
-            for row, i in enumerate(self.agent_ids):
-                for j in range(self.n_tasks):
-                    res = self.O.solve_pair(self.prods[(i, j)], W[k][i], W[k][nI + j])
-                    c[k, row, j] = res["c"]
-                    self.last[(k, i, j)] = (res["r_cost"], res["r_prob"])
+            for e, (i, j) in enumerate(self.pairs):
+                res = self.O.solve_pair(self.prods[(i, j)], W[k][i], W[k][nI + j])
+                c[k, e] = res["c"]
+                self.last[(k, i, j)] = (res["r_cost"], res["r_prob"])
         return c, False
 
     def evaluate(self, assign):
         K = assign.shape[0]
         r = np.zeros((K, self.n_agents + self.n_tasks))
-        for _, k, i, j in S.owned_pairs(assign, self.agent_ids, self.n_tasks):
+        for _, k, i, j in S.owned_pairs(assign, self.pairs):
             r[k, i], r[k, self.n_agents + j] = self.last[(k, i, j)]
         return r, False
 
@@ -65,7 +65,7 @@ def _rank_main(rank, world, port, out_dir):
     try:
         inst = I.config_tiny()
         nI, nJ = len(inst.agents), len(inst.tasks)
-        parts = S.partition_agents(S.agent_loads(inst.agents, inst.tasks), world)
+        parts = S.partition_products(S.product_loads(inst.agents, inst.tasks), world)
         shard = OracleShard(inst.agents, inst.tasks, parts[rank])
         sp = S.ShardedSupportingPoints(shard, parts, nI, nJ, S.TorchComm())
         out = sp(inst.weights[:3])
@@ -78,43 +78,60 @@ def _rank_main(rank, world, port, out_dir):
         dist.destroy_process_group()
 
 
-def test_partition_covers_every_agent_once_and_balances():
-    loads = [5.0, 1.0, 7.0, 3.0, 3.0, 2.0, 9.0]
-    for world in (1, 2, 3, 7, 9):
-        parts = S.partition_agents(loads, world)
+def test_partition_covers_every_product_once_and_balances():
+    rng = np.random.default_rng(4)
+    loads = rng.uniform(1.0, 10.0, size=(4, 5))
+    for world in (1, 2, 3, 7, 25):
+        parts = S.partition_products(loads, world)
         assert len(parts) == world
-        flat = sorted(i for p in parts for i in p)
-        assert flat == list(range(len(loads)))
-        tot = [sum(loads[i] for i in p) for p in parts]
+        flat = sorted(ij for p in parts for ij in p)
+        assert flat == [(i, j) for i in range(4) for j in range(5)]
+        tot = [sum(loads[ij] for ij in p) for p in parts]
         # greedy LPT: no rank exceeds the lightest by more than the largest load
-        assert max(tot) - min(tot) <= max(loads)
-        assert parts == S.partition_agents(loads, world)
+        assert max(tot) - min(tot) <= loads.max() + 1e-12
+        assert parts == S.partition_products(loads, world)
+    # 10 agents x 20 tasks on 8 ranks: a partition by agent would cap the
+    # speed-up at 5 (2 agents on some rank); by product it is near even
+    g = I.config_grid32()
+    L = S.product_loads(g.agents, g.tasks)
+    parts = S.partition_products(L, 8)
+    tot = [sum(L[ij] for ij in p) for p in parts]
+    assert max(tot) / (L.sum() / 8) < 1.05
+
+
+def test_product_loads_follow_size():
+    g = I.config_grid32()
+    L = S.product_loads(g.agents[:2], [I.sequence_task([1]), I.sequence_task([1, 2, 3])])
+    assert np.all(L[:, 1] > L[:, 0])  # more locations: more transitions and a longer horizon
 
 
 def test_assemble_and_owned_pairs():
-    ids = [[0, 2], [1]]
-    parts = [np.arange(2 * 2 * 3, dtype=float).reshape(2, 2, 3), 100 + np.arange(2 * 2 * 3).reshape(2, 2, 3)]
-    C = S.assemble_c(parts, ids, 3)
-    assert np.array_equal(C[:, 0], parts[0][:, 0]) and np.array_equal(C[:, 2], parts[0][:, 1])
-    assert np.array_equal(C[:, 1], parts[1][:, 0])  # padded row 1 of rank 1 is ignored
-    assign = np.array([[2, -1, 1], [0, 1, 2]])
-    assert S.owned_pairs(assign, [0, 2], 3) == [(1 * 3 + 0, 0, 2, 0), (0 * 3 + 0, 1, 0, 0), (1 * 3 + 2, 1, 2, 2)]
-    assert S.owned_pairs(assign, [1], 3) == [(0 * 3 + 2, 0, 1, 2), (0 * 3 + 1, 1, 1, 1)]
+    pairs = [[(0, 0), (0, 2), (1, 1)], [(0, 1), (1, 0), (1, 2)]]
+    parts = [np.array([[1.0, 2.0, 3.0, 0.0]]), np.array([[4.0, 5.0, 6.0, 0.0]])]  # padded to width 4
+    C = S.assemble_c(parts, pairs, 2, 3)
+    assert np.array_equal(C[0], np.array([[1.0, 4.0, 2.0], [5.0, 3.0, 6.0]]))
+    assign = np.array([[1, -1, 0], [0, 1, -1]])
+    assert S.owned_pairs(assign, pairs[0]) == [(1, 0, 0, 2), (0, 1, 0, 0), (2, 1, 1, 1)]
+    assert S.owned_pairs(assign, pairs[1]) == [(1, 0, 1, 0)]
 
 
-def test_sharded_world2_gloo_matches_unsharded_oracle(oracle_lib):
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_gloo_matches_unsharded_oracle(oracle_lib, world):
     import torch.multiprocessing as mp
 
     from oracle import core as O
     from oracle import pareto as OP
 
     inst = I.config_tiny()
+    parts = S.partition_products(S.product_loads(inst.agents, inst.tasks), world)
+    assert sorted(ij for p in parts for ij in p) == [(i, j) for i in range(2) for j in range(3)]
     with tempfile.TemporaryDirectory() as d:
-        mp.start_processes(_rank_main, args=(2, _free_port(), d), nprocs=2, join=True, start_method="spawn")
-        res = [dict(np.load(os.path.join(d, f"rank{r}.npz"))) for r in range(2)]
+        mp.start_processes(_rank_main, args=(world, _free_port(), d), nprocs=world, join=True, start_method="spawn")
+        res = [dict(np.load(os.path.join(d, f"rank{r}.npz"))) for r in range(world)]
     # every rank holds the same numbers
-    for key in res[0]:
-        assert np.array_equal(res[0][key], res[1][key]), key
+    for r in range(1, world):
+        for key in res[0]:
+            assert np.array_equal(res[0][key], res[r][key]), key
     prods = O.products(inst.agents, inst.tasks)
     for k in range(3):
         r, f, C, _, _ = O.supporting_point(prods, inst.weights[k])
@@ -132,7 +149,7 @@ def test_sharded_world2_gloo_matches_unsharded_oracle(oracle_lib):
 
 
 def test_sharded_world1_equals_local_driver(oracle_lib):
-    """One shard with every agent and loop-back collectives gives the oracle's
+    """One shard with every product and loop-back collectives gives the oracle's
     supporting point (the gather / reduce bookkeeping is the identity)."""
 
     class Loop:
@@ -146,8 +163,8 @@ def test_sharded_world1_equals_local_driver(oracle_lib):
 
     inst = I.config_tiny()
     nI, nJ = len(inst.agents), len(inst.tasks)
-    sp = S.ShardedSupportingPoints(OracleShard(inst.agents, inst.tasks, range(nI)), [list(range(nI))], nI, nJ,
-                                   Loop())
+    every = [(i, j) for i in range(nI) for j in range(nJ)]
+    sp = S.ShardedSupportingPoints(OracleShard(inst.agents, inst.tasks, every), [every], nI, nJ, Loop())
     out = sp(inst.weights[1:2])
     r, _, _, _, _ = O.supporting_point(O.products(inst.agents, inst.tasks), inst.weights[1])
     assert np.max(np.abs(out["r"][0] - r)) < 1e-12 and out["code"] == 0
