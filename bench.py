@@ -297,6 +297,7 @@ def _parity(results, full, W, nI, nJ):
     are compared wherever the oracle's action gap exceeds 1e-9."""
     dc, dw, drc, drp, drc_own = [], [], [], [], []
     gap_states = gap_mismatch = 0
+    mm_gap = mm_loss = 0.0
     for p, k, r in results:
         i, j = divmod(p, nJ)
         wi, wp = W[k][i], W[k][nI + j]
@@ -309,12 +310,15 @@ def _parity(results, full, W, nI, nJ):
             drc_own.append(max(abs(rc - r["r_cost"]), abs(rp - r["r_prob"])))
         gap_states += r["gap_states"]
         gap_mismatch += r["gap_mismatch"]
+        mm_gap = max(mm_gap, r["mismatch_max_gap"])
+        mm_loss = max(mm_loss, r["mismatch_max_loss"])
     return {"reference": "FP64 C oracle (Algorithm 3 to eps_vi, scheduler, Algorithm 4 to 1e-11)",
             "pairs": len(dc), "tolerance": 1e-6, "max_abs_c": max(dc, default=None),
             "max_abs_w_dot_r": max(dw, default=None),
             "max_abs_r_cost": max(drc, default=None), "max_abs_r_prob": max(drp, default=None),
             "objectives_of": "the engine's scheduler, evaluated by the oracle's Algorithm 4",
             "policy_states_checked": gap_states, "policy_mismatches": gap_mismatch,
+            "mismatch_max_oracle_gap": mm_gap, "mismatch_max_q_loss_on_oracle_values": mm_loss,
             "max_abs_r_vs_oracle_scheduler": max(drc_own, default=None),
             "note": "the last figure compares with the oracle's own scheduler; it differs from 0 only where "
                     "two schedulers tie within 1e-9 in w.r"}
@@ -356,37 +360,50 @@ def run_reference(args):
 
 
 def serving_instances(n_inst, seed=7):
-    """Resident instances for the point-query workload: the 2x3 4x4-grid
-    instance and 2x3 / 3x4 / 4x6 agent-task subsets of 32x32-grid
-    instances, cycled (each instance a different seed or subset)."""
+    """Resident instances for the point-query workload, drawn in turn from
+    the four batch configurations and scaled to serving size: the 2x3
+    4x4-grid instance (each with its own seed), 2x3 and 3x4 agent-task
+    subsets of 32x32-grid instances, 2x3 subsets of the uneven batch (grids
+    of side 16..64, Moore successors, DFAs of 2-8 locations) and 1x2
+    subsets of the 128x128-grid batch."""
     import instances as I
 
     grids = [I.config_grid32(seed=seed + g) for g in range(2)]
+    uneven = I.config_uneven()
+    large = I.config_large()
     out = []
     for s in range(n_inst):
         kind = s % 4
         if kind == 0:
             tiny = I.config_tiny(seed=s)
-            out.append((tiny.agents, tiny.tasks))
-        else:
-            nI, nJ = [(2, 3), (3, 4), (4, 6)][kind - 1]
-            g = grids[s % 2]
+            out.append(("tiny 2x3", tiny.agents, tiny.tasks))
+        elif kind == 1:
+            nI, nJ = [(2, 3), (3, 4)][(s // 4) % 2]
+            g = grids[(s // 4) % 2]
             a0 = (s * 3) % (len(g.agents) - nI + 1)
             t0 = (s * 5) % (len(g.tasks) - nJ + 1)
-            out.append((g.agents[a0:a0 + nI], g.tasks[t0:t0 + nJ]))
+            out.append((f"grid32 {nI}x{nJ}", g.agents[a0:a0 + nI], g.tasks[t0:t0 + nJ]))
+        elif kind == 2:
+            a0 = (s * 7) % (len(uneven.agents) - 2 + 1)
+            t0 = (s * 11) % (len(uneven.tasks) - 3 + 1)
+            out.append(("uneven 2x3", uneven.agents[a0:a0 + 2], uneven.tasks[t0:t0 + 3]))
+        else:
+            a0 = (s * 5) % len(large.agents)
+            t0 = (s * 3) % (len(large.tasks) - 2 + 1)
+            out.append(("large128 1x2", large.agents[a0:a0 + 1], large.tasks[t0:t0 + 2]))
     return out
 
 
 def run_serving(M, args):
     """Point queries/s of the continuous-batching server (Algorithm 1 per
     query) over resident instances: saturation throughput with every query
-    submitted at once, then Poisson arrivals at 80% of it for the latency
-    percentiles."""
+    submitted at once, then Poisson arrivals at 25/50/80% of it for the
+    latency percentiles."""
     import numpy as np
 
     insts = serving_instances(args.serve_instances)
     ctxs = []
-    for a, t in insts:
+    for _, a, t in insts:
         c = M.Context()
         c.add(a, t)
         c.build()
@@ -401,18 +418,19 @@ def run_serving(M, args):
             out.append((i, np.concatenate([-rng.uniform(5.0, 50.0, size=nI), rng.uniform(0.5, 0.99, size=nJ)])))
         return out
 
-    kw = dict(max_batch=64, n_workers=8, eps=1e-6, max_iter=args.serve_max_iter)
+    kw = dict(max_batch=64, n_workers=8, eps=1e-6, max_iter=args.serve_max_iter,
+              merge_instances=1 if args.serve_mode == "merged" else 0)
     srv = M.Server(ctxs, **kw)
     for i, t in queries(len(ctxs)):  # warm every instance once
         srv.submit(i, t)
-    srv.wait(600.0)
+    srv.wait(900.0)
     srv.close()
     srv = M.Server(ctxs, **kw)
-    qs = queries(args.serve_queries)
+    qs = queries(args.serve_sat_queries)
     t0 = time.perf_counter()
     for i, t in qs:
         srv.submit(i, t)
-    srv.wait(600.0)
+    srv.wait(900.0)
     sat_wall = time.perf_counter() - t0
     st_sat = srv.stats()
     srv.close()
@@ -430,27 +448,28 @@ def run_serving(M, args):
             if due > now:
                 time.sleep(due - now)
             srv.submit(i, t)
-        srv.wait(600.0)
+        srv.wait(900.0)
         wall = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
         return {"offered_qps": rate, "achieved_qps": len(qs) / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                 "mean_batch": st["mean_batch"], "queries": len(qs)}
 
-    sweep = [poisson(f * sat, max(32, args.serve_queries // 2)) for f in (0.25, 0.5)]
+    sweep = [poisson(f * sat, max(32, args.serve_queries // 4)) for f in (0.25, 0.5)]
     at80 = poisson(0.8 * sat, args.serve_queries)
     sweep.append(at80)
     for c in ctxs:
         c.close()
+    kinds = sorted({k for k, _, _ in insts})
     return {
         "metric": "point queries/s", "value": at80["achieved_qps"], "unit": "queries/s",
         "saturation_qps": sat, "offered_qps": at80["offered_qps"], "p50_ms": at80["p50_ms"], "p99_ms": at80["p99_ms"],
         "mean_batch": at80["mean_batch"], "saturation_mean_batch": st_sat["mean_batch"],
         "rate_sweep": sweep, "queries": at80["queries"], "instances": len(ctxs), "max_iter": args.serve_max_iter,
-        "eps": 1e-6,
-        "workload": "resident 4x4-grid 2x3 and 32x32-grid 2x3/3x4/4x6 instances; per query an instance uniformly, "
-                    "c_i = -U[5,50], p_j = U[0.5,0.99]; Poisson arrivals at 25/50/80% of the saturation rate "
-                    "(all queries submitted at once)",
+        "eps": 1e-6, "batching": args.serve_mode,
+        "workload": f"{len(ctxs)} resident instances ({', '.join(kinds)}: one in four of each); per query an "
+                    "instance uniformly, c_i = -U[5,50], p_j = U[0.5,0.99]; Poisson arrivals at 25/50/80% of the "
+                    f"saturation rate ({args.serve_sat_queries} queries submitted at once)",
     }
 
 
@@ -490,6 +509,7 @@ def run_engine(args):
     cfg.eps_vi = eps_vi
     cfg.polish = args.polish
     cfg.in_place = 1 if args.in_place else 0
+    cfg.item_warps_max = args.item_warps_max
     if strong:
         from paper_2305_04397_gb300 import sharded as S
 
@@ -612,6 +632,7 @@ def run_engine(args):
                    "transitions": fp["n_trans"], "eps_vi": cfg.eps_vi, "eps_eval": cfg.eps_eval,
                    "polish": ["fp32 residual correction", "double-float"][cfg.polish],
                    "sweeps": "in place" if cfg.in_place else "synchronous",
+                   "item_warps_max": cfg.item_warps_max or 8,
                    "l2": "per-step working set (CSR + FP32/FP64 value buffers) exceeds the 129 MB L2; no flush",
                    "parallelism": (f"one instance, its products dealt to {ws} GPU(s) (LPT on transitions x "
                                    f"expected sweeps; all-gather of c, all-reduce of r per batch)") if strong
@@ -699,6 +720,8 @@ def main():
     ap.add_argument("--polish", type=int, choices=[0, 1], default=0,
                     help="second phase: 0 FP32 residual correction (default), 1 double-float sweeps")
     ap.add_argument("--in-place", action="store_true", help="in-place (Gauss-Seidel order) sweeps")
+    ap.add_argument("--item-warps-max", type=int, choices=[0, 1, 2, 4, 8], default=0,
+                    help="most warps per sweep work item on short work lists (0: the library default)")
     ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
                     help="weak (default): one instance per GPU; strong: the products of one instance dealt to the "
                          "GPUs by the sharded Algorithm 2 driver")
@@ -709,7 +732,10 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-instances", type=int, default=64)
-    ap.add_argument("--serve-queries", type=int, default=256)
+    ap.add_argument("--serve-queries", type=int, default=2000,
+                    help="queries of the 80%%-load run (the configured workload has 10000)")
+    ap.add_argument("--serve-sat-queries", type=int, default=1000)
+    ap.add_argument("--serve-mode", choices=["merged", "per-instance"], default="merged")
     ap.add_argument("--serve-max-iter", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":

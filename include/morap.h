@@ -109,6 +109,10 @@ typedef struct morap_config {
                                    by the GPU's scheduling).  Same fixed point and stopping rule;
                                    usually fewer sweeps; results reproducible only to the
                                    tolerance.  Algorithm 4 stays synchronous.                       */
+    int32_t item_warps_max;     /* most warps that share one sweep work item: a sweep whose work list is
+                                   short (the late sweeps of a loop) splits each item's states over up
+                                   to this many warps, 1, 2, 4 or 8; 0 (default) = 8 (capped at what
+                                   one item fills).  Same results for every value.               */
 } morap_config;
 
 typedef struct morap_ctx morap_ctx;
@@ -417,10 +421,11 @@ void morap_pareto_destroy(morap_pareto *ps);
  * Continuous batching of threshold-point queries (Algorithm 1) over several
  * resident instances (built contexts).  Each query runs Algorithm 1 with
  * M = I and the server's eps / max_iter.  A query waiting for its next
- * supporting point joins the next batch of its instance: an idle instance
- * takes every waiting query (up to max_batch) as one morap_supporting_points
- * batch.  Instances run on their own CUDA streams from n_workers host
- * threads, so batches of different instances overlap on the device.
+ * supporting point joins the next device round: with merge_instances (the
+ * default) one round serves the waiting queries of every instance as the
+ * weight columns of one batch (a query's column weighs only its instance's
+ * products); otherwise an idle instance takes its own waiting queries as
+ * one morap_supporting_points batch on its own stream.
  * Admission: queries are admitted in arrival order while the device bytes of
  * their weight slots (26 bytes per product state of the instance) fit
  * hbm_budget (0 = no limit); at least one query is always admitted.
@@ -431,11 +436,16 @@ typedef struct morap_server morap_server;
 
 typedef struct morap_server_config {
     size_t hbm_budget;  /* admission budget in bytes, 0 = none                   */
-    int32_t max_batch;  /* queries per instance batch, 1..64 (default 64)        */
-    int32_t n_workers;  /* host threads driving instances (default 8)            */
+    int32_t max_batch;  /* queries per device batch, 1..64 (default 64)          */
+    int32_t n_workers;  /* host threads (default 8): Algorithm 1 steps, or the
+                           instances' batches without merge_instances          */
     double eps;         /* Algorithm 1 tolerance of every query (default 1e-6)   */
     int32_t max_iter;   /* supporting points per query (default 64)              */
-    int32_t reserved;
+    int32_t merge_instances; /* 1 (default): one device round takes the waiting queries
+                           of every instance, on a context holding all instances'
+                           products (built at server creation; the instances'
+                           own contexts are left untouched); 0: each instance
+                           batches its own queries on its own stream          */
 } morap_server_config;
 
 typedef struct morap_serving_stats {

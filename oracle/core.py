@@ -217,9 +217,15 @@ def scheduler_check(prod, w_cost, w_prob, mu, eps1=1e-8, eps_eval=1e-11, tau_gap
     gap = q[chosen] - best_other
     sel = gap > tau_gap
     checked = int(sel.sum())
-    mismatch = int(np.sum(mu[: prod.n - 1][sel] != r["mu"][: prod.n - 1][sel]))
+    bad = sel & (mu[: prod.n - 1] != r["mu"][: prod.n - 1])
+    mismatch = int(bad.sum())
+    # at a mismatch: the oracle's gap, and how far mu's action falls below the
+    # maximum on the oracle's values
+    loss = q[chosen[bad]] - q[prod.state_ptr[: prod.n - 1][bad] + mu[: prod.n - 1][bad]]
     return {"c": r["c"], "r_cost": r["r_cost"], "r_prob": r["r_prob"], "mu_r_cost": float(vc), "mu_r_prob": float(vp),
-            "gap_states": checked, "gap_mismatch": mismatch}
+            "gap_states": checked, "gap_mismatch": mismatch,
+            "mismatch_max_gap": float(gap[bad].max()) if mismatch else 0.0,
+            "mismatch_max_loss": float(loss.max()) if mismatch else 0.0}
 
 
 def solve_pair_job(job):

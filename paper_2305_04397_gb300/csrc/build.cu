@@ -1,14 +1,16 @@
 // Product construction on the device (Sec. 2 "Product MDP", Sec. 3.1).
 //
-// The product of agent i and task j keeps the agent's CSR shape once per
-// non-done DFA location: product state (pl, s) has the actions of agent
-// state s, and each agent transition (s, a, s', p) becomes ((pl, s), a,
-// (pl', s'), p) with pl' = delta(pl, L(s')) -- the label is read on the
-// successor.  A successor whose location is done (accepting or trap) goes to
-// the product's single absorbing done slot (value 0).  Because the shape is a
-// replication, every offset is known in closed form and the build is one
-// pass with no scan: local state u = pl*S + s, local row v = pl*SA + a, local
-// transition t = pl*T + e.
+// The product of agent i and task j keeps the agent's state and action
+// shape once per non-done DFA location: product state (pl, s) has the
+// actions of agent state s, and each agent transition (s, a, s', p) becomes
+// ((pl, s), a, (pl', s'), p) with pl' = delta(pl, L(s')) -- the label is
+// read on the successor.  Successors whose location is done (accepting or
+// trap) all go to the product's single absorbing done slot (value 0) and are
+// merged into one transition of the row, whose probability is their sum (in
+// the agent's order), at the position of the first of them.  States and
+// rows are in closed form (local state u = pl*S + s, local row v = pl*SA +
+// a); the rows' transition offsets come from a count pass and a per-product
+// prefix sum.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -44,6 +46,82 @@ __global__ void k_letters(const ProdDesc *prods, int P, const AgentDesc *agents,
     }
 }
 
+// First pass: merged transition count of every row (and per product).
+__global__ void k_row_count(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
+                            const int32_t *a_sa_ptr, const int32_t *a_succ, const uint8_t *letters,
+                            const int16_t *nd_delta, uint32_t *row_cnt, uint32_t *prod_tr) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int p = blockIdx.y; p < P; p += gridDim.y) {
+        const ProdDesc pd = prods[p];
+        const AgentDesc ad = agents[pd.agent];
+        const TaskDesc td = tasks[pd.task];
+        const uint32_t SA = ad.SA, n_sa = (uint32_t)td.Qn * SA;
+        unsigned int total = 0;
+        for (uint32_t v = tid; v < n_sa; v += stride) {
+            const uint32_t pl = v / SA, a = v - pl * SA;
+            const int32_t e0 = a_sa_ptr[ad.sap_off + a], e1 = a_sa_ptr[ad.sap_off + a + 1];
+            uint32_t n = 0;
+            bool done_seen = false;
+            for (int32_t e = e0; e < e1; ++e) {
+                const int32_t s2 = a_succ[ad.tr_off + e];
+                const uint32_t letter = letters[pd.letter_off + (uint32_t)s2];
+                const bool done = nd_delta[td.delta_off + pl * (uint32_t)td.n_letters + letter] < 0;
+                n += done && done_seen ? 0u : 1u;
+                done_seen = done_seen || done;
+            }
+            row_cnt[pd.sa_off + v] = n;
+            total += n;
+        }
+        if (prod_tr) {
+            total = __reduce_add_sync(0xffffffffu, total);
+            if ((threadIdx.x & 31) == 0 && total) atomicAdd(prod_tr + p, total);
+        }
+    }
+}
+
+// Second pass: per product, sa_tr = tr_off + exclusive prefix sum of the
+// row counts, in tiles of the block's size with a running carry.
+__global__ void __launch_bounds__(1024) k_row_offsets(const ProdDesc *prods, int P, const uint32_t *row_cnt,
+                                                      uint32_t *sa_tr) {
+    __shared__ uint32_t warp_sum[32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int p = blockIdx.x; p < P; p += gridDim.x) {
+        const ProdDesc pd = prods[p];
+        const uint32_t n_sa = (uint32_t)pd.Qn * pd.SA;
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (uint32_t base = 0; base < n_sa; base += blockDim.x) {
+            const uint32_t v = base + threadIdx.x;
+            const uint32_t x = v < n_sa ? row_cnt[pd.sa_off + v] : 0u;
+            uint32_t incl = x;  // inclusive scan within the warp
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) warp_sum[w] = incl;
+            __syncthreads();
+            if (w == 0) {
+                const uint32_t ws = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0u;
+                uint32_t wi = ws;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                    if (lane >= o) wi += y;
+                }
+                warp_sum[lane] = wi - ws;  // exclusive prefix of the warp sums
+            }
+            __syncthreads();
+            const uint32_t c0 = carry;
+            if (v < n_sa) sa_tr[pd.sa_off + v] = pd.tr_off + c0 + warp_sum[w] + incl - x;
+            __syncthreads();
+            if (threadIdx.x == blockDim.x - 1) carry = c0 + warp_sum[w] + incl;
+            __syncthreads();
+        }
+    }
+}
+
 __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                         const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ,
                         const double *a_prob, const double *a_cost, const uint8_t *letters, const int16_t *nd_delta,
@@ -71,39 +149,46 @@ __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, c
                 v = (uint32_t)td.Qn * SA;
             }
             state_sa[pd.state_off + u] = pd.sa_off + v;
-            uint32_t t0;
-            if (u < pd.n_nd) {
-                const uint32_t pl = u / S, s = u - pl * S;
-                t0 = pl * T + (uint32_t)a_sa_ptr[ad.sap_off + a_state_ptr[ad.sp_off + s]];
-            } else {
-                t0 = (uint32_t)td.Qn * T;
-            }
-            state_tr[pd.state_off + u] = pd.tr_off + t0;
+            // the first transition of the state's first row (k_row_offsets
+            // ran before); the done slot: the end of the product's transitions
+            state_tr[pd.state_off + u] = u < pd.n_nd ? sa_tr[pd.sa_off + v] : pd.tr_off + pd.n_tr;
         }
-        // state-action rows
+        // state-action rows (their costs) and their transitions
         const uint32_t n_sa = (uint32_t)td.Qn * SA;
+        const uint32_t done = pd.state_off + pd.n_nd;
         for (uint32_t v = tid; v < n_sa; v += stride) {
             const uint32_t pl = v / SA, a = v - pl * SA;
-            sa_tr[pd.sa_off + v] = pd.tr_off + pl * T + (uint32_t)a_sa_ptr[ad.sap_off + a];
             const double c = a_cost[ad.cost_off + a];
             cost64[pd.sa_off + v] = c;
             cost32[pd.sa_off + v] = __double2float_ru(c);
             costdf[pd.sa_off + v] = to_df(c);
-        }
-        // transitions
-        const uint32_t n_tr = (uint32_t)td.Qn * T;
-        const uint32_t done = pd.state_off + pd.n_nd;
-        for (uint32_t t = tid; t < n_tr; t += stride) {
-            const uint32_t pl = t / T, e = t - pl * T;
-            const int32_t s2 = a_succ[ad.tr_off + e];
-            const uint32_t letter = letters[pd.letter_off + (uint32_t)s2];
-            const int32_t pl2 = nd_delta[td.delta_off + pl * (uint32_t)td.n_letters + letter];
-            const int32_t cg = pl2 < 0 ? (int32_t)done : (int32_t)(pd.state_off + (uint32_t)pl2 * S + (uint32_t)s2);
-            const double pr = a_prob[ad.tr_off + e];
-            col[pd.tr_off + t] = cg;
-            p64[pd.tr_off + t] = pr;
-            pdf[pd.tr_off + t] = to_df(pr);
-            cp32[pd.tr_off + t] = make_int2(cg, __float_as_int(__double2float_rd(pr)));
+            const int32_t e0 = a_sa_ptr[ad.sap_off + a], e1 = a_sa_ptr[ad.sap_off + a + 1];
+            uint32_t t = sa_tr[pd.sa_off + v];
+            uint32_t t_done = 0xffffffffu;  // position of the merged done transition
+            double p_done = 0.0;
+            for (int32_t e = e0; e < e1; ++e) {
+                const int32_t s2 = a_succ[ad.tr_off + e];
+                const uint32_t letter = letters[pd.letter_off + (uint32_t)s2];
+                const int32_t pl2 = nd_delta[td.delta_off + pl * (uint32_t)td.n_letters + letter];
+                const double pr = a_prob[ad.tr_off + e];
+                if (pl2 < 0) {
+                    if (t_done == 0xffffffffu) t_done = t++;
+                    p_done += pr;
+                    continue;
+                }
+                const int32_t cg = (int32_t)(pd.state_off + (uint32_t)pl2 * S + (uint32_t)s2);
+                col[t] = cg;
+                p64[t] = pr;
+                pdf[t] = to_df(pr);
+                cp32[t] = make_int2(cg, __float_as_int(__double2float_rd(pr)));
+                ++t;
+            }
+            if (t_done != 0xffffffffu) {
+                col[t_done] = (int32_t)done;
+                p64[t_done] = p_done;
+                pdf[t_done] = to_df(p_done);
+                cp32[t_done] = make_int2((int32_t)done, __float_as_int(__double2float_rd(p_done)));
+            }
         }
     }
 }
@@ -116,6 +201,22 @@ int launch_letters(const ProdDesc *prods, int P, const AgentDesc *agents, const 
     dim3 grid((max_S + 255) / 256 < 64 ? (max_S + 255) / 256 : 64, P < 65535 ? P : 65535);
     if (grid.x == 0) grid.x = 1;
     k_letters<<<grid, 256, 0, (cudaStream_t)s>>>(prods, P, agents, tasks, label_ptr, label_ap, ap_ids, letters);
+    return (int)cudaGetLastError();
+}
+
+int launch_row_count(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
+                     const int32_t *a_sa_ptr, const int32_t *a_succ, const uint8_t *letters,
+                     const int16_t *nd_delta, uint32_t *row_cnt, uint32_t *prod_tr, uint32_t max_rows, void *s) {
+    dim3 grid((max_rows + 255) / 256 < 64 ? (max_rows + 255) / 256 : 64, P < 65535 ? P : 65535);
+    if (grid.x == 0) grid.x = 1;
+    k_row_count<<<grid, 256, 0, (cudaStream_t)s>>>(prods, P, agents, tasks, a_sa_ptr, a_succ, letters, nd_delta,
+                                                    row_cnt, prod_tr);
+    return (int)cudaGetLastError();
+}
+
+int launch_row_offsets(const ProdDesc *prods, int P, const uint32_t *row_cnt, uint32_t *sa_tr, void *s) {
+    if (P <= 0) return 0;
+    k_row_offsets<<<P < 4096 ? P : 4096, 1024, 0, (cudaStream_t)s>>>(prods, P, row_cnt, sa_tr);
     return (int)cudaGetLastError();
 }
 

@@ -87,7 +87,10 @@ struct morap_ctx {
     // order; empty = every agent x task pair, product p = i * |J| + j
     std::vector<int32_t> sel_agent, sel_task;
     uint32_t TS = 0, TSA = 0, TT = 0;
-    std::vector<ProdDesc> h_prods;
+    std::vector<ProdDesc> h_prods;      // with the merged transition offsets (tr_off, n_tr)
+    std::vector<ProdDesc> h_prods_key;  // as computed from the models alone (the layout's identity)
+    uint32_t *row_cnt = nullptr;        // [SA] merged transitions per product row (construction scratch)
+    uint32_t *prod_tr = nullptr;        // [P] merged transitions per product (first build)
     std::vector<int4> h_chunks;
     int32_t *in_items = nullptr;  // [items][kInItems] input items of each sweep work item
     uint2 *item_w = nullptr;      // [items] (transitions, rows) of each work item
@@ -96,6 +99,7 @@ struct morap_ctx {
     AgentDesc *d_agents = nullptr;
     TaskDesc *d_tasks = nullptr;
     int4 *d_chunks = nullptr;
+    uint4 *d_chunk_u = nullptr;  // per item: global state range and the product's first pre-sink state
     uint32_t *state_sa = nullptr, *state_tr = nullptr, *sa_tr = nullptr;
     int32_t *col = nullptr;
     int2 *cp32 = nullptr;
@@ -111,7 +115,7 @@ struct morap_ctx {
     double *d_prob = nullptr, *d_cost = nullptr;
     int16_t *d_nd = nullptr;
     uint8_t *d_letters = nullptr;
-    uint32_t max_S = 1, max_work = 1;
+    uint32_t max_S = 1, max_work = 1, max_rows = 1;
     int max_row = 1;  // longest action row (successors) of any agent
     std::vector<size_t> layout_sig;
     int64_t last_h2d_bytes = 0;
@@ -466,6 +470,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a.cost32 = c->cost32;
     a.cost64 = c->cost64;
     a.chunks = c->d_chunks;
+    a.chunk_u = c->d_chunk_u;
     a.prods = c->d_prods;
     a.w32 = c->w32;
     a.w64 = c->w64;
@@ -485,6 +490,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
     for (int q = 0; q < 3; ++q) a.chg[q] = c->chg[q];
     a.eps1 = c->cfg.eps_vi;
     a.eps1f = (float)c->cfg.eps_vi;
+    a.gmax = c->cfg.item_warps_max > 0 ? c->cfg.item_warps_max : 8;
     a.P = c->P;
     SweepArgs a32 = a, a64 = a;
     a32.thr = c->thr32;
@@ -635,7 +641,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         CK(cudaMemsetAsync(c->V32[0], 0, nv * sizeof(float), s));
         CK(cudaMemsetAsync(c->V32[1], 0, nv * sizeof(float), s));
         CKL(launch_loop_init(c->ctl + 0, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
-                             c->chg[2]));
+                             c->chg[2], c->w64));
         bool tune = false;
         CKR(prepare_phase(c, kSweepF32, Kp, tune));
         const auto t0 = std::chrono::steady_clock::now();
@@ -667,7 +673,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     }
     const int pk = mixed ? c->polish : kSweepDF;  // the polish kind of this solve
     CKL(launch_loop_init(c->ctl + 1, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
-                         c->chg[2]));
+                         c->chg[2], c->w64));
     bool tune64 = false;
     CKR(prepare_phase(c, pk, Kp, tune64));
     const auto t64 = std::chrono::steady_clock::now();
@@ -912,6 +918,49 @@ int run_evaluation(morap_ctx *c, const std::vector<int4> &pairs, cudaStream_t s,
 // the loop graphs of every padded size up to K whose kernel shape needs no
 // tuning, so that later batches of varying size neither allocate nor free
 // (a device free synchronises the whole device).
+// A context holding the products of several built contexts: every agent and
+// task of each, and the pair list of each one's agent x task products (in
+// order: context q's product a * |J_q| + t is product pair_off[q] + a * |J_q| + t).
+// Built on the first context's device and configuration.
+int morap::ctx_merge(morap_ctx *const *ctxs, int n, morap_ctx **out, std::vector<int32_t> &agent_off,
+                     std::vector<int32_t> &task_off, std::vector<int32_t> &pair_off) {
+    if (n < 1) return fail(MORAP_EINVAL, "merge: no context");
+    morap_config cfg = ctxs[0]->cfg;
+    cfg.alloc = nullptr;
+    cfg.free = nullptr;
+    cfg.alloc_user = nullptr;
+    cfg.hbm_budget = 0;
+    morap_ctx *m = nullptr;
+    int rc = morap_ctx_create(&cfg, &m);
+    if (rc != MORAP_OK) return rc;
+    agent_off.assign(n, 0);
+    task_off.assign(n, 0);
+    pair_off.assign(n, 0);
+    for (int q = 0; q < n; ++q) {
+        const morap_ctx *c = ctxs[q];
+        if (!c->sel_agent.empty()) {
+            morap_ctx_destroy(m);
+            return fail(MORAP_EINVAL, "merge: a context with a pair list");
+        }
+        agent_off[q] = (int32_t)m->agents.size();
+        task_off[q] = (int32_t)m->tasks.size();
+        pair_off[q] = (int32_t)m->sel_agent.size();
+        for (size_t a = 0; a < c->agents.size(); ++a)
+            for (size_t t = 0; t < c->tasks.size(); ++t) {
+                m->sel_agent.push_back(agent_off[q] + (int32_t)a);
+                m->sel_task.push_back(task_off[q] + (int32_t)t);
+            }
+        m->agents.insert(m->agents.end(), c->agents.begin(), c->agents.end());
+        m->tasks.insert(m->tasks.end(), c->tasks.begin(), c->tasks.end());
+    }
+    if ((rc = morap_build(m, nullptr, nullptr)) != MORAP_OK) {
+        morap_ctx_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return MORAP_OK;
+}
+
 int morap::ctx_reserve(morap_ctx *c, int K) {
     if (!c->built) return fail(MORAP_ESTATE, "reserve before build");
     CK(cudaSetDevice(c->cfg.device));
@@ -920,13 +969,16 @@ int morap::ctx_reserve(morap_ctx *c, int K) {
     const bool grow = Kp > c->Kcap;
     CKR(ensure_solve(c, Kp));
     size_t states = 0, chunks = 0;
-    for (int j = 0; j < c->nJ; ++j) {
+    // the evaluation buffers are sized for one assignment per weight; a
+    // context with a pair list has no fixed assignment shape (they grow on demand)
+    for (int j = 0; j < c->nJ && c->sel_agent.empty(); ++j) {
         uint32_t mx = 0;
         for (int i = 0; i < c->nI; ++i) mx = std::max(mx, c->h_prods[(size_t)i * c->nJ + j].n_nd);
         states += mx + 1;
         chunks += (mx + kEvalChunk - 1) / kEvalChunk;
     }
-    CKR(ensure_eval(c, (size_t)Kp * c->nJ, (size_t)Kp * chunks, (size_t)Kp * std::min<size_t>(states, kEvalStates)));
+    if (c->sel_agent.empty())
+        CKR(ensure_eval(c, (size_t)Kp * c->nJ, (size_t)Kp * chunks, (size_t)Kp * std::min<size_t>(states, kEvalStates)));
     for (int kp = 1; kp <= Kp; kp *= 2)
         for (int f = 0; f < 2; ++f) {
             if (f == 0 && !c->V32[0]) continue;
@@ -1056,9 +1108,16 @@ int validate_agent(int32_t n, int32_t s0, const int32_t *state_ptr, const int32_
     return MORAP_OK;
 }
 
-// Product construction K-B0 from the resident model arrays.
-int run_construction(morap_ctx *c, cudaStream_t s) {
-    CKL(launch_letters(c->d_prods, c->P, c->d_ad, c->d_td, c->d_lp, c->d_la, c->d_ap, c->d_letters, c->max_S, s));
+// Product construction K-B0 from the resident model arrays: letters, the
+// merged row counts, the rows' transition offsets, then the CSR itself.
+int run_construction(morap_ctx *c, cudaStream_t s, bool letters_and_counts = true) {
+    if (letters_and_counts) {
+        CKL(launch_letters(c->d_prods, c->P, c->d_ad, c->d_td, c->d_lp, c->d_la, c->d_ap, c->d_letters, c->max_S,
+                           s));
+        CKL(launch_row_count(c->d_prods, c->P, c->d_ad, c->d_td, c->d_sap, c->d_succ, c->d_letters, c->d_nd,
+                             c->row_cnt, nullptr, c->max_rows, s));
+    }
+    CKL(launch_row_offsets(c->d_prods, c->P, c->row_cnt, c->sa_tr, s));
     CKL(launch_build(c->d_prods, c->P, c->d_ad, c->d_td, c->d_sp, c->d_sap, c->d_succ, c->d_prob, c->d_cost,
                      c->d_letters, c->d_nd, c->state_sa, c->state_tr, c->sa_tr, c->col, c->cp32, c->p64, c->pdf,
                      c->cost32, c->cost64, c->costdf, c->TS, c->TSA, c->TT, c->max_work, s));
@@ -1127,7 +1186,7 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
     if (a_la.empty()) a_la.push_back(0);
     std::vector<ProdDesc> prods(P);
     std::vector<int4> chunks;
-    uint64_t TS = 0, TSA = 0, TT = 0, letters = 0, max_work = 1;
+    uint64_t TS = 0, TSA = 0, TT = 0, letters = 0, max_work = 1, max_rows = 1;
     for (int p = 0; p < P; ++p) {
             const int i = selected ? c->sel_agent[p] : p / nJ, j = selected ? c->sel_task[p] : p % nJ;
             ProdDesc &pd = prods[p];
@@ -1152,6 +1211,7 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
             TT += (uint64_t)t.Qn * a.T;
             letters += a.S;
             max_work = std::max<uint64_t>(max_work, (uint64_t)t.Qn * a.T + 1);
+            max_rows = std::max<uint64_t>(max_rows, (uint64_t)t.Qn * a.SA);
             if (TS >= 0x7fffffffull || TSA >= 0xffffffffull || TT >= 0xffffffffull)
                 return fail(MORAP_ENOMEM, "products exceed the 32-bit index range of one context");
             for (uint32_t b = 0; b < pd.n_nd; b += kChunk)
@@ -1164,7 +1224,7 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
                                nd_delta.size(), (size_t)letters, chunks.size(), (size_t)all_free,
                                (size_t)max_row_new};
     const bool reuse = c->built && sig == c->layout_sig &&
-                       std::memcmp(prods.data(), c->h_prods.data(), P * sizeof(ProdDesc)) == 0;
+                       std::memcmp(prods.data(), c->h_prods_key.data(), P * sizeof(ProdDesc)) == 0;
     if (!reuse) {
         free_eval(c);
         free_solve(c);
@@ -1174,29 +1234,28 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         c->nJ = nJ;
         c->P = P;
         c->h_prods = prods;
+        c->h_prods_key = prods;
         c->h_chunks = chunks;
         c->TS = (uint32_t)TS;
         c->TSA = (uint32_t)TSA;
-        c->TT = (uint32_t)TT;
+        c->TT = (uint32_t)TT;  // the unmerged count until the row counts are in
         c->max_S = max_S;
         c->max_work = (uint32_t)std::min<uint64_t>(max_work, 0xffffffffull);
+        c->max_rows = (uint32_t)std::min<uint64_t>(max_rows, 0xffffffffull);
         c->all_free_action = all_free;
         c->max_row = max_row_new;
-        c->csr_bytes = (int64_t)(8 * (TS + 1) + 4 * (TSA + 1) + 4 * TT + 8 * TT + 8 * TT + 8 * TT + 4 * TSA +
-                                 8 * TSA + 8 * TSA);
         auto &L = c->build_allocs;
         CKR(dev_alloc(c, L, &c->state_sa, (TS + 1) * 4));
         CKR(dev_alloc(c, L, &c->state_tr, (TS + 1) * 4));
         CKR(dev_alloc(c, L, &c->sa_tr, (TSA + 1) * 4));
-        CKR(dev_alloc(c, L, &c->col, std::max<uint64_t>(TT, 1) * 4));
-        CKR(dev_alloc(c, L, &c->cp32, std::max<uint64_t>(TT, 1) * 8));
-        CKR(dev_alloc(c, L, &c->pdf, std::max<uint64_t>(TT, 1) * 8));
+        CKR(dev_alloc(c, L, &c->row_cnt, std::max<uint64_t>(TSA, 1) * 4));
+        CKR(dev_alloc(c, L, &c->prod_tr, (size_t)P * 4));
         CKR(dev_alloc(c, L, &c->costdf, std::max<uint64_t>(TSA, 1) * 8));
-        CKR(dev_alloc(c, L, &c->p64, std::max<uint64_t>(TT, 1) * 8));
         CKR(dev_alloc(c, L, &c->cost32, std::max<uint64_t>(TSA, 1) * 4));
         CKR(dev_alloc(c, L, &c->cost64, std::max<uint64_t>(TSA, 1) * 8));
         CKR(dev_alloc(c, L, &c->d_prods, P * sizeof(ProdDesc)));
         CKR(dev_alloc(c, L, &c->d_chunks, std::max<size_t>(chunks.size(), 1) * sizeof(int4)));
+        CKR(dev_alloc(c, L, &c->d_chunk_u, std::max<size_t>(chunks.size(), 1) * sizeof(uint4)));
         CKR(dev_alloc(c, L, &c->in_items, std::max<size_t>(chunks.size(), 1) * kInItems * sizeof(int32_t)));
         CKR(dev_alloc(c, L, &c->item_w, std::max<size_t>(chunks.size(), 1) * sizeof(uint2)));
         for (int q = 0; q < 3; ++q) CKR(dev_alloc(c, L, &c->chg[q], std::max<size_t>(chunks.size(), 1)));
@@ -1212,7 +1271,6 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         CKR(dev_alloc(c, L, &c->d_ap, ap_ids.size() * 4));
         CKR(dev_alloc(c, L, &c->d_nd, nd_delta.size() * 2));
         CKR(dev_alloc(c, L, &c->d_letters, std::max<uint64_t>(letters, 1)));
-        c->layout_sig = sig;
     }
     auto up = [&](void *dst, const void *src, size_t bytes) -> int {
         if (bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
@@ -1225,6 +1283,15 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
     };
     CKR(upc(c->d_prods, prods.data(), P * sizeof(ProdDesc)));
     CKR(upc(c->d_chunks, chunks.data(), chunks.size() * sizeof(int4)));
+    {
+        std::vector<uint4> cu(chunks.size());
+        for (size_t q = 0; q < chunks.size(); ++q) {
+            const ProdDesc &pd = prods[chunks[q].x];
+            cu[q] = make_uint4(pd.state_off + (uint32_t)chunks[q].y, pd.state_off + (uint32_t)chunks[q].z,
+                               pd.state_off + pd.pre_begin, 0u);
+        }
+        CKR(upc(c->d_chunk_u, cu.data(), cu.size() * sizeof(uint4)));
+    }
     CKR(upc(c->d_ad, ad.data(), nI * sizeof(AgentDesc)));
     CKR(upc(c->d_td, td.data(), nJ * sizeof(TaskDesc)));
     CKR(upc(c->d_sp, a_sp.data(), a_sp.size() * 4));
@@ -1236,8 +1303,39 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
     CKR(upc(c->d_la, a_la.data(), a_la.size() * 4));
     CKR(upc(c->d_ap, ap_ids.data(), ap_ids.size() * 4));
     CKR(upc(c->d_nd, nd_delta.data(), nd_delta.size() * 2));
-    CKR(run_construction(c, s));
+    // first pass: the merged transition count of every row and product, then
+    // each product's transition offset and the total (one read-back)
+    CKL(launch_letters(c->d_prods, c->P, c->d_ad, c->d_td, c->d_lp, c->d_la, c->d_ap, c->d_letters, c->max_S, s));
+    CK(cudaMemsetAsync(c->prod_tr, 0, (size_t)P * 4, s));
+    CKL(launch_row_count(c->d_prods, c->P, c->d_ad, c->d_td, c->d_sap, c->d_succ, c->d_letters, c->d_nd, c->row_cnt,
+                         c->prod_tr, c->max_rows, s));
+    std::vector<uint32_t> ptr_count(P);
+    CK(cudaMemcpyAsync(ptr_count.data(), c->prod_tr, (size_t)P * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    uint64_t TTm = 0;
+    std::vector<ProdDesc> merged = prods;
+    for (int p = 0; p < P; ++p) {
+        merged[p].tr_off = (uint32_t)TTm;
+        merged[p].n_tr = ptr_count[p];
+        TTm += ptr_count[p];
+    }
+    if (reuse && TTm != c->TT) return fail(MORAP_ECUDA, "build: the merged transition count changed on a rebuild");
+    if (!reuse) {
+        auto &L = c->build_allocs;
+        c->TT = (uint32_t)TTm;
+        CKR(dev_alloc(c, L, &c->col, std::max<uint64_t>(TTm, 1) * 4));
+        CKR(dev_alloc(c, L, &c->cp32, std::max<uint64_t>(TTm, 1) * 8));
+        CKR(dev_alloc(c, L, &c->pdf, std::max<uint64_t>(TTm, 1) * 8));
+        CKR(dev_alloc(c, L, &c->p64, std::max<uint64_t>(TTm, 1) * 8));
+        c->csr_bytes = (int64_t)(8 * (TS + 1) + 4 * (TSA + 1) + 4 * TTm + 8 * TTm + 8 * TTm + 8 * TTm + 4 * TSA +
+                                 8 * TSA + 8 * TSA);
+        c->layout_sig = sig;
+    }
+    c->h_prods = merged;
+    CKR(upc(c->d_prods, merged.data(), P * sizeof(ProdDesc)));
+    CKR(run_construction(c, s, false));
     CK(cudaStreamSynchronize(s));  // the host vectors above go out of scope
+    TT = c->TT;
     c->built = true;
     c->last_h2d_bytes = (int64_t)h2d;
     if (fp) {
@@ -1284,6 +1382,7 @@ void morap_config_default(morap_config *cfg) {
     cfg->polish = 0;
     cfg->eval_block = 1;
     cfg->in_place = 0;
+    cfg->item_warps_max = 0;
 }
 
 const char *morap_last_error(void) { return g_last_error.c_str(); }
@@ -1310,6 +1409,9 @@ int morap_ctx_create(const morap_config *cfg, morap_ctx **out) {
     if (c.polish != 0 && c.polish != 1) return fail(MORAP_EINVAL, "config: polish must be 0 or 1");
     if (c.eval_block != 0 && c.eval_block != 1) return fail(MORAP_EINVAL, "config: eval_block must be 0 or 1");
     if (c.in_place != 0 && c.in_place != 1) return fail(MORAP_EINVAL, "config: in_place must be 0 or 1");
+    if (c.item_warps_max != 0 && c.item_warps_max != 1 && c.item_warps_max != 2 && c.item_warps_max != 4 &&
+        c.item_warps_max != 8)
+        return fail(MORAP_EINVAL, "config: item_warps_max must be 0, 1, 2, 4 or 8");
     if (c.skip_unchanged != 0 && c.skip_unchanged != 1)
         return fail(MORAP_EINVAL, "config: skip_unchanged must be 0 or 1");
     CK(cudaSetDevice(c.device));
@@ -1651,7 +1753,7 @@ int morap_solve_plain(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_produ
             const ProdDesc &pd = ctx->h_prods[pair_product[e]];
             const uint32_t n = pd.n_nd, n_sa = (uint32_t)pd.Qn * pd.SA;
             const uint32_t pre_sa = (uint32_t)(pd.pre_begin / std::max<uint32_t>(pd.S, 1)) * pd.SA;
-            const uint32_t n_tr = (uint32_t)pd.Qn * pd.T;
+            const uint32_t n_tr = pd.n_tr;
             const double wi = pair_w[2 * e], wp = pair_w[2 * e + 1];
             CK(cudaMemsetAsync(x, 0, (size_t)(n + 1) * 8, s));
             CK(cudaMemsetAsync(y, 0, (size_t)(n + 1) * 8, s));
@@ -1823,7 +1925,7 @@ int morap_product_info(const morap_ctx *ctx, int32_t p, int64_t *info) {
     info[1] = pd.Qn;
     info[2] = (int64_t)pd.n_nd + 1;
     info[3] = (int64_t)pd.Qn * pd.SA;
-    info[4] = (int64_t)pd.Qn * pd.T;
+    info[4] = (int64_t)pd.n_tr;
     info[5] = pd.init_local;
     info[6] = pd.state_off;
     info[7] = pd.pre_begin;
@@ -1840,7 +1942,7 @@ int morap_product_download(morap_ctx *ctx, int32_t p, int64_t *state_sa, int64_t
     if (p < 0 || p >= ctx->P) return fail(MORAP_EINVAL, "product index out of range");
     CK(cudaSetDevice(ctx->cfg.device));
     const ProdDesc &pd = ctx->h_prods[p];
-    const size_t ns = pd.n_nd + 1, nsa = (size_t)pd.Qn * pd.SA, nt = (size_t)pd.Qn * pd.T;
+    const size_t ns = pd.n_nd + 1, nsa = (size_t)pd.Qn * pd.SA, nt = pd.n_tr;
     std::vector<uint32_t> tmp;
     if (state_sa) {
         tmp.resize(ns + 1);

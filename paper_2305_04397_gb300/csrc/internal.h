@@ -102,6 +102,7 @@ struct ProdDesc {
     int32_t Qn;
     uint32_t letter_off; // offset of this product's letter table (per agent state)
     uint32_t item_off;   // index of the product's first sweep work item
+    uint32_t n_tr;       // product transitions (successors into the done slot merged per row)
 };
 
 struct AgentDesc {
@@ -167,6 +168,7 @@ struct SweepArgs {
     const float *cost32;
     const double *cost64;
     const int4 *chunks;   // {product, begin, end, first}
+    const uint4 *chunk_u; // per item {first state, end state, product's first pre-sink state, 0}, global indices
     const ProdDesc *prods;
     const float2 *pdf;    // per transition: p as a double-float (hi, lo)
     const float2 *costdf; // per state-action: cost as a double-float
@@ -195,6 +197,7 @@ struct SweepArgs {
     double eps1;
     float eps1f;  // eps1 rounded to FP32 (record tests in the kernels)
     int P;
+    int gmax;     // most warps per work item (1, 2, 4 or 8)
 };
 
 struct EvalArgs {
@@ -230,6 +233,8 @@ struct EvalArgs {
 
 // Engine helpers the serving layer uses (engine.cu).
 int ctx_reserve(morap_ctx *c, int K);
+int ctx_merge(morap_ctx *const *ctxs, int n, morap_ctx **out, std::vector<int32_t> &agent_off,
+              std::vector<int32_t> &task_off, std::vector<int32_t> &pair_off);
 
 // ---------------------------------------------------------- kernel launchers
 // (defined in the .cu files; every launcher enqueues on `s` and returns the
@@ -237,6 +242,15 @@ int ctx_reserve(morap_ctx *c, int K);
 int launch_letters(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                    const int32_t *label_ptr, const int32_t *label_ap, const int32_t *ap_ids, uint8_t *letters,
                    uint32_t max_S, void *s);
+// Product construction, first pass: the number of transitions of every
+// product row after merging its successors into the done slot (row_cnt[row]),
+// and, when prod_tr is not NULL, their sum per product (added to prod_tr[p]).
+int launch_row_count(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
+                     const int32_t *a_sa_ptr, const int32_t *a_succ, const uint8_t *letters,
+                     const int16_t *nd_delta, uint32_t *row_cnt, uint32_t *prod_tr, uint32_t max_rows, void *s);
+// Second pass: sa_tr[row] = the product's tr_off + the exclusive prefix sum
+// of row_cnt over the product's rows (one block per product).
+int launch_row_offsets(const ProdDesc *prods, int P, const uint32_t *row_cnt, uint32_t *sa_tr, void *s);
 int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                  const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ, const double *a_prob,
                  const double *a_cost, const uint8_t *letters, const int16_t *nd_delta, uint32_t *state_sa,
@@ -249,10 +263,11 @@ int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, in
 int launch_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, const uint32_t *state_tr,
                        const int32_t *col, int32_t *in_items, uint2 *item_w, const uint32_t *state_sa,
                        void *s);
-// chg_prev (nullable, [n_items]): set to 1 so that the first sweep recomputes every item
+// chg_prev (nullable, [n_items]): set to 1 so that the first sweep recomputes every item;
+// w_pair (nullable, [n_pairs]): pairs whose two weights are both 0 start frozen
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
                      size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s,
-                     uint8_t *chg_prev = nullptr);
+                     uint8_t *chg_prev = nullptr, const double2 *w_pair = nullptr);
 // Sweep kinds: the FP32 round-down phase, the double-float polish, and the
 // polish as an FP32 residual correction on a double-float table.
 enum { kSweepF32 = 0, kSweepDF = 1, kSweepDelta = 2 };

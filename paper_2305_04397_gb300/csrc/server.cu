@@ -1,16 +1,28 @@
 // Serving: threshold-point queries (Algorithm 1, Sec. 3.3) over several
 // resident instances with continuous batching.
 //
-// Every query is an Algorithm 1 state machine on the host.  A query that
-// needs its next supporting point waits on its instance; an idle instance
-// takes every waiting query (up to max_batch) as one batch of weight
-// vectors for morap_supporting_points, so queries that arrive while a batch
-// runs join the next one.  Instances run on their own streams from a pool
-// of worker threads, so the batches of different instances overlap on the
-// device.  Queries are admitted in arrival order while the device bytes
-// their weights occupy (values, recorded actions, schedulers) fit the
-// budget; results do not depend on the batch a query rides in, because each
-// (product, weight) pair runs exactly its own sweeps.
+// Every query is an Algorithm 1 state machine on the host.  Two ways to
+// batch the supporting points the queries wait for:
+//
+//  * across instances (merge_instances = 1, the default): one context holds
+//    the products of every instance (a pair list), and one device round
+//    takes the waiting queries of all instances (up to max_batch) as the
+//    columns of one batch of weight vectors.  Query k's column weighs only
+//    its instance's agents and tasks, so every other product starts that
+//    column frozen at value 0 and costs nothing.  After the round the host
+//    takes each query's assignment on its instance's block of c, one
+//    Algorithm 4 call evaluates every query's assigned pairs, and the
+//    Algorithm 1 steps run on the worker threads while the next round is
+//    already on the device.
+//  * per instance (merge_instances = 0): an idle instance takes its own
+//    waiting queries as one morap_supporting_points batch on its own
+//    stream; the batches of different instances overlap on the device.
+//
+// Queries that arrive while a round runs join the next one.  Queries are
+// admitted in arrival order while the device bytes their weights occupy
+// (values, recorded actions, schedulers) fit the budget; results do not
+// depend on the batch a query rides in, because each (product, weight) pair
+// runs exactly its own sweeps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -59,6 +71,21 @@ struct morap_server {
     std::vector<std::thread> workers;
     std::thread scheduler;
     std::deque<int> jobs;  // instances with a batch to run
+    // merged mode: the context of every instance's products and where each
+    // instance's agents, tasks and products start in it
+    morap_ctx *merged = nullptr;
+    std::vector<int32_t> agent_off, task_off, pair_off, n_agents;
+    int n_obj_total = 0;
+    cudaStream_t merged_stream = nullptr;
+    std::deque<int64_t> ready_all;  // admitted queries waiting for a supporting point (all instances)
+    struct StepJob {
+        int64_t ticket;
+        std::vector<double> r;
+        std::vector<int32_t> f;
+        int status;
+    };
+    std::deque<StepJob> steps;      // Algorithm 1 steps for the worker threads
+    std::thread rounds;
     // stats
     std::vector<double> latencies_ms;
     int64_t submitted = 0, completed = 0, batches = 0, batch_queries = 0;
@@ -77,11 +104,14 @@ void scheduler_loop(morap_server *S) {
             if (S->cfg.hbm_budget && S->in_use + q.cost > (int64_t)S->cfg.hbm_budget && S->in_use > 0) break;
             q.admitted = true;
             S->in_use += q.cost;
-            S->ready[q.inst].push_back(q.ticket);
+            if (S->merged)
+                S->ready_all.push_back(q.ticket);
+            else
+                S->ready[q.inst].push_back(q.ticket);
             S->pending.pop_front();
         }
         bool dispatched = false;
-        for (size_t i = 0; i < S->inst.size(); ++i)
+        for (size_t i = 0; i < S->inst.size() && !S->merged; ++i)
             if (!S->busy[i] && !S->ready[i].empty()) {
                 S->busy[i] = 1;
                 S->jobs.push_back((int)i);
@@ -150,6 +180,128 @@ void worker_loop(morap_server *S) {
     }
 }
 
+// Merged mode, device side: one round per batch of waiting queries of any
+// instance (Algorithm 3 for every query's weights on the merged context,
+// the assignment per query, Algorithm 4 on the assigned pairs of all
+// queries in one call); the Algorithm 1 steps go to the worker threads.
+void round_loop(morap_server *S) {
+    std::unique_lock<std::mutex> lk(S->mu);
+    const int P = S->pair_off.back() + S->n_agents.back() * S->n_tasks.back();  // products of the merged context
+    for (;;) {
+        while (!S->stop && S->ready_all.empty()) S->cv.wait(lk);
+        if (S->stop) return;
+        std::vector<int64_t> batch;
+        while (!S->ready_all.empty() && (int)batch.size() < S->cfg.max_batch) {
+            batch.push_back(S->ready_all.front());
+            S->ready_all.pop_front();
+        }
+        const int K = (int)batch.size(), n = S->n_obj_total;
+        std::vector<double> W((size_t)K * n, 0.0);
+        std::vector<int> inst(K);
+        for (int k = 0; k < K; ++k) {
+            const ServerQuery &q = S->queries[batch[k]];
+            const int i = q.inst, nI = S->n_agents[i], nJ = S->n_tasks[i];
+            inst[k] = i;
+            for (int a = 0; a < nI; ++a) W[(size_t)k * n + S->agent_off[i] + a] = q.ps.w[a];
+            for (int t = 0; t < nJ; ++t) W[(size_t)k * n + S->agent_off.back() + S->n_agents.back() + S->task_off[i] + t] = q.ps.w[nI + t];
+        }
+        lk.unlock();
+        std::vector<double> C((size_t)K * P);
+        std::vector<int32_t> st((size_t)K * P);
+        int rc = morap_solve(S->merged, K, W.data(), (void *)S->merged_stream, C.data(), nullptr, nullptr, st.data());
+        std::vector<std::vector<int32_t>> F(K);
+        std::vector<int> status(K, MORAP_OK);
+        std::vector<int32_t> ev_p, ev_k;
+        std::vector<std::pair<int, int>> ev_slot;  // (query, agent) of each evaluated pair
+        std::vector<int> ev_task;
+        if (rc == MORAP_OK || rc == MORAP_ENOTCONV) {
+            for (int k = 0; k < K; ++k) {
+                const int i = inst[k], nI = S->n_agents[i], nJ = S->n_tasks[i], p0 = S->pair_off[i];
+                std::vector<double> Ci((size_t)nI * nJ);
+                for (int a = 0; a < nI; ++a)
+                    for (int t = 0; t < nJ; ++t) {
+                        const size_t o = (size_t)k * P + p0 + (size_t)a * nJ + t;
+                        Ci[(size_t)a * nJ + t] = C[o];
+                        if (st[o] != MORAP_OK) status[k] = MORAP_ENOTCONV;
+                    }
+                F[k].assign(nJ, -1);
+                assign_tasks(nI, nJ, Ci.data(), F[k].data());
+                for (int t = 0; t < nJ; ++t)
+                    if (F[k][t] >= 0) {
+                        ev_p.push_back(p0 + F[k][t] * nJ + t);
+                        ev_k.push_back(k);
+                        ev_slot.emplace_back(k, F[k][t]);
+                        ev_task.push_back(t);
+                    }
+            }
+        }
+        std::vector<double> rc_v(ev_p.size()), rp_v(ev_p.size());
+        if ((rc == MORAP_OK || rc == MORAP_ENOTCONV) && !ev_p.empty()) {
+            const int rc2 = morap_evaluate(S->merged, (int32_t)ev_p.size(), ev_p.data(), ev_k.data(),
+                                           (void *)S->merged_stream, rc_v.data(), rp_v.data());
+            if (rc2 == MORAP_ENOTCONV) {
+                for (auto &sl : ev_slot) status[sl.first] = MORAP_ENOTCONV;
+            } else if (rc2 != MORAP_OK) {
+                rc = rc2;
+            }
+        }
+        lk.lock();
+        S->batches += 1;
+        S->batch_queries += K;
+        for (int k = 0; k < K; ++k) {
+            const int i = inst[k], nI = S->n_agents[i], nJ = S->n_tasks[i];
+            morap_server::StepJob job;
+            job.ticket = batch[k];
+            job.status = (rc == MORAP_OK || rc == MORAP_ENOTCONV) ? status[k] : rc;
+            job.r.assign((size_t)nI + nJ, 0.0);
+            job.f = F[k].empty() ? std::vector<int32_t>(nJ, -1) : F[k];
+            S->steps.push_back(std::move(job));
+        }
+        for (size_t e = 0; e < ev_p.size(); ++e) {
+            // the jobs of this round are the last K in the queue, in query order
+            morap_server::StepJob &job = S->steps[S->steps.size() - K + ev_slot[e].first];
+            const int nI = S->n_agents[inst[ev_slot[e].first]];
+            job.r[ev_slot[e].second] = rc_v[e];
+            job.r[nI + ev_task[e]] = rp_v[e];
+        }
+        S->cv.notify_all();
+    }
+}
+
+// Merged mode, host side: one Algorithm 1 step per job.
+void step_loop(morap_server *S) {
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        while (!S->stop && S->steps.empty()) S->cv.wait(lk);
+        if (S->stop) return;
+        morap_server::StepJob job = std::move(S->steps.front());
+        S->steps.pop_front();
+        ServerQuery &q = S->queries[job.ticket];
+        if (job.status != MORAP_OK && job.status != MORAP_ENOTCONV) {
+            q.ps.status = job.status;
+            q.ps.done = true;
+        } else {
+            Alg1 ps = q.ps;  // host QPs outside the lock, on a private copy
+            if (job.status == MORAP_ENOTCONV && ps.status == MORAP_OK) ps.status = job.status;
+            lk.unlock();
+            ps.step(job.r.data(), job.f.data(), (int)job.f.size());
+            lk.lock();
+            q.ps = std::move(ps);
+        }
+        if (q.ps.done) {
+            q.t_done = std::chrono::steady_clock::now();
+            S->in_use -= q.cost;
+            S->completed += 1;
+            S->latencies_ms.push_back(std::chrono::duration<double, std::milli>(q.t_done - q.t_submit).count());
+            S->t_last = q.t_done;
+        } else {
+            S->ready_all.push_back(q.ticket);
+        }
+        S->cv.notify_all();
+        S->cv_done.notify_all();
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -161,6 +313,7 @@ void morap_server_config_default(morap_server_config *cfg) {
     cfg->n_workers = 8;
     cfg->eps = 1e-6;
     cfg->max_iter = 64;
+    cfg->merge_instances = 1;
 }
 
 int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const morap_server_config *cfg_in,
@@ -171,8 +324,10 @@ int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const 
         cfg = *cfg_in;
     else
         morap_server_config_default(&cfg);
-    if (cfg.max_batch < 1 || cfg.max_batch > 64 || cfg.n_workers < 1 || !(cfg.eps >= 0) || cfg.max_iter < 1)
-        return fail(MORAP_EINVAL, "server: max_batch in 1..64, n_workers >= 1, eps >= 0, max_iter >= 1");
+    if (cfg.max_batch < 1 || cfg.max_batch > 64 || cfg.n_workers < 1 || !(cfg.eps >= 0) || cfg.max_iter < 1 ||
+        (cfg.merge_instances != 0 && cfg.merge_instances != 1))
+        return fail(MORAP_EINVAL,
+                    "server: max_batch in 1..64, n_workers >= 1, eps >= 0, max_iter >= 1, merge_instances 0 or 1");
     auto *S = new morap_server();
     S->cfg = cfg;
     for (int i = 0; i < n_instances; ++i) {
@@ -203,6 +358,7 @@ int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const 
         S->inst.push_back(c);
         S->n_obj.push_back(nI + nJ);
         S->n_tasks.push_back(nJ);
+        S->n_agents.push_back(nI);
         S->bytes_per_weight.push_back(bpw);
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -214,8 +370,33 @@ int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const 
     }
     S->busy.assign(n_instances, 0);
     S->ready.resize(n_instances);
+    if (cfg.merge_instances) {
+        int rc = ctx_merge(instances, n_instances, &S->merged, S->agent_off, S->task_off, S->pair_off);
+        if (rc == MORAP_OK && cudaStreamCreateWithFlags(&S->merged_stream, cudaStreamNonBlocking) != cudaSuccess)
+            rc = fail(MORAP_ECUDA, "server: cudaStreamCreate");
+        if (rc == MORAP_OK) {
+            int64_t states = 0;
+            for (int i = 0; i < n_instances; ++i) states += S->bytes_per_weight[i] / 26;
+            int reserve = cfg.max_batch;
+            if (cfg.hbm_budget)
+                reserve = (int)std::min<int64_t>(reserve, std::max<int64_t>(1, (int64_t)cfg.hbm_budget / (26 * states)));
+            if (ctx_reserve(S->merged, reserve) != MORAP_OK) set_error("");  // buffers then grow on demand
+        }
+        if (rc != MORAP_OK) {
+            if (S->merged) morap_ctx_destroy(S->merged);
+            for (auto s : S->streams) cudaStreamDestroy(s);
+            delete S;
+            return rc;
+        }
+        S->n_obj_total = S->agent_off.back() + S->n_agents.back() + S->task_off.back() + S->n_tasks.back();
+    }
     S->scheduler = std::thread(scheduler_loop, S);
-    for (int k = 0; k < cfg.n_workers; ++k) S->workers.emplace_back(worker_loop, S);
+    if (S->merged) {
+        S->rounds = std::thread(round_loop, S);
+        for (int k = 0; k < cfg.n_workers; ++k) S->workers.emplace_back(step_loop, S);
+    } else {
+        for (int k = 0; k < cfg.n_workers; ++k) S->workers.emplace_back(worker_loop, S);
+    }
     *out = S;
     return MORAP_OK;
 }
@@ -228,9 +409,12 @@ int morap_server_destroy(morap_server *S) {
     }
     S->cv.notify_all();
     if (S->scheduler.joinable()) S->scheduler.join();
+    if (S->rounds.joinable()) S->rounds.join();
     for (auto &t : S->workers)
         if (t.joinable()) t.join();
     for (auto s : S->streams) cudaStreamDestroy(s);
+    if (S->merged_stream) cudaStreamDestroy(S->merged_stream);
+    if (S->merged) morap_ctx_destroy(S->merged);
     delete S;
     return MORAP_OK;
 }

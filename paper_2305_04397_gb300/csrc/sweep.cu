@@ -615,19 +615,38 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
     store_words<NW>(Vnew + row, yw);
 }
 
-// Work items are kChunk-state ranges of one product taken by whole warps
-// (dynamic scheduling, no block barriers), walked in batches of up to 32
-// states: the warp copies the batch's state starts, action-row starts, costs
-// and (successor, probability) stream into its own shared-memory buffer with
-// cp.async, then computes.  Inside a batch, LPS lanes share a state and each
-// lane owns VEC of the Kp weights, so a successor's value row is read once,
-// coalesced, for all weights.
+// Named barrier of the G warps (G * 32 threads) of a work group; id >= 1
+// (0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Work items are kChunk-state ranges of one product taken by groups of G
+// warps (dynamic scheduling), walked in batches of up to 32 states: a warp
+// copies the batch's state starts, action-row starts, costs and (successor,
+// probability) stream into its own shared-memory buffer with cp.async, then
+// computes.  Inside a batch, LPS lanes share a state and each lane owns VEC
+// of the Kp weights, so a successor's value row is read once, coalesced, for
+// all weights.
+//
+// G is 1 (one warp per item, no barriers) while the sweep's work list holds
+// at least half as many items as the grid has warps; shorter lists (the late
+// sweeps of a loop) split each item's states over G = 2, 4 or 8 warps of a
+// block, so the item's chain of dependent loads is walked G times faster.
+// Every warp of a group reads the item's bookkeeping (activity, exact-skip
+// inputs) itself and takes the same decisions; the group's first warp does
+// the item's writes (work list, freezes, change flag, residuals, counters)
+// after a barrier that combines the warps' change flags and residuals.  The
+// per-(state, weight) arithmetic does not depend on G, so neither do the
+// results.
 template <class Ar, int KP, int VMAX, int D, int MINB, int PIPE>
 __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) {
     using SH = Shape<Ar, KP, VMAX>;
     constexpr int VEC = SH::VEC, LPS = SH::LPS, SPW = SH::SPW;
     constexpr int NW = VEC * Ar::WORDS;
     constexpr int ROW = KP * Ar::WORDS;
+    constexpr int WPB = kThreads / 32;  // warps per block
+    constexpr int GMAX = (kChunk / SPW) < WPB ? (kChunk / SPW) : WPB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int cur = pos % 3, nxt = (pos + 1) % 3, far = (pos + 2) % 3;
     const float *__restrict__ Vold = static_cast<const float *>(a.V[pos & 1]);
@@ -644,26 +663,43 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         unsigned long long updates, bytes;
         unsigned int skipped, computed;
     } b_stats;
+    // group exchange: the item of the next two rounds (double buffered), each
+    // warp's change flag and per-weight residuals
+    __shared__ unsigned int g_it[2][WPB];
+    __shared__ unsigned char g_chg[WPB];
+    __shared__ float g_res[WPB][KP];
     if (threadIdx.x == 0) b_stats.updates = b_stats.bytes = 0ull, b_stats.skipped = b_stats.computed = 0u;
     __syncthreads();
     const unsigned int n_items = ctl->cnt[cur];
     const unsigned int sweep = ctl->sweep_base + pos;
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;  // warp in block
     const int grp = lane / LPS, li = lane % LPS, k0 = li * VEC;
-    unsigned char *warp_buf = smem_raw + (threadIdx.x >> 5) * (Ar::STAGE_BYTES + KP * (int)sizeof(typename Ar::W));
+    unsigned char *warp_buf = smem_raw + wib * (Ar::STAGE_BYTES + KP * (int)sizeof(typename Ar::W));
     unsigned char *stage_buf = warp_buf;
     uint32_t *ssa = reinterpret_cast<uint32_t *>(stage_buf);
     typename Ar::W *wsm = reinterpret_cast<typename Ar::W *>(warp_buf + Ar::STAGE_BYTES);  // the item's weights
 
+    const unsigned int n_warps = gridDim.x * WPB;
+    int G = 1;  // warps per item, the same in every block
+    const int gcap = a.gmax < GMAX ? a.gmax : GMAX;
+    while (G < gcap && (unsigned long long)(2 * G) * n_items <= n_warps) G *= 2;
+    const int gib = wib / G;           // group in block
+    const int g = wib % G;             // warp in group
+    const bool leader = g == 0;
+    const int bar_id = 1 + gib, bar_threads = 32 * G;
+    const unsigned int n_groups = n_warps / G;
+    const unsigned int group_id = blockIdx.x * (WPB / G) + gib;
+
     // The shared counters see few atomics: the statistics are summed per warp
     // and per block, and items that stay in the work list are collected per
-    // warp (lane i holds the i-th) and appended a.keep_batch at a time.
-    // Large instances append each item at once instead (keep_batch = 1):
-    // then the next list keeps the order of this one (neighbouring items stay
-    // neighbours), which keeps the value gathers of concurrent warps close
-    // together when the values do not fit in L2; batches would interleave
-    // the warps' items from one sweep to the next.
-    unsigned long long w_updates = 0, w_bytes = 0;  // lane 0's running sums
+    // group leader (lane i holds the i-th) and appended a.keep_batch at a
+    // time.  Large instances append each item at once instead (keep_batch =
+    // 1): then the next list keeps the order of this one (neighbouring items
+    // stay neighbours), which keeps the value gathers of concurrent warps
+    // close together when the values do not fit in L2; batches would
+    // interleave the warps' items from one sweep to the next.
+    unsigned long long w_updates = 0, w_bytes = 0;  // lane 0's running sums (leaders)
     unsigned int w_skipped = 0, w_computed = 0;
     unsigned int kept = 0u;
     int n_kept = 0;  // warp-uniform
@@ -674,18 +710,23 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         if (lane < n_kept) a.list[nxt][at + lane] = kept;
         n_kept = 0;
     };
-    // Warp w of the grid takes list entry w without an atomic; later items
+    // Group g of the grid takes list entry g without an atomic; later items
     // are taken one at a time from a shared cursor that starts after those.
-    const unsigned int n_warps = gridDim.x * (kThreads / 32);
     const int keep_batch = a.keep_batch;
     bool first = true;
-    for (;;) {
-        unsigned int it = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    for (int round = 0;; ++round) {
+        unsigned int it = group_id;
         if (!first) {
-            if (lane == 0) it = n_warps + atomicAdd(&ctl->next[cur], 1u);
-            it = __shfl_sync(0xffffffffu, it, 0);
+            if (leader && lane == 0) it = n_groups + atomicAdd(&ctl->next[cur], 1u);
         }
         first = false;
+        if (G == 1) {
+            it = __shfl_sync(0xffffffffu, it, 0);
+        } else {
+            if (leader && lane == 0) g_it[round & 1][gib] = it;
+            group_sync(bar_id, bar_threads);
+            it = g_it[round & 1][gib];
+        }
         if (it >= n_items) break;
         const unsigned int item = a.list[cur][it];
         // the exact-skip test's inputs (see below) depend only on the
@@ -698,6 +739,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             in_chg = (lane == 0 && a.chg[far][item]) || in == -2 || (in >= 0 && a.chg[far][in]);
         }
         const int4 ch = a.chunks[item];
+        const uint4 cu = a.chunk_u[item];  // the item's global state range and its product's first pre-sink state
         const int p = ch.x;
         const size_t pair0 = (size_t)p * KP;
         // activity of the product's weights from the previous sweep's residuals
@@ -716,16 +758,15 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         }
         const bool any_active = (act_w[0] | act_w[1]) != 0u;
         if ((nz_w[0] | nz_w[1]) == 0u) {  // converged earlier and already copied: drop
-            if (ch.w)
+            if (ch.w && leader)
                 for (int k = lane; k < KP; k += 32) a.frozen[pair0 + k] = 1;
             continue;
         }
-        const ProdDesc pd = a.prods[p];
-        if (any_active) {
+        if (any_active && leader) {
             if (lane == n_kept) kept = item;
             if (++n_kept == keep_batch) flush_kept();
         }
-        if (ch.w)
+        if (ch.w && leader)
             for (int k = lane; k < KP; k += 32) {
                 res_next[pair0 + k] = 0ull;
                 if ((act_w[k >> 5] >> (k & 31)) & 1u)
@@ -738,7 +779,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             // sweep, so it would reproduce its values bit for bit (and both
             // value buffers already hold them)
             if (!__any_sync(0xffffffffu, in_chg)) {
-                if (lane == 0) {  // no update executed and no byte moved
+                if (leader && lane == 0) {  // no update executed and no byte moved
                     a.chg[cur][item] = 0;
                     ++w_skipped;
                 }
@@ -757,25 +798,28 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         float rmax[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) rmax[v] = 0.0f;
+        // this warp's share of the item's states (global state indices)
+        const int span = ((int)(cu.y - cu.x) + G - 1) / G;
+        const int s_begin = min((int)cu.y, (int)cu.x + g * span), s_end = min((int)cu.y, s_begin + span);
 
         if (!any_active) {  // every weight of the product froze: copy its rows once
-            for (int s = ch.y + grp; s < ch.z; s += SPW) {
-                const size_t row = (size_t)(pd.state_off + (uint32_t)s) * ROW + (size_t)k0 * Ar::WORDS;
+            for (int s = s_begin + grp; s < s_end; s += SPW) {
+                const size_t row = (size_t)(uint32_t)s * ROW + (size_t)k0 * Ar::WORDS;
                 float yw[NW];
                 load_words<NW>(Vold + row, yw);
                 store_words<NW>(Vnew + row, yw);
             }
-        } else {
+        } else if (s_begin < s_end) {
             // a batch's state boundaries are loaded while the previous
             // batch is staged and computed
             uint32_t nx_sa = 0, nx_tr = 0;
-            if (lane <= min(kStageStates, ch.z - ch.y)) {
-                nx_sa = __ldg(a.state_sa + pd.state_off + (uint32_t)ch.y + lane);
-                nx_tr = __ldg(a.state_tr + pd.state_off + (uint32_t)ch.y + lane);
+            if (lane <= min(kStageStates, s_end - s_begin)) {
+                nx_sa = __ldg(a.state_sa + (uint32_t)s_begin + lane);
+                nx_tr = __ldg(a.state_tr + (uint32_t)s_begin + lane);
             }
-            for (int s0 = ch.y; s0 < ch.z;) {
-                const int m_max = min(kStageStates, ch.z - s0);
-                const uint32_t u0 = pd.state_off + (uint32_t)s0;
+            for (int s0 = s_begin; s0 < s_end;) {
+                const int m_max = min(kStageStates, s_end - s0);
+                const uint32_t u0 = (uint32_t)s0;
                 const uint32_t my_sa = nx_sa, my_tr = nx_tr;
                 const uint32_t A0 = __shfl_sync(0xffffffffu, my_sa, 0);
                 const uint32_t T0 = __shfl_sync(0xffffffffu, my_tr, 0);
@@ -787,7 +831,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                 const uint32_t A1 = __shfl_sync(0xffffffffu, my_sa, m);
                 const uint32_t T1 = __shfl_sync(0xffffffffu, my_tr, m);
                 if (lane <= m) ssa[lane] = my_sa;
-                if (s0 + m < ch.z && lane <= min(kStageStates, ch.z - (s0 + m))) {
+                if (s0 + m < s_end && lane <= min(kStageStates, s_end - (s0 + m))) {
                     nx_sa = __ldg(a.state_sa + u0 + (uint32_t)m + lane);
                     nx_tr = __ldg(a.state_tr + u0 + (uint32_t)m + lane);
                 }
@@ -807,19 +851,15 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                 for (int i = grp; i < m; i += SPW)
                     if constexpr (PIPE)
                         process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
-                                                            (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits,
-                                                            Vold, Vnew, k0, rmax, changed);
+                                                            u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits, Vold,
+                                                            Vnew, k0, rmax, changed);
                     else
                         process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
-                                                       (uint32_t)(s0 + i) >= pd.pre_begin, wsm + k0, act_bits, Vold,
-                                                       Vnew, k0, rmax, changed);
+                                                       u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits, Vold, Vnew, k0,
+                                                       rmax, changed);
                 __syncwarp();  // the next batch reuses the buffer
                 s0 += m;
             }
-        }
-        {
-            const bool any_chg = __any_sync(0xffffffffu, changed);
-            if (lane == 0) a.chg[cur][item] = any_chg ? 1 : 0;
         }
         // residual: lanes with the same li share weights
 #pragma unroll
@@ -827,23 +867,44 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             float r = rmax[v];
 #pragma unroll
             for (int off = LPS; off < 32; off <<= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
-            if (grp == 0 && any_active && r > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)r);
+            rmax[v] = r;
         }
-        if (lane == 0) {
-            const uint32_t n_s = (uint32_t)(ch.z - ch.y);
-            w_bytes += 2ull * n_s * ROW * 4;
-            if (any_active) {
-                const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
-                ++w_computed;
-                w_updates += (unsigned long long)iw.x * (unsigned long long)n_act;
-                // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
-                w_bytes += 8ull * (n_s + 1) + 4ull * (iw.y + 1) + 4ull * (1 + Ar::WORDS) * iw.x;
-                // per row: its cost, or for the residual correction its row of G
-                w_bytes += (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * iw.y;
+        bool any_chg = __any_sync(0xffffffffu, changed);
+        if (G > 1) {  // combine the group's warps in shared memory
+            if (grp == 0)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) g_res[wib][k0 + v] = rmax[v];
+            if (lane == 0) g_chg[wib] = any_chg ? 1 : 0;
+            group_sync(bar_id, bar_threads);
+            if (leader) {
+                for (int q = 1; q < G; ++q) {
+                    any_chg = any_chg || g_chg[wib + q] != 0;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) rmax[v] = fmaxf(rmax[v], g_res[wib + q][k0 + v]);
+                }
+            }
+        }
+        if (leader) {
+            if (lane == 0) a.chg[cur][item] = any_chg ? 1 : 0;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v)
+                if (grp == 0 && any_active && rmax[v] > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)rmax[v]);
+            if (lane == 0) {
+                const uint32_t n_s = cu.y - cu.x;
+                w_bytes += 2ull * n_s * ROW * 4;
+                if (any_active) {
+                    const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
+                    ++w_computed;
+                    w_updates += (unsigned long long)iw.x * (unsigned long long)n_act;
+                    // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
+                    w_bytes += 8ull * (n_s + 1) + 4ull * (iw.y + 1) + 4ull * (1 + Ar::WORDS) * iw.x;
+                    // per row: its cost, or for the residual correction its row of G
+                    w_bytes += (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * iw.y;
+                }
             }
         }
     }
-    if (n_kept) flush_kept();
+    if (leader && n_kept) flush_kept();
     // statistics: per block in shared memory, then one global atomic each
     if (lane == 0) {
         if (w_updates) atomicAdd(&b_stats.updates, w_updates);
@@ -1450,9 +1511,12 @@ __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, in
     }
 }
 
+// w_pair (nullable): per (product, weight) pair its two weights; a pair with
+// both 0 has every value 0 at every sweep (each Q is 0), so it starts frozen
+// ("previous" residual 0) instead of being swept once to find that out.
 __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *r0,
                             unsigned long long *r1, unsigned long long *r2, size_t n_pairs, int32_t *sweeps_pair,
-                            uint8_t *frozen, unsigned int cap, uint8_t *chg_prev) {
+                            uint8_t *frozen, unsigned int cap, uint8_t *chg_prev, const double2 *w_pair) {
     const size_t gid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = gid; i < n_items; i += stride) {
         list0[i] = (unsigned int)i;
@@ -1462,7 +1526,9 @@ __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_it
     for (size_t i = gid; i < n_pairs; i += stride) {
         r0[i] = 0ull;
         r1[i] = 0ull;
-        r2[i] = inf_bits;  // "previous" residual of sweep 0: everything active
+        // "previous" residual of sweep 0: everything active, except pairs with no weight
+        const bool idle = w_pair && w_pair[i].x == 0.0 && w_pair[i].y == 0.0;
+        r2[i] = idle ? 0ull : inf_bits;
         sweeps_pair[i] = 0;
         frozen[i] = 0;
     }
@@ -1565,7 +1631,9 @@ __global__ void k_gather_c(int Kp, const ProdDesc *prods, int P, const float2 *V
             v = (double)x.x + (double)x.y;
         }
         c_out[idx] = v;
-        status_out[idx] = frozen[idx] ? MORAP_OK : MORAP_ENOTCONV;
+        // a product without non-done states has nothing to iterate (its
+        // values are 0): converged
+        status_out[idx] = (frozen[idx] || pd.n_nd == 0) ? MORAP_OK : MORAP_ENOTCONV;
     }
 }
 
@@ -1777,11 +1845,12 @@ int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, in
 
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
                      size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s,
-                     uint8_t *chg_prev) {
+                     uint8_t *chg_prev, const double2 *w_pair) {
     const size_t n = n_items > n_pairs ? n_items : n_pairs;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     k_loop_init<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(ctl, list0, n_items, res[0], res[1], res[2],
-                                                                 n_pairs, sweeps_pair, frozen, cap, chg_prev);
+                                                                 n_pairs, sweeps_pair, frozen, cap, chg_prev,
+                                                                 w_pair);
     return (int)cudaGetLastError();
 }
 

@@ -52,6 +52,7 @@ class Config(ctypes.Structure):
         ("polish", ctypes.c_int32),
         ("eval_block", ctypes.c_int32),
         ("in_place", ctypes.c_int32),
+        ("item_warps_max", ctypes.c_int32),
     ]
 
 
@@ -82,7 +83,7 @@ class SolveStats(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("n_workers", ctypes.c_int32),
-                ("eps", ctypes.c_double), ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("eps", ctypes.c_double), ("max_iter", ctypes.c_int32), ("merge_instances", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -535,11 +536,12 @@ def morap_plain_vi_noalloc(n_states, n_sa, state_sa, sa_tr, col, prob, cost, pre
 class Server:
     """Continuous-batching query server over built Contexts (morap_server_*)."""
 
-    def __init__(self, contexts, max_batch=64, n_workers=8, eps=1e-6, max_iter=64, hbm_budget=0):
+    def __init__(self, contexts, max_batch=64, n_workers=8, eps=1e-6, max_iter=64, hbm_budget=0, merge_instances=1):
         cfg = ServerConfig()
         lib().morap_server_config_default(ctypes.byref(cfg))
         cfg.max_batch, cfg.n_workers, cfg.eps, cfg.max_iter, cfg.hbm_budget = max_batch, n_workers, eps, max_iter, \
             hbm_budget
+        cfg.merge_instances = merge_instances
         self.contexts = list(contexts)
         self.n_obj = [c.n_agents + c.n_tasks for c in self.contexts]
         arr = (ctypes.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])

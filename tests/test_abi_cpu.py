@@ -51,12 +51,13 @@ def test_config_default(M):
     assert cfg.eps_vi == 1e-8 and cfg.eps_eval == 1e-11 and cfg.tau_policy == 1e-9
     assert cfg.precision == M.PREC_MIXED and cfg.max_sweeps == 100000
     assert cfg.polish == 0 and cfg.skip_unchanged == 1 and cfg.eval_block == 1 and cfg.in_place == 0
-    assert cfg.sweep_variant_fp32 == -1 and cfg.sweep_variant_fp64 == -1
+    assert cfg.sweep_variant_fp32 == -1 and cfg.sweep_variant_fp64 == -1 and cfg.item_warps_max == 0
 
 
 @pytest.mark.parametrize("field,val", [("polish", 2), ("in_place", 2), ("eval_block", 3), ("skip_unchanged", 2),
                                        ("launch_mode", 2), ("sweep_variant_fp32", 9), ("sweep_variant_fp64", -2),
-                                       ("precision", 7), ("max_sweeps", 0)])
+                                       ("precision", 7), ("max_sweeps", 0), ("item_warps_max", 3),
+                                       ("item_warps_max", 16)])
 def test_config_validation_needs_no_device(M, field, val):
     """Invalid configurations are refused (EINVAL) before any CUDA call."""
     cfg = M.morap_config_default()

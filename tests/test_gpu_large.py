@@ -70,17 +70,28 @@ def _check(M, inst, n_sample, seed):
                      M.morap_product_locations(ctx.h, p), M.morap_last_policy(ctx.h, k, p)[0]))
     want = O.solve_pairs_pooled(jobs)
     gap_states = 0
+    mismatches = []
     for e, ((i, j, k), r) in enumerate(zip(sample, want)):
         assert out["c"][k, i, j] == pytest.approx(r["c"], abs=TOL), (i, j, k)
         assert ev["r_cost"][e] == pytest.approx(r["mu_r_cost"], abs=TOL), (i, j, k)
         assert ev["r_prob"][e] == pytest.approx(r["mu_r_prob"], abs=TOL), (i, j, k)
-        assert r["gap_mismatch"] == 0, (i, j, k, r["gap_mismatch"], r["gap_states"])
+        # schedulers: identical wherever the oracle's action gap exceeds 1e-9,
+        # up to states whose gap is below the distance between the two final
+        # iterates (both stop at a residual of 1e-8, from different starting
+        # points, and differ by up to ~1e-6 over these long horizons): there
+        # the engine's action must be optimal to that accuracy on the
+        # oracle's values
+        if r["gap_mismatch"]:
+            assert r["mismatch_max_gap"] < 1e-6 and r["mismatch_max_loss"] < 1e-6, (i, j, k, r)
+            mismatches.append((i, j, k, r["gap_mismatch"], r["mismatch_max_gap"]))
         gap_states += r["gap_states"]
         # the scalarised value of the engine's point is the oracle's optimum
         assert W[k][i] * ev["r_cost"][e] + W[k][nI + j] * ev["r_prob"][e] == pytest.approx(r["c"], abs=TOL)
         # any size: probabilities in [0, 1], costs <= 0
         assert -1e-12 <= ev["r_prob"][e] <= 1 + 1e-12 and ev["r_cost"][e] <= 1e-12
     assert gap_states > 1000 * len(sample)
+    assert sum(m[3] for m in mismatches) <= 1e-4 * gap_states, mismatches
+    print("scheduler mismatches (i, j, k, states, largest oracle gap):", mismatches)
     ctx.close()
     return fp, st
 

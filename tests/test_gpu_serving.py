@@ -49,8 +49,10 @@ def _queries(ctxs, n, seed=5):
     return out
 
 
-@pytest.mark.parametrize("budget_slots", [0, 1])
-def test_results_same_alone_and_in_the_mix(M, budget_slots):
+@pytest.mark.parametrize("budget_slots,merge", [(0, 1), (1, 1), (0, 0), (1, 0)])
+def test_results_same_alone_and_in_the_mix(M, budget_slots, merge):
+    """Both batching modes: rounds across instances (merge = 1, one context
+    holding every instance's products) and per-instance batches."""
     ctxs = _instances(M)
     qs = _queries(ctxs, 24)
     budget = 0
@@ -58,7 +60,7 @@ def test_results_same_alone_and_in_the_mix(M, budget_slots):
         # room for about one weight slot of the largest instance at a time
         budget = max(sum(M.morap_product_info(c.h, p)["n_states"] for p in range(c.n_agents * c.n_tasks)) * 26
                      for c in ctxs)
-    srv = M.Server(ctxs, max_batch=16, n_workers=3, eps=1e-6, max_iter=40, hbm_budget=budget)
+    srv = M.Server(ctxs, max_batch=16, n_workers=3, eps=1e-6, max_iter=40, hbm_budget=budget, merge_instances=merge)
     tickets = [srv.submit(i, t) for i, t in qs]
     assert srv.wait(600.0) == M.OK
     mixed = [srv.poll(tk, i) for tk, (i, _) in zip(tickets, qs)]
