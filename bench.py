@@ -735,7 +735,7 @@ def main():
     ap.add_argument("--serve-queries", type=int, default=2000,
                     help="queries of the 80%%-load run (the configured workload has 10000)")
     ap.add_argument("--serve-sat-queries", type=int, default=1000)
-    ap.add_argument("--serve-mode", choices=["merged", "per-instance"], default="merged")
+    ap.add_argument("--serve-mode", choices=["merged", "per-instance"], default="per-instance")
     ap.add_argument("--serve-max-iter", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":

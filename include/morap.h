@@ -421,11 +421,11 @@ void morap_pareto_destroy(morap_pareto *ps);
  * Continuous batching of threshold-point queries (Algorithm 1) over several
  * resident instances (built contexts).  Each query runs Algorithm 1 with
  * M = I and the server's eps / max_iter.  A query waiting for its next
- * supporting point joins the next device round: with merge_instances (the
- * default) one round serves the waiting queries of every instance as the
- * weight columns of one batch (a query's column weighs only its instance's
- * products); otherwise an idle instance takes its own waiting queries as
- * one morap_supporting_points batch on its own stream.
+ * supporting point joins the next device round: an idle instance takes its
+ * own waiting queries as one morap_supporting_points batch on its own
+ * stream, or, with merge_instances, one round serves the waiting queries of
+ * every instance of a group as the weight columns of one batch (a query's
+ * column weighs only its instance's products).
  * Admission: queries are admitted in arrival order while the device bytes of
  * their weight slots (26 bytes per product state of the instance) fit
  * hbm_budget (0 = no limit); at least one query is always admitted.
@@ -441,11 +441,15 @@ typedef struct morap_server_config {
                            instances' batches without merge_instances          */
     double eps;         /* Algorithm 1 tolerance of every query (default 1e-6)   */
     int32_t max_iter;   /* supporting points per query (default 64)              */
-    int32_t merge_instances; /* 1 (default): one device round takes the waiting queries
-                           of every instance, on a context holding all instances'
-                           products (built at server creation; the instances'
-                           own contexts are left untouched); 0: each instance
-                           batches its own queries on its own stream          */
+    int32_t merge_instances; /* 0 (default): each instance batches its own queries on
+                           its own stream; 1: one device round takes the waiting
+                           queries of every instance of a group (instances with
+                           the same arithmetic and a similar size), on a context
+                           holding the group's products (built at server
+                           creation; the instances' own contexts are left
+                           untouched).  A merged round computes every weight
+                           column of every product it touches: lower latency at
+                           light load, lower saturation throughput           */
 } morap_server_config;
 
 typedef struct morap_serving_stats {

@@ -159,7 +159,7 @@ __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, c
         for (uint32_t v = tid; v < n_sa; v += stride) {
             const uint32_t pl = v / SA, a = v - pl * SA;
             const double c = a_cost[ad.cost_off + a];
-            cost64[pd.sa_off + v] = c;
+            if (cost64) cost64[pd.sa_off + v] = c;  // the FP64 copies only once a caller needs them
             cost32[pd.sa_off + v] = __double2float_ru(c);
             costdf[pd.sa_off + v] = to_df(c);
             const int32_t e0 = a_sa_ptr[ad.sap_off + a], e1 = a_sa_ptr[ad.sap_off + a + 1];
@@ -178,14 +178,14 @@ __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, c
                 }
                 const int32_t cg = (int32_t)(pd.state_off + (uint32_t)pl2 * S + (uint32_t)s2);
                 col[t] = cg;
-                p64[t] = pr;
+                if (p64) p64[t] = pr;
                 pdf[t] = to_df(pr);
                 cp32[t] = make_int2(cg, __float_as_int(__double2float_rd(pr)));
                 ++t;
             }
             if (t_done != 0xffffffffu) {
                 col[t_done] = (int32_t)done;
-                p64[t_done] = p_done;
+                if (p64) p64[t_done] = p_done;
                 pdf[t_done] = to_df(p_done);
                 cp32[t_done] = make_int2((int32_t)done, __float_as_int(__double2float_rd(p_done)));
             }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -961,6 +962,24 @@ int morap::ctx_merge(morap_ctx *const *ctxs, int n, morap_ctx **out, std::vector
     return MORAP_OK;
 }
 
+// What decides a context's arithmetic (precision path and stopping rules):
+// contexts with equal keys give the same results for the same product.
+std::string morap::ctx_arith_key(const morap_ctx *c) {
+    const morap_config &f = c->cfg;
+    const bool fp32 = c->all_free_action && f.precision == MORAP_PREC_MIXED;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%d/%d/%a/%a/%a/%d/%d/%d/%d", fp32 ? 1 : 0, f.polish, f.eps_vi, f.eps_eval,
+                  f.tau_policy, f.max_sweeps, f.in_place, f.eval_block, f.device);
+    return buf;
+}
+
+// The largest product (states, done slot included) of a built context.
+int64_t morap::ctx_max_states(const morap_ctx *c) {
+    int64_t m = 0;
+    for (const ProdDesc &pd : c->h_prods) m = std::max<int64_t>(m, (int64_t)pd.n_nd + 1);
+    return m;
+}
+
 int morap::ctx_reserve(morap_ctx *c, int K) {
     if (!c->built) return fail(MORAP_ESTATE, "reserve before build");
     CK(cudaSetDevice(c->cfg.device));
@@ -1126,6 +1145,20 @@ int run_construction(morap_ctx *c, cudaStream_t s, bool letters_and_counts = tru
     return MORAP_OK;
 }
 
+// The FP64 probabilities and costs of the product CSRs, which only the plain
+// baseline and morap_product_download read: allocated and filled by a
+// construction pass on first use, then kept up to date by every rebuild.
+int ensure_fp64_csr(morap_ctx *c, cudaStream_t s) {
+    if (c->p64) return MORAP_OK;
+    auto &L = c->build_allocs;
+    CKR(dev_alloc(c, L, &c->p64, std::max<uint64_t>(c->TT, 1) * 8));
+    CKR(dev_alloc(c, L, &c->cost64, std::max<uint64_t>(c->TSA, 1) * 8));
+    c->csr_bytes += (int64_t)8 * c->TT + (int64_t)8 * c->TSA;
+    CKR(run_construction(c, s, false));
+    CK(cudaStreamSynchronize(s));
+    return MORAP_OK;
+}
+
 int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
     if (c->agents.empty() || c->tasks.empty()) return fail(MORAP_ESTATE, "build: add at least one agent and one task");
     const int nI = (int)c->agents.size(), nJ = (int)c->tasks.size();
@@ -1252,7 +1285,8 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         CKR(dev_alloc(c, L, &c->prod_tr, (size_t)P * 4));
         CKR(dev_alloc(c, L, &c->costdf, std::max<uint64_t>(TSA, 1) * 8));
         CKR(dev_alloc(c, L, &c->cost32, std::max<uint64_t>(TSA, 1) * 4));
-        CKR(dev_alloc(c, L, &c->cost64, std::max<uint64_t>(TSA, 1) * 8));
+        c->cost64 = nullptr;  // FP64 copies (plain baseline, downloads) on first use: ensure_fp64_csr
+        c->p64 = nullptr;
         CKR(dev_alloc(c, L, &c->d_prods, P * sizeof(ProdDesc)));
         CKR(dev_alloc(c, L, &c->d_chunks, std::max<size_t>(chunks.size(), 1) * sizeof(int4)));
         CKR(dev_alloc(c, L, &c->d_chunk_u, std::max<size_t>(chunks.size(), 1) * sizeof(uint4)));
@@ -1326,9 +1360,8 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         CKR(dev_alloc(c, L, &c->col, std::max<uint64_t>(TTm, 1) * 4));
         CKR(dev_alloc(c, L, &c->cp32, std::max<uint64_t>(TTm, 1) * 8));
         CKR(dev_alloc(c, L, &c->pdf, std::max<uint64_t>(TTm, 1) * 8));
-        CKR(dev_alloc(c, L, &c->p64, std::max<uint64_t>(TTm, 1) * 8));
-        c->csr_bytes = (int64_t)(8 * (TS + 1) + 4 * (TSA + 1) + 4 * TTm + 8 * TTm + 8 * TTm + 8 * TTm + 4 * TSA +
-                                 8 * TSA + 8 * TSA);
+        // state starts (x2), row starts, col, cp32, pdf; cost32, costdf
+        c->csr_bytes = (int64_t)(8 * (TS + 1) + 4 * (TSA + 1) + 4 * TTm + 8 * TTm + 8 * TTm + 4 * TSA + 8 * TSA);
         c->layout_sig = sig;
     }
     c->h_prods = merged;
@@ -1720,6 +1753,7 @@ int morap_solve_plain(morap_ctx *ctx, int32_t n_pairs, const int32_t *pair_produ
     if (!ctx->built) return fail(MORAP_ESTATE, "solve_plain before build");
     CK(cudaSetDevice(ctx->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
+    CKR(ensure_fp64_csr(ctx, s));
     uint32_t max_n = 1, max_sa = 1;
     for (int e = 0; e < n_pairs; ++e) {
         if (pair_product[e] < 0 || pair_product[e] >= ctx->P) return fail(MORAP_EINVAL, "product index out of range");
@@ -1941,6 +1975,7 @@ int morap_product_download(morap_ctx *ctx, int32_t p, int64_t *state_sa, int64_t
     if (!ctx->built) return fail(MORAP_ESTATE, "not built");
     if (p < 0 || p >= ctx->P) return fail(MORAP_EINVAL, "product index out of range");
     CK(cudaSetDevice(ctx->cfg.device));
+    if (prob || cost) CKR(ensure_fp64_csr(ctx, nullptr));
     const ProdDesc &pd = ctx->h_prods[p];
     const size_t ns = pd.n_nd + 1, nsa = (size_t)pd.Qn * pd.SA, nt = pd.n_tr;
     std::vector<uint32_t> tmp;

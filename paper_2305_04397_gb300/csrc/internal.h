@@ -235,6 +235,8 @@ struct EvalArgs {
 int ctx_reserve(morap_ctx *c, int K);
 int ctx_merge(morap_ctx *const *ctxs, int n, morap_ctx **out, std::vector<int32_t> &agent_off,
               std::vector<int32_t> &task_off, std::vector<int32_t> &pair_off);
+std::string ctx_arith_key(const morap_ctx *c);
+int64_t ctx_max_states(const morap_ctx *c);
 
 // ---------------------------------------------------------- kernel launchers
 // (defined in the .cu files; every launcher enqueues on `s` and returns the

@@ -4,19 +4,29 @@
 // Every query is an Algorithm 1 state machine on the host.  Two ways to
 // batch the supporting points the queries wait for:
 //
-//  * across instances (merge_instances = 1, the default): one context holds
-//    the products of every instance (a pair list), and one device round
-//    takes the waiting queries of all instances (up to max_batch) as the
-//    columns of one batch of weight vectors.  Query k's column weighs only
-//    its instance's agents and tasks, so every other product starts that
-//    column frozen at value 0 and costs nothing.  After the round the host
-//    takes each query's assignment on its instance's block of c, one
-//    Algorithm 4 call evaluates every query's assigned pairs, and the
-//    Algorithm 1 steps run on the worker threads while the next round is
-//    already on the device.
-//  * per instance (merge_instances = 0): an idle instance takes its own
+//  * across instances (merge_instances = 1): instances are
+//    grouped by their arithmetic (precision path and stopping rules, so a
+//    result is the one the instance gives alone) and by size (a round lasts
+//    as long as its slowest pair); each group has one context holding its
+//    instances' products (a pair list) and its own round thread and stream,
+//    and one device round takes the waiting queries of every instance of
+//    the group (up to max_batch) as the columns of one batch of weight
+//    vectors.  Query k's column weighs only its instance's agents and
+//    tasks, so every other product starts that column frozen at value 0 and
+//    costs nothing.  After the round the host takes each query's assignment
+//    on its instance's block of c, one Algorithm 4 call evaluates every
+//    query's assigned pairs, and the Algorithm 1 steps run on the worker
+//    threads while the next round is already on the device.
+//  * per instance (merge_instances = 0, the default): an idle instance takes its own
 //    waiting queries as one morap_supporting_points batch on its own
 //    stream; the batches of different instances overlap on the device.
+//
+// A round of the merged mode sweeps every weight column of every product it
+// touches (the [state][weight] layout computes a product's columns
+// together), so a round over many instances does the work of each product
+// once per column of the round: it lowers latency at light load and lowers
+// the saturation throughput; per-instance batches keep every column of a
+// round useful.
 //
 // Queries that arrive while a round runs join the next one.  Queries are
 // admitted in arrival order while the device bytes their weights occupy
@@ -71,13 +81,23 @@ struct morap_server {
     std::vector<std::thread> workers;
     std::thread scheduler;
     std::deque<int> jobs;  // instances with a batch to run
-    // merged mode: the context of every instance's products and where each
-    // instance's agents, tasks and products start in it
-    morap_ctx *merged = nullptr;
-    std::vector<int32_t> agent_off, task_off, pair_off, n_agents;
-    int n_obj_total = 0;
-    cudaStream_t merged_stream = nullptr;
-    std::deque<int64_t> ready_all;  // admitted queries waiting for a supporting point (all instances)
+    // merged mode: instances are grouped by arithmetic (the same results as
+    // alone) and by size (a round lasts as long as its slowest pair); each
+    // group has one context holding its instances' products, its own stream,
+    // ready queue and round thread
+    struct Group {
+        morap_ctx *merged = nullptr;
+        cudaStream_t stream = nullptr;
+        std::vector<int> members;                  // instance indices
+        std::vector<int32_t> agent_off, task_off, pair_off;  // per member
+        int n_agents_total = 0, n_obj_total = 0, n_products = 0;
+        std::deque<int64_t> ready;                 // admitted queries waiting for a supporting point
+        std::thread thread;
+    };
+    std::vector<Group> groups;
+    std::vector<int> group_of, member_of;          // per instance
+    std::vector<int32_t> n_agents;
+    bool merged = false;
     struct StepJob {
         int64_t ticket;
         std::vector<double> r;
@@ -85,7 +105,6 @@ struct morap_server {
         int status;
     };
     std::deque<StepJob> steps;      // Algorithm 1 steps for the worker threads
-    std::thread rounds;
     // stats
     std::vector<double> latencies_ms;
     int64_t submitted = 0, completed = 0, batches = 0, batch_queries = 0;
@@ -99,18 +118,20 @@ void scheduler_loop(morap_server *S) {
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stop) {
         // admission in arrival order, by the device bytes of one weight slot
+        bool admitted = false;
         while (!S->pending.empty()) {
             ServerQuery &q = S->queries[S->pending.front()];
             if (S->cfg.hbm_budget && S->in_use + q.cost > (int64_t)S->cfg.hbm_budget && S->in_use > 0) break;
             q.admitted = true;
             S->in_use += q.cost;
             if (S->merged)
-                S->ready_all.push_back(q.ticket);
+                S->groups[S->group_of[q.inst]].ready.push_back(q.ticket);
             else
                 S->ready[q.inst].push_back(q.ticket);
             S->pending.pop_front();
+            admitted = true;
         }
-        bool dispatched = false;
+        bool dispatched = S->merged && admitted;  // the groups' round threads wait for admitted queries
         for (size_t i = 0; i < S->inst.size() && !S->merged; ++i)
             if (!S->busy[i] && !S->ready[i].empty()) {
                 S->busy[i] = 1;
@@ -181,34 +202,36 @@ void worker_loop(morap_server *S) {
 }
 
 // Merged mode, device side: one round per batch of waiting queries of any
-// instance (Algorithm 3 for every query's weights on the merged context,
-// the assignment per query, Algorithm 4 on the assigned pairs of all
-// queries in one call); the Algorithm 1 steps go to the worker threads.
-void round_loop(morap_server *S) {
+// instance of group g (Algorithm 3 for every query's weights on the group's
+// context, the assignment per query, Algorithm 4 on the assigned pairs of
+// all queries in one call); the Algorithm 1 steps go to the worker threads.
+void round_loop(morap_server *S, int g) {
     std::unique_lock<std::mutex> lk(S->mu);
-    const int P = S->pair_off.back() + S->n_agents.back() * S->n_tasks.back();  // products of the merged context
+    morap_server::Group &G = S->groups[g];
+    const int P = G.n_products;
     for (;;) {
-        while (!S->stop && S->ready_all.empty()) S->cv.wait(lk);
+        while (!S->stop && G.ready.empty()) S->cv.wait(lk);
         if (S->stop) return;
         std::vector<int64_t> batch;
-        while (!S->ready_all.empty() && (int)batch.size() < S->cfg.max_batch) {
-            batch.push_back(S->ready_all.front());
-            S->ready_all.pop_front();
+        while (!G.ready.empty() && (int)batch.size() < S->cfg.max_batch) {
+            batch.push_back(G.ready.front());
+            G.ready.pop_front();
         }
-        const int K = (int)batch.size(), n = S->n_obj_total;
+        const int K = (int)batch.size(), n = G.n_obj_total;
         std::vector<double> W((size_t)K * n, 0.0);
-        std::vector<int> inst(K);
+        std::vector<int> inst(K), mem(K);
         for (int k = 0; k < K; ++k) {
             const ServerQuery &q = S->queries[batch[k]];
-            const int i = q.inst, nI = S->n_agents[i], nJ = S->n_tasks[i];
+            const int i = q.inst, m = S->member_of[i], nI = S->n_agents[i], nJ = S->n_tasks[i];
             inst[k] = i;
-            for (int a = 0; a < nI; ++a) W[(size_t)k * n + S->agent_off[i] + a] = q.ps.w[a];
-            for (int t = 0; t < nJ; ++t) W[(size_t)k * n + S->agent_off.back() + S->n_agents.back() + S->task_off[i] + t] = q.ps.w[nI + t];
+            mem[k] = m;
+            for (int a = 0; a < nI; ++a) W[(size_t)k * n + G.agent_off[m] + a] = q.ps.w[a];
+            for (int t = 0; t < nJ; ++t) W[(size_t)k * n + G.n_agents_total + G.task_off[m] + t] = q.ps.w[nI + t];
         }
         lk.unlock();
         std::vector<double> C((size_t)K * P);
         std::vector<int32_t> st((size_t)K * P);
-        int rc = morap_solve(S->merged, K, W.data(), (void *)S->merged_stream, C.data(), nullptr, nullptr, st.data());
+        int rc = morap_solve(G.merged, K, W.data(), (void *)G.stream, C.data(), nullptr, nullptr, st.data());
         std::vector<std::vector<int32_t>> F(K);
         std::vector<int> status(K, MORAP_OK);
         std::vector<int32_t> ev_p, ev_k;
@@ -216,7 +239,7 @@ void round_loop(morap_server *S) {
         std::vector<int> ev_task;
         if (rc == MORAP_OK || rc == MORAP_ENOTCONV) {
             for (int k = 0; k < K; ++k) {
-                const int i = inst[k], nI = S->n_agents[i], nJ = S->n_tasks[i], p0 = S->pair_off[i];
+                const int i = inst[k], nI = S->n_agents[i], nJ = S->n_tasks[i], p0 = G.pair_off[mem[k]];
                 std::vector<double> Ci((size_t)nI * nJ);
                 for (int a = 0; a < nI; ++a)
                     for (int t = 0; t < nJ; ++t) {
@@ -237,33 +260,31 @@ void round_loop(morap_server *S) {
         }
         std::vector<double> rc_v(ev_p.size()), rp_v(ev_p.size());
         if ((rc == MORAP_OK || rc == MORAP_ENOTCONV) && !ev_p.empty()) {
-            const int rc2 = morap_evaluate(S->merged, (int32_t)ev_p.size(), ev_p.data(), ev_k.data(),
-                                           (void *)S->merged_stream, rc_v.data(), rp_v.data());
+            const int rc2 = morap_evaluate(G.merged, (int32_t)ev_p.size(), ev_p.data(), ev_k.data(), (void *)G.stream,
+                                           rc_v.data(), rp_v.data());
             if (rc2 == MORAP_ENOTCONV) {
                 for (auto &sl : ev_slot) status[sl.first] = MORAP_ENOTCONV;
             } else if (rc2 != MORAP_OK) {
                 rc = rc2;
             }
         }
+        std::vector<morap_server::StepJob> jobs(K);
+        for (int k = 0; k < K; ++k) {
+            const int i = inst[k], nI = S->n_agents[i], nJ = S->n_tasks[i];
+            jobs[k].ticket = batch[k];
+            jobs[k].status = (rc == MORAP_OK || rc == MORAP_ENOTCONV) ? status[k] : rc;
+            jobs[k].r.assign((size_t)nI + nJ, 0.0);
+            jobs[k].f = F[k].empty() ? std::vector<int32_t>(nJ, -1) : F[k];
+        }
+        for (size_t e = 0; e < ev_p.size(); ++e) {
+            const int k = ev_slot[e].first, nI = S->n_agents[inst[k]];
+            jobs[k].r[ev_slot[e].second] = rc_v[e];
+            jobs[k].r[nI + ev_task[e]] = rp_v[e];
+        }
         lk.lock();
         S->batches += 1;
         S->batch_queries += K;
-        for (int k = 0; k < K; ++k) {
-            const int i = inst[k], nI = S->n_agents[i], nJ = S->n_tasks[i];
-            morap_server::StepJob job;
-            job.ticket = batch[k];
-            job.status = (rc == MORAP_OK || rc == MORAP_ENOTCONV) ? status[k] : rc;
-            job.r.assign((size_t)nI + nJ, 0.0);
-            job.f = F[k].empty() ? std::vector<int32_t>(nJ, -1) : F[k];
-            S->steps.push_back(std::move(job));
-        }
-        for (size_t e = 0; e < ev_p.size(); ++e) {
-            // the jobs of this round are the last K in the queue, in query order
-            morap_server::StepJob &job = S->steps[S->steps.size() - K + ev_slot[e].first];
-            const int nI = S->n_agents[inst[ev_slot[e].first]];
-            job.r[ev_slot[e].second] = rc_v[e];
-            job.r[nI + ev_task[e]] = rp_v[e];
-        }
+        for (auto &j : jobs) S->steps.push_back(std::move(j));
         S->cv.notify_all();
     }
 }
@@ -295,7 +316,7 @@ void step_loop(morap_server *S) {
             S->latencies_ms.push_back(std::chrono::duration<double, std::milli>(q.t_done - q.t_submit).count());
             S->t_last = q.t_done;
         } else {
-            S->ready_all.push_back(q.ticket);
+            S->groups[S->group_of[q.inst]].ready.push_back(q.ticket);
         }
         S->cv.notify_all();
         S->cv_done.notify_all();
@@ -313,7 +334,7 @@ void morap_server_config_default(morap_server_config *cfg) {
     cfg->n_workers = 8;
     cfg->eps = 1e-6;
     cfg->max_iter = 64;
-    cfg->merge_instances = 1;
+    cfg->merge_instances = 0;
 }
 
 int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const morap_server_config *cfg_in,
@@ -371,28 +392,57 @@ int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const 
     S->busy.assign(n_instances, 0);
     S->ready.resize(n_instances);
     if (cfg.merge_instances) {
-        int rc = ctx_merge(instances, n_instances, &S->merged, S->agent_off, S->task_off, S->pair_off);
-        if (rc == MORAP_OK && cudaStreamCreateWithFlags(&S->merged_stream, cudaStreamNonBlocking) != cudaSuccess)
-            rc = fail(MORAP_ECUDA, "server: cudaStreamCreate");
-        if (rc == MORAP_OK) {
-            int64_t states = 0;
-            for (int i = 0; i < n_instances; ++i) states += S->bytes_per_weight[i] / 26;
+        // groups: the same arithmetic (so every result is the instance's own)
+        // and a similar size (the largest product within a factor of 4)
+        std::vector<std::pair<std::string, int>> keys;
+        S->group_of.assign(n_instances, -1);
+        S->member_of.assign(n_instances, -1);
+        for (int i = 0; i < n_instances; ++i) {
+            int64_t m = std::max<int64_t>(1, ctx_max_states(instances[i]));
+            int bucket = 0;
+            while (m > 1) m >>= 2, ++bucket;
+            std::pair<std::string, int> key(ctx_arith_key(instances[i]), bucket);
+            int g = (int)(std::find(keys.begin(), keys.end(), key) - keys.begin());
+            if (g == (int)keys.size()) {
+                keys.push_back(key);
+                S->groups.emplace_back();
+            }
+            S->group_of[i] = g;
+            S->member_of[i] = (int)S->groups[g].members.size();
+            S->groups[g].members.push_back(i);
+        }
+        int rc = MORAP_OK;
+        for (auto &G : S->groups) {
+            std::vector<morap_ctx *> cs;
+            for (int i : G.members) cs.push_back(instances[i]);
+            rc = ctx_merge(cs.data(), (int)cs.size(), &G.merged, G.agent_off, G.task_off, G.pair_off);
+            if (rc == MORAP_OK && cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking) != cudaSuccess)
+                rc = fail(MORAP_ECUDA, "server: cudaStreamCreate");
+            if (rc != MORAP_OK) break;
+            const int last = G.members.back();
+            G.n_agents_total = G.agent_off.back() + S->n_agents[last];
+            G.n_obj_total = G.n_agents_total + G.task_off.back() + S->n_tasks[last];
+            G.n_products = G.pair_off.back() + S->n_agents[last] * S->n_tasks[last];
+            int64_t bpw = 0;
+            for (int i : G.members) bpw += S->bytes_per_weight[i];
             int reserve = cfg.max_batch;
-            if (cfg.hbm_budget)
-                reserve = (int)std::min<int64_t>(reserve, std::max<int64_t>(1, (int64_t)cfg.hbm_budget / (26 * states)));
-            if (ctx_reserve(S->merged, reserve) != MORAP_OK) set_error("");  // buffers then grow on demand
+            if (cfg.hbm_budget) reserve = (int)std::min<int64_t>(reserve, std::max<int64_t>(1, (int64_t)cfg.hbm_budget / bpw));
+            if (ctx_reserve(G.merged, reserve) != MORAP_OK) set_error("");  // buffers then grow on demand
         }
         if (rc != MORAP_OK) {
-            if (S->merged) morap_ctx_destroy(S->merged);
+            for (auto &G : S->groups) {
+                if (G.merged) morap_ctx_destroy(G.merged);
+                if (G.stream) cudaStreamDestroy(G.stream);
+            }
             for (auto s : S->streams) cudaStreamDestroy(s);
             delete S;
             return rc;
         }
-        S->n_obj_total = S->agent_off.back() + S->n_agents.back() + S->task_off.back() + S->n_tasks.back();
+        S->merged = true;
     }
     S->scheduler = std::thread(scheduler_loop, S);
     if (S->merged) {
-        S->rounds = std::thread(round_loop, S);
+        for (size_t g = 0; g < S->groups.size(); ++g) S->groups[g].thread = std::thread(round_loop, S, (int)g);
         for (int k = 0; k < cfg.n_workers; ++k) S->workers.emplace_back(step_loop, S);
     } else {
         for (int k = 0; k < cfg.n_workers; ++k) S->workers.emplace_back(worker_loop, S);
@@ -409,12 +459,15 @@ int morap_server_destroy(morap_server *S) {
     }
     S->cv.notify_all();
     if (S->scheduler.joinable()) S->scheduler.join();
-    if (S->rounds.joinable()) S->rounds.join();
+    for (auto &G : S->groups)
+        if (G.thread.joinable()) G.thread.join();
     for (auto &t : S->workers)
         if (t.joinable()) t.join();
     for (auto s : S->streams) cudaStreamDestroy(s);
-    if (S->merged_stream) cudaStreamDestroy(S->merged_stream);
-    if (S->merged) morap_ctx_destroy(S->merged);
+    for (auto &G : S->groups) {
+        if (G.stream) cudaStreamDestroy(G.stream);
+        if (G.merged) morap_ctx_destroy(G.merged);
+    }
     delete S;
     return MORAP_OK;
 }

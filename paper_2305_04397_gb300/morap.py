@@ -536,7 +536,7 @@ def morap_plain_vi_noalloc(n_states, n_sa, state_sa, sa_tr, col, prob, cost, pre
 class Server:
     """Continuous-batching query server over built Contexts (morap_server_*)."""
 
-    def __init__(self, contexts, max_batch=64, n_workers=8, eps=1e-6, max_iter=64, hbm_budget=0, merge_instances=1):
+    def __init__(self, contexts, max_batch=64, n_workers=8, eps=1e-6, max_iter=64, hbm_budget=0, merge_instances=0):
         cfg = ServerConfig()
         lib().morap_server_config_default(ctypes.byref(cfg))
         cfg.max_batch, cfg.n_workers, cfg.eps, cfg.max_iter, cfg.hbm_budget = max_batch, n_workers, eps, max_iter, \
