@@ -57,10 +57,10 @@ def make_workload(name, rank=0):
 # comments removed; sha256 prefix) is the one that was profiled and the same
 # shape runs; otherwise the bench reports traffic as null.
 TRAFFIC_PROFILES = {
-    ("grid32-10x20-K16", "fp32"): {"sweep_source": "7ab7d883e47baafd", "variant": 0,
-                                   "dram_bytes": 148030976 + 28169728, "alg_bytes": 189.1e6},
-    ("grid32-10x20-K16", "delta"): {"sweep_source": "7ab7d883e47baafd", "variant": 0,
-                                    "dram_bytes": 357863424 + 42290432, "alg_bytes": 394.1e6},
+    ("grid32-10x20-K16", "fp32"): {"sweep_source": "7379658b5c4ed4c8", "variant": 0,
+                                   "dram_bytes": 137850368 + 27257600, "alg_bytes": 178.99e6},
+    ("grid32-10x20-K16", "delta"): {"sweep_source": "7379658b5c4ed4c8", "variant": 0,
+                                    "dram_bytes": 347404544 + 41346560, "alg_bytes": 384.32e6},
 }
 SWEEP_SECTION_END = "// -------------------------------------------------------------- finalise"
 
