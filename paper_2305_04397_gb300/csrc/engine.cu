@@ -104,6 +104,7 @@ struct morap_ctx {
     uint32_t *state_sa = nullptr, *state_tr = nullptr, *sa_tr = nullptr;
     int32_t *col = nullptr;
     int2 *cp32 = nullptr;
+    int2 *cpn32 = nullptr;  // the residual-correction polish's edge stream (null when it cannot run)
     float2 *pdf = nullptr, *costdf = nullptr;
     float *cost32 = nullptr;
     double *p64 = nullptr, *cost64 = nullptr;
@@ -464,6 +465,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a.sa_tr = c->sa_tr;
     a.col = c->col;
     a.cp32 = c->cp32;
+    a.cpn32 = c->cpn32;
     a.pdf = c->pdf;
     a.costdf = c->costdf;
     a.wdf = c->wdf;
@@ -631,7 +633,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     std::memcpy(c->h_stage, W, nW * sizeof(double));
     CK(cudaMemcpyAsync(c->d_W, c->h_stage, nW * sizeof(double), cudaMemcpyHostToDevice, s));
     CKL(launch_setup_weights(c->d_prods, c->P, c->nI, c->nJ, K, Kp, c->d_W, c->w32, c->w64, c->wdf, c->thr32,
-                             c->thr64, c->cfg.eps_vi, s));
+                             c->thr64, c->cfg.eps_vi, c->V32[0] != nullptr, s));
     const size_t nv = (size_t)c->TS * Kp;
     const unsigned int cap = (unsigned int)std::max(1, c->cfg.max_sweeps);
     const unsigned int n_items = (unsigned int)c->h_chunks.size();
@@ -1138,7 +1140,7 @@ int run_construction(morap_ctx *c, cudaStream_t s, bool letters_and_counts = tru
     }
     CKL(launch_row_offsets(c->d_prods, c->P, c->row_cnt, c->sa_tr, s));
     CKL(launch_build(c->d_prods, c->P, c->d_ad, c->d_td, c->d_sp, c->d_sap, c->d_succ, c->d_prob, c->d_cost,
-                     c->d_letters, c->d_nd, c->state_sa, c->state_tr, c->sa_tr, c->col, c->cp32, c->p64, c->pdf,
+                     c->d_letters, c->d_nd, c->state_sa, c->state_tr, c->sa_tr, c->col, c->cp32, c->cpn32, c->p64, c->pdf,
                      c->cost32, c->cost64, c->costdf, c->TS, c->TSA, c->TT, c->max_work, s));
     CKL(launch_item_inputs(c->d_chunks, (int)c->h_chunks.size(), c->d_prods, c->state_tr, c->col, c->in_items, c->item_w,
                                 c->state_sa, s));
@@ -1360,8 +1362,16 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         CKR(dev_alloc(c, L, &c->col, std::max<uint64_t>(TTm, 1) * 4));
         CKR(dev_alloc(c, L, &c->cp32, std::max<uint64_t>(TTm, 1) * 8));
         CKR(dev_alloc(c, L, &c->pdf, std::max<uint64_t>(TTm, 1) * 8));
-        // state starts (x2), row starts, col, cp32, pdf; cost32, costdf
-        c->csr_bytes = (int64_t)(8 * (TS + 1) + 4 * (TSA + 1) + 4 * TTm + 8 * TTm + 8 * TTm + 4 * TSA + 8 * TSA);
+        // the residual-correction polish (the default second phase of a
+        // mixed-precision solve) iterates with probabilities rounded to
+        // nearest: with the FP32 phase's rounded-down ones every row would
+        // lose up to an ulp of mass per sweep, a bias of the same sign at
+        // every step of a path that the residual test cannot see
+        const bool delta = c->all_free_action && c->cfg.precision == MORAP_PREC_MIXED && c->cfg.polish == 0;
+        if (delta) CKR(dev_alloc(c, L, &c->cpn32, std::max<uint64_t>(TTm, 1) * 8));
+        // state starts (x2), row starts, col, cp32 (+ cpn32), pdf; cost32, costdf
+        c->csr_bytes = (int64_t)(8 * (TS + 1) + 4 * (TSA + 1) + 4 * TTm + 8 * TTm * (delta ? 2 : 1) + 8 * TTm +
+                                 4 * TSA + 8 * TSA);
         c->layout_sig = sig;
     }
     c->h_prods = merged;

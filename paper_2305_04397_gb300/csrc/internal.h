@@ -164,6 +164,7 @@ struct SweepArgs {
     const uint32_t *sa_tr;
     const int32_t *col;
     const int2 *cp32;     // per transition {col, p rounded down as float bits}
+    const int2 *cpn32;    // per transition {col, p rounded to nearest}: the residual correction's stream
     const double *p64;
     const float *cost32;
     const double *cost64;
@@ -256,12 +257,13 @@ int launch_row_offsets(const ProdDesc *prods, int P, const uint32_t *row_cnt, ui
 int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                  const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ, const double *a_prob,
                  const double *a_cost, const uint8_t *letters, const int16_t *nd_delta, uint32_t *state_sa,
-                 uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf,
+                 uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32, int2 *cpn32, double *p64, float2 *pdf,
                  float *cost32, double *cost64, float2 *costdf, uint32_t total_states, uint32_t total_sa,
                  uint32_t total_tr, uint32_t max_work, void *s);
 
 int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W,
-                         float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1, void *s);
+                         float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1,
+                         bool after_fp32, void *s);
 int launch_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, const uint32_t *state_tr,
                        const int32_t *col, int32_t *in_items, uint2 *item_w, const uint32_t *state_sa,
                        void *s);

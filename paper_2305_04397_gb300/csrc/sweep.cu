@@ -92,6 +92,29 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *g) {
 __device__ __forceinline__ void prefetch_l2(const void *g, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(g), "r"(bytes) : "memory");
 }
+// Paired FP32 arithmetic (fma / mul / add on .f32x2 operands, sm_100 and
+// later): two independent FP32 operations per instruction, each element
+// rounded exactly as the scalar instruction with the same rounding modifier.
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long f2_fma_rd(unsigned long long a, unsigned long long b,
+                                                        unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma_rn(unsigned long long a, unsigned long long b,
+                                                        unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -154,6 +177,12 @@ struct ArithF32 {
     static __device__ __forceinline__ Val reward(W w, Cost c) { return reward_cw(cost_weight(w), c); }
     static __device__ __forceinline__ Val add_base(Val v, W w, bool pre) { return pre ? __fadd_rd(v, w.y) : v; }
     static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) { acc = __fmaf_rd(p, v, acc); }
+    // two weights' mac in one paired instruction (same rounding per element)
+    static constexpr bool kPair = true;
+    static __device__ __forceinline__ unsigned long long mac2(unsigned long long acc, unsigned long long pp,
+                                                              unsigned long long v) {
+        return f2_fma_rd(pp, v, acc);
+    }
     static __device__ __forceinline__ void close(Val &) {}
     static __device__ __forceinline__ bool gt(Val a, Val b) { return a > b; }
     static __device__ __forceinline__ Val neg_inf() { return -CUDART_INF_F; }
@@ -172,6 +201,7 @@ struct ArithF32 {
 
 struct ArithDF {
     using Val = DF;
+    static constexpr bool kPair = false;
     static constexpr int AMAX = 192, EMAX = 448;
     // ssa | str[AM + 1] | cost[AM] (float2) | col[EM] | p[EM] (float2)
     template <int AM, int EM>
@@ -306,6 +336,16 @@ __device__ __forceinline__ void store_words(float *p, const float (&w)[NW]) {
 // exactly in double-float at the end.
 struct ArithDelta : ArithF32 {
     using Prob = float;
+    // The transitions carry p rounded to nearest (cpn32), not the FP32
+    // phase's rounded-down p: d is of the size of B's remaining error, and
+    // rows that lose up to an ulp of mass per sweep would pull the fixed
+    // point of the correction down by that loss times the number of steps
+    // to completion (2e-6 on paths of thousands of steps), with a residual
+    // the stopping rule cannot see.  Rounded to nearest, the per-row errors
+    // take both signs.
+    static __device__ __forceinline__ View global_view(const SweepArgs &a, uint32_t A0, uint32_t T0) {
+        return {a.sa_tr + A0, a.cost32 + A0, a.cpn32 + T0};
+    }
     // the rows' costs are inside G: only the row starts and the transitions are staged
     template <int AM = AMAX, int EM = EMAX>
     static __device__ __forceinline__ void stage(const SweepArgs &a, unsigned char *b, uint32_t A0, uint32_t nA,
@@ -314,10 +354,14 @@ struct ArithDelta : ArithF32 {
         uint32_t *str = reinterpret_cast<uint32_t *>(b + L::STR);
         int2 *edge = reinterpret_cast<int2 *>(b + L::EDGE);
         for (uint32_t i = lane; i <= nA; i += 32) cp_async4(str + i, a.sa_tr + A0 + i);
-        for (uint32_t i = lane; i < nT; i += 32) cp_async8(edge + i, a.cp32 + T0 + i);
+        for (uint32_t i = lane; i < nT; i += 32) cp_async8(edge + i, a.cpn32 + T0 + i);
     }
     static __device__ __forceinline__ Val add_base(Val v, W, bool) { return v; }  // inside G
     static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) { acc = __fmaf_rn(p, v, acc); }
+    static __device__ __forceinline__ unsigned long long mac2(unsigned long long acc, unsigned long long pp,
+                                                              unsigned long long v) {
+        return f2_fma_rn(pp, v, acc);
+    }
     static __device__ __forceinline__ float record_threshold(Val, float eps1) { return eps1; }
 };
 
@@ -339,6 +383,23 @@ __device__ __forceinline__ void init_action(const SweepArgs &a, const typename A
     }
 }
 
+// acc[v] += p * g[v] for the VEC weights a lane owns; FP32 formats issue
+// the weights two at a time as paired FMAs (same roundings, same results).
+template <class Ar, int VEC>
+__device__ __forceinline__ void mac_row(typename Ar::Val (&acc)[VEC], typename Ar::Prob p, const float *g) {
+    if constexpr (Ar::kPair && VEC % 2 == 0) {
+        const unsigned long long pp = f2_pack(p, p);
+#pragma unroll
+        for (int v = 0; v < VEC; v += 2) {
+            const unsigned long long r = Ar::mac2(f2_pack(acc[v], acc[v + 1]), pp, f2_pack(g[v], g[v + 1]));
+            f2_unpack(r, acc[v], acc[v + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], p, Ar::from_words(&g[v * Ar::WORDS]));
+    }
+}
+
 // Kernel shapes the tuner chooses from, per value format: VMAX weights per
 // lane (a lane owns VEC = min(Kp, VMAX) consecutive weights of a state), D
 // successor gathers in flight per action, and MINB resident blocks per SM
@@ -351,7 +412,7 @@ template <>
 struct Variants<ArithF32> {
     static constexpr int N = 4;
     static constexpr int vmax[N] = {8, 8, 4, 8};
-    static constexpr int d[N] = {3, 4, 4, 2};
+    static constexpr int d[N] = {3, 4, 2, 2};  // shape 2: D = 2 keeps 3 blocks per SM free of spills
     static constexpr int minb[N] = {2, 2, 3, 2};
     static constexpr int pipe[N] = {0, 0, 0, 1};  // actions software-pipelined
 };
@@ -361,7 +422,7 @@ template <>
 struct Variants<ArithDF> {
     static constexpr int N = 4;
     static constexpr int vmax[N] = {4, 4, 2, 4};
-    static constexpr int d[N] = {3, 4, 4, 2};
+    static constexpr int d[N] = {3, 4, 2, 2};
     static constexpr int minb[N] = {2, 2, 3, 2};
     static constexpr int pipe[N] = {0, 0, 0, 1};
 };
@@ -455,11 +516,8 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
             for (int j = 0; j < D; ++j)
                 if (cl[j] >= 0) load_words<NW>(Vold + (size_t)cl[j] * ROW + (size_t)k0 * Ar::WORDS, gw[j]);
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                if (cl[j] < 0) continue;
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], pr[j], Ar::from_words(&gw[j][v * Ar::WORDS]));
-            }
+            for (int j = 0; j < D; ++j)
+                if (cl[j] >= 0) mac_row<Ar, VEC>(acc, pr[j], gw[j]);
         }
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
@@ -558,11 +616,8 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         init_action<Ar, KP, VEC>(a, vw, A0, la, k0, sw, acc);
         for (;;) {
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                if (S.cl[j] < 0) continue;
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], S.pr[j], Ar::from_words(&S.gw[j][v * Ar::WORDS]));
-            }
+            for (int j = 0; j < D; ++j)
+                if (S.cl[j] >= 0) mac_row<Ar, VEC>(acc, S.pr[j], S.gw[j]);
             if (S.t0 + D >= S.t1) break;
             S.t0 += D;  // rows longer than D: the next slots, unpipelined
             fill(S);
@@ -1480,6 +1535,9 @@ __global__ void __launch_bounds__(kEvalBlockThreads, 1) k_eval_block(EvalArgs a,
 // shift only trades FP32 sweeps against polish sweeps (near its fixed point
 // the round-down iteration slows down, so a later hand-over costs more
 // sweeps in total).
+#ifndef MORAP_POLISH_SHIFT
+#define MORAP_POLISH_SHIFT 0
+#endif
 #ifndef MORAP_THR32_SHIFT
 #define MORAP_THR32_SHIFT 16
 #endif
@@ -1490,7 +1548,8 @@ __device__ __forceinline__ float2 to_df(double d) {
 }
 
 __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W,
-                                float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1) {
+                                float2 *w32, double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1,
+                                double eps_polish) {
     const size_t n = (size_t)P * Kp;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
         const int p = (int)(idx / Kp), k = (int)(idx % Kp);
@@ -1505,9 +1564,10 @@ __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, in
         const float2 a = to_df(wi), b = to_df(wp);
         wdf[idx] = make_float4(a.x, a.y, b.x, b.y);
         // FP32 phase: stop once the residual is within a few ulps of the
-        // largest possible value (values lie in [0, w_p]); polish phase: eps1.
+        // largest possible value (values lie in [0, w_p]); polish phase:
+        // eps_polish (see launch_setup_weights).
         thr32[idx] = fmax(eps1, ldexp(wp, -MORAP_THR32_SHIFT));
-        thr64[idx] = eps1;
+        thr64[idx] = eps_polish;
     }
 }
 
@@ -1835,11 +1895,20 @@ int launch_eval_sweep(const EvalArgs &a, int pos, int grid, void *s) {
 }
 
 int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, int Kp, const double *W, float2 *w32,
-                         double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1, void *s) {
+                         double2 *w64, float4 *wdf, double *thr32, double *thr64, double eps1, bool after_fp32,
+                         void *s) {
     const size_t n = (size_t)P * Kp;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    // A phase that starts from the FP32 phase's values stops at a residual
+    // 2^-MORAP_POLISH_SHIFT below eps1: those values lie below the exact
+    // iterate by the FP32 roundings of the last sweeps, which accumulate
+    // along every path (to 1e-6 on paths of hundreds of steps) while each
+    // is smaller than eps1, so a residual test at eps1 stops before the
+    // deficit has been propagated away.  A phase that starts from 0 stops
+    // at eps1, as Algorithm 3 does.
+    const double eps_polish = after_fp32 ? ldexp(eps1, -MORAP_POLISH_SHIFT) : eps1;
     k_setup_weights<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(prods, P, nI, nJ, K, Kp, W, w32, w64, wdf,
-                                                                     thr32, thr64, eps1);
+                                                                     thr32, thr64, eps1, eps_polish);
     return (int)cudaGetLastError();
 }
 
