@@ -284,6 +284,10 @@ typedef struct morap_solve_stats {
     int64_t computed_fp64;
     int64_t anchored_states;  /* (state, weight) entries whose recorded action was not kept and
                                  that the scheduler's anchoring rounds decided          */
+    int64_t states_fp32;      /* state sweeps computed: inside a computed work item a state
+                                 none of whose successors (itself included) changed in the
+                                 previous sweep is skipped exactly as well              */
+    int64_t states_fp64;
 } morap_solve_stats;
 
 int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out);

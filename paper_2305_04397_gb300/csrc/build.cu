@@ -126,7 +126,7 @@ __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, c
                         const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ,
                         const double *a_prob, const double *a_cost, const uint8_t *letters, const int16_t *nd_delta,
                         uint32_t *state_sa, uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32,
-                        int2 *cpn32, double *p64, float2 *pdf, float *cost32, double *cost64, float2 *costdf,
+                        double *p64, float2 *pdf, float *cost32, double *cost64, float2 *costdf,
                         uint32_t total_states, uint32_t total_sa, uint32_t total_tr) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     if (blockIdx.y == 0 && tid == 0) {
@@ -181,7 +181,6 @@ __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, c
                 if (p64) p64[t] = pr;
                 pdf[t] = to_df(pr);
                 cp32[t] = make_int2(cg, __float_as_int(__double2float_rd(pr)));
-                if (cpn32) cpn32[t] = make_int2(cg, __float_as_int(__double2float_rn(pr)));
                 ++t;
             }
             if (t_done != 0xffffffffu) {
@@ -189,7 +188,6 @@ __global__ void k_build(const ProdDesc *prods, int P, const AgentDesc *agents, c
                 if (p64) p64[t_done] = p_done;
                 pdf[t_done] = to_df(p_done);
                 cp32[t_done] = make_int2((int32_t)done, __float_as_int(__double2float_rd(p_done)));
-                if (cpn32) cpn32[t_done] = make_int2((int32_t)done, __float_as_int(__double2float_rn(p_done)));
             }
         }
     }
@@ -225,14 +223,14 @@ int launch_row_offsets(const ProdDesc *prods, int P, const uint32_t *row_cnt, ui
 int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                  const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ, const double *a_prob,
                  const double *a_cost, const uint8_t *letters, const int16_t *nd_delta, uint32_t *state_sa,
-                 uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32, int2 *cpn32, double *p64,
-                 float2 *pdf, float *cost32, double *cost64, float2 *costdf, uint32_t total_states, uint32_t total_sa,
+                 uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf,
+                 float *cost32, double *cost64, float2 *costdf, uint32_t total_states, uint32_t total_sa,
                  uint32_t total_tr, uint32_t max_work, void *s) {
     dim3 grid((max_work + 255) / 256 < 64 ? (max_work + 255) / 256 : 64, P < 65535 ? P : 65535);
     if (grid.x == 0) grid.x = 1;
     k_build<<<grid, 256, 0, (cudaStream_t)s>>>(prods, P, agents, tasks, a_state_ptr, a_sa_ptr, a_succ, a_prob, a_cost,
-                                                letters, nd_delta, state_sa, state_tr, sa_tr, col, cp32, cpn32, p64,
-                                                pdf, cost32, cost64, costdf, total_states, total_sa, total_tr);
+                                                letters, nd_delta, state_sa, state_tr, sa_tr, col, cp32, p64, pdf,
+                                                cost32, cost64, costdf, total_states, total_sa, total_tr);
     return (int)cudaGetLastError();
 }
 

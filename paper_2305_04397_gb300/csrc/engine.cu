@@ -96,6 +96,7 @@ struct morap_ctx {
     int32_t *in_items = nullptr;  // [items][kInItems] input items of each sweep work item
     uint2 *item_w = nullptr;      // [items] (transitions, rows) of each work item
     uint8_t *chg[3] = {};         // per item: changed in sweep n % 3
+    uint8_t *stamp[2] = {};       // per state: tag of the last sweep (of each parity) that changed it
     ProdDesc *d_prods = nullptr;
     AgentDesc *d_agents = nullptr;
     TaskDesc *d_tasks = nullptr;
@@ -104,7 +105,6 @@ struct morap_ctx {
     uint32_t *state_sa = nullptr, *state_tr = nullptr, *sa_tr = nullptr;
     int32_t *col = nullptr;
     int2 *cp32 = nullptr;
-    int2 *cpn32 = nullptr;  // the residual-correction polish's edge stream (null when it cannot run)
     float2 *pdf = nullptr, *costdf = nullptr;
     float *cost32 = nullptr;
     double *p64 = nullptr, *cost64 = nullptr;
@@ -465,7 +465,6 @@ int ensure_solve(morap_ctx *c, int Kp) {
     a.sa_tr = c->sa_tr;
     a.col = c->col;
     a.cp32 = c->cp32;
-    a.cpn32 = c->cpn32;
     a.pdf = c->pdf;
     a.costdf = c->costdf;
     a.wdf = c->wdf;
@@ -491,6 +490,7 @@ int ensure_solve(morap_ctx *c, int Kp) {
     // lists in order (their values do not fit in L2; see k_sweep)
     a.keep_batch = c->h_chunks.size() >= (size_t)16 * 16 * std::max(1, c->sm_count) ? 1 : 4;
     for (int q = 0; q < 3; ++q) a.chg[q] = c->chg[q];
+    for (int q = 0; q < 2; ++q) a.stamp[q] = c->stamp[q];
     a.eps1 = c->cfg.eps_vi;
     a.eps1f = (float)c->cfg.eps_vi;
     a.gmax = c->cfg.item_warps_max > 0 ? c->cfg.item_warps_max : 8;
@@ -728,6 +728,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         st.fp32_sweeps = (int32_t)hctl[0].sweep_base;
         st.skipped_fp32 = (int64_t)hctl[0].skipped;
         st.computed_fp32 = (int64_t)hctl[0].computed;
+        st.states_fp32 = (int64_t)hctl[0].states;
         st.updates_fp32 = (int64_t)hctl[0].updates;
         st.bytes_fp32 = (int64_t)hctl[0].bytes;
         st.ms_fp32 = ms_between(c->ev[0], c->ev[1]);
@@ -735,6 +736,7 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     st.fp64_sweeps = (int32_t)hctl[1].sweep_base;
     st.skipped_fp64 = (int64_t)hctl[1].skipped;
     st.computed_fp64 = (int64_t)hctl[1].computed;
+    st.states_fp64 = (int64_t)hctl[1].states;
     st.anchored_states = (int64_t)hctl[1].undecided;
     st.work_items = (int64_t)n_items;
     st.updates_fp64 = (int64_t)hctl[1].updates;
@@ -1140,7 +1142,7 @@ int run_construction(morap_ctx *c, cudaStream_t s, bool letters_and_counts = tru
     }
     CKL(launch_row_offsets(c->d_prods, c->P, c->row_cnt, c->sa_tr, s));
     CKL(launch_build(c->d_prods, c->P, c->d_ad, c->d_td, c->d_sp, c->d_sap, c->d_succ, c->d_prob, c->d_cost,
-                     c->d_letters, c->d_nd, c->state_sa, c->state_tr, c->sa_tr, c->col, c->cp32, c->cpn32, c->p64, c->pdf,
+                     c->d_letters, c->d_nd, c->state_sa, c->state_tr, c->sa_tr, c->col, c->cp32, c->p64, c->pdf,
                      c->cost32, c->cost64, c->costdf, c->TS, c->TSA, c->TT, c->max_work, s));
     CKL(launch_item_inputs(c->d_chunks, (int)c->h_chunks.size(), c->d_prods, c->state_tr, c->col, c->in_items, c->item_w,
                                 c->state_sa, s));
@@ -1295,6 +1297,10 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         CKR(dev_alloc(c, L, &c->in_items, std::max<size_t>(chunks.size(), 1) * kInItems * sizeof(int32_t)));
         CKR(dev_alloc(c, L, &c->item_w, std::max<size_t>(chunks.size(), 1) * sizeof(uint2)));
         for (int q = 0; q < 3; ++q) CKR(dev_alloc(c, L, &c->chg[q], std::max<size_t>(chunks.size(), 1)));
+        for (int q = 0; q < 2; ++q) {
+            CKR(dev_alloc(c, L, &c->stamp[q], std::max<size_t>(TS, 1)));
+            CK(cudaMemsetAsync(c->stamp[q], 0, std::max<size_t>(TS, 1), s));
+        }
         CKR(dev_alloc(c, L, &c->d_ad, nI * sizeof(AgentDesc)));
         CKR(dev_alloc(c, L, &c->d_td, nJ * sizeof(TaskDesc)));
         CKR(dev_alloc(c, L, &c->d_sp, a_sp.size() * 4));
@@ -1362,16 +1368,8 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         CKR(dev_alloc(c, L, &c->col, std::max<uint64_t>(TTm, 1) * 4));
         CKR(dev_alloc(c, L, &c->cp32, std::max<uint64_t>(TTm, 1) * 8));
         CKR(dev_alloc(c, L, &c->pdf, std::max<uint64_t>(TTm, 1) * 8));
-        // the residual-correction polish (the default second phase of a
-        // mixed-precision solve) iterates with probabilities rounded to
-        // nearest: with the FP32 phase's rounded-down ones every row would
-        // lose up to an ulp of mass per sweep, a bias of the same sign at
-        // every step of a path that the residual test cannot see
-        const bool delta = c->all_free_action && c->cfg.precision == MORAP_PREC_MIXED && c->cfg.polish == 0;
-        if (delta) CKR(dev_alloc(c, L, &c->cpn32, std::max<uint64_t>(TTm, 1) * 8));
-        // state starts (x2), row starts, col, cp32 (+ cpn32), pdf; cost32, costdf
-        c->csr_bytes = (int64_t)(8 * (TS + 1) + 4 * (TSA + 1) + 4 * TTm + 8 * TTm * (delta ? 2 : 1) + 8 * TTm +
-                                 4 * TSA + 8 * TSA);
+        // state starts (x2), row starts, col, cp32, pdf; cost32, costdf
+        c->csr_bytes = (int64_t)(8 * (TS + 1) + 4 * (TSA + 1) + 4 * TTm + 8 * TTm + 8 * TTm + 4 * TSA + 8 * TSA);
         c->layout_sig = sig;
     }
     c->h_prods = merged;

@@ -137,6 +137,7 @@ struct LoopCtl {
     unsigned int undecided;  // scheduler states whose recorded action is not kept (k_finalize)
     unsigned int decided;    // states one anchoring round decided (k_anchor)
     unsigned int computed;   // work items a sweep computed (not skipped)
+    unsigned long long states;  // states the sweeps computed (inside computed items, see k_sweep)
 };
 
 #ifndef MORAP_CHUNK
@@ -164,7 +165,6 @@ struct SweepArgs {
     const uint32_t *sa_tr;
     const int32_t *col;
     const int2 *cp32;     // per transition {col, p rounded down as float bits}
-    const int2 *cpn32;    // per transition {col, p rounded to nearest}: the residual correction's stream
     const double *p64;
     const float *cost32;
     const double *cost64;
@@ -192,7 +192,11 @@ struct SweepArgs {
     const int32_t *in_items;
     const uint2 *item_w;  // (transitions, state-action rows) of each item, for the statistics
     uint8_t *chg[3];
-    int skip;  // 0: recompute every item (skipping disabled)
+    // State-level exact skipping inside a computed item: stamp[n & 1][state]
+    // = 1 + n % 255 for the last sweep n (of that parity) in which the
+    // state's value changed (see k_sweep).
+    uint8_t *stamp[2];
+    int skip;  // 0: recompute every item and state (skipping disabled)
     int keep_batch;  // kept items appended per atomic (1 keeps the list's order; 1..32)
     const float *G;  // residual-correction polish: [state-action][Kp] table (see ArithDelta)
     double eps1;
@@ -257,7 +261,7 @@ int launch_row_offsets(const ProdDesc *prods, int P, const uint32_t *row_cnt, ui
 int launch_build(const ProdDesc *prods, int P, const AgentDesc *agents, const TaskDesc *tasks,
                  const int32_t *a_state_ptr, const int32_t *a_sa_ptr, const int32_t *a_succ, const double *a_prob,
                  const double *a_cost, const uint8_t *letters, const int16_t *nd_delta, uint32_t *state_sa,
-                 uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32, int2 *cpn32, double *p64, float2 *pdf,
+                 uint32_t *state_tr, uint32_t *sa_tr, int32_t *col, int2 *cp32, double *p64, float2 *pdf,
                  float *cost32, double *cost64, float2 *costdf, uint32_t total_states, uint32_t total_sa,
                  uint32_t total_tr, uint32_t max_work, void *s);
 

@@ -92,29 +92,6 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *g) {
 __device__ __forceinline__ void prefetch_l2(const void *g, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(g), "r"(bytes) : "memory");
 }
-// Paired FP32 arithmetic (fma / mul / add on .f32x2 operands, sm_100 and
-// later): two independent FP32 operations per instruction, each element
-// rounded exactly as the scalar instruction with the same rounding modifier.
-__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(unsigned long long r, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ unsigned long long f2_fma_rd(unsigned long long a, unsigned long long b,
-                                                        unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ unsigned long long f2_fma_rn(unsigned long long a, unsigned long long b,
-                                                        unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -168,6 +145,7 @@ struct ArithF32 {
         c = e.x;
         p = __int_as_float(e.y);
     }
+    static __device__ __forceinline__ int32_t succ(const View &v, uint32_t lt) { return v.edge[lt].x; }
     // rd(-w_i' c) with w_i' >= w_i and c rounded up: a lower bound of the
     // action's reward; the pre-sink weight (the same for every action of a
     // state) is added once, after the maximum, by add_base
@@ -177,12 +155,6 @@ struct ArithF32 {
     static __device__ __forceinline__ Val reward(W w, Cost c) { return reward_cw(cost_weight(w), c); }
     static __device__ __forceinline__ Val add_base(Val v, W w, bool pre) { return pre ? __fadd_rd(v, w.y) : v; }
     static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) { acc = __fmaf_rd(p, v, acc); }
-    // two weights' mac in one paired instruction (same rounding per element)
-    static constexpr bool kPair = true;
-    static __device__ __forceinline__ unsigned long long mac2(unsigned long long acc, unsigned long long pp,
-                                                              unsigned long long v) {
-        return f2_fma_rd(pp, v, acc);
-    }
     static __device__ __forceinline__ void close(Val &) {}
     static __device__ __forceinline__ bool gt(Val a, Val b) { return a > b; }
     static __device__ __forceinline__ Val neg_inf() { return -CUDART_INF_F; }
@@ -201,7 +173,6 @@ struct ArithF32 {
 
 struct ArithDF {
     using Val = DF;
-    static constexpr bool kPair = false;
     static constexpr int AMAX = 192, EMAX = 448;
     // ssa | str[AM + 1] | cost[AM] (float2) | col[EM] | p[EM] (float2)
     template <int AM, int EM>
@@ -254,6 +225,7 @@ struct ArithDF {
         const float2 q = v.p[lt];
         p = {q.x, q.y};
     }
+    static __device__ __forceinline__ int32_t succ(const View &v, uint32_t lt) { return v.col[lt]; }
     // -w_i c, left unnormalised (the accumulation that follows tolerates
     // it); the pre-sink weight is added once per state by add_base
     using CW = float2;  // w_i as (hi, lo)
@@ -336,16 +308,6 @@ __device__ __forceinline__ void store_words(float *p, const float (&w)[NW]) {
 // exactly in double-float at the end.
 struct ArithDelta : ArithF32 {
     using Prob = float;
-    // The transitions carry p rounded to nearest (cpn32), not the FP32
-    // phase's rounded-down p: d is of the size of B's remaining error, and
-    // rows that lose up to an ulp of mass per sweep would pull the fixed
-    // point of the correction down by that loss times the number of steps
-    // to completion (2e-6 on paths of thousands of steps), with a residual
-    // the stopping rule cannot see.  Rounded to nearest, the per-row errors
-    // take both signs.
-    static __device__ __forceinline__ View global_view(const SweepArgs &a, uint32_t A0, uint32_t T0) {
-        return {a.sa_tr + A0, a.cost32 + A0, a.cpn32 + T0};
-    }
     // the rows' costs are inside G: only the row starts and the transitions are staged
     template <int AM = AMAX, int EM = EMAX>
     static __device__ __forceinline__ void stage(const SweepArgs &a, unsigned char *b, uint32_t A0, uint32_t nA,
@@ -354,14 +316,10 @@ struct ArithDelta : ArithF32 {
         uint32_t *str = reinterpret_cast<uint32_t *>(b + L::STR);
         int2 *edge = reinterpret_cast<int2 *>(b + L::EDGE);
         for (uint32_t i = lane; i <= nA; i += 32) cp_async4(str + i, a.sa_tr + A0 + i);
-        for (uint32_t i = lane; i < nT; i += 32) cp_async8(edge + i, a.cpn32 + T0 + i);
+        for (uint32_t i = lane; i < nT; i += 32) cp_async8(edge + i, a.cp32 + T0 + i);
     }
     static __device__ __forceinline__ Val add_base(Val v, W, bool) { return v; }  // inside G
     static __device__ __forceinline__ void mac(Val &acc, Prob p, Val v) { acc = __fmaf_rn(p, v, acc); }
-    static __device__ __forceinline__ unsigned long long mac2(unsigned long long acc, unsigned long long pp,
-                                                              unsigned long long v) {
-        return f2_fma_rn(pp, v, acc);
-    }
     static __device__ __forceinline__ float record_threshold(Val, float eps1) { return eps1; }
 };
 
@@ -380,23 +338,6 @@ __device__ __forceinline__ void init_action(const SweepArgs &a, const typename A
         const typename Ar::Cost c = Ar::cost(vw, la);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = Ar::reward(sw[v], c);
-    }
-}
-
-// acc[v] += p * g[v] for the VEC weights a lane owns; FP32 formats issue
-// the weights two at a time as paired FMAs (same roundings, same results).
-template <class Ar, int VEC>
-__device__ __forceinline__ void mac_row(typename Ar::Val (&acc)[VEC], typename Ar::Prob p, const float *g) {
-    if constexpr (Ar::kPair && VEC % 2 == 0) {
-        const unsigned long long pp = f2_pack(p, p);
-#pragma unroll
-        for (int v = 0; v < VEC; v += 2) {
-            const unsigned long long r = Ar::mac2(f2_pack(acc[v], acc[v + 1]), pp, f2_pack(g[v], g[v + 1]));
-            f2_unpack(r, acc[v], acc[v + 1]);
-        }
-    } else {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], p, Ar::from_words(&g[v * Ar::WORDS]));
     }
 }
 
@@ -475,7 +416,8 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
                                               uint32_t A0, uint32_t T0, int i, uint32_t u, bool pre,
                                               const typename Ar::W *__restrict__ sw, const unsigned int act_bits,
                                               const float *__restrict__ Vold, float *__restrict__ Vnew, int k0,
-                                              float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed) {
+                                              float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed,
+                                              uint8_t *__restrict__ stamp, uint8_t tag) {
     using Val = typename Ar::Val;
     using SH = Shape<Ar, KP, VMAX>;
     constexpr int VEC = SH::VEC;
@@ -516,8 +458,11 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
             for (int j = 0; j < D; ++j)
                 if (cl[j] >= 0) load_words<NW>(Vold + (size_t)cl[j] * ROW + (size_t)k0 * Ar::WORDS, gw[j]);
 #pragma unroll
-            for (int j = 0; j < D; ++j)
-                if (cl[j] >= 0) mac_row<Ar, VEC>(acc, pr[j], gw[j]);
+            for (int j = 0; j < D; ++j) {
+                if (cl[j] < 0) continue;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], pr[j], Ar::from_words(&gw[j][v * Ar::WORDS]));
+            }
         }
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
@@ -537,6 +482,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
     for (int v = 0; v < VEC; ++v) best[v] = Ar::add_base(best[v], sw[v], pre);
     float yw[NW];
     load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
+    bool moved = false;  // some weight of this lane changed this state's value
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
         if (!((act_bits >> v) & 1u)) continue;
@@ -549,9 +495,13 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
         Ar::to_words(best[v], &yw[v * Ar::WORDS]);
 #pragma unroll
         for (int q = 0; q < Ar::WORDS; ++q)
-            changed = changed || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
+            moved = moved || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
     }
     store_words<NW>(Vnew + row, yw);
+    if (moved) {
+        changed = true;
+        if (stamp) stamp[u] = tag;  // every lane of the state that saw a change writes the same tag
+    }
 }
 
 // The same per-state computation with the actions software-pipelined: the
@@ -566,7 +516,8 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
                                                    bool pre, const typename Ar::W *__restrict__ sw,
                                                    const unsigned int act_bits, const float *__restrict__ Vold,
                                                    float *__restrict__ Vnew, int k0,
-                                                   float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed) {
+                                                   float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed,
+                                                   uint8_t *__restrict__ stamp, uint8_t tag) {
     using Val = typename Ar::Val;
     using Prob = typename Ar::Prob;
     using SH = Shape<Ar, KP, VMAX>;
@@ -616,8 +567,11 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         init_action<Ar, KP, VEC>(a, vw, A0, la, k0, sw, acc);
         for (;;) {
 #pragma unroll
-            for (int j = 0; j < D; ++j)
-                if (S.cl[j] >= 0) mac_row<Ar, VEC>(acc, S.pr[j], S.gw[j]);
+            for (int j = 0; j < D; ++j) {
+                if (S.cl[j] < 0) continue;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) Ar::mac(acc[v], S.pr[j], Ar::from_words(&S.gw[j][v * Ar::WORDS]));
+            }
             if (S.t0 + D >= S.t1) break;
             S.t0 += D;  // rows longer than D: the next slots, unpipelined
             fill(S);
@@ -653,6 +607,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
     for (int v = 0; v < VEC; ++v) best[v] = Ar::add_base(best[v], sw[v], pre);
     float yw[NW];
     load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
+    bool moved = false;  // some weight of this lane changed this state's value
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
         if (!((act_bits >> v) & 1u)) continue;
@@ -665,9 +620,13 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         Ar::to_words(best[v], &yw[v * Ar::WORDS]);
 #pragma unroll
         for (int q = 0; q < Ar::WORDS; ++q)
-            changed = changed || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
+            moved = moved || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
     }
     store_words<NW>(Vnew + row, yw);
+    if (moved) {
+        changed = true;
+        if (stamp) stamp[u] = tag;  // every lane of the state that saw a change writes the same tag
+    }
 }
 
 // Named barrier of the G warps (G * 32 threads) of a work group; id >= 1
@@ -715,7 +674,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         ctl->next[far] = 0;
     }
     __shared__ struct {
-        unsigned long long updates, bytes;
+        unsigned long long updates, bytes, states;
         unsigned int skipped, computed;
     } b_stats;
     // group exchange: the item of the next two rounds (double buffered), each
@@ -723,7 +682,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     __shared__ unsigned int g_it[2][WPB];
     __shared__ unsigned char g_chg[WPB];
     __shared__ float g_res[WPB][KP];
-    if (threadIdx.x == 0) b_stats.updates = b_stats.bytes = 0ull, b_stats.skipped = b_stats.computed = 0u;
+    __shared__ uint8_t s_list[WPB][32];  // per warp: the batch states it computes (state-level skipping)
+    if (threadIdx.x == 0) b_stats.updates = b_stats.bytes = b_stats.states = 0ull, b_stats.skipped = b_stats.computed = 0u;
     __syncthreads();
     const unsigned int n_items = ctl->cnt[cur];
     const unsigned int sweep = ctl->sweep_base + pos;
@@ -754,8 +714,19 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     // stay neighbours), which keeps the value gathers of concurrent warps
     // close together when the values do not fit in L2; batches would
     // interleave the warps' items from one sweep to the next.
-    unsigned long long w_updates = 0, w_bytes = 0;  // lane 0's running sums (leaders)
+    unsigned long long w_updates = 0, w_bytes = 0, w_states = 0;  // lane 0's running sums
     unsigned int w_skipped = 0, w_computed = 0;
+    // Exact skipping of single states inside a computed item: the last
+    // sweep (of each parity) in which a state's value changed is stamped
+    // 1 + sweep % 255 in stamp[sweep & 1].  A state whose own stamp and its
+    // successors' stamps all differ from the previous sweep's tag kept its
+    // inputs, so it would reproduce its value (already in both buffers).
+    // A stale stamp that equals the tag only costs a recomputation; a
+    // changed state always carries the tag.  Sweep 0 of a phase computes
+    // every state.
+    uint8_t *const st_cur = a.skip ? a.stamp[sweep & 1u] : nullptr;
+    const uint8_t *const st_prev = a.skip && sweep > 0 ? a.stamp[(sweep - 1u) & 1u] : nullptr;
+    const uint8_t tag_cur = (uint8_t)(1u + sweep % 255u), tag_prev = (uint8_t)(1u + (sweep + 254u) % 255u);
     unsigned int kept = 0u;
     int n_kept = 0;  // warp-uniform
     auto flush_kept = [&]() {
@@ -787,8 +758,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         // the exact-skip test's inputs (see below) depend only on the
         // item: load them now, alongside the item's descriptor
         bool in_chg = false;
-        uint2 iw = make_uint2(0u, 0u);  // lane 0: (transitions, rows) of the item
-        if (lane == 0) iw = __ldg(a.item_w + item);
         if (a.skip) {
             const int32_t in = lane < kInItems ? __ldg(a.in_items + (size_t)item * kInItems + lane) : -1;
             in_chg = (lane == 0 && a.chg[far][item]) || in == -2 || (in >= 0 && a.chg[far][in]);
@@ -865,6 +834,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                 store_words<NW>(Vnew + row, yw);
             }
         } else if (s_begin < s_end) {
+            uint32_t it_states = 0, it_rows = 0, it_tr = 0;  // lane 0: what this warp computes of the item
             // a batch's state boundaries are loaded while the previous
             // batch is staged and computed
             uint32_t nx_sa = 0, nx_tr = 0;
@@ -903,17 +873,61 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                     vw = Ar::global_view(a, A0, T0);
                 }
                 __syncwarp();
-                for (int i = grp; i < m; i += SPW)
+                // which states of the batch are computed (lane i: state i)
+                bool nd = lane < m;
+                uint32_t n_rows = 0, n_tr = 0;
+                if (nd) {
+                    const uint32_t r0 = ssa[lane] - A0, r1 = ssa[lane + 1] - A0;
+                    const uint32_t t0 = vw.str[r0] - T0, t1 = vw.str[r1] - T0;
+                    n_rows = r1 - r0;
+                    n_tr = t1 - t0;
+                    if (st_prev) {
+                        nd = __ldg(st_prev + u0 + lane) == tag_prev;
+                        for (uint32_t t = t0; t < t1 && !nd; t += 4) {
+                            bool h = false;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (t + q < t1) h = h || __ldg(st_prev + Ar::succ(vw, t + q)) == tag_prev;
+                            nd = h;
+                        }
+                    }
+                }
+                const unsigned int need = __ballot_sync(0xffffffffu, nd);
+                const int n_need = __popc(need);
+                if (st_prev) {
+                    if (nd) s_list[wib][__popc(need & ((1u << lane) - 1u))] = (uint8_t)lane;
+                    __syncwarp();
+                }
+                {
+                    const uint32_t c_rows = __reduce_add_sync(0xffffffffu, nd ? n_rows : 0u);
+                    const uint32_t c_tr = __reduce_add_sync(0xffffffffu, nd ? n_tr : 0u);
+                    if (lane == 0) it_states += (uint32_t)n_need, it_rows += c_rows, it_tr += c_tr;
+                }
+                for (int r = grp; r < n_need; r += SPW) {
+                    const int i = st_prev ? (int)s_list[wib][r] : r;
                     if constexpr (PIPE)
                         process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
                                                             u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits, Vold,
-                                                            Vnew, k0, rmax, changed);
+                                                            Vnew, k0, rmax, changed, st_cur, tag_cur);
                     else
                         process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
                                                        u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits, Vold, Vnew, k0,
-                                                       rmax, changed);
+                                                       rmax, changed, st_cur, tag_cur);
+                }
                 __syncwarp();  // the next batch reuses the buffer
                 s0 += m;
+            }
+            // executed updates and algorithmic bytes of the states this
+            // warp computed: their boundaries (state_sa, state_tr), rows
+            // (sa_tr and cost, or the row of G), transitions (successor and
+            // probability), and their values read and written
+            if (lane == 0 && it_states) {
+                const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
+                w_states += it_states;
+                w_updates += (unsigned long long)it_tr * (unsigned long long)n_act;
+                w_bytes += 2ull * it_states * ROW * 4 + 8ull * it_states + 4ull * it_rows +
+                           4ull * (1 + Ar::WORDS) * it_tr +
+                           (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * it_rows;
             }
         }
         // residual: lanes with the same li share weights
@@ -945,17 +959,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             for (int v = 0; v < VEC; ++v)
                 if (grp == 0 && any_active && rmax[v] > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)rmax[v]);
             if (lane == 0) {
-                const uint32_t n_s = cu.y - cu.x;
-                w_bytes += 2ull * n_s * ROW * 4;
-                if (any_active) {
-                    const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
+                if (any_active)
                     ++w_computed;
-                    w_updates += (unsigned long long)iw.x * (unsigned long long)n_act;
-                    // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
-                    w_bytes += 8ull * (n_s + 1) + 4ull * (iw.y + 1) + 4ull * (1 + Ar::WORDS) * iw.x;
-                    // per row: its cost, or for the residual correction its row of G
-                    w_bytes += (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * iw.y;
-                }
+                else  // the copy of a frozen product's rows
+                    w_bytes += 2ull * (cu.y - cu.x) * ROW * 4;
             }
         }
     }
@@ -966,9 +973,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         if (w_bytes) atomicAdd(&b_stats.bytes, w_bytes);
         if (w_skipped) atomicAdd(&b_stats.skipped, w_skipped);
         if (w_computed) atomicAdd(&b_stats.computed, w_computed);
+        if (w_states) atomicAdd(&b_stats.states, w_states);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (b_stats.states) atomicAdd(&ctl->states, b_stats.states);
         if (b_stats.updates) atomicAdd(&ctl->updates, b_stats.updates);
         if (b_stats.bytes) atomicAdd(&ctl->bytes, b_stats.bytes);
         if (b_stats.skipped) atomicAdd(&ctl->skipped, b_stats.skipped);
@@ -1606,6 +1615,7 @@ __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_it
         ctl->undecided = 0;
         ctl->decided = 0;
         ctl->computed = 0;
+        ctl->states = 0;
     }
 }
 
