@@ -565,7 +565,6 @@ def run_engine(args):
     def timed(n, e2e):
         tot = {"updates": 0, "bytes_fp32": 0, "ms_fp32": 0.0, "sweeps32": 0, "sweeps64": 0, "launches": 0, "h2d": 0,
                "d2h": 0, "skipped32": 0, "computed32": 0, "skipped64": 0, "computed64": 0, "anchored": 0,
-               "states32": 0, "states64": 0,
                "variant_fp32": -1, "variant_fp64": -1,
                "ms_fp64": 0.0, "ms_eval": 0.0, "bytes_fp64": 0, "bytes_eval": 0}
         _barrier(ws)
@@ -588,8 +587,6 @@ def run_engine(args):
             tot["computed32"] += st["computed_fp32"]
             tot["skipped64"] += st["skipped_fp64"]
             tot["computed64"] += st["computed_fp64"]
-            tot["states32"] += st["states_fp32"]
-            tot["states64"] += st["states_fp64"]
             tot["anchored"] += st["anchored_states"]
             tot["variant_fp32"], tot["variant_fp64"] = st["variant_fp32"], st["variant_fp64"]
             tot["polish"] = st["polish"]
@@ -660,13 +657,10 @@ def run_engine(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"] // args.steps,
                 "d2h_bytes_per_step": e2e["d2h"] // args.steps, "ms_per_step": e2e_secs * 1e3 / args.steps},
         "gpu_launches": dev["launches"],
-        "updates_counted": "executed only: work items and single states a sweep skips exactly (nothing they "
-                           "read changed) and evaluation padding slots count neither as updates nor as bytes",
+        "updates_counted": "executed only: work items a sweep skips exactly (nothing they read changed) and "
+                           "evaluation padding slots count neither as updates nor as bytes",
         "skipped_share": {"fp32": dev["skipped32"] / max(dev["skipped32"] + dev["computed32"], 1),
                           "polish": dev["skipped64"] / max(dev["skipped64"] + dev["computed64"], 1)},
-        "computed_state_share": {  # states computed / (all states x sweeps of the loop)
-            "fp32": dev["states32"] / max(dev["sweeps32"] * fp["n_states"], 1),
-            "polish": dev["states64"] / max(dev["sweeps64"] * fp["n_states"], 1)},
         "anchored_states_per_step": dev["anchored"] / args.steps,
         "launch_mode": args.launch_mode,
         "clocks": clocks,

@@ -51,9 +51,12 @@ enum {
 /* Precision modes for the optimisation sweeps (Algorithm 3). */
 enum {
     /* FP32 sweeps with every operation rounded toward -inf (a certified lower
-     * bound of the FP64 iterate), then FP64 sweeps from that bound until the
-     * FP64 residual is <= eps_vi.  Used for products whose agent has a
-     * zero-cost action in every state; other products run MORAP_PREC_FP64. */
+     * bound of the FP64 iterate), then FP64-accurate sweeps from that bound
+     * (see morap_config.polish) until their residual is <= eps_vi / 8: the
+     * bound lies below the iterate by FP32 roundings that add up along each
+     * path while each one is below eps_vi, which a test at eps_vi itself
+     * would leave in place.  Used for products whose agent has a zero-cost
+     * action in every state; other products run MORAP_PREC_FP64. */
     MORAP_PREC_MIXED = 0,
     /* FP64 sweeps from 0, as printed. */
     MORAP_PREC_FP64 = 1
@@ -284,10 +287,6 @@ typedef struct morap_solve_stats {
     int64_t computed_fp64;
     int64_t anchored_states;  /* (state, weight) entries whose recorded action was not kept and
                                  that the scheduler's anchoring rounds decided          */
-    int64_t states_fp32;      /* state sweeps computed: inside a computed work item a state
-                                 none of whose successors (itself included) changed in the
-                                 previous sweep is skipped exactly as well              */
-    int64_t states_fp64;
 } morap_solve_stats;
 
 int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out);

@@ -96,7 +96,6 @@ struct morap_ctx {
     int32_t *in_items = nullptr;  // [items][kInItems] input items of each sweep work item
     uint2 *item_w = nullptr;      // [items] (transitions, rows) of each work item
     uint8_t *chg[3] = {};         // per item: changed in sweep n % 3
-    uint8_t *stamp[2] = {};       // per state: tag of the last sweep (of each parity) that changed it
     ProdDesc *d_prods = nullptr;
     AgentDesc *d_agents = nullptr;
     TaskDesc *d_tasks = nullptr;
@@ -490,7 +489,6 @@ int ensure_solve(morap_ctx *c, int Kp) {
     // lists in order (their values do not fit in L2; see k_sweep)
     a.keep_batch = c->h_chunks.size() >= (size_t)16 * 16 * std::max(1, c->sm_count) ? 1 : 4;
     for (int q = 0; q < 3; ++q) a.chg[q] = c->chg[q];
-    for (int q = 0; q < 2; ++q) a.stamp[q] = c->stamp[q];
     a.eps1 = c->cfg.eps_vi;
     a.eps1f = (float)c->cfg.eps_vi;
     a.gmax = c->cfg.item_warps_max > 0 ? c->cfg.item_warps_max : 8;
@@ -728,7 +726,6 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         st.fp32_sweeps = (int32_t)hctl[0].sweep_base;
         st.skipped_fp32 = (int64_t)hctl[0].skipped;
         st.computed_fp32 = (int64_t)hctl[0].computed;
-        st.states_fp32 = (int64_t)hctl[0].states;
         st.updates_fp32 = (int64_t)hctl[0].updates;
         st.bytes_fp32 = (int64_t)hctl[0].bytes;
         st.ms_fp32 = ms_between(c->ev[0], c->ev[1]);
@@ -736,7 +733,6 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     st.fp64_sweeps = (int32_t)hctl[1].sweep_base;
     st.skipped_fp64 = (int64_t)hctl[1].skipped;
     st.computed_fp64 = (int64_t)hctl[1].computed;
-    st.states_fp64 = (int64_t)hctl[1].states;
     st.anchored_states = (int64_t)hctl[1].undecided;
     st.work_items = (int64_t)n_items;
     st.updates_fp64 = (int64_t)hctl[1].updates;
@@ -1297,10 +1293,6 @@ int do_build(morap_ctx *c, cudaStream_t s, morap_footprint *fp) {
         CKR(dev_alloc(c, L, &c->in_items, std::max<size_t>(chunks.size(), 1) * kInItems * sizeof(int32_t)));
         CKR(dev_alloc(c, L, &c->item_w, std::max<size_t>(chunks.size(), 1) * sizeof(uint2)));
         for (int q = 0; q < 3; ++q) CKR(dev_alloc(c, L, &c->chg[q], std::max<size_t>(chunks.size(), 1)));
-        for (int q = 0; q < 2; ++q) {
-            CKR(dev_alloc(c, L, &c->stamp[q], std::max<size_t>(TS, 1)));
-            CK(cudaMemsetAsync(c->stamp[q], 0, std::max<size_t>(TS, 1), s));
-        }
         CKR(dev_alloc(c, L, &c->d_ad, nI * sizeof(AgentDesc)));
         CKR(dev_alloc(c, L, &c->d_td, nJ * sizeof(TaskDesc)));
         CKR(dev_alloc(c, L, &c->d_sp, a_sp.size() * 4));

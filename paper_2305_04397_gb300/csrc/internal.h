@@ -137,7 +137,6 @@ struct LoopCtl {
     unsigned int undecided;  // scheduler states whose recorded action is not kept (k_finalize)
     unsigned int decided;    // states one anchoring round decided (k_anchor)
     unsigned int computed;   // work items a sweep computed (not skipped)
-    unsigned long long states;  // states the sweeps computed (inside computed items, see k_sweep)
 };
 
 #ifndef MORAP_CHUNK
@@ -192,11 +191,7 @@ struct SweepArgs {
     const int32_t *in_items;
     const uint2 *item_w;  // (transitions, state-action rows) of each item, for the statistics
     uint8_t *chg[3];
-    // State-level exact skipping inside a computed item: stamp[n & 1][state]
-    // = 1 + n % 255 for the last sweep n (of that parity) in which the
-    // state's value changed (see k_sweep).
-    uint8_t *stamp[2];
-    int skip;  // 0: recompute every item and state (skipping disabled)
+    int skip;  // 0: recompute every item (skipping disabled)
     int keep_batch;  // kept items appended per atomic (1 keeps the list's order; 1..32)
     const float *G;  // residual-correction polish: [state-action][Kp] table (see ArithDelta)
     double eps1;

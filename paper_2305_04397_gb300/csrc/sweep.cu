@@ -145,7 +145,6 @@ struct ArithF32 {
         c = e.x;
         p = __int_as_float(e.y);
     }
-    static __device__ __forceinline__ int32_t succ(const View &v, uint32_t lt) { return v.edge[lt].x; }
     // rd(-w_i' c) with w_i' >= w_i and c rounded up: a lower bound of the
     // action's reward; the pre-sink weight (the same for every action of a
     // state) is added once, after the maximum, by add_base
@@ -225,7 +224,6 @@ struct ArithDF {
         const float2 q = v.p[lt];
         p = {q.x, q.y};
     }
-    static __device__ __forceinline__ int32_t succ(const View &v, uint32_t lt) { return v.col[lt]; }
     // -w_i c, left unnormalised (the accumulation that follows tolerates
     // it); the pre-sink weight is added once per state by add_base
     using CW = float2;  // w_i as (hi, lo)
@@ -416,8 +414,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
                                               uint32_t A0, uint32_t T0, int i, uint32_t u, bool pre,
                                               const typename Ar::W *__restrict__ sw, const unsigned int act_bits,
                                               const float *__restrict__ Vold, float *__restrict__ Vnew, int k0,
-                                              float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed,
-                                              uint8_t *__restrict__ stamp, uint8_t tag) {
+                                              float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed) {
     using Val = typename Ar::Val;
     using SH = Shape<Ar, KP, VMAX>;
     constexpr int VEC = SH::VEC;
@@ -482,7 +479,6 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
     for (int v = 0; v < VEC; ++v) best[v] = Ar::add_base(best[v], sw[v], pre);
     float yw[NW];
     load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
-    bool moved = false;  // some weight of this lane changed this state's value
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
         if (!((act_bits >> v) & 1u)) continue;
@@ -495,13 +491,9 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
         Ar::to_words(best[v], &yw[v * Ar::WORDS]);
 #pragma unroll
         for (int q = 0; q < Ar::WORDS; ++q)
-            moved = moved || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
+            changed = changed || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
     }
     store_words<NW>(Vnew + row, yw);
-    if (moved) {
-        changed = true;
-        if (stamp) stamp[u] = tag;  // every lane of the state that saw a change writes the same tag
-    }
 }
 
 // The same per-state computation with the actions software-pipelined: the
@@ -516,8 +508,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
                                                    bool pre, const typename Ar::W *__restrict__ sw,
                                                    const unsigned int act_bits, const float *__restrict__ Vold,
                                                    float *__restrict__ Vnew, int k0,
-                                                   float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed,
-                                                   uint8_t *__restrict__ stamp, uint8_t tag) {
+                                                   float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed) {
     using Val = typename Ar::Val;
     using Prob = typename Ar::Prob;
     using SH = Shape<Ar, KP, VMAX>;
@@ -607,7 +598,6 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
     for (int v = 0; v < VEC; ++v) best[v] = Ar::add_base(best[v], sw[v], pre);
     float yw[NW];
     load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
-    bool moved = false;  // some weight of this lane changed this state's value
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
         if (!((act_bits >> v) & 1u)) continue;
@@ -620,13 +610,9 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         Ar::to_words(best[v], &yw[v * Ar::WORDS]);
 #pragma unroll
         for (int q = 0; q < Ar::WORDS; ++q)
-            moved = moved || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
+            changed = changed || __float_as_uint(before[q]) != __float_as_uint(yw[v * Ar::WORDS + q]);
     }
     store_words<NW>(Vnew + row, yw);
-    if (moved) {
-        changed = true;
-        if (stamp) stamp[u] = tag;  // every lane of the state that saw a change writes the same tag
-    }
 }
 
 // Named barrier of the G warps (G * 32 threads) of a work group; id >= 1
@@ -674,7 +660,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         ctl->next[far] = 0;
     }
     __shared__ struct {
-        unsigned long long updates, bytes, states;
+        unsigned long long updates, bytes;
         unsigned int skipped, computed;
     } b_stats;
     // group exchange: the item of the next two rounds (double buffered), each
@@ -682,8 +668,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     __shared__ unsigned int g_it[2][WPB];
     __shared__ unsigned char g_chg[WPB];
     __shared__ float g_res[WPB][KP];
-    __shared__ uint8_t s_list[WPB][32];  // per warp: the batch states it computes (state-level skipping)
-    if (threadIdx.x == 0) b_stats.updates = b_stats.bytes = b_stats.states = 0ull, b_stats.skipped = b_stats.computed = 0u;
+    if (threadIdx.x == 0) b_stats.updates = b_stats.bytes = 0ull, b_stats.skipped = b_stats.computed = 0u;
     __syncthreads();
     const unsigned int n_items = ctl->cnt[cur];
     const unsigned int sweep = ctl->sweep_base + pos;
@@ -714,19 +699,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     // stay neighbours), which keeps the value gathers of concurrent warps
     // close together when the values do not fit in L2; batches would
     // interleave the warps' items from one sweep to the next.
-    unsigned long long w_updates = 0, w_bytes = 0, w_states = 0;  // lane 0's running sums
+    unsigned long long w_updates = 0, w_bytes = 0;  // lane 0's running sums (leaders)
     unsigned int w_skipped = 0, w_computed = 0;
-    // Exact skipping of single states inside a computed item: the last
-    // sweep (of each parity) in which a state's value changed is stamped
-    // 1 + sweep % 255 in stamp[sweep & 1].  A state whose own stamp and its
-    // successors' stamps all differ from the previous sweep's tag kept its
-    // inputs, so it would reproduce its value (already in both buffers).
-    // A stale stamp that equals the tag only costs a recomputation; a
-    // changed state always carries the tag.  Sweep 0 of a phase computes
-    // every state.
-    uint8_t *const st_cur = a.skip ? a.stamp[sweep & 1u] : nullptr;
-    const uint8_t *const st_prev = a.skip && sweep > 0 ? a.stamp[(sweep - 1u) & 1u] : nullptr;
-    const uint8_t tag_cur = (uint8_t)(1u + sweep % 255u), tag_prev = (uint8_t)(1u + (sweep + 254u) % 255u);
     unsigned int kept = 0u;
     int n_kept = 0;  // warp-uniform
     auto flush_kept = [&]() {
@@ -758,6 +732,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         // the exact-skip test's inputs (see below) depend only on the
         // item: load them now, alongside the item's descriptor
         bool in_chg = false;
+        uint2 iw = make_uint2(0u, 0u);  // lane 0: (transitions, rows) of the item
+        if (lane == 0) iw = __ldg(a.item_w + item);
         if (a.skip) {
             const int32_t in = lane < kInItems ? __ldg(a.in_items + (size_t)item * kInItems + lane) : -1;
             in_chg = (lane == 0 && a.chg[far][item]) || in == -2 || (in >= 0 && a.chg[far][in]);
@@ -834,7 +810,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                 store_words<NW>(Vnew + row, yw);
             }
         } else if (s_begin < s_end) {
-            uint32_t it_states = 0, it_rows = 0, it_tr = 0;  // lane 0: what this warp computes of the item
             // a batch's state boundaries are loaded while the previous
             // batch is staged and computed
             uint32_t nx_sa = 0, nx_tr = 0;
@@ -873,61 +848,17 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                     vw = Ar::global_view(a, A0, T0);
                 }
                 __syncwarp();
-                // which states of the batch are computed (lane i: state i)
-                bool nd = lane < m;
-                uint32_t n_rows = 0, n_tr = 0;
-                if (nd) {
-                    const uint32_t r0 = ssa[lane] - A0, r1 = ssa[lane + 1] - A0;
-                    const uint32_t t0 = vw.str[r0] - T0, t1 = vw.str[r1] - T0;
-                    n_rows = r1 - r0;
-                    n_tr = t1 - t0;
-                    if (st_prev) {
-                        nd = __ldg(st_prev + u0 + lane) == tag_prev;
-                        for (uint32_t t = t0; t < t1 && !nd; t += 4) {
-                            bool h = false;
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                if (t + q < t1) h = h || __ldg(st_prev + Ar::succ(vw, t + q)) == tag_prev;
-                            nd = h;
-                        }
-                    }
-                }
-                const unsigned int need = __ballot_sync(0xffffffffu, nd);
-                const int n_need = __popc(need);
-                if (st_prev) {
-                    if (nd) s_list[wib][__popc(need & ((1u << lane) - 1u))] = (uint8_t)lane;
-                    __syncwarp();
-                }
-                {
-                    const uint32_t c_rows = __reduce_add_sync(0xffffffffu, nd ? n_rows : 0u);
-                    const uint32_t c_tr = __reduce_add_sync(0xffffffffu, nd ? n_tr : 0u);
-                    if (lane == 0) it_states += (uint32_t)n_need, it_rows += c_rows, it_tr += c_tr;
-                }
-                for (int r = grp; r < n_need; r += SPW) {
-                    const int i = st_prev ? (int)s_list[wib][r] : r;
+                for (int i = grp; i < m; i += SPW)
                     if constexpr (PIPE)
                         process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
                                                             u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits, Vold,
-                                                            Vnew, k0, rmax, changed, st_cur, tag_cur);
+                                                            Vnew, k0, rmax, changed);
                     else
                         process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
                                                        u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits, Vold, Vnew, k0,
-                                                       rmax, changed, st_cur, tag_cur);
-                }
+                                                       rmax, changed);
                 __syncwarp();  // the next batch reuses the buffer
                 s0 += m;
-            }
-            // executed updates and algorithmic bytes of the states this
-            // warp computed: their boundaries (state_sa, state_tr), rows
-            // (sa_tr and cost, or the row of G), transitions (successor and
-            // probability), and their values read and written
-            if (lane == 0 && it_states) {
-                const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
-                w_states += it_states;
-                w_updates += (unsigned long long)it_tr * (unsigned long long)n_act;
-                w_bytes += 2ull * it_states * ROW * 4 + 8ull * it_states + 4ull * it_rows +
-                           4ull * (1 + Ar::WORDS) * it_tr +
-                           (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * it_rows;
             }
         }
         // residual: lanes with the same li share weights
@@ -959,10 +890,17 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             for (int v = 0; v < VEC; ++v)
                 if (grp == 0 && any_active && rmax[v] > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)rmax[v]);
             if (lane == 0) {
-                if (any_active)
+                const uint32_t n_s = cu.y - cu.x;
+                w_bytes += 2ull * n_s * ROW * 4;
+                if (any_active) {
+                    const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
                     ++w_computed;
-                else  // the copy of a frozen product's rows
-                    w_bytes += 2ull * (cu.y - cu.x) * ROW * 4;
+                    w_updates += (unsigned long long)iw.x * (unsigned long long)n_act;
+                    // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
+                    w_bytes += 8ull * (n_s + 1) + 4ull * (iw.y + 1) + 4ull * (1 + Ar::WORDS) * iw.x;
+                    // per row: its cost, or for the residual correction its row of G
+                    w_bytes += (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * iw.y;
+                }
             }
         }
     }
@@ -973,11 +911,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         if (w_bytes) atomicAdd(&b_stats.bytes, w_bytes);
         if (w_skipped) atomicAdd(&b_stats.skipped, w_skipped);
         if (w_computed) atomicAdd(&b_stats.computed, w_computed);
-        if (w_states) atomicAdd(&b_stats.states, w_states);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (b_stats.states) atomicAdd(&ctl->states, b_stats.states);
         if (b_stats.updates) atomicAdd(&ctl->updates, b_stats.updates);
         if (b_stats.bytes) atomicAdd(&ctl->bytes, b_stats.bytes);
         if (b_stats.skipped) atomicAdd(&ctl->skipped, b_stats.skipped);
@@ -1540,12 +1476,13 @@ __global__ void __launch_bounds__(kEvalBlockThreads, 1) k_eval_block(EvalArgs a,
 // The FP32 phase hands over to the polish phase once a pair's residual is
 // at most 2^-MORAP_THR32_SHIFT of its largest possible value.  Its
 // round-down iterates increase monotonically to a fixed point of the rounded
-// operator, where the residual is exactly 0, so any shift terminates; the
-// shift only trades FP32 sweeps against polish sweeps (near its fixed point
-// the round-down iteration slows down, so a later hand-over costs more
-// sweeps in total).
+// operator, where the residual is exactly 0, so any shift terminates.  The
+// residual correction that follows needs a late hand-over: its table G is
+// rounded to FP32 once, so G must be small (the hand-over values close to
+// the fixed point).  The polish then stops 2^-MORAP_POLISH_SHIFT below eps1
+// (see launch_setup_weights).
 #ifndef MORAP_POLISH_SHIFT
-#define MORAP_POLISH_SHIFT 0
+#define MORAP_POLISH_SHIFT 3
 #endif
 #ifndef MORAP_THR32_SHIFT
 #define MORAP_THR32_SHIFT 16
@@ -1615,7 +1552,6 @@ __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_it
         ctl->undecided = 0;
         ctl->decided = 0;
         ctl->computed = 0;
-        ctl->states = 0;
     }
 }
 
@@ -1911,11 +1847,12 @@ int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, in
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     // A phase that starts from the FP32 phase's values stops at a residual
     // 2^-MORAP_POLISH_SHIFT below eps1: those values lie below the exact
-    // iterate by the FP32 roundings of the last sweeps, which accumulate
-    // along every path (to 1e-6 on paths of hundreds of steps) while each
-    // is smaller than eps1, so a residual test at eps1 stops before the
-    // deficit has been propagated away.  A phase that starts from 0 stops
-    // at eps1, as Algorithm 3 does.
+    // iterate by the FP32 roundings of the last sweeps, which add up along
+    // every path (to 1e-6 on paths of hundreds of steps) while each is
+    // smaller than eps1, so a residual test at eps1 stops before the
+    // deficit has been propagated away (c 2.3e-6 below the fixed point on
+    // the 128x128 batch; 2e-7 at eps1 / 8).  A phase that starts from 0
+    // stops at eps1, as Algorithm 3 does.
     const double eps_polish = after_fp32 ? ldexp(eps1, -MORAP_POLISH_SHIFT) : eps1;
     k_setup_weights<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(prods, P, nI, nJ, K, Kp, W, w32, w64, wdf,
                                                                      thr32, thr64, eps1, eps_polish);

@@ -75,7 +75,6 @@ class SolveStats(ctypes.Structure):
         ("ms_tune", ctypes.c_double),
         ("skipped_fp32", ctypes.c_int64), ("skipped_fp64", ctypes.c_int64), ("work_items", ctypes.c_int64),
         ("computed_fp32", ctypes.c_int64), ("computed_fp64", ctypes.c_int64), ("anchored_states", ctypes.c_int64),
-        ("states_fp32", ctypes.c_int64), ("states_fp64", ctypes.c_int64),
     ]
 
     def as_dict(self):

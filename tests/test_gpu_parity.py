@@ -592,10 +592,6 @@ def test_skipping_unchanged_items_is_exact(M, grid32, polish):
             assert np.array_equal(M.morap_last_policy(on.h, k, p)[0], M.morap_last_policy(off.h, k, p)[0])
     assert st_on["fp32_sweeps"] == st_off["fp32_sweeps"] and st_on["fp64_sweeps"] == st_off["fp64_sweeps"]
     assert st_on["skipped_fp32"] > 0 and st_off["skipped_fp32"] == 0 and st_off["skipped_fp64"] == 0
-    # inside the computed items, single states were skipped as well: fewer
-    # states per computed item than without skipping
-    for ph in ("fp32", "fp64"):
-        assert st_on["states_" + ph] * st_off["computed_" + ph] < st_off["states_" + ph] * st_on["computed_" + ph], ph
     on.close()
     off.close()
 
