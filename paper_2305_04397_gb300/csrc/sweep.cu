@@ -92,16 +92,6 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *g) {
 __device__ __forceinline__ void prefetch_l2(const void *g, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(g), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async16(void *smem, const void *g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(g));
-}
-__device__ __forceinline__ float4 lds128(const float *p) {
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"((unsigned)__cvta_generic_to_shared(p)));
-    return v;
-}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -155,7 +145,6 @@ struct ArithF32 {
         c = e.x;
         p = __int_as_float(e.y);
     }
-    static __device__ __forceinline__ int32_t succ(const View &v, uint32_t lt) { return v.edge[lt].x; }
     // rd(-w_i' c) with w_i' >= w_i and c rounded up: a lower bound of the
     // action's reward; the pre-sink weight (the same for every action of a
     // state) is added once, after the maximum, by add_base
@@ -235,7 +224,6 @@ struct ArithDF {
         const float2 q = v.p[lt];
         p = {q.x, q.y};
     }
-    static __device__ __forceinline__ int32_t succ(const View &v, uint32_t lt) { return v.col[lt]; }
     // -w_i c, left unnormalised (the accumulation that follows tolerates
     // it); the pre-sink weight is added once per state by add_base
     using CW = float2;  // w_i as (hi, lo)
@@ -287,17 +275,6 @@ __device__ __forceinline__ void load_words(const float *p, float (&w)[NW]) {
         w[0] = q.x, w[1] = q.y;
     } else {
         w[0] = __ldg(p);
-    }
-}
-
-// The same from shared memory (16-byte aligned rows of at least 4 words).
-template <int NW>
-__device__ __forceinline__ void lds_words(const float *p, float (&w)[NW]) {
-    static_assert(NW % 4 == 0, "value tiles hold rows of whole 16-byte chunks");
-#pragma unroll
-    for (int i = 0; i < NW / 4; ++i) {
-        const float4 q = lds128(p + 4 * i);
-        w[4 * i] = q.x, w[4 * i + 1] = q.y, w[4 * i + 2] = q.z, w[4 * i + 3] = q.w;
     }
 }
 
@@ -374,10 +351,9 @@ template <>
 struct Variants<ArithF32> {
     static constexpr int N = 4;
     static constexpr int vmax[N] = {8, 8, 4, 8};
-    static constexpr int d[N] = {3, 2, 2, 2};  // shape 2: D = 2 keeps 3 blocks per SM free of spills
+    static constexpr int d[N] = {3, 4, 2, 2};  // shape 2: D = 2 keeps 3 blocks per SM free of spills
     static constexpr int minb[N] = {2, 2, 3, 2};
     static constexpr int pipe[N] = {0, 0, 0, 1};  // actions software-pipelined
-    static constexpr int tile[N] = {0, 1, 0, 0};  // value rows gathered into shared memory per batch
 };
 template <>
 struct Variants<ArithDelta> : Variants<ArithF32> {};
@@ -388,7 +364,6 @@ struct Variants<ArithDF> {
     static constexpr int d[N] = {3, 4, 2, 2};
     static constexpr int minb[N] = {2, 2, 3, 2};
     static constexpr int pipe[N] = {0, 0, 0, 1};
-    static constexpr int tile[N] = {0, 0, 0, 0};
 };
 
 // Lanes per state and weights per lane for each (format, Kp, VMAX).
@@ -423,26 +398,6 @@ __device__ __forceinline__ Vec<T, VEC> vload(const T *p) {
     return r;
 }
 
-// Per-warp shared memory of a sweep shape: the staged CSR of a batch, the
-// item's weights and, for the value-tile shapes, the batch's value rows.  A
-// value-tile shape stages fewer rows and transitions per batch (AM, EM) and
-// gathers, after the CSR has arrived, the value row of every state of the
-// batch and of every transition's successor into a tile of kTileBytes with
-// 16-byte cp.async copies: all gathers of the batch are in flight at once,
-// and the arithmetic then reads shared memory.  Only FP32 words (Kp >= 4,
-// rows of whole 16-byte chunks) have a tile.
-constexpr int kTileBytes = 10240;
-template <class Ar, int KP, int TILE_>
-struct WarpBuf {
-    static constexpr bool TILE = TILE_ != 0 && Ar::WORDS == 1 && KP >= 4;
-    static constexpr int AM = TILE ? 96 : Ar::AMAX, EM = TILE ? 224 : Ar::EMAX;
-    static constexpr int W_OFF = Ar::template Lay<AM, EM>::BYTES;
-    static constexpr int TILE_OFF = W_OFF + 64 * (int)sizeof(typename Ar::W);
-    static constexpr int TILE_ROWS = TILE ? kTileBytes / (KP * 4) : 0;
-    static constexpr int BYTES = TILE_OFF + (TILE ? kTileBytes : 0);
-    static_assert(W_OFF % 16 == 0 && TILE_OFF % 16 == 0 && BYTES % 16 == 0, "16-byte aligned areas");
-};
-
 // ------------------------------------------------------------- the sweep
 //
 // Work items are kChunk-state ranges of one product taken by whole warps
@@ -454,17 +409,12 @@ struct WarpBuf {
 // each lane owns VEC of the Kp weights, so a successor's value row is read
 // once, coalesced, for all weights.  Actions are the outer loop; within an
 // action a lane issues D independent value gathers before it consumes them.
-//
-// With TILE the batch's value rows are already in shared memory (see
-// k_sweep): tile row i is the batch's state i (its x), tile row m + t the
-// successor of the batch's transition t.  The arithmetic is the same.
-template <class Ar, int KP, int VMAX, int D, bool TILE = false>
+template <class Ar, int KP, int VMAX, int D>
 __device__ __forceinline__ void process_state(const SweepArgs &a, const typename Ar::View &vw, const uint32_t *ssa,
                                               uint32_t A0, uint32_t T0, int i, uint32_t u, bool pre,
                                               const typename Ar::W *__restrict__ sw, const unsigned int act_bits,
                                               const float *__restrict__ Vold, float *__restrict__ Vnew, int k0,
-                                              float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed,
-                                              const float *tile = nullptr, int m = 0) {
+                                              float (&rmax)[Shape<Ar, KP, VMAX>::VEC], bool &changed) {
     using Val = typename Ar::Val;
     using SH = Shape<Ar, KP, VMAX>;
     constexpr int VEC = SH::VEC;
@@ -502,13 +452,8 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
             }
             float gw[D][NW];
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                if (cl[j] < 0) continue;
-                if constexpr (TILE)
-                    lds_words<NW>(tile + (size_t)(m + (int)(base + j)) * ROW + k0, gw[j]);
-                else
-                    load_words<NW>(Vold + (size_t)cl[j] * ROW + (size_t)k0 * Ar::WORDS, gw[j]);
-            }
+            for (int j = 0; j < D; ++j)
+                if (cl[j] >= 0) load_words<NW>(Vold + (size_t)cl[j] * ROW + (size_t)k0 * Ar::WORDS, gw[j]);
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 if (cl[j] < 0) continue;
@@ -533,10 +478,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
 #pragma unroll
     for (int v = 0; v < VEC; ++v) best[v] = Ar::add_base(best[v], sw[v], pre);
     float yw[NW];
-    if constexpr (TILE)
-        lds_words<NW>(tile + (size_t)i * ROW + k0, yw);  // x; replaced below by y for the active weights
-    else
-        load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
+    load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
         if (!((act_bits >> v) & 1u)) continue;
@@ -697,15 +639,12 @@ __device__ __forceinline__ void group_sync(int id, int nthreads) {
 // after a barrier that combines the warps' change flags and residuals.  The
 // per-(state, weight) arithmetic does not depend on G, so neither do the
 // results.
-template <class Ar, int KP, int VMAX, int D, int MINB, int PIPE, int TILE_ = 0>
+template <class Ar, int KP, int VMAX, int D, int MINB, int PIPE>
 __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) {
     using SH = Shape<Ar, KP, VMAX>;
     constexpr int VEC = SH::VEC, LPS = SH::LPS, SPW = SH::SPW;
     constexpr int NW = VEC * Ar::WORDS;
     constexpr int ROW = KP * Ar::WORDS;
-    using WB = WarpBuf<Ar, KP, TILE_>;
-    constexpr bool TILE = WB::TILE;
-    constexpr int AM = WB::AM, EM = WB::EM;
     constexpr int WPB = kThreads / 32;  // warps per block
     constexpr int GMAX = (kChunk / SPW) < WPB ? (kChunk / SPW) : WPB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -736,11 +675,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;  // warp in block
     const int grp = lane / LPS, li = lane % LPS, k0 = li * VEC;
-    unsigned char *warp_buf = smem_raw + wib * WB::BYTES;
+    unsigned char *warp_buf = smem_raw + wib * (Ar::STAGE_BYTES + KP * (int)sizeof(typename Ar::W));
     unsigned char *stage_buf = warp_buf;
     uint32_t *ssa = reinterpret_cast<uint32_t *>(stage_buf);
-    typename Ar::W *wsm = reinterpret_cast<typename Ar::W *>(warp_buf + WB::W_OFF);  // the item's weights
-    float *tile = reinterpret_cast<float *>(warp_buf + WB::TILE_OFF);                  // value rows (TILE)
+    typename Ar::W *wsm = reinterpret_cast<typename Ar::W *>(warp_buf + Ar::STAGE_BYTES);  // the item's weights
 
     const unsigned int n_warps = gridDim.x * WPB;
     int G = 1;  // warps per item, the same in every block
@@ -885,9 +823,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                 const uint32_t my_sa = nx_sa, my_tr = nx_tr;
                 const uint32_t A0 = __shfl_sync(0xffffffffu, my_sa, 0);
                 const uint32_t T0 = __shfl_sync(0xffffffffu, my_tr, 0);
-                bool fits = lane <= m_max && my_sa - A0 <= (uint32_t)AM && my_tr - T0 <= (uint32_t)EM;
-                if constexpr (TILE)  // the batch's own rows and one row per transition
-                    fits = fits && (uint32_t)lane + (my_tr - T0) <= (uint32_t)WB::TILE_ROWS;
+                const bool fits =
+                    lane <= m_max && my_sa - A0 <= (uint32_t)Ar::AMAX && my_tr - T0 <= (uint32_t)Ar::EMAX;
                 int m = __popc(__ballot_sync(0xffffffffu, fits)) - 1;  // boundaries 0..m fit
                 const bool staged = m >= 1;
                 if (!staged) m = 1;  // one state too large for the buffer: read it from global memory
@@ -904,39 +841,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                 if constexpr (std::is_same<Ar, ArithDelta>::value && KP % 4 == 0)
                     if (lane == 0 && A1 > A0) prefetch_l2(a.G + (size_t)A0 * KP, (A1 - A0) * (uint32_t)(KP * 4));
                 if (staged) {
-                    Ar::template stage<AM, EM>(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
-                    if constexpr (TILE) {  // the batch's own value rows (contiguous), with the CSR
-                        constexpr int C = KP / 4;  // 16-byte chunks per row
-                        for (int q = lane; q < m * C; q += 32)
-                            cp_async16(tile + (size_t)q * 4, Vold + (size_t)u0 * ROW + (size_t)q * 4);
-                    }
+                    Ar::stage(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
                     cp_async_wait_all();
-                    vw = Ar::template smem_view<AM, EM>(stage_buf);
+                    vw = Ar::smem_view(stage_buf);
                 } else {
                     vw = Ar::global_view(a, A0, T0);
                 }
                 __syncwarp();
-                if constexpr (TILE) {
-                    if (staged) {  // every transition's successor row, all in flight at once
-                        constexpr int C = KP / 4;
-                        const int nT = (int)(T1 - T0);
-                        float *trow = tile + (size_t)m * ROW;
-                        for (int q = lane; q < nT * C; q += 32) {
-                            const int t = q / C, c = q % C;
-                            cp_async16(trow + (size_t)t * ROW + c * 4,
-                                       Vold + (size_t)Ar::succ(vw, (uint32_t)t) * ROW + c * 4);
-                        }
-                        cp_async_wait_all();
-                        __syncwarp();
-                        for (int i = grp; i < m; i += SPW)
-                            process_state<Ar, KP, VMAX, D, true>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
-                                                                 u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits,
-                                                                 Vold, Vnew, k0, rmax, changed, tile, m);
-                        __syncwarp();  // the next batch reuses the buffers
-                        s0 += m;
-                        continue;
-                    }
-                }
                 for (int i = grp; i < m; i += SPW)
                     if constexpr (PIPE)
                         process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
@@ -1748,9 +1659,9 @@ __global__ void k_gather_eval(const int4 *pairs, int n_pairs, const ProdDesc *pr
     }
 }
 
-template <class Ar, int KP, int TILE>
+template <class Ar>
 constexpr int smem_of() {
-    return (kThreads / 32) * WarpBuf<Ar, KP, TILE>::BYTES;
+    return (kThreads / 32) * (Ar::STAGE_BYTES + 64 * (int)sizeof(typename Ar::W));  // sized for the largest Kp
 }
 
 using SweepFn = void (*)(SweepArgs, int);
@@ -1763,8 +1674,7 @@ struct SweepKernel {
 template <class Ar, int KP, int V>
 SweepKernel sweep_kernel() {
     using VA = Variants<Ar>;
-    return {&k_sweep<Ar, KP, VA::vmax[V], VA::d[V], VA::minb[V], VA::pipe[V], VA::tile[V]>,
-            smem_of<Ar, KP, VA::tile[V]>()};
+    return {&k_sweep<Ar, KP, VA::vmax[V], VA::d[V], VA::minb[V], VA::pipe[V]>, smem_of<Ar>()};
 }
 
 template <class Ar, int KP, int... V>
@@ -1852,10 +1762,8 @@ int launch_eval_block(const EvalArgs &a, const int *bpairs, int n_bpairs, uint32
     return (int)cudaGetLastError();
 }
 
-int sweep_smem_bytes(int kind) {  // the largest of the kind's shapes
-    return kind == kSweepDF ? smem_of<ArithDF, 64, 0>()
-           : kind == kSweepDelta ? smem_of<ArithDelta, 64, 1>()
-                                 : smem_of<ArithF32, 64, 1>();
+int sweep_smem_bytes(int kind) {
+    return kind == kSweepDF ? smem_of<ArithDF>() : kind == kSweepDelta ? smem_of<ArithDelta>() : smem_of<ArithF32>();
 }
 
 int sweep_blocks_per_sm(int kind, int Kp, int variant) {
