@@ -47,7 +47,10 @@ def make_workload(name, rank=0):
     import instances as I
 
     gen, eps = WORKLOADS[name]
-    return getattr(I, gen)(seed={"config_grid32": 1, "config_uneven": 2, "config_large": 3}[gen] + rank), eps
+    seed = {"config_grid32": 1, "config_uneven": 2, "config_large": 3}[gen] + rank
+    if gen == "config_grid32":  # its 16 weight vectors: recorded Algorithm 1 directions
+        return I.config_grid32(seed=seed, pareto_weights=True), eps
+    return getattr(I, gen)(seed=seed), eps
 
 
 # DRAM traffic of one fully active sweep of each sweep kernel (tuned shape)

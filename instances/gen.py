@@ -31,6 +31,7 @@ with slip/2; a move into the border or an obstacle leaves the agent in place
 
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -462,10 +463,19 @@ def config_tiny(seed=0):
     return Instance(agents, tasks, Wt, t, "tiny-4x4-2x3")
 
 
-def config_grid32(seed=1, n_agents=10, n_tasks=20, side=32, K=16, obstacle_frac=0.15):
+PARETO_WEIGHTS_GRID32 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
+                                     "grid32_pareto_weights.txt")
+
+
+def config_grid32(seed=1, n_agents=10, n_tasks=20, side=32, K=16, obstacle_frac=0.15, pareto_weights=False):
     """10 agents on one 32x32 warehouse grid with 15% random obstacles,
     per-agent slip ~ U[0.05, 0.2]; 20 tasks of 3-6 DFA locations (sequenced
-    visits, half of them with an avoid region that is a trap)."""
+    visits, half of them with an avoid region that is a trap).
+
+    pareto_weights: take the K = 16 weight vectors recorded from Algorithm 1
+    runs on the seed-1 instance (the default sizes; data file written by
+    the oracle's record_pareto_weights) instead of the synthetic draws.
+    Other seeds of the same sizes reuse those directions."""
     rng = _rng(seed, 2)
     blocked = rng.random((side, side)) < obstacle_frac
     comp = _largest_free_component(blocked)
@@ -497,6 +507,10 @@ def config_grid32(seed=1, n_agents=10, n_tasks=20, side=32, K=16, obstacle_frac=
     slips = rng.uniform(0.05, 0.2, size=n_agents)
     agents = [grid_agent(side, side, float(slips[i]), starts[i], blocked, regions) for i in range(n_agents)]
     Wt = weight_vectors(n_agents, n_tasks, K, seed)
+    if pareto_weights:
+        if (n_agents, n_tasks, K) != (10, 20, 16):
+            raise ValueError("the recorded Pareto-loop weights are 16 directions of 10 agents and 20 tasks")
+        Wt = np.loadtxt(PARETO_WEIGHTS_GRID32, dtype=np.float64, comments="#").reshape(K, n_agents + n_tasks)
     t = threshold_points(n_agents, n_tasks, 4, seed)
     return Instance(agents, tasks, Wt, t, f"grid{side}-{n_agents}x{n_tasks}",
                     {"side": side, "obstacle_frac": obstacle_frac})
