@@ -437,7 +437,7 @@ def run_serving(M, args):
             out.append((i, np.concatenate([-rng.uniform(5.0, 50.0, size=nI), rng.uniform(0.5, 0.99, size=nJ)])))
         return out
 
-    kw = dict(max_batch=64, n_workers=8, eps=1e-6, max_iter=args.serve_max_iter,
+    kw = dict(max_batch=64, n_workers=args.serve_workers, eps=1e-6, max_iter=args.serve_max_iter,
               merge_instances=1 if args.serve_mode == "merged" else 0)
     srv = M.Server(ctxs, **kw)
     for i, t in queries(len(ctxs)):  # warm every instance once
@@ -485,7 +485,7 @@ def run_serving(M, args):
         "saturation_qps": sat, "offered_qps": at80["offered_qps"], "p50_ms": at80["p50_ms"], "p99_ms": at80["p99_ms"],
         "mean_batch": at80["mean_batch"], "saturation_mean_batch": st_sat["mean_batch"],
         "rate_sweep": sweep, "queries": at80["queries"], "instances": len(ctxs), "max_iter": args.serve_max_iter,
-        "eps": 1e-6, "batching": args.serve_mode,
+        "eps": 1e-6, "batching": args.serve_mode, "workers": args.serve_workers,
         "workload": f"{len(ctxs)} resident instances ({', '.join(kinds)}: one in four of each); per query an "
                     "instance uniformly, c_i = -U[5,50], p_j = U[0.5,0.99]; Poisson arrivals at 25/50/80% of the "
                     f"saturation rate ({args.serve_sat_queries} queries submitted at once)",
@@ -756,6 +756,7 @@ def main():
     ap.add_argument("--serve-sat-queries", type=int, default=1000)
     ap.add_argument("--serve-mode", choices=["merged", "per-instance"], default="per-instance")
     ap.add_argument("--serve-max-iter", type=int, default=32)
+    ap.add_argument("--serve-workers", type=int, default=8, help="server host threads (concurrent device rounds)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
