@@ -529,6 +529,8 @@ def run_engine(args):
     cfg.polish = args.polish
     cfg.in_place = 1 if args.in_place else 0
     cfg.item_warps_max = args.item_warps_max
+    if args.eval_block is not None:
+        cfg.eval_block = args.eval_block
     if strong:
         from paper_2305_04397_gb300 import sharded as S
 
@@ -641,7 +643,8 @@ def run_engine(args):
     dominant, other = (polish, "fp32") if dev["ms_fp64"] >= dev["ms_fp32"] else ("fp32", polish)
     roofline = phase_roofline(dominant)
     roofline["other_phases"] = {other + "_sweeps": phase_roofline(other),
-                                "evaluation_GBps": dev["bytes_eval"] / max(dev["ms_eval"], 1e-9) / 1e6}
+                                "evaluation_GBps": dev["bytes_eval"] / max(dev["ms_eval"], 1e-9) / 1e6,
+                                "evaluation_share_of_step": dev["ms_eval"] / dev["ms"]}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -651,7 +654,7 @@ def run_engine(args):
                    "transitions": fp["n_trans"], "eps_vi": cfg.eps_vi, "eps_eval": cfg.eps_eval,
                    "polish": ["fp32 residual correction", "double-float"][cfg.polish],
                    "sweeps": "in place" if cfg.in_place else "synchronous",
-                   "item_warps_max": cfg.item_warps_max or 8,
+                   "item_warps_max": cfg.item_warps_max or 8, "eval_block": cfg.eval_block,
                    "l2": "per-step working set (CSR + FP32/FP64 value buffers) exceeds the 129 MB L2; no flush",
                    "parallelism": (f"one instance, its products dealt to {ws} GPU(s) (LPT on transitions x "
                                    f"expected sweeps; all-gather of c, all-reduce of r per batch)") if strong
@@ -757,6 +760,8 @@ def main():
     ap.add_argument("--serve-mode", choices=["merged", "per-instance"], default="per-instance")
     ap.add_argument("--serve-max-iter", type=int, default=32)
     ap.add_argument("--serve-workers", type=int, default=8, help="server host threads (concurrent device rounds)")
+    ap.add_argument("--eval-block", type=int, default=None, choices=[0, 1, 2],
+                    help="Algorithm 4 form: 0 sweep loop, 1 one block per pair, 2 a cluster of blocks per pair")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
