@@ -760,8 +760,8 @@ def main():
     ap.add_argument("--serve-mode", choices=["merged", "per-instance"], default="per-instance")
     ap.add_argument("--serve-max-iter", type=int, default=32)
     ap.add_argument("--serve-workers", type=int, default=8, help="server host threads (concurrent device rounds)")
-    ap.add_argument("--eval-block", type=int, default=None, choices=[0, 1, 2],
-                    help="Algorithm 4 form: 0 sweep loop, 1 one block per pair, 2 a cluster of blocks per pair")
+    ap.add_argument("--eval-block", type=int, default=None, choices=[0, 1],
+                    help="Algorithm 4 form: 0 the multi-launch sweep loop, 1 one block per pair")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
