@@ -69,7 +69,8 @@ typedef void *(*morap_alloc_fn)(size_t bytes, void *user);
 typedef void (*morap_free_fn)(void *ptr, size_t bytes, void *user);
 
 typedef struct morap_config {
-    double eps_vi;      /* epsilon_1 of Algorithm 3 (stop when max|y - x| <= eps_vi); default 1e-8     */
+    double eps_vi;      /* epsilon_1 of Algorithm 3 (stop when max|y - x| <= eps_vi; eps_vi / 8 for the
+                           phase that follows an FP32 phase, see MORAP_PREC_MIXED); default 1e-8      */
     double eps_eval;    /* epsilon_2 of Algorithm 4; default 1e-11 (its stop error grows with the
                            expected number of steps, so it is kept below the 1e-6 value tolerance)   */
     double tau_policy;  /* tie tolerance of the returned scheduler, see morap_solve; default 1e-9     */
