@@ -1296,16 +1296,18 @@ __global__ void __launch_bounds__(kEvalBlockThreads, 1) k_eval_block(EvalArgs a,
     const float thr_f = __double2float_rd(a.thr);  // float r > thr_f exactly when (double)r > thr
     // block-wide maxima of up to four quantities; every warp reduces the
     // per-warp values itself, so one barrier per sweep suffices
-    auto block_max4 = [&](float (&v)[4], int parity) {
+    // (the correction stage's test reads only the two moves: NQ = 2 there)
+    auto block_max = [&](float (&v)[4], int parity, auto nq) {
+        constexpr int NQ = decltype(nq)::value;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v[q] = fmaxf(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
             if (lane == 0) s_red[parity][q][warp] = v[q];
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             float m = lane < NWARP ? s_red[parity][q][lane] : 0.0f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -1403,7 +1405,7 @@ __global__ void __launch_bounds__(kEvalBlockThreads, 1) k_eval_block(EvalArgs a,
         if (sweeps >= cap) break;
         float m[4];
         sweep(X(sweeps), X(sweeps + 1), nullptr, m);
-        block_max4(m, sweeps & 1);
+        block_max(m, sweeps & 1, std::integral_constant<int, 4>{});
         ++sweeps;
         const float f = 3.814697265625e-06f; /* 2^-18 */
         if (m[0] <= f * m[2] && m[1] <= f * m[3]) break;
@@ -1436,7 +1438,7 @@ __global__ void __launch_bounds__(kEvalBlockThreads, 1) k_eval_block(EvalArgs a,
         while (sweeps < cap) {
             float m[4];
             sweep(D(k), D(k + 1), G, m);
-            block_max4(m, sweeps & 1);
+            block_max(m, sweeps & 1, std::integral_constant<int, 2>{});
             ++sweeps;
             ++k;
             if (!(fmaxf(m[0], m[1]) > thr_f)) {
