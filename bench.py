@@ -531,6 +531,8 @@ def run_engine(args):
     cfg.item_warps_max = args.item_warps_max
     if args.eval_block is not None:
         cfg.eval_block = args.eval_block
+    if args.tail_items is not None:
+        cfg.tail_items = args.tail_items
     if strong:
         from paper_2305_04397_gb300 import sharded as S
 
@@ -570,6 +572,7 @@ def run_engine(args):
     def timed(n, e2e):
         tot = {"updates": 0, "bytes_fp32": 0, "ms_fp32": 0.0, "sweeps32": 0, "sweeps64": 0, "launches": 0, "h2d": 0,
                "d2h": 0, "skipped32": 0, "computed32": 0, "skipped64": 0, "computed64": 0, "anchored": 0,
+               "tail32": 0, "tail64": 0,
                "variant_fp32": -1, "variant_fp64": -1,
                "ms_fp64": 0.0, "ms_eval": 0.0, "bytes_fp64": 0, "bytes_eval": 0}
         _barrier(ws)
@@ -588,6 +591,8 @@ def run_engine(args):
             tot["ms_eval"] += st["ms_eval"]
             tot["sweeps32"] += st["fp32_sweeps"]
             tot["sweeps64"] += st["fp64_sweeps"]
+            tot["tail32"] += st["tail_sweeps_fp32"]
+            tot["tail64"] += st["tail_sweeps_fp64"]
             tot["skipped32"] += st["skipped_fp32"]
             tot["computed32"] += st["computed_fp32"]
             tot["skipped64"] += st["skipped_fp64"]
@@ -629,15 +634,18 @@ def run_engine(args):
              "df64": "k_sweep<ArithDF,…> shape %d (double-float Bellman sweep)"}
 
     def phase_roofline(phase):
-        b, ms, n = (dev["bytes_fp32"], dev["ms_fp32"], dev["sweeps32"]) if phase == "fp32" else \
-            (dev["bytes_fp64"], dev["ms_fp64"], dev["sweeps64"])
+        b, ms, n, nt = (dev["bytes_fp32"], dev["ms_fp32"], dev["sweeps32"], dev["tail32"]) if phase == "fp32" else \
+            (dev["bytes_fp64"], dev["ms_fp64"], dev["sweeps64"], dev["tail64"])
         ach = b / (ms / 1e3) / 1e9 if ms > 0 else None
         per = b / max(n, 1)
         v = dev["variant_fp32"] if phase == "fp32" else dev["variant_fp64"]
-        return {"bound": "hbm", "kernel": names[phase] % v + ", graph-launched loop", "achieved": ach, "peak": peak,
+        loop = ", graph-launched loop: one launch per sweep while the work list is long, the rest in one " \
+               "cooperative launch (k_sweep_tail, shape 0)" if nt else ", graph-launched loop, one launch per sweep"
+        return {"bound": "hbm", "kernel": names[phase] % v + loop, "achieved": ach, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": (ach / peak) if ach else None,
                 "traffic": _traffic(args.workload, phase, v, per), "bytes_per_sweep": per,
-                "ms_per_sweep": ms / max(n, 1), "share_of_step": ms / dev["ms"]}
+                "ms_per_sweep": ms / max(n, 1), "share_of_step": ms / dev["ms"],
+                "tail_share_of_sweeps": nt / max(n, 1)}
 
     # the roofline object is the sweep loop with the largest share of the step
     dominant, other = (polish, "fp32") if dev["ms_fp64"] >= dev["ms_fp32"] else ("fp32", polish)
@@ -655,6 +663,7 @@ def run_engine(args):
                    "polish": ["fp32 residual correction", "double-float"][cfg.polish],
                    "sweeps": "in place" if cfg.in_place else "synchronous",
                    "item_warps_max": cfg.item_warps_max or 8, "eval_block": cfg.eval_block,
+                   "tail_items": cfg.tail_items,
                    "l2": "per-step working set (CSR + FP32/FP64 value buffers) exceeds the 129 MB L2; no flush",
                    "parallelism": (f"one instance, its products dealt to {ws} GPU(s) (LPT on transitions x "
                                    f"expected sweeps; all-gather of c, all-reduce of r per batch)") if strong
@@ -760,6 +769,9 @@ def main():
     ap.add_argument("--serve-mode", choices=["merged", "per-instance"], default="per-instance")
     ap.add_argument("--serve-max-iter", type=int, default=32)
     ap.add_argument("--serve-workers", type=int, default=8, help="server host threads (concurrent device rounds)")
+    ap.add_argument("--tail-items", type=int, default=None,
+                    help="work-list length at which a sweep loop runs its remaining sweeps in one cooperative "
+                         "launch (0 never, the default; -1 automatic)")
     ap.add_argument("--eval-block", type=int, default=None, choices=[0, 1],
                     help="Algorithm 4 form: 0 the multi-launch sweep loop, 1 one block per pair")
     args = ap.parse_args()

@@ -117,6 +117,20 @@ typedef struct morap_config {
                                    short (the late sweeps of a loop) splits each item's states over up
                                    to this many warps, 1, 2, 4 or 8; 0 (default) = 8 (capped at what
                                    one item fills).  Same results for every value.               */
+    int32_t tail_items;         /* the end of each Algorithm 3 sweep loop: once the loop's work list
+                                   holds at most this many work items, its remaining sweeps run in
+                                   one cooperative launch (every block resident; a grid-wide barrier
+                                   between sweeps instead of a launch per sweep).  0 (default): no
+                                   such launch (one launch per sweep to the end); -1: once the list
+                                   has fewer items than that launch has warps; > 0: this many.
+                                   Same results for every value; on the 32x32-grid batch the tail
+                                   launch is not faster (a late sweep is the items' chain of
+                                   dependent loads, and values written by other blocks of the
+                                   launch are read from L2), hence off.  Each barrier wait is
+                                   bounded (1 s): a wait that runs out ends the launch and the call
+                                   returns MORAP_ECUDA.  The cooperative launch needs the whole
+                                   GPU's resident blocks, so the serving workers (several loops at
+                                   once on one GPU) run without it.                                */
 } morap_config;
 
 typedef struct morap_ctx morap_ctx;
@@ -134,6 +148,15 @@ int morap_ctx_destroy(morap_ctx *ctx);
 /* Message of the calling thread's most recent failed call ("" if none).
  * The pointer stays valid until the thread's next failing call. */
 const char *morap_last_error(void);
+
+/* Self-check of the bounded wait in the grid barrier that separates the
+ * sweeps of a tail launch (config tail_items): one cooperative launch of that
+ * barrier on `device` in which one block never arrives, so every other
+ * block's wait runs out (after 1 s) and the kernel ends by itself.
+ * *timed_out = 1 when the waits ran out and reported it, *ms = the launch's
+ * device time.  Synchronous; allocates and frees one small device buffer; no
+ * context needed.  Errors: EINVAL (NULL output), ECUDA. */
+int morap_barrier_selfcheck(int32_t device, int32_t *timed_out, double *ms);
 
 /* ---------------------------------------------------------------- models */
 
@@ -253,8 +276,8 @@ int morap_supporting_points(morap_ctx *ctx, int32_t K, const double *W, void *st
 /* Statistics of the last morap_solve / morap_supporting_points call. */
 typedef struct morap_solve_stats {
     int32_t K;                /* weights in the batch                              */
-    int32_t fp32_sweeps;      /* sweep launches of the FP32 phase (0 if unused)    */
-    int32_t fp64_sweeps;      /* sweep launches of the second (polish) phase         */
+    int32_t fp32_sweeps;      /* sweeps of the FP32 phase (0 if unused), counted in bodies of six */
+    int32_t fp64_sweeps;      /* sweeps of the second (polish) phase                 */
     int32_t eval_sweeps;      /* sweep launches of the evaluation phase             */
     int64_t updates_fp32;     /* transition-updates executed: one (s,a,s') term for one weight in one
                                  sweep (work items skipped exactly are not counted)   */
@@ -288,6 +311,9 @@ typedef struct morap_solve_stats {
     int64_t computed_fp64;
     int64_t anchored_states;  /* (state, weight) entries whose recorded action was not kept and
                                  that the scheduler's anchoring rounds decided          */
+    int32_t tail_sweeps_fp32; /* of fp32_sweeps / fp64_sweeps: the sweeps the loop's tail launch
+                                 ran (config tail_items)                                */
+    int32_t tail_sweeps_fp64;
 } morap_solve_stats;
 
 int morap_last_solve_stats(const morap_ctx *ctx, morap_solve_stats *out);

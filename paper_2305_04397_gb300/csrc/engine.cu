@@ -68,6 +68,8 @@ struct LoopGraph {
     cudaGraphExec_t exec = nullptr;
     int grid = 0;
     int variant = -1;  // kernel shape of the sweeps (chosen before the graph is built)
+    unsigned int tail = 0;  // work-list length at which k_sweep_tail takes the rest (0: none)
+    int tail_grid = 0;      // its cooperative grid
 };
 
 struct morap_ctx {
@@ -273,11 +275,14 @@ void free_eval(morap_ctx *c) {
 // blocks pull work items until the sweep's list is exhausted).
 int sweep_grid(morap_ctx *c, int blocks_per_sm) { return c->sm_count * std::max(1, blocks_per_sm); }
 
+int no_tail(cudaStream_t) { return 0; }
+
 // Build one device loop: a graph whose while node repeats a body of six
 // sweep launches and one control launch until the control kernel clears the
-// condition (empty work list or sweep cap).
-template <typename F>
-int build_loop_graph(morap_ctx *c, LoopGraph &g, LoopCtl *ctl, F &&launch_sweep_at) {
+// condition (work list down to g.tail items, or empty, or sweep cap), then,
+// with g.tail > 0, one tail launch that runs the remaining sweeps.
+template <typename F, typename T>
+int build_loop_graph(morap_ctx *c, LoopGraph &g, LoopCtl *ctl, F &&launch_sweep_at, T &&launch_tail) {
     destroy_graph(g);
     cudaGraph_t graph = nullptr;
     CK(cudaGraphCreate(&graph, 0));
@@ -305,6 +310,19 @@ int build_loop_graph(morap_ctx *c, LoopGraph &g, LoopCtl *ctl, F &&launch_sweep_
         cudaGraphDestroy(graph);
         return fail(MORAP_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
     }
+    if (g.tail > 0) {  // the tail launch, after the while node
+        e = cudaStreamBeginCaptureToGraph(c->cap_stream, graph, &node, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = launch_tail(c->cap_stream);
+            captured = nullptr;
+            e = cudaStreamEndCapture(c->cap_stream, &captured);
+        }
+        if (rc != 0 || e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return fail(MORAP_ECUDA, std::string("capturing a tail launch: ") +
+                                         cudaGetErrorString(rc != 0 ? (cudaError_t)rc : e));
+        }
+    }
     e = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(MORAP_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
@@ -313,8 +331,8 @@ int build_loop_graph(morap_ctx *c, LoopGraph &g, LoopCtl *ctl, F &&launch_sweep_
 
 // Run one sweep loop: the captured graph (launch_mode 0), or the same
 // kernels body by body from the host, reading the work list in between.
-template <typename F>
-int run_loop(morap_ctx *c, LoopGraph &g, LoopCtl *ctl, cudaStream_t s, F &&launch_sweep_at) {
+template <typename F, typename T>
+int run_loop(morap_ctx *c, LoopGraph &g, LoopCtl *ctl, cudaStream_t s, F &&launch_sweep_at, T &&launch_tail) {
     if (c->cfg.launch_mode == 0) {
         CK(cudaGraphLaunch(g.exec, s));
         return MORAP_OK;
@@ -325,8 +343,9 @@ int run_loop(morap_ctx *c, LoopGraph &g, LoopCtl *ctl, cudaStream_t s, F &&launc
         CKL(launch_loop_control_host(ctl, 0, s));
         CK(cudaMemcpyAsync(c->h_ctl, ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (c->h_ctl->cnt[0] == 0 || c->h_ctl->sweep_base >= c->h_ctl->cap) break;
+        if (c->h_ctl->cnt[0] <= g.tail || c->h_ctl->sweep_base >= c->h_ctl->cap) break;
     }
+    if (g.tail > 0) CKL(launch_tail(s));
     return MORAP_OK;
 }
 
@@ -343,16 +362,33 @@ const SweepArgs &args_of(morap_ctx *c, int kind) {
     return kind == kSweepF32 ? c->args32 : kind == kSweepDF ? c->args64 : c->argsd;
 }
 
+// The tail of a phase's loop (config tail_items): the cooperative grid is
+// every block that can be resident (no more than one warp per work item
+// needs), and the loop hands over once its list has at most tail_items
+// items (-1: once it has fewer items than that grid has warps).
+void setup_tail(morap_ctx *c, LoopGraph &G, int kind, int Kp) {
+    G.tail = 0;
+    G.tail_grid = 0;
+    if (c->cfg.tail_items == 0) return;
+    const int bps = sweep_tail_blocks_per_sm(kind, Kp);
+    if (bps <= 0) return;  // no occupancy figure: the loop runs to the end one launch per sweep
+    const size_t useful = (c->h_chunks.size() + kThreads / 32 - 1) / (kThreads / 32);
+    G.tail_grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->sm_count * bps, useful));
+    G.tail = c->cfg.tail_items > 0 ? (unsigned int)c->cfg.tail_items
+                                   : (unsigned int)G.tail_grid * (unsigned int)(kThreads / 32);
+}
+
 int build_phase_graph(morap_ctx *c, LoopGraph &G, int kind, int Kp, int v) {
     destroy_graph(G);
     G.variant = v;
     G.grid = sweep_launch_grid(c, kind, Kp, v);
+    setup_tail(c, G, kind, Kp);
     if (c->cfg.launch_mode != 0) return MORAP_OK;
     const SweepArgs a = args_of(c, kind);
-    const int grid = G.grid;
-    return build_loop_graph(c, G, a.ctl, [&](int pos, cudaStream_t st) {
-        return launch_sweep(kind, Kp, v, a, pos, grid, st);
-    });
+    const int grid = G.grid, tgrid = G.tail_grid;
+    return build_loop_graph(
+        c, G, a.ctl, [&](int pos, cudaStream_t st) { return launch_sweep(kind, Kp, v, a, pos, grid, st); },
+        [&](cudaStream_t st) { return launch_sweep_tail(kind, Kp, a, tgrid, st); });
 }
 
 // The tuner.  The first solve of a phase at a given Kp runs its loop from the
@@ -592,7 +628,8 @@ LoopGraph *eval_graph(morap_ctx *c, size_t n_chunks, int &rc) {
     if (c->cfg.launch_mode == 0) {
         const EvalArgs e = c->eargs;
         const int grid = g.grid;
-        rc = build_loop_graph(c, g, e.ctl, [&](int pos, cudaStream_t s) { return launch_eval_sweep(e, pos, grid, s); });
+        rc = build_loop_graph(
+            c, g, e.ctl, [&](int pos, cudaStream_t s) { return launch_eval_sweep(e, pos, grid, s); }, no_tail);
     }
     return &g;
 }
@@ -641,21 +678,22 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     if (mixed) {
         CK(cudaMemsetAsync(c->V32[0], 0, nv * sizeof(float), s));
         CK(cudaMemsetAsync(c->V32[1], 0, nv * sizeof(float), s));
-        CKL(launch_loop_init(c->ctl + 0, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
-                             c->chg[2], c->w64));
         bool tune = false;
         CKR(prepare_phase(c, kSweepF32, Kp, tune));
+        LoopGraph &G32 = c->g32[log2_of(Kp)];
+        CKL(launch_loop_init(c->ctl + 0, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
+                             c->chg[2], c->w64, tune ? 0u : G32.tail));
         const auto t0 = std::chrono::steady_clock::now();
         CK(cudaEventRecord(c->ev[0], s));
         if (tune) {
-            CKR(run_loop_tuning(c, c->g32[log2_of(Kp)], kSweepF32, Kp, s));
+            CKR(run_loop_tuning(c, G32, kSweepF32, Kp, s));
         } else {
             const SweepArgs a32 = c->args32;
-            const LoopGraph &G = c->g32[log2_of(Kp)];
-            const int grid = G.grid, v = G.variant;
-            CKR(run_loop(c, c->g32[log2_of(Kp)], c->ctl + 0, s, [&](int pos, cudaStream_t st) {
-                return launch_sweep(kSweepF32, Kp, v, a32, pos, grid, st);
-            }));
+            const int grid = G32.grid, v = G32.variant, tgrid = G32.tail_grid;
+            CKR(run_loop(
+                c, G32, c->ctl + 0, s,
+                [&](int pos, cudaStream_t st) { return launch_sweep(kSweepF32, Kp, v, a32, pos, grid, st); },
+                [&](cudaStream_t st) { return launch_sweep_tail(kSweepF32, Kp, a32, tgrid, st); }));
         }
         CK(cudaEventRecord(c->ev[1], s));
         if (tune) c->ms_tune += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -673,21 +711,22 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
         CK(cudaMemsetAsync(c->V64[1], 0, nv * sizeof(double), s));
     }
     const int pk = mixed ? c->polish : kSweepDF;  // the polish kind of this solve
-    CKL(launch_loop_init(c->ctl + 1, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
-                         c->chg[2], c->w64));
     bool tune64 = false;
     CKR(prepare_phase(c, pk, Kp, tune64));
+    LoopGraph &G64 = c->g64[log2_of(Kp)];
+    CKL(launch_loop_init(c->ctl + 1, c->list[0], n_items, c->res, np, c->sweeps_pair, c->frozen, cap, s,
+                         c->chg[2], c->w64, tune64 ? 0u : G64.tail));
     const auto t64 = std::chrono::steady_clock::now();
     CK(cudaEventRecord(c->ev[6], s));
     if (tune64) {
-        CKR(run_loop_tuning(c, c->g64[log2_of(Kp)], pk, Kp, s));
+        CKR(run_loop_tuning(c, G64, pk, Kp, s));
     } else {
         const SweepArgs a2 = args_of(c, pk);
-        const LoopGraph &G = c->g64[log2_of(Kp)];
-        const int grid = G.grid, v = G.variant;
-        CKR(run_loop(c, c->g64[log2_of(Kp)], c->ctl + 1, s, [&](int pos, cudaStream_t st) {
-            return launch_sweep(pk, Kp, v, a2, pos, grid, st);
-        }));
+        const int grid = G64.grid, v = G64.variant, tgrid = G64.tail_grid;
+        CKR(run_loop(
+            c, G64, c->ctl + 1, s,
+            [&](int pos, cudaStream_t st) { return launch_sweep(pk, Kp, v, a2, pos, grid, st); },
+            [&](cudaStream_t st) { return launch_sweep_tail(pk, Kp, a2, tgrid, st); }));
     }
     CK(cudaEventRecord(c->ev[2], s));
     if (tune64) c->ms_tune += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t64).count();
@@ -706,6 +745,8 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     CK(cudaMemcpyAsync(hs, c->d_status, np * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hctl, c->ctl, 2 * sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if ((mixed && hctl[0].bar_err) || hctl[1].bar_err)
+        return fail(MORAP_ECUDA, "a sweep loop's tail launch gave up waiting at a grid barrier (1 s)");
     // The scheduler's anchoring rounds, only when some recorded action was
     // not kept (rare: its value drifted by steps below eps1 after the record).
     for (int round = 1, pending = (int)hctl[1].undecided; pending > 0 && round <= kAnchorRounds; ++round) {
@@ -741,8 +782,17 @@ int run_optimisation(morap_ctx *c, int K, const double *W, cudaStream_t s, std::
     st.ms_finalise = ms_between(c->ev[2], c->ev[3]);
     st.h2d_bytes = (int64_t)(nW * sizeof(double));
     st.d2h_bytes = (int64_t)(np * (sizeof(double) + sizeof(int32_t)) + 2 * sizeof(LoopCtl));
-    // sweep launches plus one control launch per body of six
-    launches += st.fp32_sweeps + st.fp32_sweeps / 6 + st.fp64_sweeps + st.fp64_sweeps / 6;
+    // one launch per sweep and one control launch per body of six, except
+    // the sweeps of a tail launch (one launch, which a loop with a tail
+    // threshold makes even when no sweep is left for it)
+    if (mixed) {
+        st.tail_sweeps_fp32 = (int32_t)hctl[0].tail_sweeps;
+        const int n = st.fp32_sweeps - st.tail_sweeps_fp32;
+        launches += n + n / 6 + (hctl[0].tail > 0 ? 1 : 0);
+    }
+    st.tail_sweeps_fp64 = (int32_t)hctl[1].tail_sweeps;
+    const int n64 = st.fp64_sweeps - st.tail_sweeps_fp64;
+    launches += n64 + n64 / 6 + (hctl[1].tail > 0 ? 1 : 0);
     st.kernel_launches = launches;
     st.variant_fp32 = mixed ? c->g32[log2_of(Kp)].variant : -1;
     st.variant_fp64 = c->g64[log2_of(Kp)].variant;
@@ -835,9 +885,9 @@ int run_evaluation_group(morap_ctx *c, const std::vector<int4> &pairs_in, cudaSt
         LoopGraph *ge = eval_graph(c, n_loop, rc);
         CKR(rc);
         const int grid = ge->grid;
-        CKR(run_loop(c, *ge, c->ctl + 2, s, [&](int pos, cudaStream_t st) {
-            return launch_eval_sweep(ea, pos, grid, st);
-        }));
+        CKR(run_loop(
+            c, *ge, c->ctl + 2, s, [&](int pos, cudaStream_t st) { return launch_eval_sweep(ea, pos, grid, st); },
+            no_tail));
     }
     CK(cudaEventRecord(c->ev[5], s));
     CKL(launch_gather_eval(c->d_epairs, (int)npair, c->d_prods, c->E[0], c->d_rc, c->d_rp, s));
@@ -959,6 +1009,21 @@ int morap::ctx_merge(morap_ctx *const *ctxs, int n, morap_ctx **out, std::vector
         return rc;
     }
     *out = m;
+    return MORAP_OK;
+}
+
+// The serving workers run several sweep loops on one GPU at once, where the
+// cooperative tail launches of two loops could each hold part of the GPU
+// while waiting for the rest: their contexts run every sweep as its own
+// launch.  Graphs built with a tail are rebuilt without it.
+int morap::ctx_no_tail(morap_ctx *c) {
+    c->cfg.tail_items = 0;
+    for (int i = 0; i < 7; ++i) {
+        if (c->g32[i].variant >= 0 && c->g32[i].tail > 0)
+            CKR(build_phase_graph(c, c->g32[i], kSweepF32, 1 << i, c->g32[i].variant));
+        if (c->g64[i].variant >= 0 && c->g64[i].tail > 0)
+            CKR(build_phase_graph(c, c->g64[i], c->polish, 1 << i, c->g64[i].variant));
+    }
     return MORAP_OK;
 }
 
@@ -1416,9 +1481,43 @@ void morap_config_default(morap_config *cfg) {
     cfg->eval_block = 1;
     cfg->in_place = 0;
     cfg->item_warps_max = 0;
+    cfg->tail_items = 0;
 }
 
 const char *morap_last_error(void) { return g_last_error.c_str(); }
+
+int morap_barrier_selfcheck(int32_t device, int32_t *timed_out, double *ms) {
+    API_BEGIN
+    if (!timed_out || !ms) return fail(MORAP_EINVAL, "barrier selfcheck: NULL output");
+    CK(cudaSetDevice(device));
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    LoopCtl *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(LoopCtl)));
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(LoopCtl), s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = (cudaError_t)launch_barrier_selfcheck(d, std::max(2, sms), s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    LoopCtl h{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(MORAP_ECUDA, std::string("barrier selfcheck: ") + cudaGetErrorString(e));
+    *timed_out = h.bar_err ? 1 : 0;
+    *ms = (double)t;
+    return MORAP_OK;
+    API_END
+}
 
 int morap_ctx_create(const morap_config *cfg, morap_ctx **out) {
     API_BEGIN
@@ -1447,6 +1546,7 @@ int morap_ctx_create(const morap_config *cfg, morap_ctx **out) {
         return fail(MORAP_EINVAL, "config: item_warps_max must be 0, 1, 2, 4 or 8");
     if (c.skip_unchanged != 0 && c.skip_unchanged != 1)
         return fail(MORAP_EINVAL, "config: skip_unchanged must be 0 or 1");
+    if (c.tail_items < -1) return fail(MORAP_EINVAL, "config: tail_items must be -1 (automatic), 0 (off) or > 0");
     CK(cudaSetDevice(c.device));
     morap_ctx *ctx = new morap_ctx();
     ctx->cfg = c;

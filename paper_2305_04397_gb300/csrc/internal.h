@@ -137,6 +137,11 @@ struct LoopCtl {
     unsigned int undecided;  // scheduler states whose recorded action is not kept (k_finalize)
     unsigned int decided;    // states one anchoring round decided (k_anchor)
     unsigned int computed;   // work items a sweep computed (not skipped)
+    unsigned int tail;       // the graph's while loop stops once the work list has <= tail items
+                             // (0: runs to the end; otherwise k_sweep_tail runs the rest)
+    unsigned int bar;        // k_sweep_tail's grid-barrier arrivals
+    unsigned int bar_err;    // 1: a grid-barrier wait of k_sweep_tail ran out
+    unsigned int tail_sweeps;  // sweeps k_sweep_tail ran
 };
 
 #ifndef MORAP_CHUNK
@@ -237,6 +242,7 @@ int ctx_merge(morap_ctx *const *ctxs, int n, morap_ctx **out, std::vector<int32_
               std::vector<int32_t> &task_off, std::vector<int32_t> &pair_off);
 std::string ctx_arith_key(const morap_ctx *c);
 int64_t ctx_max_states(const morap_ctx *c);
+int ctx_no_tail(morap_ctx *c);  // every sweep of the context's loops its own launch (tail_items = 0)
 
 // ---------------------------------------------------------- kernel launchers
 // (defined in the .cu files; every launcher enqueues on `s` and returns the
@@ -270,7 +276,7 @@ int launch_item_inputs(const int4 *chunks, int n_items, const ProdDesc *prods, c
 // w_pair (nullable, [n_pairs]): pairs whose two weights are both 0 start frozen
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
                      size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s,
-                     uint8_t *chg_prev = nullptr, const double2 *w_pair = nullptr);
+                     uint8_t *chg_prev = nullptr, const double2 *w_pair = nullptr, unsigned int tail = 0);
 // Sweep kinds: the FP32 round-down phase, the double-float polish, and the
 // polish as an FP32 residual correction on a double-float table.
 enum { kSweepF32 = 0, kSweepDF = 1, kSweepDelta = 2 };
@@ -278,6 +284,15 @@ enum { kSweepF32 = 0, kSweepDF = 1, kSweepDelta = 2 };
 // shapes give bit-identical results, they differ only in speed).
 int launch_sweep(int kind, int Kp, int variant, const SweepArgs &a, int pos, int grid, void *s);
 int sweep_blocks_per_sm(int kind, int Kp, int variant);
+// The rest of a loop whose work list has fallen to ctl->tail items, in one
+// cooperative launch of `grid` blocks (at most sweep_tail_blocks_per_sm per
+// SM; 0 there: the occupancy query failed).  Same results as the sweeps one
+// launch each.  A grid-barrier wait that runs out sets ctl->bar_err.
+int launch_sweep_tail(int kind, int Kp, const SweepArgs &a, int grid, void *s);
+int sweep_tail_blocks_per_sm(int kind, int Kp);
+// A cooperative launch of the tail's grid barrier in which one block never
+// arrives (the others' bounded waits run out; ctl->bar_err is set).
+int launch_barrier_selfcheck(LoopCtl *ctl, int grid, void *s);
 int sweep_variant_count(int kind);
 
 int eval_blocks_per_sm();

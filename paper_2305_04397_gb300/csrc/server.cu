@@ -375,6 +375,11 @@ int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const 
         const int64_t bpw = states * (2 * 4 + 2 * 8 + 1 + 1);
         int reserve = cfg.max_batch;
         if (cfg.hbm_budget) reserve = (int)std::min<int64_t>(reserve, std::max<int64_t>(1, (int64_t)cfg.hbm_budget / bpw));
+        if (const int rc = ctx_no_tail(c); rc != MORAP_OK) {  // the workers' loops run concurrently
+            for (auto s : S->streams) cudaStreamDestroy(s);
+            delete S;
+            return rc;
+        }
         if (ctx_reserve(c, reserve) != MORAP_OK) set_error("");  // not fatal: buffers then grow on demand
         S->inst.push_back(c);
         S->n_obj.push_back(nI + nJ);
@@ -427,6 +432,7 @@ int morap_server_create(morap_ctx *const *instances, int32_t n_instances, const 
             for (int i : G.members) bpw += S->bytes_per_weight[i];
             int reserve = cfg.max_batch;
             if (cfg.hbm_budget) reserve = (int)std::min<int64_t>(reserve, std::max<int64_t>(1, (int64_t)cfg.hbm_budget / bpw));
+            if ((rc = ctx_no_tail(G.merged)) != MORAP_OK) break;
             if (ctx_reserve(G.merged, reserve) != MORAP_OK) set_error("");  // buffers then grow on demand
         }
         if (rc != MORAP_OK) {

@@ -278,6 +278,38 @@ __device__ __forceinline__ void load_words(const float *p, float (&w)[NW]) {
     }
 }
 
+// Value loads of the sweeps.  One launch per sweep reads values no kernel of
+// the launch writes (the read-only path); a launch that runs several sweeps
+// (COH) reads values other blocks wrote in its previous sweep, so it loads
+// them from L2 (ld.global.cg), never from an SM's non-coherent cache.
+template <int NW, bool COH>
+__device__ __forceinline__ void load_vals(const float *p, float (&w)[NW]) {
+    if constexpr (!COH) {
+        load_words<NW>(p, w);
+    } else if constexpr (NW >= 4) {
+#pragma unroll
+        for (int i = 0; i < NW / 4; ++i) {
+            const float4 q = __ldcg(reinterpret_cast<const float4 *>(p) + i);
+            w[4 * i] = q.x, w[4 * i + 1] = q.y, w[4 * i + 2] = q.z, w[4 * i + 3] = q.w;
+        }
+    } else if constexpr (NW == 2) {
+        const float2 q = __ldcg(reinterpret_cast<const float2 *>(p));
+        w[0] = q.x, w[1] = q.y;
+    } else {
+        w[0] = __ldcg(p);
+    }
+}
+
+// A load of loop state written during the launch (residuals, change flags,
+// work lists, counters): from L2 when the launch runs several sweeps.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_loop(const T *p) {
+    if constexpr (COH)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
 template <int NW>
 __device__ __forceinline__ void store_words(float *p, const float (&w)[NW]) {
     if constexpr (NW >= 4) {
@@ -409,7 +441,7 @@ __device__ __forceinline__ Vec<T, VEC> vload(const T *p) {
 // each lane owns VEC of the Kp weights, so a successor's value row is read
 // once, coalesced, for all weights.  Actions are the outer loop; within an
 // action a lane issues D independent value gathers before it consumes them.
-template <class Ar, int KP, int VMAX, int D>
+template <class Ar, int KP, int VMAX, int D, bool COH>
 __device__ __forceinline__ void process_state(const SweepArgs &a, const typename Ar::View &vw, const uint32_t *ssa,
                                               uint32_t A0, uint32_t T0, int i, uint32_t u, bool pre,
                                               const typename Ar::W *__restrict__ sw, const unsigned int act_bits,
@@ -453,7 +485,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
             float gw[D][NW];
 #pragma unroll
             for (int j = 0; j < D; ++j)
-                if (cl[j] >= 0) load_words<NW>(Vold + (size_t)cl[j] * ROW + (size_t)k0 * Ar::WORDS, gw[j]);
+                if (cl[j] >= 0) load_vals<NW, COH>(Vold + (size_t)cl[j] * ROW + (size_t)k0 * Ar::WORDS, gw[j]);
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 if (cl[j] < 0) continue;
@@ -478,7 +510,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
 #pragma unroll
     for (int v = 0; v < VEC; ++v) best[v] = Ar::add_base(best[v], sw[v], pre);
     float yw[NW];
-    load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
+    load_vals<NW, COH>(Vold + row, yw);  // x; replaced below by y for the active weights
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
         if (!((act_bits >> v) & 1u)) continue;
@@ -502,7 +534,7 @@ __device__ __forceinline__ void process_state(const SweepArgs &a, const typename
 // exposed per state instead of one per action.  Actions with more than D
 // transitions finish their remaining slots unpipelined.  Same operations in
 // the same order per (state, weight) as process_state.
-template <class Ar, int KP, int VMAX, int D>
+template <class Ar, int KP, int VMAX, int D, bool COH>
 __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typename Ar::View &vw,
                                                    const uint32_t *ssa, uint32_t A0, uint32_t T0, int i, uint32_t u,
                                                    bool pre, const typename Ar::W *__restrict__ sw,
@@ -546,7 +578,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
         }
 #pragma unroll
         for (int j = 0; j < D; ++j)
-            if (S.cl[j] >= 0) load_words<NW>(vbase + (size_t)S.cl[j] * ROW, S.gw[j]);
+            if (S.cl[j] >= 0) load_vals<NW, COH>(vbase + (size_t)S.cl[j] * ROW, S.gw[j]);
     };
     auto fetch = [&](uint32_t la, Slots &S) {
         S.t0 = vw.str[la] - T0;
@@ -597,7 +629,7 @@ __device__ __forceinline__ void process_state_pipe(const SweepArgs &a, const typ
 #pragma unroll
     for (int v = 0; v < VEC; ++v) best[v] = Ar::add_base(best[v], sw[v], pre);
     float yw[NW];
-    load_words<NW>(Vold + row, yw);  // x; replaced below by y for the active weights
+    load_vals<NW, COH>(Vold + row, yw);  // x; replaced below by y for the active weights
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
         if (!((act_bits >> v) & 1u)) continue;
@@ -639,8 +671,18 @@ __device__ __forceinline__ void group_sync(int id, int nthreads) {
 // after a barrier that combines the warps' change flags and residuals.  The
 // per-(state, weight) arithmetic does not depend on G, so neither do the
 // results.
-template <class Ar, int KP, int VMAX, int D, int MINB, int PIPE>
-__global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) {
+// Per-thread running sums of a launch's statistics (kept by the group
+// leaders' lane 0), added to the loop's counters once per launch.
+struct PassStats {
+    unsigned long long updates, bytes;
+    unsigned int skipped, computed;
+};
+
+// One sweep (pos = sweep mod 6: value buffer pos & 1, work list pos % 3).
+// COH: the launch runs several sweeps, so everything the previous sweep wrote
+// (values, residuals, change flags, lists, counters) is read from L2.
+template <class Ar, int KP, int VMAX, int D, int PIPE, bool COH>
+__device__ __forceinline__ void sweep_pass(const SweepArgs &a, int pos, unsigned int sweep, PassStats &ps) {
     using SH = Shape<Ar, KP, VMAX>;
     constexpr int VEC = SH::VEC, LPS = SH::LPS, SPW = SH::SPW;
     constexpr int NW = VEC * Ar::WORDS;
@@ -659,19 +701,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         ctl->cnt[far] = 0;
         ctl->next[far] = 0;
     }
-    __shared__ struct {
-        unsigned long long updates, bytes;
-        unsigned int skipped, computed;
-    } b_stats;
     // group exchange: the item of the next two rounds (double buffered), each
     // warp's change flag and per-weight residuals
     __shared__ unsigned int g_it[2][WPB];
     __shared__ unsigned char g_chg[WPB];
     __shared__ float g_res[WPB][KP];
-    if (threadIdx.x == 0) b_stats.updates = b_stats.bytes = 0ull, b_stats.skipped = b_stats.computed = 0u;
-    __syncthreads();
-    const unsigned int n_items = ctl->cnt[cur];
-    const unsigned int sweep = ctl->sweep_base + pos;
+    const unsigned int n_items = ld_loop<COH>(&ctl->cnt[cur]);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;  // warp in block
     const int grp = lane / LPS, li = lane % LPS, k0 = li * VEC;
@@ -699,8 +734,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
     // stay neighbours), which keeps the value gathers of concurrent warps
     // close together when the values do not fit in L2; batches would
     // interleave the warps' items from one sweep to the next.
-    unsigned long long w_updates = 0, w_bytes = 0;  // lane 0's running sums (leaders)
-    unsigned int w_skipped = 0, w_computed = 0;
     unsigned int kept = 0u;
     int n_kept = 0;  // warp-uniform
     auto flush_kept = [&]() {
@@ -728,7 +761,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             it = g_it[round & 1][gib];
         }
         if (it >= n_items) break;
-        const unsigned int item = a.list[cur][it];
+        const unsigned int item = ld_loop<COH>(&a.list[cur][it]);
         // the exact-skip test's inputs (see below) depend only on the
         // item: load them now, alongside the item's descriptor
         bool in_chg = false;
@@ -736,7 +769,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
         if (lane == 0) iw = __ldg(a.item_w + item);
         if (a.skip) {
             const int32_t in = lane < kInItems ? __ldg(a.in_items + (size_t)item * kInItems + lane) : -1;
-            in_chg = (lane == 0 && a.chg[far][item]) || in == -2 || (in >= 0 && a.chg[far][in]);
+            in_chg = (lane == 0 && ld_loop<COH>(&a.chg[far][item])) || in == -2 ||
+                     (in >= 0 && ld_loop<COH>(&a.chg[far][in]));
         }
         const int4 ch = a.chunks[item];
         const uint4 cu = a.chunk_u[item];  // the item's global state range and its product's first pre-sink state
@@ -749,7 +783,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             const int k = lane + 32 * h;
             bool act = false, nz = false;
             if (k < KP) {
-                const double prev = as_double(res_prev[pair0 + k]);
+                const double prev = as_double(ld_loop<COH>(&res_prev[pair0 + k]));
                 act = prev > a.thr[pair0 + k];
                 nz = prev > 0.0;
             }
@@ -781,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             if (!__any_sync(0xffffffffu, in_chg)) {
                 if (leader && lane == 0) {  // no update executed and no byte moved
                     a.chg[cur][item] = 0;
-                    ++w_skipped;
+                    ++ps.skipped;
                 }
                 continue;
             }
@@ -806,7 +840,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
             for (int s = s_begin + grp; s < s_end; s += SPW) {
                 const size_t row = (size_t)(uint32_t)s * ROW + (size_t)k0 * Ar::WORDS;
                 float yw[NW];
-                load_words<NW>(Vold + row, yw);
+                load_vals<NW, COH>(Vold + row, yw);
                 store_words<NW>(Vnew + row, yw);
             }
         } else if (s_begin < s_end) {
@@ -850,11 +884,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                 __syncwarp();
                 for (int i = grp; i < m; i += SPW)
                     if constexpr (PIPE)
-                        process_state_pipe<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                        process_state_pipe<Ar, KP, VMAX, D, COH>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
                                                             u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits, Vold,
                                                             Vnew, k0, rmax, changed);
                     else
-                        process_state<Ar, KP, VMAX, D>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                        process_state<Ar, KP, VMAX, D, COH>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
                                                        u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits, Vold, Vnew, k0,
                                                        rmax, changed);
                 __syncwarp();  // the next batch reuses the buffer
@@ -891,34 +925,138 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) 
                 if (grp == 0 && any_active && rmax[v] > 0.0f) atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)rmax[v]);
             if (lane == 0) {
                 const uint32_t n_s = cu.y - cu.x;
-                w_bytes += 2ull * n_s * ROW * 4;
+                ps.bytes += 2ull * n_s * ROW * 4;
                 if (any_active) {
                     const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
-                    ++w_computed;
-                    w_updates += (unsigned long long)iw.x * (unsigned long long)n_act;
+                    ++ps.computed;
+                    ps.updates += (unsigned long long)iw.x * (unsigned long long)n_act;
                     // state_sa + state_tr, sa_tr, cost and (col, p) per transition, 4 bytes per word
-                    w_bytes += 8ull * (n_s + 1) + 4ull * (iw.y + 1) + 4ull * (1 + Ar::WORDS) * iw.x;
+                    ps.bytes += 8ull * (n_s + 1) + 4ull * (iw.y + 1) + 4ull * (1 + Ar::WORDS) * iw.x;
                     // per row: its cost, or for the residual correction its row of G
-                    w_bytes += (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * iw.y;
+                    ps.bytes += (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * iw.y;
                 }
             }
         }
     }
     if (leader && n_kept) flush_kept();
-    // statistics: per block in shared memory, then one global atomic each
-    if (lane == 0) {
-        if (w_updates) atomicAdd(&b_stats.updates, w_updates);
-        if (w_bytes) atomicAdd(&b_stats.bytes, w_bytes);
-        if (w_skipped) atomicAdd(&b_stats.skipped, w_skipped);
-        if (w_computed) atomicAdd(&b_stats.computed, w_computed);
+}
+
+// A launch's statistics: per block in shared memory, then one global atomic each.
+__device__ __forceinline__ void flush_stats(LoopCtl *ctl, const PassStats &ps) {
+    __shared__ PassStats b;
+    if (threadIdx.x == 0) b = PassStats{0ull, 0ull, 0u, 0u};
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        if (ps.updates) atomicAdd(&b.updates, ps.updates);
+        if (ps.bytes) atomicAdd(&b.bytes, ps.bytes);
+        if (ps.skipped) atomicAdd(&b.skipped, ps.skipped);
+        if (ps.computed) atomicAdd(&b.computed, ps.computed);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (b_stats.updates) atomicAdd(&ctl->updates, b_stats.updates);
-        if (b_stats.bytes) atomicAdd(&ctl->bytes, b_stats.bytes);
-        if (b_stats.skipped) atomicAdd(&ctl->skipped, b_stats.skipped);
-        if (b_stats.computed) atomicAdd(&ctl->computed, b_stats.computed);
+        if (b.updates) atomicAdd(&ctl->updates, b.updates);
+        if (b.bytes) atomicAdd(&ctl->bytes, b.bytes);
+        if (b.skipped) atomicAdd(&ctl->skipped, b.skipped);
+        if (b.computed) atomicAdd(&ctl->computed, b.computed);
     }
+}
+
+// One sweep per launch: the loop's graph (or the host) launches it six times
+// per body, then the control kernel.
+template <class Ar, int KP, int VMAX, int D, int MINB, int PIPE>
+__global__ void __launch_bounds__(kThreads, MINB) k_sweep(SweepArgs a, int pos) {
+    PassStats ps = {0ull, 0ull, 0u, 0u};
+    sweep_pass<Ar, KP, VMAX, D, PIPE, false>(a, pos, a.ctl->sweep_base + pos, ps);
+    flush_stats(a.ctl, ps);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier of all blocks of a cooperative launch (every block is resident):
+// a block arrives by one atomic on ctl->bar and waits until all gridDim.x
+// arrivals of this round are in.  The wait is bounded: after kBarrierNs of
+// wall-clock time (or kBarrierSpins polls), or once another block has given
+// up (ctl->bar_err), the block sets ctl->bar_err and the call returns false;
+// the kernel then ends and the host reports the error.
+constexpr unsigned long long kBarrierNs = 1000000000ull;  // 1 s
+constexpr unsigned int kBarrierSpins = 1u << 24;
+__device__ __forceinline__ bool grid_barrier(LoopCtl *ctl, unsigned int &target) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += gridDim.x;
+        __threadfence();  // this block's writes of the sweep before its arrival
+        atomicAdd(&ctl->bar, 1u);
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        for (unsigned int n = 0; ld_acquire_gpu(&ctl->bar) < target; ++n) {
+            if ((n & 31u) == 31u &&
+                (ld_acquire_gpu(&ctl->bar_err) != 0u || n >= kBarrierSpins || global_ns() - t0 > kBarrierNs)) {
+                atomicExch(&ctl->bar_err, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Self-check of grid_barrier's bounded wait: the last block never arrives,
+// so every other block's wait runs out and the kernel ends on its own with
+// ctl->bar_err set.
+__global__ void k_barrier_selfcheck(LoopCtl *ctl) {
+    if (blockIdx.x == gridDim.x - 1) return;
+    unsigned int target = 0u;
+    grid_barrier(ctl, target);
+}
+
+// The rest of a loop in one cooperative launch (the loop's "tail": its work
+// list has fallen to ctl->tail items or fewer, so a sweep is a short chain of
+// dependent loads per item and a launch per sweep would cost as much again).
+// Sweep n of the launch is the loop's sweep sweep_base + n; a grid barrier
+// separates consecutive sweeps; each sweep runs the same pass as k_sweep, so
+// the results are bit for bit those of the launch-per-sweep loop.  It ends
+// when the work list is empty (the sweep count rounded up to a body of six,
+// as the launch-per-sweep loop counts it) or at the cap.
+template <class Ar, int KP, int VMAX, int D, int MINB, int PIPE>
+__global__ void __launch_bounds__(kThreads, MINB) k_sweep_tail(SweepArgs a) {
+    LoopCtl *ctl = a.ctl;
+    // sweep_base is rewritten below only by block 0, after a barrier that
+    // every block reaches after this read, or with the value read here
+    const unsigned int base = ctl->sweep_base, cap = ctl->cap;
+    PassStats ps = {0ull, 0ull, 0u, 0u};
+    unsigned int target = 0u, n = 0u;
+    for (;; ++n) {
+        if (ld_loop<true>(&ctl->cnt[n % 3]) == 0u) {
+            n = (n + 5u) / 6u * 6u;
+            break;
+        }
+        if (n % 6u == 0u && base + n >= cap) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) ctl->hit_cap = 1;
+            break;
+        }
+        sweep_pass<Ar, KP, VMAX, D, PIPE, true>(a, (int)(n % 6u), base + n, ps);
+        if (!grid_barrier(ctl, target)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->sweep_base = base + n;
+        ctl->tail_sweeps = n;
+    }
+    flush_stats(ctl, ps);
 }
 
 // -------------------------------------------------------------- finalise
@@ -1524,7 +1662,8 @@ __global__ void k_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, in
 // ("previous" residual 0) instead of being swept once to find that out.
 __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *r0,
                             unsigned long long *r1, unsigned long long *r2, size_t n_pairs, int32_t *sweeps_pair,
-                            uint8_t *frozen, unsigned int cap, uint8_t *chg_prev, const double2 *w_pair) {
+                            uint8_t *frozen, unsigned int cap, uint8_t *chg_prev, const double2 *w_pair,
+                            unsigned int tail) {
     const size_t gid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = gid; i < n_items; i += stride) {
         list0[i] = (unsigned int)i;
@@ -1554,15 +1693,20 @@ __global__ void k_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_it
         ctl->undecided = 0;
         ctl->decided = 0;
         ctl->computed = 0;
+        ctl->tail = tail;
+        ctl->bar = 0;
+        ctl->bar_err = 0;
+        ctl->tail_sweeps = 0;
     }
 }
 
 // Evaluated after each body of 6 sweeps: continue while the work list of
-// the next sweep is non-empty and the sweep cap is not reached.
+// the next sweep is longer than ctl->tail (non-empty without a tail launch)
+// and the sweep cap is not reached.
 __global__ void k_loop_control(LoopCtl *ctl, cudaGraphConditionalHandle handle, int next_idx) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     ctl->sweep_base += 6;
-    const bool more = ctl->cnt[next_idx] > 0;
+    const bool more = ctl->cnt[next_idx] > ctl->tail;
     const bool go = more && ctl->sweep_base < ctl->cap;
     if (more && !go) ctl->hit_cap = 1;
     cudaGraphSetConditional(handle, go ? 1u : 0u);
@@ -1695,6 +1839,33 @@ const SweepKernel *sweep_fn(int lg, int v) {
     return &table[lg][v];
 }
 
+struct TailKernel {
+    void (*f)(SweepArgs);
+    int smem;
+};
+
+// k_sweep_tail in one kernel shape per format (MORAP_TAIL_SHAPE, 0 by
+// default), per log2 Kp.
+#ifndef MORAP_TAIL_SHAPE
+#define MORAP_TAIL_SHAPE 0
+#endif
+template <class Ar, int KP>
+TailKernel tail_kernel() {
+    using VA = Variants<Ar>;
+    constexpr int V = MORAP_TAIL_SHAPE;
+    return {&k_sweep_tail<Ar, KP, VA::vmax[V], VA::d[V], VA::minb[V], VA::pipe[V]>, smem_of<Ar>()};
+}
+
+template <class Ar>
+const TailKernel *tail_fn(int lg) {
+    static const std::array<TailKernel, 7> table = {tail_kernel<Ar, 1>(),  tail_kernel<Ar, 2>(),
+                                                     tail_kernel<Ar, 4>(),  tail_kernel<Ar, 8>(),
+                                                     tail_kernel<Ar, 16>(), tail_kernel<Ar, 32>(),
+                                                     tail_kernel<Ar, 64>()};
+    if (lg < 0 || lg > 6) return nullptr;
+    return &table[lg];
+}
+
 int log2_kp(int Kp) {
     int l = 0;
     while ((1 << l) < Kp) ++l;
@@ -1709,14 +1880,38 @@ int launch_sweep_t(int Kp, int variant, const SweepArgs &a, int pos, int grid, c
     return (int)cudaGetLastError();
 }
 
+// A cooperative launch (every block resident at once, which the grid
+// barriers of k_sweep_tail need); the runtime refuses a grid that does not fit.
+template <class Ar>
+int launch_sweep_tail_t(int Kp, const SweepArgs &a, int grid, cudaStream_t s) {
+    const TailKernel *k = tail_fn<Ar>(log2_kp(Kp));
+    if (!k || grid <= 0) return (int)cudaErrorInvalidValue;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned int)grid);
+    lc.blockDim = dim3(kThreads);
+    lc.dynamicSmemBytes = (size_t)k->smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    void *args[] = {const_cast<SweepArgs *>(&a)};
+    return (int)cudaLaunchKernelExC(&lc, reinterpret_cast<const void *>(k->f), args);
+}
+
 template <class Ar>
 cudaError_t set_attr_t() {
-    for (int lg = 0; lg < 7; ++lg)
+    for (int lg = 0; lg < 7; ++lg) {
         for (int v = 0; v < Variants<Ar>::N; ++v) {
             const SweepKernel *k = sweep_fn<Ar>(lg, v);
             const cudaError_t e = cudaFuncSetAttribute(k->f, cudaFuncAttributeMaxDynamicSharedMemorySize, k->smem);
             if (e != cudaSuccess) return e;
         }
+        const TailKernel *t = tail_fn<Ar>(lg);
+        const cudaError_t e = cudaFuncSetAttribute(t->f, cudaFuncAttributeMaxDynamicSharedMemorySize, t->smem);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
@@ -1797,6 +1992,43 @@ int launch_sweep(int kind, int Kp, int variant, const SweepArgs &a, int pos, int
                                  : launch_sweep_t<ArithF32>(Kp, variant, a, pos, grid, (cudaStream_t)s);
 }
 
+int launch_sweep_tail(int kind, int Kp, const SweepArgs &a, int grid, void *s) {
+    return kind == kSweepDF      ? launch_sweep_tail_t<ArithDF>(Kp, a, grid, (cudaStream_t)s)
+           : kind == kSweepDelta ? launch_sweep_tail_t<ArithDelta>(Kp, a, grid, (cudaStream_t)s)
+                                 : launch_sweep_tail_t<ArithF32>(Kp, a, grid, (cudaStream_t)s);
+}
+
+int launch_barrier_selfcheck(LoopCtl *ctl, int grid, void *s) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned int)grid);
+    lc.blockDim = dim3(kThreads);
+    lc.stream = (cudaStream_t)s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    void *args[] = {&ctl};
+    return (int)cudaLaunchKernelExC(&lc, reinterpret_cast<const void *>(&k_barrier_selfcheck), args);
+}
+
+template <class Ar>
+int tail_blocks_per_sm_t(int Kp) {
+    const TailKernel *k = tail_fn<Ar>(log2_kp(Kp));
+    int n = 0;
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k->f, kThreads, k->smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int sweep_tail_blocks_per_sm(int kind, int Kp) {
+    return kind == kSweepDF      ? tail_blocks_per_sm_t<ArithDF>(Kp)
+           : kind == kSweepDelta ? tail_blocks_per_sm_t<ArithDelta>(Kp)
+                                 : tail_blocks_per_sm_t<ArithF32>(Kp);
+}
+
 int launch_finalize(int Kp, const SweepArgs &a, int n_chunks, double tau, uint8_t *policy, void *sv) {
     cudaStream_t s = (cudaStream_t)sv;
     const int grid = n_chunks < 8192 ? n_chunks : 8192;
@@ -1863,12 +2095,12 @@ int launch_setup_weights(const ProdDesc *prods, int P, int nI, int nJ, int K, in
 
 int launch_loop_init(LoopCtl *ctl, unsigned int *list0, unsigned int n_items, unsigned long long *res[3],
                      size_t n_pairs, int32_t *sweeps_pair, uint8_t *frozen, unsigned int cap, void *s,
-                     uint8_t *chg_prev, const double2 *w_pair) {
+                     uint8_t *chg_prev, const double2 *w_pair, unsigned int tail) {
     const size_t n = n_items > n_pairs ? n_items : n_pairs;
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     k_loop_init<<<grid > 0 ? grid : 1, 256, 0, (cudaStream_t)s>>>(ctl, list0, n_items, res[0], res[1], res[2],
                                                                  n_pairs, sweeps_pair, frozen, cap, chg_prev,
-                                                                 w_pair);
+                                                                 w_pair, tail);
     return (int)cudaGetLastError();
 }
 

@@ -53,6 +53,7 @@ class Config(ctypes.Structure):
         ("eval_block", ctypes.c_int32),
         ("in_place", ctypes.c_int32),
         ("item_warps_max", ctypes.c_int32),
+        ("tail_items", ctypes.c_int32),
     ]
 
 
@@ -75,6 +76,7 @@ class SolveStats(ctypes.Structure):
         ("ms_tune", ctypes.c_double),
         ("skipped_fp32", ctypes.c_int64), ("skipped_fp64", ctypes.c_int64), ("work_items", ctypes.c_int64),
         ("computed_fp32", ctypes.c_int64), ("computed_fp64", ctypes.c_int64), ("anchored_states", ctypes.c_int64),
+        ("tail_sweeps_fp32", ctypes.c_int32), ("tail_sweeps_fp64", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -157,6 +159,7 @@ _SIGS = {
     "morap_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(PointResult)]),
     "morap_server_wait": (ctypes.c_int, [_P, ctypes.c_double]),
     "morap_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "morap_barrier_selfcheck": (ctypes.c_int, [ctypes.c_int32, _I32P, _DP]),
     "morap_plain_vi_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int32, _P, _P, _P, _DP, _I32P]),
@@ -516,6 +519,14 @@ def morap_last_policy(ctx, k, p):
     v = np.zeros(info["n_states"])
     _check(lib().morap_last_policy(ctx, int(k), int(p), _ptr(mu, ctypes.c_uint8), _ptr(v, ctypes.c_double)))
     return mu, v
+
+
+def morap_barrier_selfcheck(device=0):
+    """Run the grid barrier's timeout self-check; returns (timed_out, ms)."""
+    t = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(lib().morap_barrier_selfcheck(int(device), ctypes.byref(t), ctypes.byref(ms)))
+    return bool(t.value), ms.value
 
 
 def morap_plain_vi_noalloc(n_states, n_sa, state_sa, sa_tr, col, prob, cost, pre_begin, init_state, w_cost, w_prob,

@@ -52,12 +52,13 @@ def test_config_default(M):
     assert cfg.precision == M.PREC_MIXED and cfg.max_sweeps == 100000
     assert cfg.polish == 0 and cfg.skip_unchanged == 1 and cfg.eval_block == 1 and cfg.in_place == 0
     assert cfg.sweep_variant_fp32 == -1 and cfg.sweep_variant_fp64 == -1 and cfg.item_warps_max == 0
+    assert cfg.tail_items == 0
 
 
 @pytest.mark.parametrize("field,val", [("polish", 2), ("in_place", 2), ("eval_block", 3), ("skip_unchanged", 2),
                                        ("launch_mode", 2), ("sweep_variant_fp32", 9), ("sweep_variant_fp64", -2),
                                        ("precision", 7), ("max_sweeps", 0), ("item_warps_max", 3),
-                                       ("item_warps_max", 16)])
+                                       ("item_warps_max", 16), ("tail_items", -2)])
 def test_config_validation_needs_no_device(M, field, val):
     """Invalid configurations are refused (EINVAL) before any CUDA call."""
     cfg = M.morap_config_default()

@@ -572,6 +572,69 @@ def test_warps_per_item_give_identical_results(M, grid32, polish):
     many.close()
 
 
+@pytest.mark.parametrize("launch_mode", [0, 1])
+@pytest.mark.parametrize("polish", [0, 1])
+def test_tail_launch_gives_identical_results(M, grid32, polish, launch_mode):
+    """The end of each sweep loop in one cooperative launch (a grid barrier
+    between sweeps) against one launch per sweep to the end: the same values,
+    evaluations, schedulers and sweep counts, bit for bit.  With the
+    automatic threshold the tail launch takes the loop's last sweeps; with a
+    threshold above every list length it takes all but the first body of six."""
+    pair = (grid32.agents[:3], grid32.tasks[:6])
+    W = np.ascontiguousarray(grid32.weights[:8][:, [0, 1, 2, 10, 11, 12, 13, 14, 15]])
+    ctxs = {t: make_ctx(M, pair, polish=polish, launch_mode=launch_mode, tail_items=t) for t in (0, -1, 1 << 30)}
+    out, st = {}, {}
+    for t, ctx in ctxs.items():
+        out[t] = ctx.solve(W, evaluate=True)
+        st[t] = ctx.stats()
+    for t in (-1, 1 << 30):
+        for key in ("c", "r_cost", "r_prob"):
+            assert np.array_equal(out[0][key], out[t][key]), (t, key)
+        for k in range(len(W)):
+            for p in range(3 * 6):
+                assert np.array_equal(M.morap_last_policy(ctxs[0].h, k, p)[0], M.morap_last_policy(ctxs[t].h, k, p)[0])
+        for key in ("fp32_sweeps", "fp64_sweeps", "skipped_fp32", "skipped_fp64", "computed_fp32", "computed_fp64",
+                    "updates_fp32", "updates_fp64", "bytes_fp32", "bytes_fp64", "pairs_not_converged"):
+            assert st[0][key] == st[t][key], (t, key)
+        assert st[t]["tail_sweeps_fp32"] > 0 and st[t]["tail_sweeps_fp64"] > 0, t
+        assert st[t]["kernel_launches"] < st[0]["kernel_launches"], t
+    assert st[0]["tail_sweeps_fp32"] == 0 and st[0]["tail_sweeps_fp64"] == 0
+    whole = st[1 << 30]
+    assert whole["fp32_sweeps"] - whole["tail_sweeps_fp32"] == 6 and whole["fp64_sweeps"] - whole["tail_sweeps_fp64"] == 6
+    for ctx in ctxs.values():
+        ctx.close()
+
+
+def test_tail_barrier_wait_is_bounded(M, tiny):
+    """The grid barrier between a tail launch's sweeps waits about a second
+    at most: in a launch where one block never arrives, the other blocks give
+    up, report it and end; the device stays usable afterwards."""
+    timed_out, ms = M.morap_barrier_selfcheck(0)
+    assert timed_out and 900.0 <= ms <= 20000.0, (timed_out, ms)
+    ctx = make_ctx(M, tiny)
+    out = ctx.solve(tiny.weights)
+    assert np.all(np.isfinite(out["c"]))
+    ctx.close()
+
+
+def test_tail_launch_at_full_size(M, grid32):
+    """The 32x32-grid batch (200 products, 16 weights) with and without the
+    tail launch, after the shape tuning of a first solve: the same c, the
+    same sweep counts."""
+    W = grid32.weights
+    on = make_ctx(M, grid32, tail_items=-1)
+    off = make_ctx(M, grid32)
+    for ctx in (on, off):
+        ctx.solve(W)  # the first solve at this batch size tunes the kernel shapes (no tail launch)
+    a, b = on.solve(W), off.solve(W)
+    sa, sb = on.stats(), off.stats()
+    assert np.array_equal(a["c"], b["c"])
+    assert sa["fp32_sweeps"] == sb["fp32_sweeps"] and sa["fp64_sweeps"] == sb["fp64_sweeps"]
+    assert sa["tail_sweeps_fp64"] > 0 and sb["tail_sweeps_fp64"] == 0
+    on.close()
+    off.close()
+
+
 @pytest.mark.parametrize("polish", [0, 1])
 def test_skipping_unchanged_items_is_exact(M, grid32, polish):
     """A sweep skips work items none of whose inputs changed in the previous
