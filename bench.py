@@ -284,6 +284,9 @@ def _oracle_sample_parallel(inst, budget_s, eps1=1e-8, seed=0, procs=None, engin
             loc, mu = engine(pp, k) if engine is not None else (None, None)
             chunk.append((pp, k, inst.agents[i], inst.tasks[j], float(W[k][i]), float(W[k][nI + j]), loc, mu))
         jobs.append((chunk, eps1, budget_s))
+    from oracle.build import build as build_oracle
+
+    build_oracle()  # once, before the workers load it
     with mp.get_context("spawn").Pool(procs) as pool:
         res = pool.map(_oracle_worker, jobs)
     updates = sum(r[0] for r in res)

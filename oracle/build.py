@@ -14,7 +14,9 @@ def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "oracle.c")
     out = os.path.join(_HERE, "liboracle.so")
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
-        tmp = out + ".tmp"
+        # one temporary file per process: processes that build at once each
+        # replace the library atomically with a complete copy
+        tmp = f"{out}.{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, src, "-lm"])
         os.replace(tmp, out)
     return out

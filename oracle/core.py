@@ -252,6 +252,7 @@ def solve_pairs_pooled(jobs, procs=None):
     import multiprocessing as mp
 
     procs = procs or len(os.sched_getaffinity(0))
+    lib()  # built once here, not by every worker at once
     with mp.get_context("spawn").Pool(procs) as pool:
         return pool.map(solve_pair_job, jobs, chunksize=max(1, len(jobs) // (4 * procs)))
 
