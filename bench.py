@@ -774,7 +774,7 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=8, help="server host threads (concurrent device rounds)")
     ap.add_argument("--tail-items", type=int, default=None,
                     help="work-list length at which a sweep loop runs its remaining sweeps in one cooperative "
-                         "launch (0 never, the default; -1 automatic)")
+                         "launch (-1 automatic, the default; 0 never)")
     ap.add_argument("--eval-block", type=int, default=None, choices=[0, 1],
                     help="Algorithm 4 form: 0 the multi-launch sweep loop, 1 one block per pair")
     args = ap.parse_args()

@@ -120,17 +120,17 @@ typedef struct morap_config {
     int32_t tail_items;         /* the end of each Algorithm 3 sweep loop: once the loop's work list
                                    holds at most this many work items, its remaining sweeps run in
                                    one cooperative launch (every block resident; a grid-wide barrier
-                                   between sweeps instead of a launch per sweep).  0 (default): no
-                                   such launch (one launch per sweep to the end); -1: once the list
-                                   has fewer items than that launch has warps; > 0: this many.
-                                   Same results for every value; on the 32x32-grid batch the tail
-                                   launch is not faster (a late sweep is the items' chain of
-                                   dependent loads, and values written by other blocks of the
-                                   launch are read from L2), hence off.  Each barrier wait is
-                                   bounded (1 s): a wait that runs out ends the launch and the call
-                                   returns MORAP_ECUDA.  The cooperative launch needs the whole
-                                   GPU's resident blocks, so the serving workers (several loops at
-                                   once on one GPU) run without it.                                */
+                                   between sweeps instead of a launch per sweep) in which each warp
+                                   group keeps one item, with its staged rows, for the rest of the
+                                   loop.  -1 (default): a quarter of that launch's warps (every
+                                   item then split over two or more warps, each warp's share one
+                                   staged batch); 0: no such launch (one launch per sweep to the
+                                   end); > 0: this many, at most one item per warp of the launch.
+                                   Same results for every value.  Each barrier wait is bounded
+                                   (1 s): a wait that runs out ends the launch and the call returns
+                                   MORAP_ECUDA.  The cooperative launch needs the whole GPU's
+                                   resident blocks, so the serving workers (several loops at once on
+                                   one GPU) run without it.                                        */
 } morap_config;
 
 typedef struct morap_ctx morap_ctx;

@@ -365,7 +365,10 @@ const SweepArgs &args_of(morap_ctx *c, int kind) {
 // The tail of a phase's loop (config tail_items): the cooperative grid is
 // every block that can be resident (no more than one warp per work item
 // needs), and the loop hands over once its list has at most tail_items
-// items (-1: once it has fewer items than that grid has warps).
+// items, and never more than that grid has warps.  -1: a quarter of its
+// warps, the longest list at which every item is split over two or more
+// warps (a warp's share of 32 states or fewer, one staged batch that the
+// warp keeps for the rest of the launch).
 void setup_tail(morap_ctx *c, LoopGraph &G, int kind, int Kp) {
     G.tail = 0;
     G.tail_grid = 0;
@@ -374,8 +377,9 @@ void setup_tail(morap_ctx *c, LoopGraph &G, int kind, int Kp) {
     if (bps <= 0) return;  // no occupancy figure: the loop runs to the end one launch per sweep
     const size_t useful = (c->h_chunks.size() + kThreads / 32 - 1) / (kThreads / 32);
     G.tail_grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->sm_count * bps, useful));
-    G.tail = c->cfg.tail_items > 0 ? (unsigned int)c->cfg.tail_items
-                                   : (unsigned int)G.tail_grid * (unsigned int)(kThreads / 32);
+    // the tail launch deals its first list to its warps, one item per warp at most
+    const unsigned int warps = (unsigned int)G.tail_grid * (unsigned int)(kThreads / 32);
+    G.tail = c->cfg.tail_items > 0 ? std::min((unsigned int)c->cfg.tail_items, warps) : std::max(1u, warps / 4);
 }
 
 int build_phase_graph(morap_ctx *c, LoopGraph &G, int kind, int Kp, int v) {
@@ -1481,7 +1485,7 @@ void morap_config_default(morap_config *cfg) {
     cfg->eval_block = 1;
     cfg->in_place = 0;
     cfg->item_warps_max = 0;
-    cfg->tail_items = 0;
+    cfg->tail_items = -1;
 }
 
 const char *morap_last_error(void) { return g_last_error.c_str(); }

@@ -1025,19 +1025,84 @@ __global__ void k_barrier_selfcheck(LoopCtl *ctl) {
 }
 
 // The rest of a loop in one cooperative launch (the loop's "tail": its work
-// list has fallen to ctl->tail items or fewer, so a sweep is a short chain of
-// dependent loads per item and a launch per sweep would cost as much again).
-// Sweep n of the launch is the loop's sweep sweep_base + n; a grid barrier
-// separates consecutive sweeps; each sweep runs the same pass as k_sweep, so
-// the results are bit for bit those of the launch-per-sweep loop.  It ends
+// list has fallen to ctl->tail items or fewer, at most one per warp of the
+// launch).  Sweep n of the launch is the loop's sweep sweep_base + n; a grid
+// barrier separates consecutive sweeps.  An item only ever leaves the work
+// list, so the launch deals the items of its first list to warp groups once
+// (group g keeps entry g): a group keeps its item's descriptor, weights and,
+// when a warp's share of the item fits one staged batch, that batch in
+// shared memory, and rereads per sweep only what the sweep decides on
+// (residuals, change flags) and the values it gathers (from L2: other
+// blocks wrote them in the previous sweep).  Each state is computed as in
+// sweep_pass, and the item set of each sweep is the one the launch-per-sweep
+// loop would have, so the results are bit for bit the same.  The launch ends
 // when the work list is empty (the sweep count rounded up to a body of six,
 // as the launch-per-sweep loop counts it) or at the cap.
 template <class Ar, int KP, int VMAX, int D, int MINB, int PIPE>
 __global__ void __launch_bounds__(kThreads, MINB) k_sweep_tail(SweepArgs a) {
+    using SH = Shape<Ar, KP, VMAX>;
+    constexpr int VEC = SH::VEC, LPS = SH::LPS, SPW = SH::SPW;
+    constexpr int NW = VEC * Ar::WORDS;
+    constexpr int ROW = KP * Ar::WORDS;
+    constexpr int WPB = kThreads / 32;
+    constexpr int GMAX = (kChunk / SPW) < WPB ? (kChunk / SPW) : WPB;
+    constexpr unsigned int NONE = 0xFFFFFFFFu;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned char g_chg[WPB];
+    __shared__ float g_res[WPB][KP];
     LoopCtl *ctl = a.ctl;
     // sweep_base is rewritten below only by block 0, after a barrier that
     // every block reaches after this read, or with the value read here
     const unsigned int base = ctl->sweep_base, cap = ctl->cap;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane / LPS, li = lane % LPS, k0 = li * VEC;
+    unsigned char *stage_buf = smem_raw + wib * (Ar::STAGE_BYTES + KP * (int)sizeof(typename Ar::W));
+    uint32_t *ssa = reinterpret_cast<uint32_t *>(stage_buf);
+    typename Ar::W *wsm = reinterpret_cast<typename Ar::W *>(stage_buf + Ar::STAGE_BYTES);
+
+    // warp groups, fixed for the launch from its first list (sweep position 0)
+    const unsigned int n0 = ld_loop<true>(&ctl->cnt[0]);
+    const unsigned int n_warps = gridDim.x * WPB;
+    int G = 1;
+    const int gcap = a.gmax < GMAX ? a.gmax : GMAX;
+    while (G < gcap && (unsigned long long)(2 * G) * n0 <= n_warps) G *= 2;
+    const int gib = wib / G, g = wib % G;
+    const bool leader = g == 0;
+    const int bar_id = 1 + gib, bar_threads = 32 * G;
+    const unsigned int n_groups = n_warps / G;
+    if (n0 > n_groups) {  // more items than groups: the host sizes the tail so that this cannot be
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ctl->bar_err, 1u);
+        return;
+    }
+    const unsigned int group_id = blockIdx.x * (WPB / G) + gib;
+
+    // the group's item and what the launch keeps of it
+    unsigned int item = group_id < n0 ? ld_loop<true>(&a.list[0][group_id]) : NONE;
+    int4 ch = make_int4(0, 0, 0, 0);
+    uint4 cu = make_uint4(0u, 0u, 0u, 0u);
+    uint2 iw = make_uint2(0u, 0u);  // lane 0: (transitions, rows) of the item
+    int32_t in = -1;                // lanes < kInItems: an input item of the item
+    size_t pair0 = 0;
+    double thr_w[2] = {0.0, 0.0};   // freeze thresholds of weights lane and lane + 32
+    int s_begin = 0, s_end = 0;     // this warp's share of the item's states
+    if (item != NONE) {
+        ch = a.chunks[item];
+        cu = a.chunk_u[item];
+        if (lane == 0) iw = __ldg(a.item_w + item);
+        if (a.skip && lane < kInItems) in = __ldg(a.in_items + (size_t)item * kInItems + lane);
+        pair0 = (size_t)ch.x * KP;
+#pragma unroll
+        for (int h = 0; h < (KP + 31) / 32; ++h)
+            if (lane + 32 * h < KP) thr_w[h] = a.thr[pair0 + lane + 32 * h];
+        const int span = ((int)(cu.y - cu.x) + G - 1) / G;
+        s_begin = min((int)cu.y, (int)cu.x + g * span);
+        s_end = min((int)cu.y, s_begin + span);
+    }
+    bool have_w = false;  // the item's weights are in wsm
+    bool kept_batch = false;  // the warp's whole share is the batch staged in its buffer
+    uint32_t kA0 = 0u, kT0 = 0u;
+    int km = 0;
+
     PassStats ps = {0ull, 0ull, 0u, 0u};
     unsigned int target = 0u, n = 0u;
     for (;; ++n) {
@@ -1049,7 +1114,191 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_tail(SweepArgs a) {
             if (blockIdx.x == 0 && threadIdx.x == 0) ctl->hit_cap = 1;
             break;
         }
-        sweep_pass<Ar, KP, VMAX, D, PIPE, true>(a, (int)(n % 6u), base + n, ps);
+        const int pos = (int)(n % 6u);
+        const int cur = pos % 3, nxt = (pos + 1) % 3, far = (pos + 2) % 3;
+        const float *__restrict__ Vold = static_cast<const float *>(a.V[pos & 1]);
+        float *__restrict__ Vnew = static_cast<float *>(a.V[(pos + 1) & 1]);
+        const unsigned long long *res_prev = a.res[far];
+        unsigned long long *res_cur = a.res[cur];
+        unsigned long long *res_next = a.res[nxt];
+        const unsigned int sweep = base + n;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->cnt[far] = 0;
+            ctl->next[far] = 0;
+        }
+        if (item != NONE) {
+            bool in_chg = false;
+            if (a.skip)
+                in_chg = (lane == 0 && ld_loop<true>(&a.chg[far][item])) || in == -2 ||
+                         (in >= 0 && ld_loop<true>(&a.chg[far][in]));
+            unsigned int act_w[2] = {0u, 0u}, nz_w[2] = {0u, 0u};
+#pragma unroll
+            for (int h = 0; h < (KP + 31) / 32; ++h) {
+                const int k = lane + 32 * h;
+                bool act = false, nz = false;
+                if (k < KP) {
+                    const double prev = as_double(ld_loop<true>(&res_prev[pair0 + k]));
+                    act = prev > thr_w[h];
+                    nz = prev > 0.0;
+                }
+                act_w[h] = __ballot_sync(0xffffffffu, act);
+                nz_w[h] = __ballot_sync(0xffffffffu, nz);
+            }
+            const bool any_active = (act_w[0] | act_w[1]) != 0u;
+            if ((nz_w[0] | nz_w[1]) == 0u) {  // converged earlier and already copied: the item leaves
+                if (ch.w && leader)
+                    for (int k = lane; k < KP; k += 32) a.frozen[pair0 + k] = 1;
+                item = NONE;
+            } else {
+                if (any_active && leader && lane == 0) atomicAdd(&ctl->cnt[nxt], 1u);  // stays in the list
+                if (ch.w && leader)
+                    for (int k = lane; k < KP; k += 32) {
+                        res_next[pair0 + k] = 0ull;
+                        if ((act_w[k >> 5] >> (k & 31)) & 1u)
+                            a.sweeps_pair[pair0 + k] = (int32_t)(sweep + 1);
+                        else
+                            a.frozen[pair0 + k] = 1;
+                    }
+                const bool skipped = any_active && a.skip && !__any_sync(0xffffffffu, in_chg);
+                if (skipped) {  // exact skipping, as in sweep_pass
+                    if (leader && lane == 0) {
+                        a.chg[cur][item] = 0;
+                        ++ps.skipped;
+                    }
+                } else {
+                    bool changed = false;
+                    unsigned int act_bits = 0u;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        const int k = k0 + v;
+                        act_bits |= ((act_w[k >> 5] >> (k & 31)) & 1u) << v;
+                    }
+                    if (!have_w) {
+                        for (int k = lane; k < KP; k += 32) wsm[k] = Ar::weight(a, pair0 + k);
+                        __syncwarp();
+                        have_w = true;
+                    }
+                    float rmax[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) rmax[v] = 0.0f;
+                    if (!any_active) {  // every weight of the product froze: copy its rows once
+                        for (int s = s_begin + grp; s < s_end; s += SPW) {
+                            const size_t row = (size_t)(uint32_t)s * ROW + (size_t)k0 * Ar::WORDS;
+                            float yw[NW];
+                            load_vals<NW, true>(Vold + row, yw);
+                            store_words<NW>(Vnew + row, yw);
+                        }
+                    } else if (kept_batch) {
+                        const typename Ar::View vw = Ar::smem_view(stage_buf);
+                        const uint32_t u0 = (uint32_t)s_begin;
+                        for (int i = grp; i < km; i += SPW)
+                            if constexpr (PIPE)
+                                process_state_pipe<Ar, KP, VMAX, D, true>(a, vw, ssa, kA0, kT0, i, u0 + (uint32_t)i,
+                                                                          u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits,
+                                                                          Vold, Vnew, k0, rmax, changed);
+                            else
+                                process_state<Ar, KP, VMAX, D, true>(a, vw, ssa, kA0, kT0, i, u0 + (uint32_t)i,
+                                                                     u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits,
+                                                                     Vold, Vnew, k0, rmax, changed);
+                        __syncwarp();
+                    } else if (s_begin < s_end) {
+                        uint32_t nx_sa = 0, nx_tr = 0;
+                        if (lane <= min(kStageStates, s_end - s_begin)) {
+                            nx_sa = __ldg(a.state_sa + (uint32_t)s_begin + lane);
+                            nx_tr = __ldg(a.state_tr + (uint32_t)s_begin + lane);
+                        }
+                        for (int s0 = s_begin; s0 < s_end;) {
+                            const int m_max = min(kStageStates, s_end - s0);
+                            const uint32_t u0 = (uint32_t)s0;
+                            const uint32_t my_sa = nx_sa, my_tr = nx_tr;
+                            const uint32_t A0 = __shfl_sync(0xffffffffu, my_sa, 0);
+                            const uint32_t T0 = __shfl_sync(0xffffffffu, my_tr, 0);
+                            const bool fits = lane <= m_max && my_sa - A0 <= (uint32_t)Ar::AMAX &&
+                                              my_tr - T0 <= (uint32_t)Ar::EMAX;
+                            int m = __popc(__ballot_sync(0xffffffffu, fits)) - 1;
+                            const bool staged = m >= 1;
+                            if (!staged) m = 1;
+                            const uint32_t A1 = __shfl_sync(0xffffffffu, my_sa, m);
+                            const uint32_t T1 = __shfl_sync(0xffffffffu, my_tr, m);
+                            if (lane <= m) ssa[lane] = my_sa;
+                            if (s0 + m < s_end && lane <= min(kStageStates, s_end - (s0 + m))) {
+                                nx_sa = __ldg(a.state_sa + u0 + (uint32_t)m + lane);
+                                nx_tr = __ldg(a.state_tr + u0 + (uint32_t)m + lane);
+                            }
+                            typename Ar::View vw;
+                            if (staged) {
+                                Ar::stage(a, stage_buf, A0, A1 - A0, T0, T1 - T0, lane);
+                                cp_async_wait_all();
+                                vw = Ar::smem_view(stage_buf);
+                            } else {
+                                vw = Ar::global_view(a, A0, T0);
+                            }
+                            __syncwarp();
+                            for (int i = grp; i < m; i += SPW)
+                                if constexpr (PIPE)
+                                    process_state_pipe<Ar, KP, VMAX, D, true>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                                                                              u0 + (uint32_t)i >= cu.z, wsm + k0,
+                                                                              act_bits, Vold, Vnew, k0, rmax, changed);
+                                else
+                                    process_state<Ar, KP, VMAX, D, true>(a, vw, ssa, A0, T0, i, u0 + (uint32_t)i,
+                                                                         u0 + (uint32_t)i >= cu.z, wsm + k0, act_bits,
+                                                                         Vold, Vnew, k0, rmax, changed);
+                            __syncwarp();
+                            if (staged && s0 == s_begin && m == s_end - s_begin) {  // the whole share: keep it
+                                kept_batch = true;
+                                kA0 = A0;
+                                kT0 = T0;
+                                km = m;
+                            }
+                            s0 += m;
+                        }
+                    }
+                    // residual: lanes with the same li share weights
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        float r = rmax[v];
+#pragma unroll
+                        for (int off = LPS; off < 32; off <<= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
+                        rmax[v] = r;
+                    }
+                    bool any_chg = __any_sync(0xffffffffu, changed);
+                    if (G > 1) {
+                        if (grp == 0)
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) g_res[wib][k0 + v] = rmax[v];
+                        if (lane == 0) g_chg[wib] = any_chg ? 1 : 0;
+                        group_sync(bar_id, bar_threads);
+                        if (leader) {
+                            for (int q = 1; q < G; ++q) {
+                                any_chg = any_chg || g_chg[wib + q] != 0;
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) rmax[v] = fmaxf(rmax[v], g_res[wib + q][k0 + v]);
+                            }
+                        }
+                    }
+                    if (leader) {
+                        if (lane == 0) a.chg[cur][item] = any_chg ? 1 : 0;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v)
+                            if (grp == 0 && any_active && rmax[v] > 0.0f)
+                                atomic_max_nonneg(res_cur + pair0 + k0 + v, (double)rmax[v]);
+                        if (lane == 0) {
+                            const uint32_t n_s = cu.y - cu.x;
+                            ps.bytes += 2ull * n_s * ROW * 4;
+                            if (any_active) {
+                                const int n_act = __popc(act_w[0]) + __popc(act_w[1]);
+                                ++ps.computed;
+                                ps.updates += (unsigned long long)iw.x * (unsigned long long)n_act;
+                                ps.bytes += 8ull * (n_s + 1) + 4ull * (iw.y + 1) + 4ull * (1 + Ar::WORDS) * iw.x;
+                                ps.bytes +=
+                                    (std::is_same<Ar, ArithDelta>::value ? 4ull * KP : 4ull * Ar::WORDS) * iw.y;
+                            }
+                        }
+                    }
+                }
+                if (!any_active) item = NONE;  // copied once; not in the next list
+            }
+        }
         if (!grid_barrier(ctl, target)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1849,11 +2098,16 @@ struct TailKernel {
 #ifndef MORAP_TAIL_SHAPE
 #define MORAP_TAIL_SHAPE 0
 #endif
+// Blocks per SM the tail kernel's registers are sized for: it keeps each
+// warp's item across sweeps, which at two blocks per SM spills.
+#ifndef MORAP_TAIL_MINB
+#define MORAP_TAIL_MINB 1
+#endif
 template <class Ar, int KP>
 TailKernel tail_kernel() {
     using VA = Variants<Ar>;
     constexpr int V = MORAP_TAIL_SHAPE;
-    return {&k_sweep_tail<Ar, KP, VA::vmax[V], VA::d[V], VA::minb[V], VA::pipe[V]>, smem_of<Ar>()};
+    return {&k_sweep_tail<Ar, KP, VA::vmax[V], VA::d[V], MORAP_TAIL_MINB, VA::pipe[V]>, smem_of<Ar>()};
 }
 
 template <class Ar>

@@ -52,7 +52,7 @@ def test_config_default(M):
     assert cfg.precision == M.PREC_MIXED and cfg.max_sweeps == 100000
     assert cfg.polish == 0 and cfg.skip_unchanged == 1 and cfg.eval_block == 1 and cfg.in_place == 0
     assert cfg.sweep_variant_fp32 == -1 and cfg.sweep_variant_fp64 == -1 and cfg.item_warps_max == 0
-    assert cfg.tail_items == 0
+    assert cfg.tail_items == -1
 
 
 @pytest.mark.parametrize("field,val", [("polish", 2), ("in_place", 2), ("eval_block", 3), ("skip_unchanged", 2),

@@ -576,10 +576,11 @@ def test_warps_per_item_give_identical_results(M, grid32, polish):
 @pytest.mark.parametrize("polish", [0, 1])
 def test_tail_launch_gives_identical_results(M, grid32, polish, launch_mode):
     """The end of each sweep loop in one cooperative launch (a grid barrier
-    between sweeps) against one launch per sweep to the end: the same values,
-    evaluations, schedulers and sweep counts, bit for bit.  With the
-    automatic threshold the tail launch takes the loop's last sweeps; with a
-    threshold above every list length it takes all but the first body of six."""
+    between sweeps, each warp group keeping its item) against one launch per
+    sweep to the end: the same values, evaluations, schedulers and sweep
+    counts, bit for bit.  With the automatic threshold the tail launch takes
+    the loop's last sweeps; with a threshold above every list length (capped
+    at one item per warp of the launch) it takes all but the first body of six."""
     pair = (grid32.agents[:3], grid32.tasks[:6])
     W = np.ascontiguousarray(grid32.weights[:8][:, [0, 1, 2, 10, 11, 12, 13, 14, 15]])
     ctxs = {t: make_ctx(M, pair, polish=polish, launch_mode=launch_mode, tail_items=t) for t in (0, -1, 1 << 30)}
@@ -622,8 +623,8 @@ def test_tail_launch_at_full_size(M, grid32):
     tail launch, after the shape tuning of a first solve: the same c, the
     same sweep counts."""
     W = grid32.weights
-    on = make_ctx(M, grid32, tail_items=-1)
-    off = make_ctx(M, grid32)
+    on = make_ctx(M, grid32)
+    off = make_ctx(M, grid32, tail_items=0)
     for ctx in (on, off):
         ctx.solve(W)  # the first solve at this batch size tunes the kernel shapes (no tail launch)
     a, b = on.solve(W), off.solve(W)
