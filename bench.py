@@ -60,10 +60,10 @@ def make_workload(name, rank=0):
 # comments removed; sha256 prefix) is the one that was profiled and the same
 # shape runs; otherwise the bench reports traffic as null.
 TRAFFIC_PROFILES = {
-    ("grid32-10x20-K16", "fp32"): {"sweep_source": "c49a23adc5577afe", "variant": 0,
-                                   "dram_bytes": 137857792 + 26885632, "alg_bytes": 178.99e6},
-    ("grid32-10x20-K16", "delta"): {"sweep_source": "c49a23adc5577afe", "variant": 0,
-                                    "dram_bytes": 345657088 + 39284992, "alg_bytes": 384.32e6},
+    ("grid32-10x20-K16", "fp32"): {"sweep_source": "704663e0c0ed16ef", "variant": 0,
+                                   "dram_bytes": 137830400 + 27310848, "alg_bytes": 178.99e6},
+    ("grid32-10x20-K16", "delta"): {"sweep_source": "704663e0c0ed16ef", "variant": 0,
+                                    "dram_bytes": 345627904 + 39656448, "alg_bytes": 384.32e6},
 }
 SWEEP_SECTION_END = "// -------------------------------------------------------------- finalise"
 
