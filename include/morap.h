@@ -78,9 +78,11 @@ typedef struct morap_config {
     int32_t precision;  /* MORAP_PREC_MIXED (default) or MORAP_PREC_FP64                            */
     int32_t device;     /* CUDA device ordinal; default 0                                            */
     int32_t launch_mode;/* 0 (default): each sweep loop is one CUDA graph whose while node runs
-                           bodies of six sweeps until the device work list is empty; 1: the host
-                           launches the same kernels body by body and reads the work list between
-                           bodies (same results; for profilers that cannot enter conditional graphs) */
+                           bodies of six sweeps until the device work list is empty or short
+                           enough for the tail launch (tail_items) that ends the graph; 1: the
+                           host launches the same kernels body by body and reads the work list
+                           between bodies (same results; for profilers that cannot enter
+                           conditional graphs)                                                     */
     size_t hbm_budget;  /* admission limit in bytes for all device memory of the context; 0 = none  */
     morap_alloc_fn alloc;
     morap_free_fn free;
