@@ -132,7 +132,8 @@ typedef struct morap_config {
                                    (1 s): a wait that runs out ends the launch and the call returns
                                    MORAP_ECUDA.  The cooperative launch needs the whole GPU's
                                    resident blocks, so the serving workers (several loops at once on
-                                   one GPU) run without it.                                        */
+                                   one GPU) run without it; contexts that solve at the same time on
+                                   one GPU (several streams or threads) should set 0 as well.      */
 } morap_config;
 
 typedef struct morap_ctx morap_ctx;
